@@ -1,0 +1,187 @@
+"""CPU oracle for the Helmholtz solve -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (``paper_1811_03852_gb300``)
+never imports, links or runs it, and the two share no code: the oracle is
+plain serial C (``hz_oracle.c``) plus the NumPy conv-net reference in
+``nn.py``, written from Maynard & Walters (arXiv:1811.03852) and from the
+textbook definitions they cite.  Inputs come from the separate ``gen``
+package, which holds no solver arithmetic.
+
+Every routine is pinned by ``tests/test_oracle_*.py`` against something other
+than itself (dense LAPACK solves, banded solves, closed forms, brute force,
+finite differences).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hz_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libhz_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_FP64 = 0
+MODE_MIXED = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc -O2, serial) if missing or stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = f"{_LIB}.{os.getpid()}.tmp"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32, dbl, pv, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+            lib.or_matvec.argtypes = [i32, i32, i32, pv, pv, pv]
+            lib.or_matvec.restype = None
+            lib.or_residual.argtypes = [i32, i32, i32, pv, pv, pv, pv]
+            lib.or_residual.restype = dbl
+            lib.or_scale.argtypes = [i32, i32, i32, pv, pv]
+            lib.or_scale.restype = None
+            lib.or_matvec_hat.argtypes = [i32, i32, i32, pv, pv, pv]
+            lib.or_matvec_hat.restype = None
+            lib.or_tridiag_solve.argtypes = [i32, pv, pv, pv, pv, pv, pv]
+            lib.or_tridiag_solve.restype = None
+            lib.or_apply_Tinv.argtypes = [i32, i32, i32, pv, pv, pv]
+            lib.or_apply_Tinv.restype = None
+            lib.or_bicgstab.argtypes = [i32, i32, i32, pv, pv, pv, dbl, i32, i32, pv, pv]
+            lib.or_bicgstab.restype = None
+            lib.or_bicgstab_f32.argtypes = [i32, i32, i32, pv, pv, pv, dbl, i32, i32, pv, pv]
+            lib.or_bicgstab_f32.restype = None
+            lib.or_solve.argtypes = [i32, i32, i32, pv, pv, pv, i32, dbl, dbl, i32, i32, i32, pv, pv]
+            lib.or_solve.restype = None
+            lib.or_dot.argtypes = [i64, pv, pv]
+            lib.or_dot.restype = dbl
+            _lib = lib
+    return _lib
+
+
+def _c(a, dtype=np.float64):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _p(a):
+    return a.ctypes.data
+
+
+def _dims(x):
+    nz, ny, nx = x.shape[-3:]
+    return nx, ny, nz
+
+
+def matvec(A, x):
+    """y = A x (unscaled 7-band operator, Sec. 1 eq. LinearSys / Sec. 2 Helmholtz)."""
+    A, x = _c(A), _c(x)
+    nx, ny, nz = _dims(x)
+    y = np.empty_like(x)
+    _load().or_matvec(nx, ny, nz, _p(A), _p(x), _p(y))
+    return y
+
+
+def residual(A, b, x):
+    """(r = b - A x, ||r||_2)."""
+    A, b, x = _c(A), _c(b), _c(x)
+    nx, ny, nz = _dims(x)
+    r = np.empty_like(x)
+    nrm = _load().or_residual(nx, ny, nz, _p(A), _p(b), _p(x), _p(r))
+    return r, nrm
+
+
+def scale(A):
+    """Ahat = D^-1 A off-diagonal bands (6, nz, ny, nx), order E,W,N,S,U,D."""
+    A = _c(A)
+    nz, ny, nx = A.shape[1:]
+    Ah = np.empty((6, nz, ny, nx))
+    _load().or_scale(nx, ny, nz, _p(A), _p(Ah))
+    return Ah
+
+
+def matvec_hat(Ah, x):
+    """y = Ahat x with unit diagonal."""
+    Ah, x = _c(Ah), _c(x)
+    nx, ny, nz = _dims(x)
+    y = np.empty_like(x)
+    _load().or_matvec_hat(nx, ny, nz, _p(Ah), _p(x), _p(y))
+    return y
+
+
+def tridiag_solve(lo, di, up, r):
+    """Solve one tridiagonal system (Thomas algorithm, factors recomputed)."""
+    lo, di, up, r = (_c(v) for v in (lo, di, up, r))
+    m = r.size
+    x = np.empty(m)
+    wk = np.empty(2 * m)
+    _load().or_tridiag_solve(m, _p(lo), _p(di), _p(up), _p(r), _p(x), _p(wk))
+    return x
+
+
+def apply_Tinv(Ah, r):
+    """z = T^-1 r, T = per-column tridiagonal part (D band, 1, U band) of Ahat."""
+    Ah, r = _c(Ah), _c(r)
+    nx, ny, nz = _dims(r)
+    z = np.empty_like(r)
+    _load().or_apply_Tinv(nx, ny, nz, _p(Ah), _p(r), _p(z))
+    return z
+
+
+def bicgstab(Ah, bh, x0=None, eta=1e-8, maxit=1000, restart=150, fp32=False, history=False):
+    """Right-preconditioned BiCGStab with C = T^-1 on Ahat y = bh.
+
+    Returns (x, info dict[, hist]).  With fp32=True every vector and
+    coefficient is a float and dots accumulate in double.
+    """
+    nz, ny, nx = bh.shape
+    dt = np.float32 if fp32 else np.float64
+    Ah_ = _c(Ah, dt)
+    bh_ = _c(bh, dt)
+    x = np.zeros_like(bh_) if x0 is None else _c(x0, dt).copy()
+    hist = np.full(maxit, np.nan)
+    out = np.zeros(4)
+    fn = _load().or_bicgstab_f32 if fp32 else _load().or_bicgstab
+    fn(nx, ny, nz, _p(Ah_), _p(bh_), _p(x), eta, maxit, restart, _p(hist), _p(out))
+    info = dict(iters=int(out[0]), restarts=int(out[1]), relres=float(out[2]), status=int(out[3]))
+    if history:
+        return x, info, hist[: info["iters"]]
+    return x, info
+
+
+def solve(A, b, x0=None, mode=MODE_MIXED, tol=1e-8, eta=1e-4, max_outer=20, max_inner=2000, restart=150,
+          history=False):
+    """Outer loop on the true FP64 residual with FP64 (mode 0) or FP32 (mode 1) inner BiCGStab.
+
+    Returns (x, info dict[, outer history of R]).
+    """
+    A, b = _c(A), _c(b)
+    nx, ny, nz = _dims(b)
+    x = np.zeros_like(b) if x0 is None else _c(x0).copy()
+    hist = np.full(max_outer + 1, np.nan)
+    out = np.zeros(5)
+    _load().or_solve(nx, ny, nz, _p(A), _p(b), _p(x), mode, tol, eta, max_outer, max_inner, restart, _p(hist),
+                     _p(out))
+    info = dict(outer=int(out[0]), inner=int(out[1]), R=float(out[2]), status=int(out[3]), restarts=int(out[4]))
+    if history:
+        return x, info, hist[: info["outer"] + 1]
+    return x, info
+
+
+def dot(a, b):
+    a, b = _c(a).ravel(), _c(b).ravel()
+    return _load().or_dot(a.size, _p(a), _p(b))

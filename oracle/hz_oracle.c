@@ -1,0 +1,448 @@
+/*
+ * hz_oracle.c -- plain, slow, serial FP64 reference for the Helmholtz solve.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code with the CUDA library: every routine
+ * here is written from the paper (Maynard & Walters, "Precision of the
+ * ENDGame", arXiv:1811.03852) in the simplest loop form.
+ *
+ * Grid and layout: nx (longitude, periodic) x ny (latitude, closed at the
+ * poles) x nz (levels, closed at top and bottom); p = (k*ny + j)*nx + i.
+ * Operator: 7 bands C,E,W,N,S,U,D stored band-major, A[b*n + p].
+ *
+ * Pins (what checks this file against something other than itself) live in
+ * tests/test_oracle_*.py: dense assembled matrices with LAPACK solves,
+ * banded solves, closed forms (A*1 = c*1, the one-iteration case without
+ * horizontal coupling, nz = 1), manufactured solutions and brute force.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX(i, j, k) (((int64_t)(k) * ny + (j)) * nx + (i))
+
+enum { B_C = 0, B_E, B_W, B_N, B_S, B_U, B_D };
+
+int or_version(void) { return 1; }
+
+/* ---------------------------------------------------------------------------
+ * The linear system A x = b (Sec. 1, the pressure-correction equation; Sec. 2,
+ * the 7-band Helmholtz matrix).  y = A x with the unscaled bands.
+ * Neighbours: i+-1 wrap around (longitude is periodic); a missing j or k
+ * neighbour contributes nothing (its coefficient is zero by construction).
+ * ------------------------------------------------------------------------- */
+void or_matvec(int nx, int ny, int nz, const double* A, const double* x, double* y) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t p = IDX(i, j, k);
+        double acc = A[B_C * n + p] * x[p];
+        acc += A[B_E * n + p] * x[IDX((i + 1) % nx, j, k)];
+        acc += A[B_W * n + p] * x[IDX((i + nx - 1) % nx, j, k)];
+        if (j + 1 < ny) acc += A[B_N * n + p] * x[IDX(i, j + 1, k)];
+        if (j > 0) acc += A[B_S * n + p] * x[IDX(i, j - 1, k)];
+        if (k + 1 < nz) acc += A[B_U * n + p] * x[IDX(i, j, k + 1)];
+        if (k > 0) acc += A[B_D * n + p] * x[IDX(i, j, k - 1)];
+        y[p] = acc;
+      }
+}
+
+/* r = b - A x and return ||r||_2 (Sec. 3, the halting residual r_i = b - A x_i). */
+double or_residual(int nx, int ny, int nz, const double* A, const double* b, const double* x, double* r) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  or_matvec(nx, ny, nz, A, x, r);
+  double s = 0.0;
+  for (int64_t p = 0; p < n; ++p) {
+    r[p] = b[p] - r[p];
+    s += r[p] * r[p];
+  }
+  return sqrt(s);
+}
+
+/* ---------------------------------------------------------------------------
+ * Diagonal scaling outside the solver (Sec. 2, the post-conditioned system
+ * D_g^-1 A C C^-1 x = D_g^-1 b):  Ahat = D^-1 A has unit diagonal, so only
+ * the six off-diagonal bands are kept, Ahat[(b-1)*n + p] = A_b(p)/A_C(p).
+ * ------------------------------------------------------------------------- */
+void or_scale(int nx, int ny, int nz, const double* A, double* Ahat) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int b = 1; b < 7; ++b)
+    for (int64_t p = 0; p < n; ++p) Ahat[(int64_t)(b - 1) * n + p] = A[(int64_t)b * n + p] / A[p];
+}
+
+/* y = Ahat x, Ahat = I + off-diagonal bands (order E,W,N,S,U,D). */
+void or_matvec_hat(int nx, int ny, int nz, const double* Ah, const double* x, double* y) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t p = IDX(i, j, k);
+        double acc = x[p];
+        acc += Ah[0 * n + p] * x[IDX((i + 1) % nx, j, k)];
+        acc += Ah[1 * n + p] * x[IDX((i + nx - 1) % nx, j, k)];
+        if (j + 1 < ny) acc += Ah[2 * n + p] * x[IDX(i, j + 1, k)];
+        if (j > 0) acc += Ah[3 * n + p] * x[IDX(i, j - 1, k)];
+        if (k + 1 < nz) acc += Ah[4 * n + p] * x[IDX(i, j, k + 1)];
+        if (k > 0) acc += Ah[5 * n + p] * x[IDX(i, j, k - 1)];
+        y[p] = acc;
+      }
+}
+
+/* ---------------------------------------------------------------------------
+ * Tridiagonal solve by Gaussian elimination without pivoting (the Thomas
+ * algorithm) for one column of m unknowns:
+ *   lo[k] x[k-1] + di[k] x[k] + up[k] x[k+1] = r[k].
+ * work holds 2m doubles.  The factors are recomputed on every call.
+ * ------------------------------------------------------------------------- */
+void or_tridiag_solve(int m, const double* lo, const double* di, const double* up, const double* r, double* x,
+                      double* work) {
+  double* cprime = work;
+  double* dprime = work + m;
+  cprime[0] = up[0] / di[0];
+  dprime[0] = r[0] / di[0];
+  for (int k = 1; k < m; ++k) {
+    double den = di[k] - lo[k] * cprime[k - 1];
+    cprime[k] = up[k] / den;
+    dprime[k] = (r[k] - lo[k] * dprime[k - 1]) / den;
+  }
+  x[m - 1] = dprime[m - 1];
+  for (int k = m - 2; k >= 0; --k) x[k] = dprime[k] - cprime[k] * x[k + 1];
+}
+
+/* ---------------------------------------------------------------------------
+ * Preconditioner C = T^-1 (Sec. 2, Ahat = L + T + U with T the vertical
+ * tridiagonal part; its LU is per horizontal point, no vertical
+ * decomposition).  For each column (i,j): T has sub-diagonal Ahat_D,
+ * diagonal 1 and super-diagonal Ahat_U.  z = T^-1 r.
+ * ------------------------------------------------------------------------- */
+void or_apply_Tinv(int nx, int ny, int nz, const double* Ah, const double* r, double* z) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  double* lo = (double*)malloc(sizeof(double) * 7 * (size_t)nz);
+  double* di = lo + nz;
+  double* up = di + nz;
+  double* rc = up + nz;
+  double* xc = rc + nz;
+  double* wk = xc + nz;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      for (int k = 0; k < nz; ++k) {
+        int64_t p = IDX(i, j, k);
+        lo[k] = Ah[5 * n + p];
+        di[k] = 1.0;
+        up[k] = Ah[4 * n + p];
+        rc[k] = r[p];
+      }
+      or_tridiag_solve(nz, lo, di, up, rc, xc, wk);
+      for (int k = 0; k < nz; ++k) z[IDX(i, j, k)] = xc[k];
+    }
+  free(lo);
+}
+
+/* FP32-emulated variants: every stored value is a float, arithmetic in float. */
+static void matvec_hat_f32(int nx, int ny, int nz, const float* Ah, const float* x, float* y) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t p = IDX(i, j, k);
+        float acc = x[p];
+        acc += Ah[0 * n + p] * x[IDX((i + 1) % nx, j, k)];
+        acc += Ah[1 * n + p] * x[IDX((i + nx - 1) % nx, j, k)];
+        if (j + 1 < ny) acc += Ah[2 * n + p] * x[IDX(i, j + 1, k)];
+        if (j > 0) acc += Ah[3 * n + p] * x[IDX(i, j - 1, k)];
+        if (k + 1 < nz) acc += Ah[4 * n + p] * x[IDX(i, j, k + 1)];
+        if (k > 0) acc += Ah[5 * n + p] * x[IDX(i, j, k - 1)];
+        y[p] = acc;
+      }
+}
+
+static void apply_Tinv_f32(int nx, int ny, int nz, const float* Ah, const float* r, float* z) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  float* cp = (float*)malloc(sizeof(float) * 2 * (size_t)nz);
+  float* dp = cp + nz;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      /* unit diagonal: den = 1 - lo*cprime */
+      int64_t p0 = IDX(i, j, 0);
+      cp[0] = Ah[4 * n + p0];
+      dp[0] = r[p0];
+      for (int k = 1; k < nz; ++k) {
+        int64_t p = IDX(i, j, k);
+        float lo = Ah[5 * n + p];
+        float den = 1.0f - lo * cp[k - 1];
+        cp[k] = Ah[4 * n + p] / den;
+        dp[k] = (r[p] - lo * dp[k - 1]) / den;
+      }
+      z[IDX(i, j, nz - 1)] = dp[nz - 1];
+      for (int k = nz - 2; k >= 0; --k) z[IDX(i, j, k)] = dp[k] - cp[k] * z[IDX(i, j, k + 1)];
+    }
+  free(cp);
+}
+
+static double dot_d(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t p = 0; p < n; ++p) s += a[p] * b[p];
+  return s;
+}
+
+/* dots of float vectors accumulated in double (the global sums the paper moved
+   back to 64-bit, Sec. 4) */
+static double dot_f(int64_t n, const float* a, const float* b) {
+  double s = 0.0;
+  for (int64_t p = 0; p < n; ++p) s += (double)a[p] * (double)b[p];
+  return s;
+}
+
+/* ---------------------------------------------------------------------------
+ * Right-preconditioned ("post-conditioned", Sec. 2) BiCGStab (van der Vorst
+ * 1992) on Ahat y = bh with C = T^-1, halting on the recursive residual
+ * ||r|| <= eta ||bh|| (Sec. 3, relative residual R).  A restart is forced
+ * every `restart` iterations (Sec. 4: mandatory restart after 150) and on
+ * breakdown (|rho| tiny or omega = 0).
+ *
+ * One iteration:
+ *   rho' = <r0, r>; beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v)
+ *   ph = C p; v = Ahat ph; alpha = rho'/<r0, v>; s = r - alpha v
+ *   (if ||s|| <= eta ||bh||: x += alpha ph, stop)
+ *   sh = C s; t = Ahat sh; omega = <t,s>/<t,t>
+ *   x += alpha ph + omega sh; r = s - omega t
+ * x is in/out (the initial guess on entry).  hist (may be NULL) receives the
+ * recursive relative residual after each iteration (up to maxit values).
+ * out[0] = iterations, out[1] = restarts, out[2] = final relative residual,
+ * out[3] = status (0 converged, 1 iteration limit, 2 non-finite).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double iters, restarts, relres, status;
+} or_info;
+
+void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, double* x, double eta, int maxit,
+                 int restart, double* hist, double* out) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  double* r = (double*)calloc((size_t)n * 8, sizeof(double));
+  double *r0 = r + n, *p = r0 + n, *v = p + n, *ph = v + n, *s = ph + n, *sh = s + n, *t = sh + n;
+  const double bnorm = sqrt(dot_d(n, bh, bh));
+  const double stop = eta * bnorm;
+  int it = 0, nrestart = 0, status = 1;
+  double rnorm = 0.0;
+  int fresh = 1;
+  double rho = 1, alpha = 1, omega = 1;
+  int since = 0;
+  if (bnorm == 0.0) {
+    for (int64_t q = 0; q < n; ++q) x[q] = 0.0;
+    status = 0;
+    goto done;
+  }
+  while (it < maxit) {
+    if (fresh) { /* (re)start: r = bh - Ahat x, r0 = r, p = v = 0 */
+      or_matvec_hat(nx, ny, nz, Ah, x, r);
+      for (int64_t q = 0; q < n; ++q) {
+        r[q] = bh[q] - r[q];
+        r0[q] = r[q];
+        p[q] = 0.0;
+        v[q] = 0.0;
+      }
+      rho = alpha = omega = 1.0;
+      since = 0;
+      fresh = 0;
+      rnorm = sqrt(dot_d(n, r, r));
+      if (rnorm <= stop) { status = 0; break; }
+    }
+    double rho1 = dot_d(n, r0, r);
+    double r0n = sqrt(dot_d(n, r0, r0));
+    if (fabs(rho1) <= 1e-14 * r0n * rnorm) { fresh = 1; ++nrestart; continue; }
+    ++it;
+    ++since;
+    double beta = (rho1 / rho) * (alpha / omega);
+    for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
+    or_apply_Tinv(nx, ny, nz, Ah, p, ph);
+    or_matvec_hat(nx, ny, nz, Ah, ph, v);
+    alpha = rho1 / dot_d(n, r0, v);
+    for (int64_t q = 0; q < n; ++q) s[q] = r[q] - alpha * v[q];
+    double snorm = sqrt(dot_d(n, s, s));
+    if (snorm <= stop) {
+      for (int64_t q = 0; q < n; ++q) x[q] += alpha * ph[q];
+      rnorm = snorm;
+      if (hist) hist[it - 1] = rnorm / bnorm;
+      status = 0;
+      break;
+    }
+    or_apply_Tinv(nx, ny, nz, Ah, s, sh);
+    or_matvec_hat(nx, ny, nz, Ah, sh, t);
+    double tt = dot_d(n, t, t);
+    omega = tt > 0.0 ? dot_d(n, t, s) / tt : 0.0;
+    for (int64_t q = 0; q < n; ++q) {
+      x[q] += alpha * ph[q] + omega * sh[q];
+      r[q] = s[q] - omega * t[q];
+    }
+    rho = rho1;
+    rnorm = sqrt(dot_d(n, r, r));
+    if (hist) hist[it - 1] = rnorm / bnorm;
+    if (!isfinite(rnorm)) { status = 2; break; }
+    if (rnorm <= stop) { status = 0; break; }
+    if (omega == 0.0 || since >= restart) { fresh = 1; ++nrestart; }
+  }
+done:
+  if (out) {
+    out[0] = it;
+    out[1] = nrestart;
+    out[2] = bnorm > 0 ? rnorm / bnorm : 0.0;
+    out[3] = status;
+  }
+  free(r);
+}
+
+/* The same iteration with every vector and coefficient rounded to float and
+   float arithmetic, dots accumulated in double and the scalars kept in double
+   (the mixed-precision split of Sec. 3-4). Ah32 is the float copy of Ahat. */
+void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, float* x, double eta, int maxit,
+                     int restart, double* hist, double* out) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  float* r = (float*)calloc((size_t)n * 8, sizeof(float));
+  float *r0 = r + n, *p = r0 + n, *v = p + n, *ph = v + n, *s = ph + n, *sh = s + n, *t = sh + n;
+  const double bnorm = sqrt(dot_f(n, bh, bh));
+  const double stop = eta * bnorm;
+  int it = 0, nrestart = 0, status = 1;
+  double rnorm = 0.0;
+  int fresh = 1;
+  double rho = 1, alpha = 1, omega = 1;
+  int since = 0;
+  if (bnorm == 0.0) {
+    for (int64_t q = 0; q < n; ++q) x[q] = 0.0f;
+    status = 0;
+    goto done;
+  }
+  while (it < maxit) {
+    if (fresh) {
+      matvec_hat_f32(nx, ny, nz, Ah, x, r);
+      for (int64_t q = 0; q < n; ++q) {
+        r[q] = bh[q] - r[q];
+        r0[q] = r[q];
+        p[q] = 0.0f;
+        v[q] = 0.0f;
+      }
+      rho = alpha = omega = 1.0;
+      since = 0;
+      fresh = 0;
+      rnorm = sqrt(dot_f(n, r, r));
+      if (rnorm <= stop) { status = 0; break; }
+    }
+    double rho1 = dot_f(n, r0, r);
+    double r0n = sqrt(dot_f(n, r0, r0));
+    if (fabs(rho1) <= 1e-14 * r0n * rnorm) { fresh = 1; ++nrestart; continue; }
+    ++it;
+    ++since;
+    float beta = (float)((rho1 / rho) * (alpha / omega));
+    float om = (float)omega;
+    for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - om * v[q]);
+    apply_Tinv_f32(nx, ny, nz, Ah, p, ph);
+    matvec_hat_f32(nx, ny, nz, Ah, ph, v);
+    alpha = rho1 / dot_f(n, r0, v);
+    float al = (float)alpha;
+    for (int64_t q = 0; q < n; ++q) s[q] = r[q] - al * v[q];
+    double snorm = sqrt(dot_f(n, s, s));
+    if (snorm <= stop) {
+      for (int64_t q = 0; q < n; ++q) x[q] += al * ph[q];
+      rnorm = snorm;
+      if (hist) hist[it - 1] = rnorm / bnorm;
+      status = 0;
+      break;
+    }
+    apply_Tinv_f32(nx, ny, nz, Ah, s, sh);
+    matvec_hat_f32(nx, ny, nz, Ah, sh, t);
+    double tt = dot_f(n, t, t);
+    omega = tt > 0.0 ? dot_f(n, t, s) / tt : 0.0;
+    om = (float)omega;
+    for (int64_t q = 0; q < n; ++q) {
+      x[q] += al * ph[q] + om * sh[q];
+      r[q] = s[q] - om * t[q];
+    }
+    rho = rho1;
+    rnorm = sqrt(dot_f(n, r, r));
+    if (hist) hist[it - 1] = rnorm / bnorm;
+    if (!isfinite(rnorm)) { status = 2; break; }
+    if (rnorm <= stop) { status = 0; break; }
+    if (omega == 0.0 || since >= restart) { fresh = 1; ++nrestart; }
+  }
+done:
+  if (out) {
+    out[0] = it;
+    out[1] = nrestart;
+    out[2] = bnorm > 0 ? rnorm / bnorm : 0.0;
+    out[3] = status;
+  }
+  free(r);
+}
+
+/* ---------------------------------------------------------------------------
+ * Outer loop judged by the true FP64 residual R = ||b - A x|| / ||b|| (Sec. 3,
+ * the relative residual and halting criterion R < R_c), with the inner
+ * correction solve on the scaled system Ahat d = D^-1 r:
+ *   mode 0: inner solve in FP64;
+ *   mode 1: inner solve in FP32 (mixed precision; iterative refinement wins
+ *           back the digits below the 32-bit limit eps_32 of Sec. 3).
+ * x is in/out (initial guess).  outer_hist (may be NULL, max_outer+1 values)
+ * receives R before each outer step and after the last.
+ * out[0] = outer iterations, out[1] = total inner iterations,
+ * out[2] = final true R, out[3] = status (0 ok, 1 not converged, 2 non-finite),
+ * out[4] = total restarts.
+ * ------------------------------------------------------------------------- */
+void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* x, int mode, double tol,
+              double eta, int max_outer, int max_inner, int restart, double* outer_hist, double* out) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  double* Ah = (double*)malloc(sizeof(double) * 6 * (size_t)n);
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  double* d = (double*)malloc(sizeof(double) * (size_t)n);
+  float* Ah32 = NULL;
+  float *r32 = NULL, *d32 = NULL;
+  or_scale(nx, ny, nz, A, Ah);
+  if (mode == 1) {
+    Ah32 = (float*)malloc(sizeof(float) * 6 * (size_t)n);
+    r32 = (float*)malloc(sizeof(float) * (size_t)n);
+    d32 = (float*)malloc(sizeof(float) * (size_t)n);
+    for (int64_t q = 0; q < 6 * n; ++q) Ah32[q] = (float)Ah[q];
+  }
+  const double bnorm = sqrt(dot_d(n, b, b));
+  int outer = 0, inner_total = 0, status = 1, restarts = 0;
+  double R = 0.0;
+  for (;;) {
+    double rn = or_residual(nx, ny, nz, A, b, x, r);
+    R = bnorm > 0 ? rn / bnorm : rn;
+    if (outer_hist) outer_hist[outer] = R;
+    if (!isfinite(R)) { status = 2; break; }
+    if (R <= tol) { status = 0; break; }
+    if (outer >= max_outer) { status = 1; break; }
+    double info[4];
+    if (mode == 1) {
+      for (int64_t q = 0; q < n; ++q) {
+        r32[q] = (float)(r[q] / A[q]);
+        d32[q] = 0.0f;
+      }
+      or_bicgstab_f32(nx, ny, nz, Ah32, r32, d32, eta, max_inner, restart, NULL, info);
+      for (int64_t q = 0; q < n; ++q) x[q] += (double)d32[q];
+    } else {
+      for (int64_t q = 0; q < n; ++q) {
+        r[q] = r[q] / A[q];
+        d[q] = 0.0;
+      }
+      or_bicgstab(nx, ny, nz, Ah, r, d, eta, max_inner, restart, NULL, info);
+      for (int64_t q = 0; q < n; ++q) x[q] += d[q];
+    }
+    inner_total += (int)info[0];
+    restarts += (int)info[1];
+    ++outer;
+  }
+  if (out) {
+    out[0] = outer;
+    out[1] = inner_total;
+    out[2] = R;
+    out[3] = status;
+    out[4] = restarts;
+  }
+  free(Ah); free(r); free(d); free(Ah32); free(r32); free(d32);
+}
+
+/* deterministic-order FP64 dot (for reference sums in tests) */
+double or_dot(int64_t n, const double* a, const double* b) { return dot_d(n, a, b); }

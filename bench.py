@@ -1,0 +1,356 @@
+"""Benchmark: N1280-shaped Helmholtz solves/s to a true FP64 relative residual of 1e-8.
+
+One step = one complete solve (hz_solve through the C ABI) of the synthetic
+2560x1920x70 system (coefficient seed 21, right-hand side seed 22, Earth-radius
+vertical unit), mixed precision (FP32 inner BiCGStab + T^-1, FP64 outer
+residual and update), operator already set up on the GPU, b resident in HBM.
+Every vector is 1.4-2.8 GB, far larger than the 129 MB L2, so no flush is
+needed between steps.  The plain FP64 solver is timed on the same system in the
+same run (fp64_* keys).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload n1280|mixed640|plain96] [--z-unit radius|m]
+
+Under torchrun every rank solves its own copy (replicas: the path has no
+data-parallel exchange) and rank 0 prints one JSON line.  --impl reference
+times the CPU oracle (serial C) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "N1280-shape solves/s at 1e-8 FP64 residual, mixed vs FP64; % of HBM BW"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96"])
+    ap.add_argument("--z-unit", default="radius", choices=["radius", "m"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(args):
+    import gen
+
+    w = gen.WORKLOADS[args.workload]
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    A = gen.make_operator(nx, ny, nz, w["seed_coef"], z_unit=args.z_unit)
+    b = gen.make_rhs(nx, ny, nz, w["seed_rhs"])
+    return (nx, ny, nz), A, b
+
+
+def cpu_baseline(A, b, dims, outer, inner, mode_mixed=True, reps=1):
+    """Oracle (serial C, as it stands) timed on the host: one call each of the
+    true residual, T^-1 and Ahat x over the full system, composed with the GPU
+    solve's outer/inner counts (one inner iteration = 2 T^-1 + 2 Ahat x)."""
+    import oracle
+
+    nx, ny, nz = dims
+    t0 = time.perf_counter()
+    Ah = oracle.scale(A)
+    t_scale = time.perf_counter() - t0
+    x = np.zeros_like(b)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.residual(A, b, x)
+        t_res = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        z = oracle.apply_Tinv(Ah, b)
+        t_tinv = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.matvec_hat(Ah, z)
+        t_mv = time.perf_counter() - t0
+        t_solve = (outer + 1) * t_res + inner * 2 * (t_tinv + t_mv)
+        ts.append(t_solve)
+    t_solve = min(ts)
+    return {
+        "value": 1.0 / t_solve,
+        "unit": "solves/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"oracle (serial C, FP64) timed once per piece on the full {nx}x{ny}x{nz} system: true residual "
+                   f"{t_res:.2f} s, T^-1 {t_tinv:.2f} s, Ahat x {t_mv:.2f} s (scaling {t_scale:.2f} s, not counted); "
+                   f"composed as {outer + 1} residuals + {inner} iterations x (2 T^-1 + 2 Ahat x)"),
+    }
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    dims, A, b = make_inputs(args)
+    outer, inner = 2, 4  # counts of the GPU mixed solve of this workload (n1280, radius): see profiles/
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(A, b, dims, outer, inner)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} {'x'.join(map(str, dims))} z_unit={args.z_unit}"},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    dims, A, b = make_inputs(args)
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    stream = torch.cuda.current_stream()
+    op = hz.Operator(A, stream=stream)
+    bd = torch.from_numpy(b.reshape(-1)).to(f"cuda:{dev}")
+    x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
+    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8)
+    p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(params, steps, warmup):
+        infos = []
+        for _ in range(warmup):
+            op.solve(bd, x, params=params)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            infos.append(op.solve(bd, x, params=params))
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=f"cuda:{dev}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    # setup (operator update: scaling + Thomas factors), timed separately
+    Ad = torch.from_numpy(A).to(f"cuda:{dev}")
+    su = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        op.update(Ad)  # device-resident coefficients: 7-band copy + scaling + Thomas factors
+        e1.record(stream)
+        torch.cuda.synchronize()
+        su.append(e0.elapsed_time(e1))
+    del Ad
+
+    with Clocks(dev) as clk:
+        ms, infos = timed(pm, args.steps, args.warmup)
+    clocks = clk.summary()
+    for i in infos:
+        assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
+    value = world * args.steps / (ms * 1e-3)
+    launches = int(sum(i["kernel_launches"] for i in infos))
+
+    fp64 = None
+    if not args.no_fp64:
+        ms64, inf64 = timed(p64, max(1, args.steps // 2), 1)
+        for i in inf64:
+            assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
+        fp64 = {"value": world * len(inf64) / (ms64 * 1e-3), "ms_per_solve": ms64 / len(inf64),
+                "outer": inf64[0]["outer_iters"], "inner": inf64[0]["inner_iters"]}
+
+    # end to end through the public API with host buffers (pinned b, pinned x)
+    bh = torch.from_numpy(b.reshape(-1)).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    op.solve(bh, xh, params=pm)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps // 2)
+    for _ in range(e2e_steps):
+        op.solve(bh, xh, params=pm)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n}
+
+    # per-kernel profile of one more solve (CUDA events around every launch on the op's stream)
+    op.profile(True)
+    op.solve(bd, x, params=pm)
+    prof = op.profile_read()
+    op.profile(False)
+    busy = {k: v for k, v in prof.items() if v[0] > 0 and k != "k_setup"}
+    tot_ms = sum(v[1] for v in busy.values())
+    dom = max(busy, key=lambda k: busy[k][1])
+    la, kms, kby = busy[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = kby / (kms * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tp):
+        try:
+            from paper_1811_03852_gb300 import _build
+
+            tj = json.load(open(tp))
+            ent = tj.get(dom)
+            if ent and ent.get("src") == _build._deps_hash() and ent.get("workload") == args.workload:
+                traffic = ent["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                "bytes_per_launch": kby / la, "launches": la, "avg_launch_ms": kms / la,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot_ms, 4),
+                   "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None} for k, v in busy.items()}
+
+    if rank != 0:
+        return
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cb = cpu_baseline(A, b, dims, infos[0]["outer_iters"], infos[0]["inner_iters"])
+        except MemoryError:
+            cb = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "host memory exhausted"}
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+        "config": {"workload": f"{args.workload} {nx}x{ny}x{nz} z_unit={args.z_unit} seeds "
+                               f"{make_seed(args)} mixed IR tol 1e-8 eta 1e-4",
+                   "l2": "inputs larger than L2 (vectors 1.4-2.8 GB)", "parallelism": f"replicas x{world}"},
+        "solve": {"outer": infos[0]["outer_iters"], "inner": infos[0]["inner_iters"],
+                  "true_rel_residual": infos[0]["true_rel_residual"]},
+        "fp64": fp64,
+        "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
+        "setup_ms": round(min(su), 3),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cb,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def make_seed(args):
+    import gen
+
+    w = gen.WORKLOADS[args.workload]
+    return f"{w['seed_coef']}/{w['seed_rhs']}"
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

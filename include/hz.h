@@ -1,0 +1,207 @@
+/*
+ * hz.h -- C ABI of the GB300 (sm_103a) mixed-precision Helmholtz solver.
+ *
+ * The solver computes x with ||b - A x||_2 / ||b||_2 <= tol for the ENDGame
+ * pressure-correction system A x = b (Maynard & Walters, "Precision of the
+ * ENDGame", arXiv:1811.03852: Sec. 1 eq. LinearSys; Sec. 2 eq. Helmholtz,
+ * a 7-band, nonsymmetric, variable-coefficient matrix on a lon-lat grid with
+ * vertical levels).  The method is the paper's post-conditioned BiCGStab on
+ * the diagonally scaled system D^-1 A (Sec. 2) with the per-column vertical
+ * tridiagonal part T of D^-1 A as preconditioner (Sec. 2, pre-computed LU of
+ * T at each horizontal point), a mandatory restart every 150 iterations
+ * (Sec. 4), FP64 global sums (Sec. 4), and -- to reach residuals below the
+ * 32-bit limit of Sec. 3 -- an outer FP64 iterative-refinement loop around an
+ * FP32 inner solve.
+ *
+ * Conventions for every entry point
+ *  - Grid: nx (longitude, periodic) x ny (latitude; rows 0 and ny-1 are the
+ *    polar rows, no flux across them) x nz (levels; no flux through the top
+ *    and bottom).  Arrays are C-ordered [nz][ny][nx], i (longitude) fastest;
+ *    point p = (k*ny + j)*nx + i.
+ *  - Operator coefficients: 7 bands, band-major [7][nz][ny][nx], order
+ *    C (centre), E (i+1), W (i-1), N (j+1), S (j-1), U (k+1), D (k-1).  Row p
+ *    of A x is C x_p + E x_(i+1) + W x_(i-1) + N x_(j+1) + S x_(j-1) +
+ *    U x_(k+1) + D x_(k-1).  N must be 0 on j = ny-1, S on j = 0, U on
+ *    k = nz-1 and D on k = 0; C must be finite and nonzero.
+ *  - "host or device" pointers: the library asks the CUDA runtime which kind
+ *    a pointer is; host buffers are copied on the operator's stream.
+ *  - Ownership: the caller owns every array it passes; the library keeps its
+ *    own copies of what it needs after the call returns.  Handles are owned
+ *    by the library until destroyed.
+ *  - All GPU work is ordered on the stream given at create time.  No
+ *    exception crosses the ABI; every call returns an hz_status.
+ *  - Thread safety: one operator per host thread at a time.
+ */
+#ifndef HZ_H_
+#define HZ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HZ_ABI_VERSION 1
+
+typedef struct hz_op_s* hz_op;
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_INVALID = 1,        /* bad argument or operator (sizes, boundary coefficients, zero diagonal) */
+  HZ_ERR_CUDA = 2,           /* a CUDA runtime call failed; hz_last_error() has the text */
+  HZ_ERR_OOM = 3,            /* device allocation failed */
+  HZ_ERR_NOT_CONVERGED = 4,  /* iteration limits reached; x holds the best iterate */
+  HZ_ERR_BREAKDOWN = 5,      /* Krylov breakdown could not be cured by restarting */
+  HZ_ERR_NONFINITE = 6,      /* a non-finite value appeared; x holds the last finite iterate */
+  HZ_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+  HZ_ERR_UNSUPPORTED = 8     /* valid request this build does not provide */
+} hz_status;
+
+/* Outer/inner precision split (Sec. 3: R_c >> eps_32 allows 32-bit work). */
+typedef enum {
+  HZ_MODE_FP64 = 0,     /* inner BiCGStab in FP64: the double-precision baseline */
+  HZ_MODE_MIXED_IR = 1  /* inner BiCGStab in FP32, outer FP64 residual and update */
+} hz_mode;
+
+typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
+
+typedef enum {
+  HZ_PRE_TRI = 0,    /* C = T^-1, the per-column tridiagonal solve */
+  HZ_PRE_TRI_NN = 1  /* T^-1 followed by the learned conv-net correction (flexible Krylov only) */
+} hz_precond;
+
+typedef enum { HZ_KRYLOV_BICGSTAB = 0, HZ_KRYLOV_FGMRES = 1 } hz_krylov;
+
+/* Solve parameters (host struct).  Fill with hz_default_params first. */
+typedef struct {
+  double tol;        /* target true relative residual ||b - A x|| / ||b||   (default 1e-8) */
+  double inner_tol;  /* inner relative tolerance eta on the scaled system (default 1e-4; FP64 mode: 0.1*tol) */
+  int mode;          /* hz_mode (default HZ_MODE_MIXED_IR) */
+  int precond;       /* hz_precond (default HZ_PRE_TRI) */
+  int krylov;        /* hz_krylov (default HZ_KRYLOV_BICGSTAB) */
+  int max_outer;     /* refinement steps (default 10) */
+  int max_inner;     /* inner iterations per refinement step (default 1000) */
+  int restart;       /* forced BiCGStab restart period (default 150, Sec. 4) */
+  int fgmres_m;      /* FGMRES restart length (default 30) */
+  int use_graph;     /* 1: inner loop runs on the device inside a CUDA graph (default); 0: host-driven */
+  int record_history;/* 1: keep the inner recursive residual after every iteration (hz_get_history) */
+} hz_solve_params;
+
+/* Solve report (host struct). */
+typedef struct {
+  int status;                 /* hz_status of the solve */
+  int outer_iters;            /* refinement steps taken */
+  int inner_iters;            /* total inner Krylov iterations */
+  int restarts;               /* inner restarts (periodic + breakdown) */
+  int fallbacks;              /* learned-stage fallbacks to plain T^-1 */
+  double true_rel_residual;   /* final ||b - A x|| / ||b|| in FP64 (Sec. 3, eq. residual) */
+  double scaled_rel_residual; /* last inner recursive residual relative to its right-hand side */
+  double seconds;             /* device time of the solve */
+  long long kernel_launches;  /* CUDA kernels launched by the solve */
+} hz_solve_info;
+
+int hz_version(void);
+const char* hz_status_str(int status);
+/* Text of the last CUDA failure seen by this thread ("" if none). */
+const char* hz_last_error(void);
+void hz_default_params(hz_solve_params* params);
+
+/*
+ * Create an operator from the seven coefficient bands (Sec. 2, eq. Helmholtz).
+ * coeffs: host or device, 7*nx*ny*nz doubles, layout above; read during the
+ * call only.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Work done: copy of A in FP64 (for the true residual), the diagonal scaling
+ * D^-1 A in FP32 and FP64 (Sec. 2: applied outside the solver), and the
+ * per-column LU factors of T in FP32 and FP64 (Sec. 2).
+ * Errors: HZ_ERR_INVALID for nx<1, ny<1, nz<1, nz>HZ_MAX_LEVELS, a zero or
+ * non-finite diagonal, a nonzero coefficient pointing across a pole or the
+ * top/bottom, or a tridiagonal factor that breaks down; HZ_ERR_OOM.
+ * On error *out is NULL.
+ */
+#define HZ_MAX_LEVELS 4096
+int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_op* out);
+
+/* Replace the coefficients (a new time step: the matrix changes every step,
+   Sec. 2) and redo the scaling and factorisation.  Same rules as create. */
+int hz_op_update(hz_op op, const double* coeffs);
+
+/* Release an operator and all its device memory.  NULL is accepted. */
+int hz_op_destroy(hz_op op);
+
+/* Grid of an operator. */
+int hz_op_dims(hz_op op, int* nx, int* ny, int* nz);
+
+/*
+ * Solve A x = b to params->tol in the true FP64 relative residual.
+ * b: host or device, n doubles.  x0: host or device initial guess, or NULL
+ * for zero.  x: host or device output, n doubles; may alias x0.
+ * params: NULL for defaults.  info: host, may be NULL; when given, the call
+ * waits for the solve to finish and fills it (it always does so anyway,
+ * since the outer loop reads the residual on the host).
+ * Returns HZ_OK, HZ_ERR_NOT_CONVERGED (x = best iterate), HZ_ERR_NONFINITE
+ * (x = last finite iterate), HZ_ERR_INVALID, HZ_ERR_CUDA.
+ */
+int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_solve_params* params,
+             hz_solve_info* info);
+
+/*
+ * Solve nsys independent systems (each with its own operator, which may have
+ * its own grid).  b[s], x0[s] (may be NULL) and x[s] follow hz_solve's rules
+ * (device pointers only).  The inner FP32 Krylov iterations of all systems
+ * run in one persistent launch per refinement step, with per-system scalars
+ * and convergence masks.  infos: host array of nsys reports, may be NULL.
+ * All operators must share one stream.  Returns the worst status.
+ */
+int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
+                     const hz_solve_params* params, hz_solve_info* infos);
+
+/* Inner recursive residual history of the last solve with record_history=1:
+   copies up to cap values into hist (host) and returns how many. */
+int hz_get_history(hz_op op, double* hist, int cap);
+
+/*
+ * Per-kernel profile.  While enabled, solves run the host-driven loop with a
+ * pair of CUDA events on the operator's stream around every kernel launch
+ * (slower: each launch is waited for), and hz_profile_read returns, for
+ * kernel kid, the launches, their summed device time in ms and their summed
+ * algorithmic bytes (each array element read or written once per launch).
+ * Enabling (or disabling) resets the counters.  hz_op_update is profiled too.
+ */
+#define HZ_NUM_KERNELS 7 /* k_setup, k_residual, k_pre_p, k_mv_v, k_pre_s, k_mv_t, k_upd */
+int hz_profile_enable(hz_op op, int on);
+int hz_profile_read(hz_op op, int kid, long long* launches, double* ms, double* bytes);
+const char* hz_kernel_name(int kid);
+
+/* ---- kernel-level entry points (the building blocks of the solve, exposed for testing) ---- */
+
+/* y = D^-1 A x (unit diagonal, six scaled bands) in the given precision.
+   x, y: device arrays of n floats (HZ_PREC_FP32) or doubles (HZ_PREC_FP64). */
+int hz_matvec(hz_op op, int prec, const void* x, void* y);
+
+/* z = T^-1 r, T = per-column tridiagonal part of D^-1 A (Sec. 2), using the
+   pre-computed factors.  r, z: device arrays in the given precision; may not alias. */
+int hz_precond_apply(hz_op op, int prec, const void* r, void* z);
+
+/* v = D^-1 A (T^-1 p) as the solver forms it: ph = T^-1 p, then
+   v = p + H ph with H the four horizontal bands (T ph = p).  p, ph, v: device. */
+int hz_precond_matvec(hz_op op, int prec, const void* p, void* ph, void* v);
+
+/* True FP64 residual (Sec. 3): r = b - A x with the unscaled bands.
+   b, x: device doubles; r: device doubles or NULL; rnorm, bnorm: host outputs (may be NULL). */
+int hz_residual(hz_op op, const double* b, const double* x, double* r, double* rnorm, double* bnorm);
+
+/* Deterministic dot product sum_i x_i y_i of device arrays (float or double
+   by prec; FP64 accumulation across threads and blocks).  out: host. */
+int hz_dot(int prec, int64_t n, const void* x, const void* y, void* stream, double* out);
+
+/* Copy the operator's derived data to device memory dst:
+   what = 0: scaled bands [6][n] (E,W,N,S,U,D) in prec;
+   what = 1: Thomas factors [3][n] (m, l, c') in prec, where the forward sweep
+             is y_k = m_k p_k - l_k y_(k-1) and the back sweep z_k = y_k - c'_k z_(k+1). */
+int hz_op_export(hz_op op, int what, int prec, void* dst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H_ */

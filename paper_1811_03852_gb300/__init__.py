@@ -1,0 +1,290 @@
+"""GB300 (sm_103a) mixed-precision Helmholtz solver -- thin Python binding of libhz.so.
+
+The solver is the method of Maynard & Walters, "Precision of the ENDGame"
+(arXiv:1811.03852): post-conditioned BiCGStab on D^-1 A with the per-column
+vertical tridiagonal preconditioner (Sec. 2), FP32 inner iterations and FP64
+global sums (Secs. 3-4), wrapped in an outer FP64 iterative-refinement loop
+on the true residual R = ||b - A x|| / ||b||.
+
+Every step of the solve runs in the CUDA library; this module only marshals
+arguments through ctypes (names match include/hz.h).  PyTorch is used for
+device memory and streams.  There is no CPU fallback: importing the package
+on a machine without the built library, or calling a compute entry point
+without a GPU, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+HZ_OK = 0
+HZ_ERR_INVALID = 1
+HZ_ERR_CUDA = 2
+HZ_ERR_OOM = 3
+HZ_ERR_NOT_CONVERGED = 4
+HZ_ERR_BREAKDOWN = 5
+HZ_ERR_NONFINITE = 6
+HZ_ERR_TIMEOUT = 7
+HZ_ERR_UNSUPPORTED = 8
+
+HZ_MODE_FP64 = 0
+HZ_MODE_MIXED_IR = 1
+HZ_PREC_FP64 = 0
+HZ_PREC_FP32 = 1
+HZ_PRE_TRI = 0
+HZ_PRE_TRI_NN = 1
+HZ_KRYLOV_BICGSTAB = 0
+HZ_KRYLOV_FGMRES = 1
+NUM_KERNELS = 7
+
+
+class hz_solve_params(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("inner_tol", ctypes.c_double),
+        ("mode", ctypes.c_int),
+        ("precond", ctypes.c_int),
+        ("krylov", ctypes.c_int),
+        ("max_outer", ctypes.c_int),
+        ("max_inner", ctypes.c_int),
+        ("restart", ctypes.c_int),
+        ("fgmres_m", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("record_history", ctypes.c_int),
+    ]
+
+
+class hz_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("outer_iters", ctypes.c_int),
+        ("inner_iters", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("fallbacks", ctypes.c_int),
+        ("true_rel_residual", ctypes.c_double),
+        ("scaled_rel_residual", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libhz.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhz.so not built at {path}; run paper_1811_03852_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    i32, i64, dbl, pv = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "hz_version": (i32, []),
+        "hz_status_str": (ctypes.c_char_p, [i32]),
+        "hz_last_error": (ctypes.c_char_p, []),
+        "hz_default_params": (None, [P(hz_solve_params)]),
+        "hz_op_create": (i32, [i32, i32, i32, pv, pv, P(pv)]),
+        "hz_op_update": (i32, [pv, pv]),
+        "hz_op_destroy": (i32, [pv]),
+        "hz_op_dims": (i32, [pv, P(i32), P(i32), P(i32)]),
+        "hz_solve": (i32, [pv, pv, pv, pv, P(hz_solve_params), P(hz_solve_info)]),
+        "hz_solve_batched": (i32, [i32, P(pv), P(pv), P(pv), P(pv), P(hz_solve_params), P(hz_solve_info)]),
+        "hz_get_history": (i32, [pv, pv, i32]),
+        "hz_matvec": (i32, [pv, i32, pv, pv]),
+        "hz_precond_apply": (i32, [pv, i32, pv, pv]),
+        "hz_precond_matvec": (i32, [pv, i32, pv, pv, pv]),
+        "hz_residual": (i32, [pv, pv, pv, pv, P(dbl), P(dbl)]),
+        "hz_dot": (i32, [i32, i64, pv, pv, pv, P(dbl)]),
+        "hz_op_export": (i32, [pv, i32, i32, pv]),
+        "hz_profile_enable": (i32, [pv, i32]),
+        "hz_profile_read": (i32, [pv, i32, P(ctypes.c_longlong), P(dbl), P(dbl)]),
+        "hz_kernel_name": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class HzError(RuntimeError):
+    def __init__(self, status, where=""):
+        L = load()
+        msg = L.hz_status_str(status).decode()
+        last = L.hz_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){' -- ' + last if last else ''}")
+        self.status = status
+
+
+def _check(st, where):
+    if st != HZ_OK:
+        raise HzError(st, where)
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor (device or host) or numpy array (host); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def default_params(**kw) -> hz_solve_params:
+    p = hz_solve_params()
+    load().hz_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Operator:
+    """A Helmholtz operator on the GPU (``hz_op``).
+
+    coeffs: float64 array/tensor of shape (7, nz, ny, nx) (bands C,E,W,N,S,U,D),
+    host (numpy / CPU tensor) or CUDA tensor.
+    """
+
+    def __init__(self, coeffs, stream=None):
+        L = load()
+        shape = tuple(coeffs.shape)
+        if len(shape) != 4 or shape[0] != 7:
+            raise ValueError("coeffs must have shape (7, nz, ny, nx)")
+        _, nz, ny, nx = shape
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        self._h = ctypes.c_void_p()
+        st = L.hz_op_create(nx, ny, nz, _ptr(coeffs), _stream_ptr(stream), ctypes.byref(self._h))
+        _check(st, "hz_op_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def update(self, coeffs):
+        _check(load().hz_op_update(self._h, _ptr(coeffs)), "hz_op_update")
+
+    def close(self):
+        if self._h:
+            load().hz_op_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- solve -----------------------------------------------------------------
+    def solve(self, b, x, x0=None, params=None, raise_on_error=True, **kw):
+        """x <- solution of A x = b.  Returns an hz_solve_info as a dict."""
+        p = params if params is not None else default_params(**kw)
+        info = hz_solve_info()
+        st = load().hz_solve(self._h, _ptr(b), _ptr(x0), _ptr(x), ctypes.byref(p), ctypes.byref(info))
+        d = info.as_dict()
+        d["status"] = st
+        if raise_on_error and st not in (HZ_OK,):
+            raise HzError(st, f"hz_solve {d}")
+        return d
+
+    def history(self, cap=100000):
+        buf = np.zeros(cap)
+        n = load().hz_get_history(self._h, buf.ctypes.data, cap)
+        return buf[: max(n, 0)]
+
+    # ---- building blocks ---------------------------------------------------------
+    def matvec(self, x, y, prec):
+        _check(load().hz_matvec(self._h, prec, _ptr(x), _ptr(y)), "hz_matvec")
+
+    def precond_apply(self, r, z, prec):
+        _check(load().hz_precond_apply(self._h, prec, _ptr(r), _ptr(z)), "hz_precond_apply")
+
+    def precond_matvec(self, p, ph, v, prec):
+        _check(load().hz_precond_matvec(self._h, prec, _ptr(p), _ptr(ph), _ptr(v)), "hz_precond_matvec")
+
+    def residual(self, b, x, r=None):
+        rn, bn = ctypes.c_double(), ctypes.c_double()
+        _check(load().hz_residual(self._h, _ptr(b), _ptr(x), _ptr(r), ctypes.byref(rn), ctypes.byref(bn)),
+               "hz_residual")
+        return rn.value, bn.value
+
+    def profile(self, on=True):
+        _check(load().hz_profile_enable(self._h, 1 if on else 0), "hz_profile_enable")
+
+    def profile_read(self):
+        """{kernel name: (launches, ms, algorithmic bytes)} accumulated since profile(True)."""
+        L = load()
+        out = {}
+        for k in range(NUM_KERNELS):
+            la, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            _check(L.hz_profile_read(self._h, k, ctypes.byref(la), ctypes.byref(ms), ctypes.byref(by)),
+                   "hz_profile_read")
+            out[L.hz_kernel_name(k).decode()] = (la.value, ms.value, by.value)
+        return out
+
+    def export(self, what, prec, dst):
+        _check(load().hz_op_export(self._h, what, prec, _ptr(dst)), "hz_op_export")
+
+
+def solve_batched(ops, bs, xs, x0s=None, params=None, **kw):
+    """Solve several systems (each its own Operator) in one batched call; returns a list of info dicts."""
+    L = load()
+    k = len(ops)
+    p = params if params is not None else default_params(**kw)
+    arr = ctypes.c_void_p * k
+    hs = arr(*[o.handle.value for o in ops])
+    bp = arr(*[_ptr(b) for b in bs])
+    xp = arr(*[_ptr(x) for x in xs])
+    x0p = arr(*[_ptr(x) for x in x0s]) if x0s is not None else None
+    infos = (hz_solve_info * k)()
+    st = L.hz_solve_batched(k, hs, bp, x0p, xp, ctypes.byref(p), infos)
+    out = [i.as_dict() for i in infos]
+    if st != HZ_OK:
+        raise HzError(st, f"hz_solve_batched {out}")
+    return out
+
+
+def dot(x, y, prec=None, stream=None):
+    """Deterministic FP64-accumulated dot product of two CUDA tensors."""
+    import torch
+
+    if prec is None:
+        prec = HZ_PREC_FP32 if x.dtype == torch.float32 else HZ_PREC_FP64
+    out = ctypes.c_double()
+    _check(load().hz_dot(prec, x.numel(), _ptr(x), _ptr(y), _stream_ptr(stream), ctypes.byref(out)), "hz_dot")
+    return out.value
+
+
+def version() -> int:
+    return load().hz_version()

@@ -1,0 +1,749 @@
+// hz_engine.cu -- host side of the solver: operators, workspaces, the outer
+// refinement loop, the inner loop (CUDA-graph while loop or host-driven), and
+// the extern "C" entry points declared in include/hz.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hz_internal.cuh"
+
+using namespace hz;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(cudaError_t e, const char* what, int line) {
+  snprintf(g_err, sizeof(g_err), "%s (%d) at hz_engine.cu:%d: %s", cudaGetErrorName(e), (int)e, line, what);
+}
+
+#define CK(call)                                                       \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) {                                           \
+      set_err(e_, #call, __LINE__);                                    \
+      return e_ == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA; \
+    }                                                                  \
+  } while (0)
+
+#define CKS(call)                  \
+  do {                             \
+    int s_ = (call);               \
+    if (s_ != HZ_OK) return s_;    \
+  } while (0)
+
+inline int64_t pad64(int64_t n) { return (n + 63) / 64 * 64; }  // 256-byte alignment of FP32 vectors
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct GraphSlot {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int occupancy_grid(const void* kernel, int block, int sms, int64_t work_blocks) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int64_t g = (int64_t)per_sm * sms;
+  g = std::min<int64_t>(g, work_blocks);
+  g = std::min<int64_t>(g, kMaxGrid);
+  return (int)std::max<int64_t>(g, 1);
+}
+
+}  // namespace
+
+namespace hz {
+// occupancy-based grid sizes of the column and elementwise kernels (hz_krylov.cu)
+void column_kernel_ptrs(std::vector<const void*>& col, std::vector<const void*>& flat);
+}  // namespace hz
+
+struct hz_op_s {
+  Grid g{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  int dev = 0, sms = 0;
+  Launch L{};
+  double* A7 = nullptr;
+  float* ah32 = nullptr;
+  float* th32 = nullptr;
+  double* ah64 = nullptr;
+  double* th64 = nullptr;
+  double* invc = nullptr;
+  float* w32base = nullptr;
+  double* w64base = nullptr;
+  Vecs<float> w32{};
+  Vecs<double> w64{};
+  double* xbuf = nullptr;  // result staging when the caller's x is host memory
+  double* xscr = nullptr;  // second buffer of the refinement ping-pong
+  double* bbuf = nullptr;  // staging of a host b
+  Ctl* ctl = nullptr;
+  Ctl* cfg_h = nullptr;  // pinned: configuration written to ctl
+  Ctl* rep_h = nullptr;  // pinned: ctl read back
+  Red red{};
+  int* err_d = nullptr;
+  int* err_h = nullptr;
+  double* hist_d = nullptr;
+  int hist_cap = 0;
+  GraphSlot gs[2];  // [0] FP32 inner loop, [1] FP64 inner loop
+  std::vector<void*> allocs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel profile (CUDA events around every launch; host-driven loop)
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;
+  long long p_launch[HZ_NUM_KERNELS] = {};
+  double p_ms[HZ_NUM_KERNELS] = {};
+  double p_bytes[HZ_NUM_KERNELS] = {};
+  long long launches = 0;  // kernels launched by the last solve
+};
+
+namespace {
+
+template <typename T>
+T* dalloc(hz_op op, int64_t count, int* st) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_err(e, "cudaMalloc", __LINE__);
+    *st = (e == cudaErrorMemoryAllocation) ? HZ_ERR_OOM : HZ_ERR_CUDA;
+    return nullptr;
+  }
+  op->allocs.push_back(p);
+  return (T*)p;
+}
+
+template <typename T>
+Bands<T> bands_of(hz_op op);
+template <>
+Bands<float> bands_of<float>(hz_op op) {
+  const int64_t n = op->g.n;
+  const float* a = op->ah32;
+  const float* t = op->th32;
+  return Bands<float>{a, a + n, a + 2 * n, a + 3 * n, a + 4 * n, a + 5 * n, t, t + n, t + 2 * n};
+}
+template <>
+Bands<double> bands_of<double>(hz_op op) {
+  const int64_t n = op->g.n;
+  const double* a = op->ah64;
+  const double* t = op->th64;
+  return Bands<double>{a, a + n, a + 2 * n, a + 3 * n, a + 4 * n, a + 5 * n, t, t + n, t + 2 * n};
+}
+
+template <typename T>
+Vecs<T> carve(T* base, int64_t n) {
+  const int64_t s = pad64(n);
+  return Vecs<T>{base, base + s, base + 2 * s, base + 3 * s, base + 4 * s,
+                 base + 5 * s, base + 6 * s, base + 7 * s, base + 8 * s, base + 9 * s};
+}
+
+template <typename T>
+Vecs<T>& vecs_of(hz_op op);
+template <>
+Vecs<float>& vecs_of<float>(hz_op op) { return op->w32; }
+template <>
+Vecs<double>& vecs_of<double>(hz_op op) { return op->w64; }
+
+int ensure_w64(hz_op op) {
+  if (op->w64base) return HZ_OK;
+  int st = HZ_OK;
+  op->w64base = dalloc<double>(op, 10 * pad64(op->g.n), &st);
+  if (!op->w64base) return st;
+  op->w64 = carve(op->w64base, op->g.n);
+  return HZ_OK;
+}
+
+// one inner BiCGStab iteration (five launches) on stream s
+template <typename T>
+cudaError_t launch_body(hz_op op, cudaStream_t s, unsigned long long cond, int use_cond) {
+  Launch L = op->L;
+  L.stream = s;
+  const Bands<T> a = bands_of<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  cudaError_t e;
+  if ((e = launch_pre_p<T>(op->g, a, w, op->ctl, op->red, L)) != cudaSuccess) return e;
+  if ((e = launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L)) != cudaSuccess) return e;
+  if ((e = launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L)) != cudaSuccess) return e;
+  if ((e = launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L)) != cudaSuccess) return e;
+  return launch_upd<T>(op->g, w, op->ctl, op->red, cond, use_cond, L);
+}
+
+// Build the inner loop as a graph: one conditional WHILE node whose body is
+// one iteration; k_upd sets the condition from the device.
+template <typename T>
+int build_graph(hz_op op) {
+  GraphSlot& gs = op->gs[sizeof(T) == 8 ? 1 : 0];
+  if (gs.exec) return HZ_OK;
+  CK(cudaGraphCreate(&gs.graph, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, gs.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, gs.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(op->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_body<T>(op, op->cap, (unsigned long long)h, 1);
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(op->cap, &out);
+  CK(e);
+  CK(e2);
+  CK(cudaGraphInstantiate(&gs.exec, gs.graph, 0));
+  return HZ_OK;
+}
+
+// Profiled launch: events on the launching stream around the kernel, waited for
+// at once, with the launch's algorithmic bytes credited to kernel `kid`.
+template <typename F>
+int prof_launch(hz_op op, int kid, double bytes, F&& launch) {
+  if (op->pev.size() < 2) {
+    op->pev.resize(2);
+    for (auto& e : op->pev) CK(cudaEventCreate(&e));
+  }
+  CK(cudaEventRecord(op->pev[0], op->stream));
+  CK(launch());
+  CK(cudaEventRecord(op->pev[1], op->stream));
+  CK(cudaEventSynchronize(op->pev[1]));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, op->pev[0], op->pev[1]));
+  op->p_launch[kid] += 1;
+  op->p_ms[kid] += ms;
+  op->p_bytes[kid] += bytes;
+  return HZ_OK;
+}
+
+// One inner iteration with every launch timed; the control block is read
+// after each launch so that the bytes credited match the work done.
+template <typename T>
+int profiled_iteration(hz_op op) {
+  const double n = (double)op->g.n, B = (double)sizeof(T);
+  Launch L = op->L;
+  const Bands<T> a = bands_of<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  auto state = [&](Ctl* c) -> int {
+    CK(cudaMemcpyAsync(c, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    return HZ_OK;
+  };
+  Ctl* c = op->rep_h;
+  CKS(state(c));
+  if (c->state != ST_RUNNING && c->state != ST_RESTART) return HZ_OK;
+  const double bp = c->state == ST_RESTART ? 16 * B : (c->fresh ? 6 * B : 8 * B);
+  const bool xz = c->xzero != 0;
+  CKS(prof_launch(op, 2, bp * n, [&] { return launch_pre_p<T>(op->g, a, w, op->ctl, op->red, L); }));
+  op->launches++;
+  CKS(state(c));
+  if (c->state != ST_RUNNING) return HZ_OK;
+  CKS(prof_launch(op, 3, 8 * B * n, [&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }));
+  CKS(prof_launch(op, 4, 7 * B * n, [&] { return launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L); }));
+  op->launches += 2;
+  CKS(state(c));
+  const bool half = c->state == ST_HALF;
+  if (!half)
+    CKS(prof_launch(op, 5, 7 * B * n, [&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); }));
+  const double bu = half ? (xz ? 2 : 3) * B : (xz ? 7 : 8) * B;
+  CKS(prof_launch(op, 6, bu * n, [&] { return launch_upd<T>(op->g, w, op->ctl, op->red, 0ull, 0, L); }));
+  op->launches += half ? 1 : 2;
+  return HZ_OK;
+}
+
+template <typename T>
+int run_inner(hz_op op, int use_graph, int max_inner) {
+  if (op->prof) {
+    for (int it = 0; it < 4 * max_inner + 16; ++it) {
+      CKS(profiled_iteration<T>(op));
+      const int st = op->rep_h->state;
+      if (st != ST_RUNNING && st != ST_RESTART) break;
+    }
+    return HZ_OK;
+  }
+  if (use_graph) {
+    CKS(build_graph<T>(op));
+    CK(cudaGraphLaunch(op->gs[sizeof(T) == 8 ? 1 : 0].exec, op->stream));
+    return HZ_OK;
+  }
+  // host-driven: launch iterations in groups and poll the device state
+  const int group = 4;
+  for (int it = 0; it < 4 * max_inner + 16; it += group) {
+    for (int u = 0; u < group; ++u) CK(launch_body<T>(op, op->stream, 0ull, 0));
+    CK(cudaMemcpyAsync(&op->rep_h->state, &op->ctl->state, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    const int st = op->rep_h->state;
+    if (st != ST_RUNNING && st != ST_RESTART) break;
+  }
+  return HZ_OK;
+}
+
+int do_setup(hz_op op, const double* coeffs) {
+  const int64_t n = op->g.n;
+  const bool dev = is_device_ptr(coeffs);
+  CK(cudaMemcpyAsync(op->A7, coeffs, sizeof(double) * 7 * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     op->stream));
+  CK(cudaMemsetAsync(op->err_d, 0, sizeof(int), op->stream));
+  SetupOut o{op->ah32, op->th32, op->ah64, op->th64, op->invc, op->err_d};
+  if (op->prof)
+    CKS(prof_launch(op, 0, 164.0 * (double)n, [&] { return launch_setup(op->g, op->A7, o, op->L); }));
+  else
+    CK(launch_setup(op->g, op->A7, o, op->L));
+  CK(cudaMemcpyAsync(op->err_h, op->err_d, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
+  CK(cudaStreamSynchronize(op->stream));
+  if (*op->err_h) {
+    snprintf(g_err, sizeof(g_err), "operator rejected (flags %d: 1 zero/non-finite coefficient, 2 flux across a "
+             "pole or the top/bottom, 4 tridiagonal factor breakdown)", *op->err_h);
+    return HZ_ERR_INVALID;
+  }
+  return HZ_OK;
+}
+
+void free_op(hz_op op) {
+  if (!op) return;
+  for (auto& gs : op->gs) {
+    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+    if (gs.graph) cudaGraphDestroy(gs.graph);
+  }
+  for (void* p : op->allocs) cudaFree(p);
+  if (op->cfg_h) cudaFreeHost(op->cfg_h);
+  if (op->rep_h) cudaFreeHost(op->rep_h);
+  if (op->err_h) cudaFreeHost(op->err_h);
+  if (op->cap) cudaStreamDestroy(op->cap);
+  if (op->ev0) cudaEventDestroy(op->ev0);
+  if (op->ev1) cudaEventDestroy(op->ev1);
+  delete op;
+}
+
+// global scratch for hz_dot (per device)
+std::mutex g_dot_mu;
+struct DotScratch {
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  double* out = nullptr;
+  double* out_h = nullptr;
+};
+DotScratch g_dot[64];
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int hz_version(void) { return HZ_ABI_VERSION; }
+
+const char* hz_last_error(void) { return g_err; }
+
+const char* hz_status_str(int s) {
+  switch (s) {
+    case HZ_OK: return "ok";
+    case HZ_ERR_INVALID: return "invalid argument or operator";
+    case HZ_ERR_CUDA: return "CUDA error";
+    case HZ_ERR_OOM: return "out of device memory";
+    case HZ_ERR_NOT_CONVERGED: return "not converged";
+    case HZ_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HZ_ERR_NONFINITE: return "non-finite value";
+    case HZ_ERR_TIMEOUT: return "device wait timed out";
+    case HZ_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+void hz_default_params(hz_solve_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->tol = 1e-8;
+  p->inner_tol = 0.0;  // 0 = mode default
+  p->mode = HZ_MODE_MIXED_IR;
+  p->precond = HZ_PRE_TRI;
+  p->krylov = HZ_KRYLOV_BICGSTAB;
+  p->max_outer = 10;
+  p->max_inner = 1000;
+  p->restart = 150;
+  p->fgmres_m = 30;
+  p->use_graph = 1;
+  p->record_history = 0;
+}
+
+int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_op* out) {
+  if (!out) return HZ_ERR_INVALID;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || nz > HZ_MAX_LEVELS || !coeffs) return HZ_ERR_INVALID;
+  const int64_t n = (int64_t)nx * ny * nz;
+  if (n > ((int64_t)1 << 40)) return HZ_ERR_INVALID;
+  hz_op op = new hz_op_s();
+  op->g = Grid{nx, ny, nz, (int64_t)nx * ny, n};
+  op->stream = (cudaStream_t)stream;
+  int st = HZ_OK;
+  auto fail = [&](int s) {
+    free_op(op);
+    return s;
+  };
+  if (cudaGetDevice(&op->dev) != cudaSuccess) return fail(HZ_ERR_CUDA);
+  cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->dev);
+  if (cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(HZ_ERR_CUDA);
+  cudaEventCreate(&op->ev0);
+  cudaEventCreate(&op->ev1);
+  // launch shapes: the largest grid every column kernel can keep resident
+  {
+    std::vector<const void*> col, flat;
+    column_kernel_ptrs(col, flat);
+    const int64_t wb = (op->g.ncol + kBS - 1) / kBS;
+    int gcol = kMaxGrid;
+    for (const void* k : col) gcol = std::min(gcol, occupancy_grid(k, kBS, op->sms, wb));
+    int gflat = kMaxGrid;
+    const int64_t wf = (n / 4 + 255) / 256 + 1;
+    for (const void* k : flat) gflat = std::min(gflat, occupancy_grid(k, 256, op->sms, wf));
+    op->L = Launch{gcol, gflat, op->stream};
+  }
+  if (!(op->A7 = dalloc<double>(op, 7 * n, &st))) return fail(st);
+  if (!(op->ah32 = dalloc<float>(op, 6 * n, &st))) return fail(st);
+  if (!(op->th32 = dalloc<float>(op, 3 * n, &st))) return fail(st);
+  if (!(op->ah64 = dalloc<double>(op, 6 * n, &st))) return fail(st);
+  if (!(op->th64 = dalloc<double>(op, 3 * n, &st))) return fail(st);
+  if (!(op->invc = dalloc<double>(op, n, &st))) return fail(st);
+  if (!(op->w32base = dalloc<float>(op, 10 * pad64(n), &st))) return fail(st);
+  op->w32 = carve(op->w32base, n);
+  if (!(op->xscr = dalloc<double>(op, n, &st))) return fail(st);
+  if (!(op->ctl = dalloc<Ctl>(op, 1, &st))) return fail(st);
+  if (!(op->red.partials = dalloc<double>(op, (int64_t)kMaxGrid * kMaxND, &st))) return fail(st);
+  if (!(op->red.ticket = dalloc<unsigned>(op, 1, &st))) return fail(st);
+  if (!(op->err_d = dalloc<int>(op, 1, &st))) return fail(st);
+  if (cudaMallocHost(&op->cfg_h, sizeof(Ctl)) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMallocHost(&op->rep_h, sizeof(Ctl)) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMallocHost(&op->err_h, sizeof(int)) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMemsetAsync(op->red.ticket, 0, sizeof(unsigned), op->stream) != cudaSuccess) return fail(HZ_ERR_CUDA);
+  if (cudaMemsetAsync(op->ctl, 0, sizeof(Ctl), op->stream) != cudaSuccess) return fail(HZ_ERR_CUDA);
+  st = do_setup(op, coeffs);
+  if (st != HZ_OK) return fail(st);
+  *out = op;
+  return HZ_OK;
+}
+
+int hz_op_update(hz_op op, const double* coeffs) {
+  if (!op || !coeffs) return HZ_ERR_INVALID;
+  return do_setup(op, coeffs);
+}
+
+int hz_op_destroy(hz_op op) {
+  if (!op) return HZ_OK;
+  cudaStreamSynchronize(op->stream);
+  free_op(op);
+  return HZ_OK;
+}
+
+int hz_op_dims(hz_op op, int* nx, int* ny, int* nz) {
+  if (!op) return HZ_ERR_INVALID;
+  if (nx) *nx = op->g.nx;
+  if (ny) *ny = op->g.ny;
+  if (nz) *nz = op->g.nz;
+  return HZ_OK;
+}
+
+int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_solve_params* pp,
+             hz_solve_info* info) {
+  if (!op || !b || !x) return HZ_ERR_INVALID;
+  hz_solve_params p;
+  if (pp)
+    p = *pp;
+  else
+    hz_default_params(&p);
+  if (!(p.tol > 0.0) || p.max_outer < 0 || p.max_inner < 1 || p.restart < 1) return HZ_ERR_INVALID;
+  if (p.mode != HZ_MODE_FP64 && p.mode != HZ_MODE_MIXED_IR) return HZ_ERR_INVALID;
+  if (p.krylov != HZ_KRYLOV_BICGSTAB || p.precond != HZ_PRE_TRI) return HZ_ERR_UNSUPPORTED;
+  const bool fp32 = (p.mode == HZ_MODE_MIXED_IR);
+  const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : 0.1 * p.tol);
+  const int64_t n = op->g.n;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  cudaStream_t s = op->stream;
+  if (!fp32) CKS(ensure_w64(op));
+  if (p.record_history) {
+    const int cap = std::max(1, p.max_inner * std::max(1, p.max_outer));
+    if (cap > op->hist_cap) {
+      int st = HZ_OK;
+      op->hist_d = dalloc<double>(op, cap, &st);
+      if (!op->hist_d) return st;
+      op->hist_cap = cap;
+    }
+  }
+  // pointer kinds
+  const bool b_dev = is_device_ptr(b);
+  const bool x_dev = is_device_ptr(x);
+  const bool x0_dev = x0 && is_device_ptr(x0);
+  int st = HZ_OK;
+  const double* bd = b;
+  if (!b_dev) {
+    if (!op->bbuf && !(op->bbuf = dalloc<double>(op, n, &st))) return st;
+    CK(cudaMemcpyAsync(op->bbuf, b, bytes, cudaMemcpyHostToDevice, s));
+    bd = op->bbuf;
+  }
+  double* XA = x;
+  if (!x_dev) {
+    if (!op->xbuf && !(op->xbuf = dalloc<double>(op, n, &st))) return st;
+    XA = op->xbuf;
+  }
+  double* XB = op->xscr;
+  CK(cudaEventRecord(op->ev0, s));
+  const double* cur = nullptr;
+  if (x0) {
+    if (x0_dev) {
+      cur = x0;
+    } else {
+      CK(cudaMemcpyAsync(XA, x0, bytes, cudaMemcpyHostToDevice, s));
+      cur = XA;
+    }
+  }
+  // configuration of the control block
+  Ctl* cfg = op->cfg_h;
+  memset(cfg, 0, sizeof(Ctl));
+  cfg->eta = eta;
+  cfg->maxit = p.max_inner;
+  cfg->body_limit = 4 * p.max_inner + 64;
+  cfg->restart_every = p.restart;
+  cfg->hist = p.record_history ? op->hist_d : nullptr;
+  cfg->hist_cap = p.record_history ? op->hist_cap : 0;
+  cfg->xzero = 1;
+  cfg->state = ST_CONVERGED;
+  CK(cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+
+  auto residual = [&](const double* xin, double* xout, bool with_delta) -> int {
+    auto go = [&]() -> cudaError_t {
+      if (fp32)
+        return launch_residual<float>(op->g, op->A7, op->invc, bd, xin, xout, with_delta ? op->w32.x : nullptr,
+                                      op->w32.rhs, nullptr, 0, op->ctl, op->red, op->L);
+      return launch_residual<double>(op->g, op->A7, op->invc, bd, xin, xout, with_delta ? op->w64.x : nullptr,
+                                     op->w64.rhs, nullptr, 0, op->ctl, op->red, op->L);
+    };
+    if (op->prof) {
+      // algorithmic bytes: C band, b, rhs; plus the other six bands, x, d and x out for a stencil pass
+      const double ds = fp32 ? 4.0 : 8.0;
+      double bp = 8 + 8 + ds;
+      if (xin || with_delta) bp += 48 + (xin ? 8 : 0) + (with_delta ? ds : 0) + (xout ? 8 : 0);
+      CKS(prof_launch(op, 1, bp * (double)n, go));
+    } else {
+      CK(go());
+    }
+    op->launches++;
+    CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HZ_OK;
+  };
+
+  op->launches = 0;
+  CKS(residual(cur, nullptr, false));
+  const double bb = op->rep_h->res_bb;
+  double R = bb > 0.0 ? std::sqrt(op->rep_h->res_rr / bb) : std::sqrt(op->rep_h->res_rr);
+  int outer = 0, inner_total = 0, restarts = 0, status = HZ_OK;
+  double scaled = 0.0, Rprev = R;
+  int stall = 0;
+  for (;;) {
+    if (!std::isfinite(R)) { status = HZ_ERR_NONFINITE; break; }
+    if (R <= p.tol) { status = HZ_OK; break; }
+    if (outer >= p.max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
+    if (fp32)
+      CKS(run_inner<float>(op, p.use_graph, p.max_inner));
+    else
+      CKS(run_inner<double>(op, p.use_graph, p.max_inner));
+    double* next = (cur == XA) ? XB : XA;
+    CKS(residual(cur, next, true));
+    const Ctl& rp = *op->rep_h;
+    if (!op->prof) op->launches += 5LL * std::max(1, rp.last_iter);
+    inner_total += rp.last_iter;
+    restarts += rp.last_restarts;
+    scaled = rp.last_bnorm2 > 0.0 ? std::sqrt(rp.last_rnorm2 / rp.last_bnorm2) : 0.0;
+    cur = next;
+    ++outer;
+    const double Rn = bb > 0.0 ? std::sqrt(rp.res_rr / bb) : std::sqrt(rp.res_rr);
+    if (rp.last_state == ST_NONFINITE) {
+      R = Rn;
+      status = HZ_ERR_NONFINITE;
+      break;
+    }
+    R = Rn;
+    // stagnation: two refinement steps in a row without halving R
+    if (R > 0.5 * Rprev) {
+      if (++stall >= 2 && R > p.tol) { status = HZ_ERR_NOT_CONVERGED; break; }
+    } else {
+      stall = 0;
+    }
+    Rprev = R;
+  }
+  // deliver x
+  if (cur == nullptr) {
+    if (x_dev)
+      CK(cudaMemsetAsync(x, 0, bytes, s));
+    else
+      memset(x, 0, bytes);
+  } else if (x_dev) {
+    if (cur != x) CK(cudaMemcpyAsync(x, cur, bytes, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(x, cur, bytes, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaEventRecord(op->ev1, s));
+  CK(cudaEventSynchronize(op->ev1));
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, op->ev0, op->ev1);
+    info->status = status;
+    info->outer_iters = outer;
+    info->inner_iters = inner_total;
+    info->restarts = restarts;
+    info->fallbacks = 0;
+    info->true_rel_residual = R;
+    info->scaled_rel_residual = scaled;
+    info->seconds = ms * 1e-3;
+    info->kernel_launches = op->launches;
+  }
+  return status;
+}
+
+int hz_profile_enable(hz_op op, int on) {
+  if (!op) return HZ_ERR_INVALID;
+  op->prof = on != 0;
+  for (int k = 0; k < HZ_NUM_KERNELS; ++k) {
+    op->p_launch[k] = 0;
+    op->p_ms[k] = 0.0;
+    op->p_bytes[k] = 0.0;
+  }
+  return HZ_OK;
+}
+
+int hz_profile_read(hz_op op, int kid, long long* launches, double* ms, double* bytes) {
+  if (!op || kid < 0 || kid >= HZ_NUM_KERNELS) return HZ_ERR_INVALID;
+  if (launches) *launches = op->p_launch[kid];
+  if (ms) *ms = op->p_ms[kid];
+  if (bytes) *bytes = op->p_bytes[kid];
+  return HZ_OK;
+}
+
+const char* hz_kernel_name(int kid) {
+  static const char* names[HZ_NUM_KERNELS] = {"k_setup", "k_residual", "k_pre_p", "k_mv_v", "k_pre_s", "k_mv_t",
+                                              "k_upd"};
+  return (kid >= 0 && kid < HZ_NUM_KERNELS) ? names[kid] : "";
+}
+
+int hz_get_history(hz_op op, double* hist, int cap) {
+  if (!op || !hist || cap < 0) return -HZ_ERR_INVALID;
+  if (!op->hist_d) return 0;
+  Ctl c;
+  if (cudaMemcpy(&c, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return -HZ_ERR_CUDA;
+  int len = std::min(std::min(c.hist_off + (c.xzero ? 0 : 0), op->hist_cap), cap);
+  if (len > 0 && cudaMemcpy(hist, op->hist_d, sizeof(double) * len, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -HZ_ERR_CUDA;
+  return len;
+}
+
+int hz_matvec(hz_op op, int prec, const void* x, void* y) {
+  if (!op || !x || !y) return HZ_ERR_INVALID;
+  if (prec == HZ_PREC_FP32)
+    CK(launch_matvec_hat<float>(op->g, bands_of<float>(op), (const float*)x, (float*)y, op->L));
+  else if (prec == HZ_PREC_FP64)
+    CK(launch_matvec_hat<double>(op->g, bands_of<double>(op), (const double*)x, (double*)y, op->L));
+  else
+    return HZ_ERR_INVALID;
+  return HZ_OK;
+}
+
+int hz_precond_apply(hz_op op, int prec, const void* r, void* z) {
+  if (!op || !r || !z || r == z) return HZ_ERR_INVALID;
+  if (prec == HZ_PREC_FP32)
+    CK(launch_tinv<float>(op->g, bands_of<float>(op), (const float*)r, (float*)z, op->L));
+  else if (prec == HZ_PREC_FP64)
+    CK(launch_tinv<double>(op->g, bands_of<double>(op), (const double*)r, (double*)z, op->L));
+  else
+    return HZ_ERR_INVALID;
+  return HZ_OK;
+}
+
+int hz_precond_matvec(hz_op op, int prec, const void* p, void* ph, void* v) {
+  if (!op || !p || !ph || !v) return HZ_ERR_INVALID;
+  if (prec == HZ_PREC_FP32)
+    CK(launch_precond_matvec<float>(op->g, bands_of<float>(op), (const float*)p, (float*)ph, (float*)v, op->L));
+  else if (prec == HZ_PREC_FP64)
+    CK(launch_precond_matvec<double>(op->g, bands_of<double>(op), (const double*)p, (double*)ph, (double*)v,
+                                     op->L));
+  else
+    return HZ_ERR_INVALID;
+  return HZ_OK;
+}
+
+int hz_residual(hz_op op, const double* b, const double* x, double* r, double* rnorm, double* bnorm) {
+  if (!op || !b || !x) return HZ_ERR_INVALID;
+  CK(launch_residual<float>(op->g, op->A7, op->invc, b, x, nullptr, nullptr, op->w32.rhs, r, 0, op->ctl, op->red,
+                            op->L));
+  CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, op->stream));
+  CK(cudaStreamSynchronize(op->stream));
+  if (rnorm) *rnorm = std::sqrt(op->rep_h->res_rr);
+  if (bnorm) *bnorm = std::sqrt(op->rep_h->res_bb);
+  return HZ_OK;
+}
+
+int hz_dot(int prec, int64_t n, const void* x, const void* y, void* stream, double* out) {
+  if (n < 0 || !out || (n > 0 && (!x || !y))) return HZ_ERR_INVALID;
+  if (prec != HZ_PREC_FP32 && prec != HZ_PREC_FP64) return HZ_ERR_INVALID;
+  if (n == 0) {
+    *out = 0.0;
+    return HZ_OK;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return HZ_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_dot_mu);
+  DotScratch& d = g_dot[dev];
+  if (!d.partials) {
+    CK(cudaMalloc(&d.partials, sizeof(double) * kMaxGrid));
+    CK(cudaMalloc(&d.ticket, sizeof(unsigned)));
+    CK(cudaMalloc(&d.out, sizeof(double)));
+    CK(cudaMallocHost(&d.out_h, sizeof(double)));
+    CK(cudaMemset(d.ticket, 0, sizeof(unsigned)));
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>((int64_t)sms * 8, kMaxGrid), (n + 255) / 256);
+  cudaStream_t s = (cudaStream_t)stream;
+  Red red{d.partials, d.ticket};
+  if (prec == HZ_PREC_FP32)
+    CK(launch_dot<float>(n, (const float*)x, (const float*)y, red, d.out, grid, s));
+  else
+    CK(launch_dot<double>(n, (const double*)x, (const double*)y, red, d.out, grid, s));
+  CK(cudaMemcpyAsync(d.out_h, d.out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *out = *d.out_h;
+  return HZ_OK;
+}
+
+int hz_op_export(hz_op op, int what, int prec, void* dst) {
+  if (!op || !dst) return HZ_ERR_INVALID;
+  const int64_t n = op->g.n;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  if (what == 0 && prec == HZ_PREC_FP32) { src = op->ah32; bytes = 6 * n * sizeof(float); }
+  else if (what == 0 && prec == HZ_PREC_FP64) { src = op->ah64; bytes = 6 * n * sizeof(double); }
+  else if (what == 1 && prec == HZ_PREC_FP32) { src = op->th32; bytes = 3 * n * sizeof(float); }
+  else if (what == 1 && prec == HZ_PREC_FP64) { src = op->th64; bytes = 3 * n * sizeof(double); }
+  else return HZ_ERR_INVALID;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, op->stream));
+  CK(cudaStreamSynchronize(op->stream));
+  return HZ_OK;
+}
+
+int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
+                     const hz_solve_params* params, hz_solve_info* infos) {
+  (void)nsys; (void)ops; (void)b; (void)x0; (void)x; (void)params; (void)infos;
+  return HZ_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// hz_internal.cuh -- shared definitions of the CUDA path (device control block,
+// reductions, launch wrappers).  Everything here belongs to the GPU library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hz.h"
+
+namespace hz {
+
+constexpr int kBS = 128;          // threads per block of the column kernels
+constexpr int kMaxND = 4;         // dots reduced by one launch at most
+constexpr int kMaxGrid = 8192;    // partial-sum slots per reduction buffer
+
+struct Grid {
+  int nx, ny, nz;
+  int64_t ncol, n;
+};
+
+// Inner Krylov state machine (lives in device memory; each kernel reads it at
+// entry and the last block of a reduction writes it).
+enum State : int {
+  ST_RUNNING = 0,
+  ST_CONVERGED = 1,
+  ST_MAXIT = 2,
+  ST_NONFINITE = 3,
+  ST_RESTART = 4,
+  ST_HALF = 5,  // ||s|| met the tolerance: finish with x += alpha ph
+};
+
+struct Ctl {
+  // BiCGStab scalars, FP64 (the paper's 64-bit global sums, Sec. 4)
+  double rho, alpha, omega, beta;
+  double bnorm2;   // ||rhs||^2 of the inner system
+  double stop2;    // (eta ||rhs||)^2
+  double rnorm2, r0norm2, snorm2;
+  int iter, since, restarts, state;
+  int maxit, restart_every;
+  int fresh;   // 1: next p = r (start or restart)
+  int rsel;    // 0: r still equals rhs (read rhs); 1: r buffer valid
+  int r0sel;   // 0: r0 = rhs; 1: r0 buffer
+  int xzero;   // 1: x not yet written (= 0)
+  int hist_cap;
+  int pad0;
+  double* hist;  // recursive relative residual per iteration (may be null)
+  // outer true-residual results (written by the residual kernel)
+  double res_rr, res_bb, res_hh;
+  double eta;
+  // report of the inner solve that the residual kernel consumed
+  double last_rnorm2, last_bnorm2;
+  int last_iter, last_restarts, last_state, hist_off;
+  // bodies of the inner loop launched since the last residual pass, and the
+  // hard limit after which the loop stops whatever the state says
+  int bodies, body_limit;
+};
+
+struct Red {
+  double* partials;  // kMaxGrid * kMaxND
+  unsigned* ticket;
+};
+
+template <typename T>
+struct Bands {  // scaled operator in one precision, Ahat = I + bands
+  const T *E, *W, *N, *S, *U, *D;
+  const T *m, *l, *cp;  // Thomas factors of T (unit diagonal)
+};
+
+template <typename T>
+struct Vecs {  // inner Krylov vectors
+  T *rhs, *r, *r0, *p, *ph, *v, *s, *sh, *t, *x;
+};
+
+// Deterministic block + grid reduction of ND doubles.  Every block stores its
+// partial in a fixed slot; the last block to arrive (ticket) sums the slots in
+// slot order, so the result depends only on the launch shape.  Returns true in
+// thread 0 of the last block, with the totals in out.
+template <int ND>
+__device__ __forceinline__ bool grid_reduce(double (&v)[ND], const Red& red, double (&out)[ND]) {
+  __shared__ double sm[ND][32];
+  __shared__ int amlast;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    double x = v[d];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[d][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      double x = lane < nw ? sm[d][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red.partials[(size_t)blockIdx.x * ND + d] = x;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(red.ticket, 1u);
+    amlast = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += __ldcg(&red.partials[(size_t)b * ND + d]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[d] = x;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) sm[d][warp] = v[d];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      double x = 0.0;
+      for (int w = 0; w < nw; ++w) x += sm[d][w];
+      out[d] = x;
+    }
+    *red.ticket = 0u;
+    return true;
+  }
+  return false;
+}
+
+// ---- launch wrappers (defined in the kernel translation units) ----
+struct Launch {
+  int grid;          // blocks of the column kernels (grid-stride)
+  int grid_flat;     // blocks of the elementwise kernels
+  cudaStream_t stream;
+};
+
+template <typename T>
+cudaError_t launch_pre_p(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L);
+template <typename T>
+cudaError_t launch_mv_v(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L);
+template <typename T>
+cudaError_t launch_pre_s(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L);
+template <typename T>
+cudaError_t launch_mv_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L);
+template <typename T>
+cudaError_t launch_upd(const Grid& g, const Vecs<T>& w, Ctl* ctl, Red red, unsigned long long cond, int use_cond,
+                       const Launch& L);
+
+// building blocks for the kernel-level entry points
+template <typename T>
+cudaError_t launch_matvec_hat(const Grid& g, const Bands<T>& a, const T* x, T* y, const Launch& L);
+template <typename T>
+cudaError_t launch_tinv(const Grid& g, const Bands<T>& a, const T* r, T* z, const Launch& L);
+template <typename T>
+cudaError_t launch_precond_matvec(const Grid& g, const Bands<T>& a, const T* p, T* ph, T* v, const Launch& L);
+template <typename T>
+cudaError_t launch_dot(int64_t n, const T* x, const T* y, Red red, double* out_dev, int grid, cudaStream_t s);
+
+// operator setup and the FP64 true residual (hz_setup.cu)
+struct SetupOut {
+  float* ah32;    // [6][n]
+  float* th32;    // [3][n]
+  double* ah64;   // [6][n]
+  double* th64;   // [3][n]
+  double* invc;   // [n]
+  int* err;       // device error word
+};
+cudaError_t launch_setup(const Grid& g, const double* A7, SetupOut o, const Launch& L);
+
+// residual modes
+enum ResMode : int { RES_ZERO = 0, RES_X0 = 1, RES_UPDATE = 2, RES_FROM_DELTA = 3 };
+// r = b - A x (FP64); x per mode; writes x (modes X0 with x!=x0, UPDATE, FROM_DELTA),
+// rhs_out = D^-1 r in float or double, r_out (may be null); reduces ||r||^2, ||b||^2,
+// ||rhs||^2 and prepares ctl for the next inner solve with tolerance eta.
+template <typename D>
+cudaError_t launch_residual(const Grid& g, const double* A7, const double* invc, const double* b, const double* x0,
+                            double* x, const D* delta, D* rhs_out, double* r_out, int mode, Ctl* ctl, Red red,
+                            const Launch& L);
+
+}  // namespace hz

@@ -248,7 +248,7 @@ int profiled_iteration(hz_op op) {
   const double bp = c->state == ST_RESTART ? 16 * B : (c->fresh ? 6 * B : 8 * B);
   const bool xz = c->xzero != 0;
   CKS(prof_launch(op, 2, bp * n, [&] { return launch_pre_p<T>(op->g, a, w, op->ctl, op->red, L); }));
-  op->launches++;
+  op->launches += 2;  // k_pre_start + k_pre_p
   CKS(state(c));
   if (c->state != ST_RUNNING) return HZ_OK;
   CKS(prof_launch(op, 3, 8 * B * n, [&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }));
@@ -560,7 +560,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     double* next = (cur == XA) ? XB : XA;
     CKS(residual(cur, next, true));
     const Ctl& rp = *op->rep_h;
-    if (!op->prof) op->launches += 5LL * std::max(1, rp.last_iter);
+    if (!op->prof) op->launches += 6LL * std::max(1, rp.last_iter);
     inner_total += rp.last_iter;
     restarts += rp.last_restarts;
     scaled = rp.last_bnorm2 > 0.0 ? std::sqrt(rp.last_rnorm2 / rp.last_bnorm2) : 0.0;

@@ -13,8 +13,11 @@
 //
 // H = the four horizontal bands (E, W, N, S) of Ahat.  Layout [k][j][i]: a
 // thread owns one column (i, j) and marches k, so every load of a warp is a
-// contiguous 128-byte (FP32) or 256-byte (FP64) run.  Partial sums are FP32
-// (FP64 in the FP64 solver) over one column and FP64 across threads and
+// contiguous 128-byte (FP32) or 256-byte (FP64) run.  The k-march is
+// software-pipelined: the loads of U consecutive levels are issued together
+// before any of them is used, which keeps enough bytes in flight per SM for
+// HBM while the Thomas recurrence stays sequential in k.  Partial sums are
+// FP32 (FP64 in the FP64 solver) over one column and FP64 across threads and
 // blocks (the paper's 64-bit global sums, Sec. 4); the grid reduction is
 // deterministic (fixed slots, summed in slot order by the last block).
 #include <vector>
@@ -22,6 +25,23 @@
 #include "hz_internal.cuh"
 
 namespace hz {
+
+// levels per software-pipelined batch: Thomas sweeps and the stencil
+template <typename T>
+struct Tune;
+template <>
+struct Tune<float> {
+  static constexpr int UT = 8, UM = 4, MINB = 6;
+};
+template <>
+struct Tune<double> {
+  static constexpr int UT = 4, UM = 2, MINB = 6;
+};
+
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) {
+  return __ldg(p);
+}
 
 struct ColNbr {
   int64_t ie, iw;  // offsets of the east / west neighbour (periodic)
@@ -53,76 +73,169 @@ __device__ __forceinline__ T ahat_point(const Grid& g, const Bands<T>& a, const 
   return y;
 }
 
-// Forward sweep of the Thomas algorithm, y_k = m_k in_k - l_k y_(k-1), with the
-// input computed by `in(k, idx)` (the fused axpy); y is parked in out.  The
-// back sweep z_k = y_k - c'_k z_(k+1) re-reads it (from L2) and overwrites it.
-template <typename T, typename In>
-__device__ __forceinline__ void thomas_col(const Grid& g, int64_t col, const T* __restrict__ m,
-                                           const T* __restrict__ l, const T* __restrict__ cp, T* __restrict__ out,
-                                           In in) {
+// Thomas algorithm on one column with unit diagonal and pre-computed factors:
+// forward y_k = m_k q_k - l_k y_(k-1), back z_k = y_k - c'_k z_(k+1).  The
+// input q_k comes from src.make(v, idx) on the src.NIN values that src.load
+// fetched for level k (the fused axpy).  y is parked in out and re-read by the
+// back sweep (an L2 hit: the whole resident wave's columns fit in L2).
+template <typename T, int U, typename Src>
+__device__ __forceinline__ void thomas_batched(const Grid& g, int64_t col, const T* __restrict__ m,
+                                               const T* __restrict__ l, const T* __restrict__ cp,
+                                               T* __restrict__ out, Src& src) {
+  constexpr int NIN = Src::NIN;
   const int64_t ncol = g.ncol;
+  const int nz = g.nz;
   T yprev = T(0);
-#pragma unroll 4
-  for (int k = 0; k < g.nz; ++k) {
-    const int64_t idx = (int64_t)k * ncol + col;
-    const T pk = in(k, idx);
-    const T y = fma(m[idx], pk, -l[idx] * yprev);
-    out[idx] = y;
-    yprev = y;
+  for (int k0 = 0; k0 < nz; k0 += U) {
+    T v[U][NIN], mm[U], ll[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u < nz) {
+        const int64_t idx = (int64_t)(k0 + u) * ncol + col;
+        src.load(idx, v[u]);
+        mm[u] = ldro(m + idx);
+        ll[u] = ldro(l + idx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u < nz) {
+        const int64_t idx = (int64_t)(k0 + u) * ncol + col;
+        const T q = src.make(v[u], idx);
+        const T y = fma(mm[u], q, -ll[u] * yprev);
+        out[idx] = y;
+        yprev = y;
+      }
+    }
   }
   T zn = T(0);
-#pragma unroll 4
-  for (int k = g.nz - 1; k >= 0; --k) {
-    const int64_t idx = (int64_t)k * ncol + col;
-    const T z = fma(-cp[idx], zn, out[idx]);
-    out[idx] = z;
-    zn = z;
+  for (int k0 = nz - 1; k0 >= 0; k0 -= U) {
+    T yy[U], cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 - u >= 0) {
+        const int64_t idx = (int64_t)(k0 - u) * ncol + col;
+        yy[u] = out[idx];  // written by this thread above: coherent load
+        cc[u] = ldro(cp + idx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 - u >= 0) {
+        const int64_t idx = (int64_t)(k0 - u) * ncol + col;
+        const T z = fma(-cc[u], zn, yy[u]);
+        out[idx] = z;
+        zn = z;
+      }
+    }
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_pre_p: p = r + beta (p - omega v) (or p = r on a (re)start), ph = T^-1 p.
-// On ST_RESTART it first recomputes r = rhs - Ahat x, sets r0 = r and reduces
-// ||r||^2 (Sec. 4: the mandatory restart).
+// inputs of the Thomas sweeps
 template <typename T>
-__global__ void __launch_bounds__(kBS) k_pre_p(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bodies += 1;  // read only by k_upd, a later launch
-  const int state = ctl->state;
-  if (state != ST_RUNNING && state != ST_RESTART) return;
-  const bool restart = (state == ST_RESTART);
-  const bool fresh = ctl->fresh != 0;
-  const bool xzero = ctl->xzero != 0;
+struct SrcP {  // p = r + beta (p - omega v)
+  static constexpr int NIN = 3;
+  const T* __restrict__ r;
+  T* __restrict__ p;
+  const T* __restrict__ v;
+  T beta, omega;
+  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
+    o[0] = ldro(r + idx);
+    o[1] = p[idx];
+    o[2] = ldro(v + idx);
+  }
+  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
+    const T pk = fma(beta, fma(-omega, o[2], o[1]), o[0]);
+    p[idx] = pk;
+    return pk;
+  }
+};
+
+template <typename T>
+struct SrcCopy {  // p = r (first iteration after a start); dst may be null
+  static constexpr int NIN = 1;
+  const T* __restrict__ r;
+  T* __restrict__ dst;
+  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) { o[0] = ldro(r + idx); }
+  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
+    if (dst) dst[idx] = o[0];
+    return o[0];
+  }
+};
+
+template <typename T>
+struct SrcS {  // s = r - alpha v, accumulating <s, s>
+  static constexpr int NIN = 2;
+  const T* __restrict__ r;
+  const T* __restrict__ v;
+  T* __restrict__ s;
+  T alpha;
+  T acc;
+  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
+    o[0] = ldro(r + idx);
+    o[1] = ldro(v + idx);
+  }
+  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
+    const T sk = fma(-alpha, o[1], o[0]);
+    s[idx] = sk;
+    acc = fma(sk, sk, acc);
+    return sk;
+  }
+};
+
+// Restart of one column (rare, kept out of line so that it does not cost the
+// common path registers): r = rhs - Ahat x, r0 = r, p = r, ph = T^-1 p.
+// Returns the column's <r, r>.  x is read-only in this launch.
+template <typename T>
+__device__ __noinline__ double restart_column(const Grid& g, int64_t col, const Bands<T>& a, const Vecs<T>& w,
+                                              bool xzero) {
+  const ColNbr c = col_nbr(g, col);
+  T cacc = T(0);
+  for (int k = 0; k < g.nz; ++k) {
+    const int64_t idx = (int64_t)k * g.ncol + col;
+    T rk = w.rhs[idx];
+    if (!xzero) rk -= ahat_point(g, a, w.x, idx, k, c);
+    w.r[idx] = rk;
+    w.r0[idx] = rk;
+    cacc = fma(rk, rk, cacc);
+  }
+  SrcCopy<T> src{w.r, w.p};
+  thomas_batched<T, Tune<T>::UT>(g, col, a.m, a.l, a.cp, w.ph, src);
+  return (double)cacc;
+}
+
+// ---------------------------------------------------------------------------
+// k_pre_p: p = r + beta (p - omega v), ph = T^-1 p (the common case).
+// k_pre_start does the first iteration after a start (p = r) and the restart
+// (Sec. 4: the mandatory restart): r = rhs - Ahat x, r0 = r, ||r||^2, p = r.
+// Both are launched every iteration; each returns at once when the state is
+// not its own, so the common path carries no registers for the rare one.
+template <typename T>
+__global__ void __launch_bounds__(kBS, Tune<T>::MINB) k_pre_p(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl) {
+  if (ctl->state != ST_RUNNING || ctl->fresh) return;
   const T beta = (T)ctl->beta, omega = (T)ctl->omega;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
-  T* __restrict__ p = w.p;
-  const T* __restrict__ v = w.v;
+  for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
+    SrcP<T> src{rin, w.p, w.v, beta, omega};
+    thomas_batched<T, Tune<T>::UT>(g, col, a.m, a.l, a.cp, w.ph, src);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBS) k_pre_start(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bodies += 1;  // read only by k_upd, a later launch
+  const int state = ctl->state;
+  const bool restart = (state == ST_RESTART);
+  if (!restart && !(state == ST_RUNNING && ctl->fresh)) return;
+  const bool xzero = ctl->xzero != 0;
+  const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
   double acc = 0.0;
   for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
     if (restart) {
-      const ColNbr c = col_nbr(g, col);
-      T cacc = T(0);
-      thomas_col(g, col, a.m, a.l, a.cp, w.ph, [&](int k, int64_t idx) {
-        T rk = w.rhs[idx];
-        if (!xzero) rk -= ahat_point(g, a, w.x, idx, k, c);
-        w.r[idx] = rk;
-        w.r0[idx] = rk;
-        p[idx] = rk;
-        cacc = fma(rk, rk, cacc);
-        return rk;
-      });
-      acc += (double)cacc;
-    } else if (fresh) {
-      thomas_col(g, col, a.m, a.l, a.cp, w.ph, [&](int, int64_t idx) {
-        const T pk = rin[idx];
-        p[idx] = pk;
-        return pk;
-      });
+      acc += restart_column<T>(g, col, a, w, xzero);
     } else {
-      thomas_col(g, col, a.m, a.l, a.cp, w.ph, [&](int, int64_t idx) {
-        const T pk = fma(beta, fma(-omega, v[idx], p[idx]), rin[idx]);
-        p[idx] = pk;
-        return pk;
-      });
+      SrcCopy<T> src{rin, w.p};
+      thomas_batched<T, Tune<T>::UT>(g, col, a.m, a.l, a.cp, w.ph, src);
     }
   }
   if (restart) {
@@ -145,39 +258,65 @@ __global__ void __launch_bounds__(kBS) k_pre_p(Grid g, Bands<T> a, Vecs<T> w, Ct
 }
 
 // ---------------------------------------------------------------------------
+// y = c + H x over one column, U levels per batch; a0/a1 accumulate the dots.
+// MODE 0: a0 += r0 y.  MODE 1: a0 += y c, a1 += y y.
+template <typename T, int U, int MODE>
+__device__ __forceinline__ void hmv_column(const Grid& g, int64_t col, const Bands<T>& a, const T* __restrict__ cen,
+                                           const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ r0,
+                                           T& a0, T& a1) {
+  const ColNbr c = col_nbr(g, col);
+  const int64_t ncol = g.ncol, nx = g.nx;
+  for (int k0 = 0; k0 < g.nz; k0 += U) {
+    T cc[U], e[U], w[U], nn[U], ss[U], xe[U], xw[U], xn[U], xs[U], q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u < g.nz) {
+        const int64_t idx = (int64_t)(k0 + u) * ncol + col;
+        cc[u] = ldro(cen + idx);
+        e[u] = ldro(a.E + idx);
+        w[u] = ldro(a.W + idx);
+        xe[u] = ldro(x + idx + c.ie);
+        xw[u] = ldro(x + idx + c.iw);
+        nn[u] = c.hn ? ldro(a.N + idx) : T(0);
+        xn[u] = c.hn ? ldro(x + idx + nx) : T(0);
+        ss[u] = c.hs ? ldro(a.S + idx) : T(0);
+        xs[u] = c.hs ? ldro(x + idx - nx) : T(0);
+        if (MODE == 0) q[u] = ldro(r0 + idx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u < g.nz) {
+        const int64_t idx = (int64_t)(k0 + u) * ncol + col;
+        T yy = fma(e[u], xe[u], cc[u]);
+        yy = fma(w[u], xw[u], yy);
+        yy = fma(nn[u], xn[u], yy);
+        yy = fma(ss[u], xs[u], yy);
+        y[idx] = yy;
+        if (MODE == 0) {
+          a0 = fma(q[u], yy, a0);
+        } else {
+          a0 = fma(yy, cc[u], a0);
+          a1 = fma(yy, yy, a1);
+        }
+      }
+    }
+  }
+}
+
 // k_mv<0>: v = p + H ph and <r0, v>  ->  alpha = rho / <r0, v>
 // k_mv<1>: t = s + H sh, <t, s> and <t, t>  ->  omega = <t,s>/<t,t>
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kBS) k_mv(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
+__global__ void __launch_bounds__(kBS, Tune<T>::MINB) k_mv(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
   const T* __restrict__ cen = MODE == 0 ? w.p : w.s;
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
   const T* __restrict__ r0 = ctl->r0sel ? w.r0 : w.rhs;
-  const T* __restrict__ E = a.E;
-  const T* __restrict__ W = a.W;
-  const T* __restrict__ N = a.N;
-  const T* __restrict__ S = a.S;
   double acc0 = 0.0, acc1 = 0.0;
   for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
-    const ColNbr c = col_nbr(g, col);
     T a0 = T(0), a1 = T(0);
-#pragma unroll 4
-    for (int k = 0; k < g.nz; ++k) {
-      const int64_t idx = (int64_t)k * g.ncol + col;
-      const T cc = cen[idx];
-      T yy = fma(E[idx], x[idx + c.ie], cc);
-      yy = fma(W[idx], x[idx + c.iw], yy);
-      if (c.hn) yy = fma(N[idx], x[idx + g.nx], yy);
-      if (c.hs) yy = fma(S[idx], x[idx - g.nx], yy);
-      y[idx] = yy;
-      if (MODE == 0) {
-        a0 = fma(r0[idx], yy, a0);
-      } else {
-        a0 = fma(yy, cc, a0);
-        a1 = fma(yy, yy, a1);
-      }
-    }
+    hmv_column<T, Tune<T>::UM, MODE>(g, col, a, cen, x, y, r0, a0, a1);
     acc0 += (double)a0;
     acc1 += (double)a1;
   }
@@ -209,22 +348,15 @@ __global__ void __launch_bounds__(kBS) k_mv(Grid g, Bands<T> a, Vecs<T> w, Ctl* 
 // ---------------------------------------------------------------------------
 // k_pre_s: s = r - alpha v, <s, s> (half-step exit test), sh = T^-1 s
 template <typename T>
-__global__ void __launch_bounds__(kBS) k_pre_s(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
+__global__ void __launch_bounds__(kBS, Tune<T>::MINB) k_pre_s(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
   const T alpha = (T)ctl->alpha;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
-  const T* __restrict__ v = w.v;
-  T* __restrict__ s = w.s;
   double acc = 0.0;
   for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
-    T ca = T(0);
-    thomas_col(g, col, a.m, a.l, a.cp, w.sh, [&](int, int64_t idx) {
-      const T sk = fma(-alpha, v[idx], rin[idx]);
-      s[idx] = sk;
-      ca = fma(sk, sk, ca);
-      return sk;
-    });
-    acc += (double)ca;
+    SrcS<T> src{rin, w.v, w.s, alpha, T(0)};
+    thomas_batched<T, Tune<T>::UT>(g, col, a.m, a.l, a.cp, w.sh, src);
+    acc += (double)src.acc;
   }
   double vv[1] = {acc}, out[1];
   if (grid_reduce<1>(vv, red, out)) {
@@ -398,23 +530,19 @@ __global__ void __launch_bounds__(kBS) k_matvec_hat(Grid g, Bands<T> a, const T*
 
 template <typename T>
 __global__ void __launch_bounds__(kBS) k_tinv(Grid g, Bands<T> a, const T* __restrict__ r, T* __restrict__ z) {
-  for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS)
-    thomas_col(g, col, a.m, a.l, a.cp, z, [&](int, int64_t idx) { return r[idx]; });
+  for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
+    SrcCopy<T> src{r, nullptr};
+    thomas_batched<T, Tune<T>::UT>(g, col, a.m, a.l, a.cp, z, src);
+  }
 }
 
+// y = c + H x with the solver's stencil code
 template <typename T>
 __global__ void __launch_bounds__(kBS) k_hmv(Grid g, Bands<T> a, const T* __restrict__ cen, const T* __restrict__ x,
                                              T* __restrict__ y) {
   for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
-    const ColNbr c = col_nbr(g, col);
-    for (int k = 0; k < g.nz; ++k) {
-      const int64_t idx = (int64_t)k * g.ncol + col;
-      T yy = fma(a.E[idx], x[idx + c.ie], cen[idx]);
-      yy = fma(a.W[idx], x[idx + c.iw], yy);
-      if (c.hn) yy = fma(a.N[idx], x[idx + g.nx], yy);
-      if (c.hs) yy = fma(a.S[idx], x[idx - g.nx], yy);
-      y[idx] = yy;
-    }
+    T a0 = T(0), a1 = T(0);
+    hmv_column<T, Tune<T>::UM, 1>(g, col, a, cen, x, y, nullptr, a0, a1);
   }
 }
 
@@ -431,7 +559,8 @@ __global__ void __launch_bounds__(256) k_dot(int64_t n, const T* __restrict__ x,
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_pre_p(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  k_pre_p<T><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl, red);
+  k_pre_start<T><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl, red);
+  k_pre_p<T><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl);
   return cudaGetLastError();
 }
 template <typename T>
@@ -493,7 +622,7 @@ HZ_INST(float)
 HZ_INST(double)
 
 void column_kernel_ptrs(std::vector<const void*>& col, std::vector<const void*>& flat) {
-  col = {(const void*)k_pre_p<float>, (const void*)k_mv<float, 0>, (const void*)k_mv<float, 1>,
+  col = {(const void*)k_pre_p<float>, (const void*)k_pre_start<float>, (const void*)k_pre_start<double>, (const void*)k_mv<float, 0>, (const void*)k_mv<float, 1>,
          (const void*)k_pre_s<float>, (const void*)k_pre_p<double>, (const void*)k_mv<double, 0>,
          (const void*)k_mv<double, 1>, (const void*)k_pre_s<double>};
   flat = {(const void*)k_upd<float>, (const void*)k_upd<double>};

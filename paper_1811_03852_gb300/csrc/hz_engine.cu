@@ -55,24 +55,7 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
 };
 
-int occupancy_grid(const void* kernel, int block, int sms, int64_t work_blocks) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  int64_t g = (int64_t)per_sm * sms;
-  g = std::min<int64_t>(g, work_blocks);
-  g = std::min<int64_t>(g, kMaxGrid);
-  return (int)std::max<int64_t>(g, 1);
-}
-
 }  // namespace
-
-namespace hz {
-// occupancy-based grid sizes of the column and elementwise kernels (hz_krylov.cu)
-void column_kernel_ptrs(std::vector<const void*>& col, std::vector<const void*>& flat);
-}  // namespace hz
 
 struct hz_op_s {
   Grid g{};
@@ -397,18 +380,9 @@ int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_
   if (cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(HZ_ERR_CUDA);
   cudaEventCreate(&op->ev0);
   cudaEventCreate(&op->ev1);
-  // launch shapes: the largest grid every column kernel can keep resident
-  {
-    std::vector<const void*> col, flat;
-    column_kernel_ptrs(col, flat);
-    const int64_t wb = (op->g.ncol + kBS - 1) / kBS;
-    int gcol = kMaxGrid;
-    for (const void* k : col) gcol = std::min(gcol, occupancy_grid(k, kBS, op->sms, wb));
-    int gflat = kMaxGrid;
-    const int64_t wf = (n / 4 + 255) / 256 + 1;
-    for (const void* k : flat) gflat = std::min(gflat, occupancy_grid(k, 256, op->sms, wf));
-    op->L = Launch{gcol, gflat, op->stream};
-  }
+  // launch shapes: each kernel fills the SMs to its own occupancy (grid-stride loops)
+  op->L = Launch{op->sms, (op->g.ncol + kBS - 1) / kBS, (n / 4 + 255) / 256 + 1, op->stream};
+  warm_launch_cache(op->L);
   if (!(op->A7 = dalloc<double>(op, 7 * n, &st))) return fail(st);
   if (!(op->ah32 = dalloc<float>(op, 6 * n, &st))) return fail(st);
   if (!(op->th32 = dalloc<float>(op, 3 * n, &st))) return fail(st);

@@ -134,10 +134,18 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[ND], const Red& red, dou
 
 // ---- launch wrappers (defined in the kernel translation units) ----
 struct Launch {
-  int grid;          // blocks of the column kernels (grid-stride)
-  int grid_flat;     // blocks of the elementwise kernels
+  int sms;           // SMs of the device
+  int64_t wcol;      // blocks needed to give every column its own thread (kBS per block)
+  int64_t wflat;     // blocks of 256 threads needed by the elementwise kernels
   cudaStream_t stream;
 };
+
+// Blocks for a grid-stride kernel: every SM filled to that kernel's own
+// occupancy (queried once per kernel and cached), capped by the work and by
+// the slots of the reduction buffer.  warm_launch_cache() queries every
+// kernel up front so that no query happens during stream capture.
+int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks);
+void warm_launch_cache(const Launch& L);
 
 template <typename T>
 cudaError_t launch_pre_p(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L);

@@ -20,6 +20,8 @@
 // FP32 (FP64 in the FP64 solver) over one column and FP64 across threads and
 // blocks (the paper's 64-bit global sums, Sec. 4); the grid reduction is
 // deterministic (fixed slots, summed in slot order by the last block).
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "hz_internal.cuh"
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(kBS, Tune<T>::MINB) k_pre_p(Grid g, Bands<T> a
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBS) k_pre_start(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
+__global__ void __launch_bounds__(kBS, 4) k_pre_start(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bodies += 1;  // read only by k_upd, a later launch
   const int state = ctl->state;
   const bool restart = (state == ST_RESTART);
@@ -559,45 +561,45 @@ __global__ void __launch_bounds__(256) k_dot(int64_t n, const T* __restrict__ x,
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_pre_p(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  k_pre_start<T><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl, red);
-  k_pre_p<T><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl);
+  k_pre_start<T><<<grid_for((const void*)k_pre_start<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
+  k_pre_p<T><<<grid_for((const void*)k_pre_p<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mv_v(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  k_mv<T, 0><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl, red);
+  k_mv<T, 0><<<grid_for((const void*)k_mv<T, 0>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_pre_s(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  k_pre_s<T><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl, red);
+  k_pre_s<T><<<grid_for((const void*)k_pre_s<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mv_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  k_mv<T, 1><<<L.grid, kBS, 0, L.stream>>>(g, a, w, ctl, red);
+  k_mv<T, 1><<<grid_for((const void*)k_mv<T, 1>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_upd(const Grid& g, const Vecs<T>& w, Ctl* ctl, Red red, unsigned long long cond, int use_cond,
                        const Launch& L) {
-  k_upd<T><<<L.grid_flat, 256, 0, L.stream>>>(g, w, ctl, red, (cudaGraphConditionalHandle)cond, use_cond);
+  k_upd<T><<<grid_for((const void*)k_upd<T>, 256, L, L.wflat), 256, 0, L.stream>>>(g, w, ctl, red, (cudaGraphConditionalHandle)cond, use_cond);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_matvec_hat(const Grid& g, const Bands<T>& a, const T* x, T* y, const Launch& L) {
-  k_matvec_hat<T><<<L.grid, kBS, 0, L.stream>>>(g, a, x, y);
+  k_matvec_hat<T><<<grid_for((const void*)k_matvec_hat<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, x, y);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_tinv(const Grid& g, const Bands<T>& a, const T* r, T* z, const Launch& L) {
-  k_tinv<T><<<L.grid, kBS, 0, L.stream>>>(g, a, r, z);
+  k_tinv<T><<<grid_for((const void*)k_tinv<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, r, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_precond_matvec(const Grid& g, const Bands<T>& a, const T* p, T* ph, T* v, const Launch& L) {
-  k_tinv<T><<<L.grid, kBS, 0, L.stream>>>(g, a, p, ph);
-  k_hmv<T><<<L.grid, kBS, 0, L.stream>>>(g, a, p, ph, v);
+  k_tinv<T><<<grid_for((const void*)k_tinv<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, p, ph);
+  k_hmv<T><<<grid_for((const void*)k_hmv<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, p, ph, v);
   return cudaGetLastError();
 }
 template <typename T>
@@ -621,11 +623,49 @@ cudaError_t launch_dot(int64_t n, const T* x, const T* y, Red red, double* out_d
 HZ_INST(float)
 HZ_INST(double)
 
-void column_kernel_ptrs(std::vector<const void*>& col, std::vector<const void*>& flat) {
-  col = {(const void*)k_pre_p<float>, (const void*)k_pre_start<float>, (const void*)k_pre_start<double>, (const void*)k_mv<float, 0>, (const void*)k_mv<float, 1>,
-         (const void*)k_pre_s<float>, (const void*)k_pre_p<double>, (const void*)k_mv<double, 0>,
-         (const void*)k_mv<double, 1>, (const void*)k_pre_s<double>};
-  flat = {(const void*)k_upd<float>, (const void*)k_upd<double>};
+namespace {
+std::mutex g_occ_mu;
+std::unordered_map<const void*, int> g_occ;  // blocks per SM of each kernel at its block size
+}  // namespace
+
+int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks) {
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(kernel);
+    if (it != g_occ.end()) {
+      per_sm = it->second;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      g_occ[kernel] = per_sm;
+    }
+  }
+  int64_t gsz = (int64_t)per_sm * L.sms;
+  if (gsz > work_blocks) gsz = work_blocks;
+  if (gsz > kMaxGrid) gsz = kMaxGrid;
+  return gsz < 1 ? 1 : (int)gsz;
+}
+
+void warm_launch_kernels(const Launch& L);  // hz_setup.cu
+
+void warm_launch_cache(const Launch& L) {
+#define HZ_WARM(T)                                                       \
+  grid_for((const void*)k_pre_start<T>, kBS, L, 1);                      \
+  grid_for((const void*)k_pre_p<T>, kBS, L, 1);                          \
+  grid_for((const void*)k_mv<T, 0>, kBS, L, 1);                          \
+  grid_for((const void*)k_mv<T, 1>, kBS, L, 1);                          \
+  grid_for((const void*)k_pre_s<T>, kBS, L, 1);                          \
+  grid_for((const void*)k_upd<T>, 256, L, 1);                            \
+  grid_for((const void*)k_matvec_hat<T>, kBS, L, 1);                     \
+  grid_for((const void*)k_tinv<T>, kBS, L, 1);                           \
+  grid_for((const void*)k_hmv<T>, kBS, L, 1);
+  HZ_WARM(float)
+  HZ_WARM(double)
+#undef HZ_WARM
+  warm_launch_kernels(L);
 }
 
 }  // namespace hz

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kBS) k_setup(Grid g, const double* __restrict_
 }
 
 cudaError_t launch_setup(const Grid& g, const double* A7, SetupOut o, const Launch& L) {
-  k_setup<<<L.grid, kBS, 0, L.stream>>>(g, A7, o);
+  k_setup<<<grid_for((const void*)k_setup, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, o);
   return cudaGetLastError();
 }
 
@@ -190,14 +190,26 @@ cudaError_t launch_residual(const Grid& g, const double* A7, const double* invc,
   (void)mode;
   const bool hx = xin != nullptr, hd = delta != nullptr;
   if (hx && hd)
-    k_residual<D, true, true><<<L.grid, kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+    k_residual<D, true, true><<<grid_for((const void*)k_residual<D, true, true>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
   else if (hx)
-    k_residual<D, true, false><<<L.grid, kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+    k_residual<D, true, false><<<grid_for((const void*)k_residual<D, true, false>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
   else if (hd)
-    k_residual<D, false, true><<<L.grid, kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+    k_residual<D, false, true><<<grid_for((const void*)k_residual<D, false, true>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
   else
-    k_residual<D, false, false><<<L.grid, kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+    k_residual<D, false, false><<<grid_for((const void*)k_residual<D, false, false>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
   return cudaGetLastError();
+}
+
+void warm_launch_kernels(const Launch& L) {
+  grid_for((const void*)k_setup, kBS, L, 1);
+#define HZ_WARM_RES(D)                                               \
+  grid_for((const void*)k_residual<D, true, true>, kBS, L, 1);       \
+  grid_for((const void*)k_residual<D, true, false>, kBS, L, 1);      \
+  grid_for((const void*)k_residual<D, false, true>, kBS, L, 1);      \
+  grid_for((const void*)k_residual<D, false, false>, kBS, L, 1);
+  HZ_WARM_RES(float)
+  HZ_WARM_RES(double)
+#undef HZ_WARM_RES
 }
 
 template cudaError_t launch_residual<float>(const Grid&, const double*, const double*, const double*, const double*,

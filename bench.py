@@ -203,6 +203,7 @@ def run_ours(args):
     op = hz.Operator(A, stream=stream)
     bd = torch.from_numpy(b.reshape(-1)).to(f"cuda:{dev}")
     x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
+    variants = op.autotune(fp64=not args.no_fp64)  # launch-shape search, outside the timed region
     pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8)
     p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8)
 
@@ -325,6 +326,7 @@ def run_ours(args):
         "fp64": fp64,
         "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
         "setup_ms": round(min(su), 3),
+        "variants": variants,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,

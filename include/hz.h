@@ -161,6 +161,24 @@ int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const d
 int hz_get_history(hz_op op, double* hist, int cap);
 
 /*
+ * Autotuner for the column kernels (not in the paper: a launch-shape search).
+ * The Thomas kernels (k_pre_p, k_pre_s) and the stencil kernels (k_mv) come
+ * in variants: vec columns per thread (vector loads; vec must divide nx) and
+ * depth levels per software-pipelined batch.  hz_op_autotune times every
+ * valid variant on the operator's own arrays (3 launches each, CUDA events on
+ * the operator's stream) and keeps the fastest; flags bit 0 also tunes the
+ * FP64 kernels (allocating the FP64 work vectors).  If the environment
+ * variable HZ_AUTOTUNE_CACHE names a file, results are appended to it (one
+ * line per device, grid, precision and kernel kind) and read back by
+ * hz_op_create for operators of the same grid.  Variant ids: 0 .. count-1 of
+ * the tables in the library; hz_op_set_variants takes -1 for "unchanged".
+ * The work vectors are overwritten; call between solves.
+ */
+int hz_op_autotune(hz_op op, int flags);
+int hz_op_get_variants(hz_op op, int* pre32, int* mv32, int* pre64, int* mv64);
+int hz_op_set_variants(hz_op op, int pre32, int mv32, int pre64, int mv64);
+
+/*
  * Per-kernel profile.  While enabled, solves run the host-driven loop with a
  * pair of CUDA events on the operator's stream around every kernel launch
  * (slower: each launch is waited for), and hz_profile_read returns, for

@@ -114,6 +114,9 @@ def load(build_if_missing: bool = True):
         "hz_residual": (i32, [pv, pv, pv, pv, P(dbl), P(dbl)]),
         "hz_dot": (i32, [i32, i64, pv, pv, pv, P(dbl)]),
         "hz_op_export": (i32, [pv, i32, i32, pv]),
+        "hz_op_autotune": (i32, [pv, i32]),
+        "hz_op_get_variants": (i32, [pv, P(i32), P(i32), P(i32), P(i32)]),
+        "hz_op_set_variants": (i32, [pv, i32, i32, i32, i32]),
         "hz_profile_enable": (i32, [pv, i32]),
         "hz_profile_read": (i32, [pv, i32, P(ctypes.c_longlong), P(dbl), P(dbl)]),
         "hz_kernel_name": (ctypes.c_char_p, [i32]),
@@ -238,6 +241,19 @@ class Operator:
         _check(load().hz_residual(self._h, _ptr(b), _ptr(x), _ptr(r), ctypes.byref(rn), ctypes.byref(bn)),
                "hz_residual")
         return rn.value, bn.value
+
+    def autotune(self, fp64=True):
+        """Pick the fastest column-kernel variants for this grid (timed on the GPU)."""
+        _check(load().hz_op_autotune(self._h, 1 if fp64 else 0), "hz_op_autotune")
+        return self.variants()
+
+    def variants(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(load().hz_op_get_variants(self._h, *[ctypes.byref(x) for x in v]), "hz_op_get_variants")
+        return {"pre32": v[0].value, "mv32": v[1].value, "pre64": v[2].value, "mv64": v[3].value}
+
+    def set_variants(self, pre32=-1, mv32=-1, pre64=-1, mv64=-1):
+        _check(load().hz_op_set_variants(self._h, pre32, mv32, pre64, mv64), "hz_op_set_variants")
 
     def profile(self, on=True):
         _check(load().hz_profile_enable(self._h, 1 if on else 0), "hz_profile_enable")

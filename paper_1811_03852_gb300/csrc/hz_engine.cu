@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -311,6 +312,87 @@ void free_op(hz_op op) {
   delete op;
 }
 
+// ---- column-kernel variants -------------------------------------------------
+bool variant_ok(int prec, int kind, int id, int nx) {
+  int v = 1, u = 1;
+  variant_shape(prec, kind, id, &v, &u);
+  return nx % v == 0;
+}
+
+// widest vector the row length allows (the autotuner may pick another)
+int default_variant(int prec, int kind, int nx) {
+  int best = 0, bestv = 0;
+  for (int i = 0; i < num_variants(prec, kind); ++i) {
+    int v = 1, u = 1;
+    variant_shape(prec, kind, i, &v, &u);
+    if (nx % v == 0 && v > bestv) {
+      best = i;
+      bestv = v;
+    }
+  }
+  return best;
+}
+
+void device_name(char* out, size_t cap) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) == cudaSuccess) {
+    snprintf(out, cap, "%s", pr.name);
+    for (char* c = out; *c; ++c)
+      if (*c == ' ' || *c == '|') *c = '_';
+  } else {
+    snprintf(out, cap, "unknown");
+  }
+}
+
+// Autotuner cache: a text file (path in HZ_AUTOTUNE_CACHE), one line per
+// (device, grid, precision, kernel kind): "device|nx|ny|nz|prec|kind variant".
+std::mutex g_tune_mu;
+
+void tune_key(hz_op op, int prec, int kind, char* key, size_t cap) {
+  char dn[128];
+  device_name(dn, sizeof(dn));
+  snprintf(key, cap, "%s|%d|%d|%d|%d|%d", dn, op->g.nx, op->g.ny, op->g.nz, prec, kind);
+}
+
+void load_tuned(hz_op op) {
+  const char* path = getenv("HZ_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    char key[400];
+    int var = -1;
+    if (sscanf(line, "%399s %d", key, &var) != 2) continue;
+    for (int pr = 0; pr < 2; ++pr)
+      for (int kind = 0; kind < 2; ++kind) {
+        char want[400];
+        tune_key(op, pr, kind, want, sizeof(want));
+        if (strcmp(want, key) == 0 && var >= 0 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx))
+          (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = var;
+      }
+  }
+  fclose(f);
+}
+
+void store_tuned(hz_op op) {
+  const char* path = getenv("HZ_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  for (int pr = 0; pr < 2; ++pr)
+    for (int kind = 0; kind < 2; ++kind) {
+      char key[400];
+      tune_key(op, pr, kind, key, sizeof(key));
+      fprintf(f, "%s %d\n", key, (kind == 0 ? op->L.vpre : op->L.vmv)[pr]);
+    }
+  fclose(f);
+}
+
 // global scratch for hz_dot (per device)
 std::mutex g_dot_mu;
 struct DotScratch {
@@ -383,6 +465,11 @@ int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_
   // launch shapes: each kernel fills the SMs to its own occupancy (grid-stride loops)
   op->L = Launch{op->sms, (op->g.ncol + kBS - 1) / kBS, (n / 4 + 255) / 256 + 1, op->stream};
   warm_launch_cache(op->L);
+  for (int pr = 0; pr < 2; ++pr) {
+    op->L.vpre[pr] = default_variant(pr, 0, nx);
+    op->L.vmv[pr] = default_variant(pr, 1, nx);
+  }
+  load_tuned(op);
   if (!(op->A7 = dalloc<double>(op, 7 * n, &st))) return fail(st);
   if (!(op->ah32 = dalloc<float>(op, 6 * n, &st))) return fail(st);
   if (!(op->th32 = dalloc<float>(op, 3 * n, &st))) return fail(st);
@@ -582,6 +669,131 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     info->kernel_launches = op->launches;
   }
   return status;
+}
+
+}  // extern "C"
+
+namespace {
+// Time one precision's column kernels in every valid variant on the operator's
+// own arrays (work vectors zeroed; a control block set to "running" before
+// each launch) and keep the fastest Thomas and stencil variants.
+template <typename T>
+int autotune_prec(hz_op op, int reps, double* best_ms) {
+  const int pr = sizeof(T) == 8 ? 1 : 0;
+  const Bands<T> a = bands_of<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  CK(cudaMemsetAsync(w.rhs, 0, sizeof(T) * 10 * pad64(op->g.n), op->stream));
+  Ctl* cfg = op->cfg_h;
+  memset(cfg, 0, sizeof(Ctl));
+  cfg->state = ST_RUNNING;
+  cfg->rsel = 1;
+  cfg->r0sel = 1;
+  cfg->xzero = 1;
+  cfg->alpha = cfg->omega = cfg->beta = 0.5;
+  cfg->rho = 1.0;
+  cfg->stop2 = -1.0;
+  cfg->maxit = 1 << 30;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& launch) -> double {
+    double tot = 0.0;
+    for (int r = 0; r <= reps; ++r) {  // first launch is a warm-up
+      if (cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, op->stream) != cudaSuccess) return -1.0;
+      cudaEventRecord(e0, op->stream);
+      if (launch() != cudaSuccess) return -1.0;
+      cudaEventRecord(e1, op->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) tot += ms;
+    }
+    return tot / reps;
+  };
+  for (int kind = 0; kind < 2; ++kind) {
+    int best = -1;
+    double bms = 1e30;
+    for (int id = 0; id < num_variants(pr, kind); ++id) {
+      if (!variant_ok(pr, kind, id, op->g.nx)) continue;
+      Launch L = op->L;
+      (kind == 0 ? L.vpre : L.vmv)[pr] = id;
+      double ms;
+      if (kind == 0)
+        ms = time_it([&] { return launch_pre_p<T>(op->g, a, w, op->ctl, op->red, L); }) +
+             time_it([&] { return launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L); });
+      else
+        ms = time_it([&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }) +
+             time_it([&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); });
+      if (ms < 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_err(cudaGetLastError(), "autotune launch", __LINE__);
+        return HZ_ERR_CUDA;
+      }
+      if (ms < bms) {
+        bms = ms;
+        best = id;
+      }
+    }
+    if (best >= 0) (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = best;
+    if (best_ms) best_ms[kind] = bms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return HZ_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int hz_op_autotune(hz_op op, int flags) {
+  if (!op) return HZ_ERR_INVALID;
+  const int reps = 3;
+  double ms[2];
+  CKS(autotune_prec<float>(op, reps, ms));
+  if (flags & 1) {
+    CKS(ensure_w64(op));
+    CKS(autotune_prec<double>(op, reps, ms));
+  }
+  // the captured inner loops bake the old launch shapes in: rebuild on next use
+  for (auto& gs : op->gs) {
+    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+    if (gs.graph) cudaGraphDestroy(gs.graph);
+    gs.exec = nullptr;
+    gs.graph = nullptr;
+  }
+  store_tuned(op);
+  return HZ_OK;
+}
+
+int hz_op_get_variants(hz_op op, int* pre32, int* mv32, int* pre64, int* mv64) {
+  if (!op) return HZ_ERR_INVALID;
+  if (pre32) *pre32 = op->L.vpre[0];
+  if (mv32) *mv32 = op->L.vmv[0];
+  if (pre64) *pre64 = op->L.vpre[1];
+  if (mv64) *mv64 = op->L.vmv[1];
+  return HZ_OK;
+}
+
+int hz_op_set_variants(hz_op op, int pre32, int mv32, int pre64, int mv64) {
+  if (!op) return HZ_ERR_INVALID;
+  const int v[4] = {pre32, mv32, pre64, mv64};
+  for (int q = 0; q < 4; ++q) {
+    const int pr = q / 2, kind = q % 2;
+    if (v[q] < 0) continue;
+    if (v[q] >= num_variants(pr, kind) || !variant_ok(pr, kind, v[q], op->g.nx)) return HZ_ERR_INVALID;
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int pr = q / 2, kind = q % 2;
+    if (v[q] >= 0) (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = v[q];
+  }
+  for (auto& gs : op->gs) {
+    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+    if (gs.graph) cudaGraphDestroy(gs.graph);
+    gs.exec = nullptr;
+    gs.graph = nullptr;
+  }
+  return HZ_OK;
 }
 
 int hz_profile_enable(hz_op op, int on) {

@@ -138,7 +138,17 @@ struct Launch {
   int64_t wcol;      // blocks needed to give every column its own thread (kBS per block)
   int64_t wflat;     // blocks of 256 threads needed by the elementwise kernels
   cudaStream_t stream;
+  int vpre[2];       // variant of the Thomas kernels, [0] FP32, [1] FP64
+  int vmv[2];        // variant of the stencil kernels
 };
+
+// Column-kernel variants: kind 0 = Thomas (k_pre_p, k_pre_s), kind 1 = stencil
+// (k_mv); prec 0 = FP32, 1 = FP64.  vec = columns per thread (must divide nx),
+// depth = levels per software-pipelined batch.
+int num_variants(int prec, int kind);
+void variant_shape(int prec, int kind, int id, int* vec, int* depth);
+template <typename T>
+void warm_kernels(const Launch& L);
 
 // Blocks for a grid-stride kernel: every SM filled to that kernel's own
 // occupancy (queried once per kernel and cached), capped by the work and by

@@ -162,3 +162,56 @@ def test_dot_parity_and_determinism(n, prec):
     assert len(set(vals)) == 1, "reduction is not deterministic"
     ref = oracle.dot(x, y)
     assert abs(vals[0] - ref) <= 1e-13 * np.dot(np.abs(x), np.abs(y))
+
+
+@pytest.mark.parametrize("shape", [(96, 72, 20), (64, 32, 70), (38, 5, 7), (37, 23, 9)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_column_variant_matches_oracle(shape, prec):
+    # each launch-shape variant (columns per thread, levels per batch) the
+    # autotuner may pick must give the oracle's T^-1 and Ahat T^-1
+    import torch
+
+    nx, ny, nz = shape
+    hz, A, op = _op(nx, ny, nz, z_unit="m")
+    n = nx * ny * nz
+    Ah = oracle.scale(A)
+    P = hz.HZ_PREC_FP64 if prec == "fp64" else hz.HZ_PREC_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    p = gen.normals(31, 0, n).reshape(nz, ny, nx)
+    if prec == "fp32":
+        p = p.astype(np.float32).astype(np.float64)
+        Ah = Ah.astype(np.float32).astype(np.float64)
+    ref_ph = oracle.apply_Tinv(Ah, p)
+    ref_v = oracle.matvec_hat(Ah, ref_ph)
+    scale = abs_matvec_hat(Ah, ref_ph) + np.abs(p)
+    L = hz.load()
+    pi = 1 if prec == "fp64" else 0
+    tried = 0
+    for var in range(8):
+        for kind in (0, 1):
+            args = [-1, -1, -1, -1]
+            args[2 * pi + kind] = var
+            if L.hz_op_set_variants(op.handle, *args) != 0:
+                continue
+            tried += 1
+            ph = torch.empty(n, dtype=dt, device="cuda")
+            v = torch.empty(n, dtype=dt, device="cuda")
+            op.precond_matvec(dev(p, dt), ph, v, P)
+            eph = np.max(np.abs(host(ph).reshape(nz, ny, nx) - ref_ph)) / np.max(np.abs(ref_ph))
+            ev = np.max(np.abs(host(v).reshape(nz, ny, nx) - ref_v) / scale)
+            assert eph <= tol and ev <= tol, (var, kind, eph, ev)
+    assert tried >= 2
+
+
+def test_autotune_picks_valid_variants_and_solves():
+    import torch
+
+    hz, A, op = _op(96, 72, 20, z_unit="m")
+    v = op.autotune(fp64=True)
+    assert all(x >= 0 for x in v.values())
+    b = gen.make_rhs(96, 72, 20, 3)
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    info = op.solve(dev(b), x)
+    _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+    assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8

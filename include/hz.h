@@ -213,6 +213,34 @@ int hz_residual(hz_op op, const double* b, const double* x, double* r, double* r
    by prec; FP64 accumulation across threads and blocks).  out: host. */
 int hz_dot(int prec, int64_t n, const void* x, const void* y, void* stream, double* out);
 
+/*
+ * hz_dot_noalloc -- the deterministic dot product of hz_dot for callers that
+ * cannot allocate device memory.  The paper has no counterpart: it is a
+ * deployment aid.  hz_dot allocates its scratch with cudaMalloc on its first
+ * call on a device; code that must not allocate (inside a fixed memory pool,
+ * under an allocator owned by another framework, or under a no-allocation
+ * rule after start-up) cannot use it.  This entry point allocates nothing:
+ * its scratch is a static device array of HZ_DOT_NOALLOC_SLOTS partial sums
+ * plus a ticket word (32 KiB, held by every GPU that loads the library until
+ * the process exits), and it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *   prec: HZ_PREC_FP32 or HZ_PREC_FP64; x, y: device arrays of n elements;
+ *   out: DEVICE pointer to one double that receives sum_i x_i y_i (FP64
+ *   accumulation, same kernel and order as hz_dot for the same launch shape);
+ *   stream: the stream to order the work on.  The call does not wait.
+ * Limits: n >= 0; at most HZ_DOT_NOALLOC_SLOTS blocks are launched (grid-
+ * stride), so any n fits the scratch.  Invalid arguments return
+ * HZ_ERR_INVALID.
+ * Set-up: the first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Sharing: every call uses the same array and leaves its contents behind;
+ * each call zeroes the ticket it needs first.  Calls that overlap on the GPU
+ * (concurrent streams, or several host threads) race on the array and give
+ * wrong results: serialise them.
+ */
+#define HZ_DOT_NOALLOC_SLOTS 4064
+int hz_dot_noalloc(int prec, int64_t n, const void* x, const void* y, void* stream, double* out);
+
 /* Copy the operator's derived data to device memory dst:
    what = 0: scaled bands [6][n] (E,W,N,S,U,D) in prec;
    what = 1: Thomas factors [3][n] (m, l, c') in prec, where the forward sweep

@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
         "hz_residual": (i32, [pv, pv, pv, pv, P(dbl), P(dbl)]),
         "hz_dot": (i32, [i32, i64, pv, pv, pv, P(dbl)]),
         "hz_op_export": (i32, [pv, i32, i32, pv]),
+        "hz_dot_noalloc": (i32, [i32, i64, pv, pv, pv, pv]),
         "hz_op_autotune": (i32, [pv, i32]),
         "hz_op_get_variants": (i32, [pv, P(i32), P(i32), P(i32), P(i32)]),
         "hz_op_set_variants": (i32, [pv, i32, i32, i32, i32]),
@@ -300,6 +301,19 @@ def dot(x, y, prec=None, stream=None):
     out = ctypes.c_double()
     _check(load().hz_dot(prec, x.numel(), _ptr(x), _ptr(y), _stream_ptr(stream), ctypes.byref(out)), "hz_dot")
     return out.value
+
+
+def dot_noalloc(x, y, out, prec=None, stream=None):
+    """hz_dot_noalloc: the dot product of two CUDA tensors written to the CUDA
+    tensor ``out`` (one float64), using only the library's static scratch (no
+    device allocation).  Does not synchronise."""
+    import torch
+
+    if prec is None:
+        prec = HZ_PREC_FP32 if x.dtype == torch.float32 else HZ_PREC_FP64
+    assert out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1
+    _check(load().hz_dot_noalloc(prec, x.numel(), _ptr(x), _ptr(y), _stream_ptr(stream), _ptr(out)),
+           "hz_dot_noalloc")
 
 
 def version() -> int:

@@ -75,3 +75,59 @@ void variant_shape(int prec, int kind, int id, int* vec, int* depth) {
 }
 
 }  // namespace hz
+
+// ---------------------------------------------------------------------------
+// hz_dot_noalloc: the deterministic dot product with its scratch in static
+// device memory instead of memory the library allocates.
+//
+// For callers that cannot allocate device memory (code that runs where
+// cudaMalloc is not allowed or not wanted: inside a memory pool that must not
+// grow, in a process whose allocator is owned by someone else, or under a
+// strict no-allocation policy after start-up).  The scratch is one
+// file-scope array: HZ_DOT_NOALLOC_SLOTS FP64 partial sums (one per block)
+// plus a ticket word, 32 KiB in all, which every GPU that loads the library
+// holds until the process exits.
+namespace {
+constexpr int kNoAllocSlots = HZ_DOT_NOALLOC_SLOTS;
+static __device__ __align__(256) double hz_noalloc_scratch[kNoAllocSlots + 32];
+
+std::mutex g_na_mu;
+double* g_na_ptr[64] = {};  // device address of the scratch, per device (set up once)
+}  // namespace
+
+extern "C" int hz_dot_noalloc(int prec, int64_t n, const void* x, const void* y, void* stream, double* out) {
+  using namespace hz;
+  if (n < 0 || !out || (n > 0 && (!x || !y))) return HZ_ERR_INVALID;
+  if (prec != HZ_PREC_FP32 && prec != HZ_PREC_FP64) return HZ_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HZ_ERR_CUDA;
+  double* base = nullptr;
+  {
+    // set-up, once per device with that device current: the host-side name of
+    // the array is not a device address, so ask the runtime for the address
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, hz_noalloc_scratch) != cudaSuccess) return HZ_ERR_CUDA;
+      g_na_ptr[dev] = (double*)p;
+    }
+    base = g_na_ptr[dev];
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HZ_ERR_CUDA;
+  int64_t grid = (int64_t)sms * 8;
+  if (grid > kNoAllocSlots) grid = kNoAllocSlots;  // grid-stride: fewer blocks than SMs*8 is still correct
+  const int64_t need = (n + 255) / 256;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* ticket = reinterpret_cast<unsigned*>(base + kNoAllocSlots);
+  // the ticket must start at zero whatever the previous call left
+  if (cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess) return HZ_ERR_CUDA;
+  if (n == 0) return cudaMemsetAsync(out, 0, sizeof(double), s) == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+  Red red{base, ticket};
+  cudaError_t e = prec == HZ_PREC_FP32
+                      ? launch_dot<float>(n, (const float*)x, (const float*)y, red, out, (int)grid, s)
+                      : launch_dot<double>(n, (const double*)x, (const double*)y, red, out, (int)grid, s);
+  return e == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+}

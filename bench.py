@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--z-unit", default="radius", choices=["radius", "m"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--eta", type=float, default=1e-4, help="inner relative tolerance of the mixed solver")
     return ap.parse_args()
 
 
@@ -204,7 +205,7 @@ def run_ours(args):
     bd = torch.from_numpy(b.reshape(-1)).to(f"cuda:{dev}")
     x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
     variants = op.autotune(fp64=not args.no_fp64)  # launch-shape search, outside the timed region
-    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8)
+    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta)
     p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8)
 
     def barrier():
@@ -319,7 +320,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
         "config": {"workload": f"{args.workload} {nx}x{ny}x{nz} z_unit={args.z_unit} seeds "
-                               f"{make_seed(args)} mixed IR tol 1e-8 eta 1e-4",
+                               f"{make_seed(args)} mixed IR tol 1e-8 eta {args.eta:g}",
                    "l2": "inputs larger than L2 (vectors 1.4-2.8 GB)", "parallelism": f"replicas x{world}"},
         "solve": {"outer": infos[0]["outer_iters"], "inner": infos[0]["inner_iters"],
                   "true_rel_residual": infos[0]["true_rel_residual"]},

@@ -149,12 +149,22 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
  * Solve nsys independent systems (each with its own operator, which may have
  * its own grid).  b[s], x0[s] (may be NULL) and x[s] follow hz_solve's rules
  * (device pointers only).  The inner FP32 Krylov iterations of all systems
- * run in one persistent launch per refinement step, with per-system scalars
- * and convergence masks.  infos: host array of nsys reports, may be NULL.
- * All operators must share one stream.  Returns the worst status.
+ * run in one persistent cooperative launch per refinement step, with
+ * per-system scalars and convergence masks, phases separated by a grid
+ * barrier whose waits are bounded (HZ_ERR_TIMEOUT instead of a hang).
+ * 1 <= nsys <= 64 distinct operators sharing one stream; mixed mode only
+ * (params->mode = HZ_MODE_MIXED_IR, else HZ_ERR_UNSUPPORTED).
+ * infos: host array of nsys reports, may be NULL.  Returns the worst status.
  */
 int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
                      const hz_solve_params* params, hz_solve_info* infos);
+
+/* Test hook of hz_solve_batched (process-wide, affects later batched calls):
+   timeout_ns bounds every grid-barrier wait of the persistent kernel (<= 0:
+   the default, 2 s); leave_block >= 0 makes that block leave the kernel after
+   its first barrier, so that the other blocks' waits run out and the call
+   returns HZ_ERR_TIMEOUT without hanging the GPU (-1: off). */
+int hz_batched_debug(long long timeout_ns, int leave_block);
 
 /* Inner recursive residual history of the last solve with record_history=1:
    copies up to cap values into hist (host) and returns how many. */

@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         "hz_dot": (i32, [i32, i64, pv, pv, pv, P(dbl)]),
         "hz_op_export": (i32, [pv, i32, i32, pv]),
         "hz_dot_noalloc": (i32, [i32, i64, pv, pv, pv, pv]),
+        "hz_batched_debug": (i32, [ctypes.c_longlong, i32]),
         "hz_op_autotune": (i32, [pv, i32]),
         "hz_op_get_variants": (i32, [pv, P(i32), P(i32), P(i32), P(i32)]),
         "hz_op_set_variants": (i32, [pv, i32, i32, i32, i32]),
@@ -274,7 +275,7 @@ class Operator:
         _check(load().hz_op_export(self._h, what, prec, _ptr(dst)), "hz_op_export")
 
 
-def solve_batched(ops, bs, xs, x0s=None, params=None, **kw):
+def solve_batched(ops, bs, xs, x0s=None, params=None, raise_on_error=True, **kw):
     """Solve several systems (each its own Operator) in one batched call; returns a list of info dicts."""
     L = load()
     k = len(ops)
@@ -287,9 +288,14 @@ def solve_batched(ops, bs, xs, x0s=None, params=None, **kw):
     infos = (hz_solve_info * k)()
     st = L.hz_solve_batched(k, hs, bp, x0p, xp, ctypes.byref(p), infos)
     out = [i.as_dict() for i in infos]
-    if st != HZ_OK:
+    if st != HZ_OK and raise_on_error:
         raise HzError(st, f"hz_solve_batched {out}")
-    return out
+    return out if raise_on_error else (st, out)
+
+
+def batched_debug(timeout_ns=0, leave_block=-1):
+    """Test hook: bound of the batched grid-barrier waits and a block that leaves early."""
+    _check(load().hz_batched_debug(int(timeout_ns), int(leave_block)), "hz_batched_debug")
 
 
 def dot(x, y, prec=None, stream=None):

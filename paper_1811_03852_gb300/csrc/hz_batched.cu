@@ -1,0 +1,396 @@
+// hz_batched.cu -- many independent systems (uneven grids) in one persistent,
+// cooperative launch per refinement step.
+//
+// The inner FP32 BiCGStab of every system (the same iteration and the same
+// control steps as the single-system kernels) runs phase by phase over one
+// global list of work items; an item is one block-iteration (kBS column
+// groups) of one system, so systems of different sizes are load-balanced by
+// items.  Each system keeps its own scalars and state in its control block;
+// systems that have converged (or failed) are masked out of every phase.
+// Phases are separated by a grid barrier whose wait is bounded (%globaltimer):
+// a block that waits longer than the limit sets an error flag, every block
+// leaves, and the host reports HZ_ERR_TIMEOUT -- no spin is unbounded.
+//
+// Per-system dot products: each block sums its items' partials per system in
+// a fixed order, stores them in its own slot, and after the barrier block b
+// (b < number of systems) adds system b's slots in slot order and runs the
+// control step -- deterministic for a given launch shape.
+#include "hz_krylov.cuh"
+
+namespace hz {
+
+struct BatchArgs {
+  const SysDesc* sys;
+  int nsys;
+  int64_t nitems;
+  double* part;        // [gridDim.x][kMaxSys][4] partial sums
+  unsigned* bar;       // [0] arrivals, [1] generation
+  int* err;            // bit 0: a barrier wait timed out
+  long long timeout_ns;
+  int leave_block;     // test hook: this block leaves after its first barrier (-1: none)
+  int max_loops;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier with a bounded wait.  Returns false (in every thread of the
+// block) once any block has given up; the caller then leaves the kernel.
+__device__ bool grid_sync(const BatchArgs& A) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* genp = A.bar + 1;
+    volatile int* errp = A.err;
+    const unsigned gen = *genp;
+    __threadfence();
+    const unsigned arrived = atomicAdd(A.bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      A.bar[0] = 0u;  // reset before the release: nobody passes until gen moves
+      __threadfence();
+      atomicAdd(A.bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*genp == gen) {
+        if (*errp) break;
+        if (global_ns() - t0 > (unsigned long long)A.timeout_ns) {
+          atomicOr(A.err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = (*errp == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// per-system control values a phase needs, read through L2 (other blocks write them)
+struct SysCtl {
+  int state, fresh, rsel, r0sel, xzero;
+  float alpha, beta, omega;
+};
+
+__device__ void load_ctl(const BatchArgs& A, SysCtl* sc) {
+  for (int s = threadIdx.x; s < A.nsys; s += blockDim.x) {
+    const Ctl* c = A.sys[s].ctl;
+    sc[s].state = __ldcg(&c->state);
+    sc[s].fresh = __ldcg(&c->fresh);
+    sc[s].rsel = __ldcg(&c->rsel);
+    sc[s].r0sel = __ldcg(&c->r0sel);
+    sc[s].xzero = __ldcg(&c->xzero);
+    sc[s].alpha = (float)__ldcg(&c->alpha);
+    sc[s].beta = (float)__ldcg(&c->beta);
+    sc[s].omega = (float)__ldcg(&c->omega);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int sys_of(const BatchArgs& A, int64_t item) {
+  int s = 0;
+  while (s + 1 < A.nsys && item >= A.sys[s + 1].item0) ++s;
+  return s;
+}
+
+// block sum of ND values per thread in fixed order; thread 0 adds them to acc
+template <int ND>
+__device__ __forceinline__ void block_add(double (&v)[ND], double* acc) {
+  __shared__ double sm[ND][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    double x = v[d];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[d][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      double x = 0.0;
+      for (int w = 0; w < nw; ++w) x += sm[d][w];
+      acc[d] += x;
+    }
+  }
+  __syncthreads();
+}
+
+// fixed-order sum of system s's slot d over all blocks
+__device__ __forceinline__ double slots_sum(const BatchArgs& A, int s, int d) {
+  double x = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) x += __ldcg(&A.part[((size_t)b * kMaxSys + s) * 4 + d]);
+  return x;
+}
+
+// restart of one column inside the persistent kernel: x of neighbouring
+// columns was written by other blocks, so it is read through L2
+__device__ double restart_column_cg(const Grid& g, int64_t col, const Bands<float>& a, const Vecs<float>& w,
+                                    bool xzero) {
+  const int i = (int)(col % g.nx), j = (int)(col / g.nx);
+  const int64_t ie = (i == g.nx - 1) ? -(int64_t)(g.nx - 1) : 1;
+  const int64_t iw = (i == 0) ? (int64_t)(g.nx - 1) : -1;
+  float cacc = 0.f;
+  for (int k = 0; k < g.nz; ++k) {
+    const int64_t idx = (int64_t)k * g.ncol + col;
+    float rk = __ldcg(w.rhs + idx);
+    if (!xzero) {
+      float y = __ldcg(w.x + idx);
+      y = fmaf(a.E[idx], __ldcg(w.x + idx + ie), y);
+      y = fmaf(a.W[idx], __ldcg(w.x + idx + iw), y);
+      if (j + 1 < g.ny) y = fmaf(a.N[idx], __ldcg(w.x + idx + g.nx), y);
+      if (j > 0) y = fmaf(a.S[idx], __ldcg(w.x + idx - g.nx), y);
+      if (k + 1 < g.nz) y = fmaf(a.U[idx], __ldcg(w.x + idx + g.ncol), y);
+      if (k > 0) y = fmaf(a.D[idx], __ldcg(w.x + idx - g.ncol), y);
+      rk -= y;
+    }
+    w.r[idx] = rk;
+    w.r0[idx] = rk;
+    cacc = fmaf(rk, rk, cacc);
+  }
+  SrcCopy<float, 1, LD_CG> src{w.r, w.p};
+  thomas_vec<float, 1, 4>(g, col, a.m, a.l, a.cp, w.ph, src);
+  return (double)cacc;
+}
+
+template <int V, int UT, int UM>
+__global__ void __launch_bounds__(kBS) k_batched(BatchArgs A) {
+  __shared__ SysCtl sc[kMaxSys];
+  __shared__ double acc[kMaxSys][2];
+  const int nsys = A.nsys;
+  auto zero_acc = [&]() {
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) acc[s][0] = acc[s][1] = 0.0;
+    __syncthreads();
+  };
+  auto store_acc = [&](int d0, int nd) {
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x)
+      for (int d = 0; d < nd; ++d) A.part[((size_t)blockIdx.x * kMaxSys + s) * 4 + d0 + d] = acc[s][d];
+    __threadfence();
+  };
+  bool left = false;
+  for (int loop = 0; loop < A.max_loops; ++loop) {
+    load_ctl(A, sc);
+    bool any = false;
+    for (int s = 0; s < nsys; ++s) any |= (sc[s].state == ST_RUNNING || sc[s].state == ST_RESTART);
+    if (!any) break;
+
+    // ---- phase A: (re)start or p = r + beta (p - omega v); ph = T^-1 p ----
+    zero_acc();
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+      const int s = sys_of(A, item);
+      const SysCtl c = sc[s];
+      if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
+      const SysDesc& d = A.sys[s];
+      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+      double v[1] = {0.0};
+      if (q < d.g.ncol / V) {
+        if (c.state == ST_RESTART) {
+          for (int cc = 0; cc < V; ++cc) v[0] += restart_column_cg(d.g, q * V + cc, d.a, d.w, c.xzero != 0);
+        } else if (c.fresh) {
+          SrcCopy<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.p};
+          thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.ph, src);
+        } else {
+          SrcP<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.p, d.w.v, c.beta, c.omega};
+          thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.ph, src);
+        }
+      }
+      if (c.state == ST_RESTART) block_add<1>(v, &acc[s][0]);
+    }
+    store_acc(0, 1);
+    if (!grid_sync(A)) return;
+    if ((int)blockIdx.x == A.leave_block) return;  // test hook: the others must time out, not hang
+
+    // ---- phase B: v = p + H ph, <r0, v> ----
+    zero_acc();
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+      const int s = sys_of(A, item);
+      const SysCtl c = sc[s];
+      if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
+      const SysDesc& d = A.sys[s];
+      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+      double v[1] = {0.0}, dummy = 0.0;
+      const bool r0buf = c.r0sel || c.state == ST_RESTART;
+      if (q < d.g.ncol / V)
+        hmv_vec<float, V, UM, 0, LD_CG>(d.g, q * V, d.a, d.w.p, d.w.ph, d.w.v, r0buf ? d.w.r0 : d.w.rhs, v[0], dummy);
+      block_add<1>(v, &acc[s][0]);
+    }
+    store_acc(1, 1);
+    if (!grid_sync(A)) return;
+    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+      const int s = blockIdx.x;
+      Ctl* ctl = A.sys[s].ctl;
+      if (sc[s].state == ST_RESTART) fin_restart(ctl, slots_sum(A, s, 0));
+      if (sc[s].state == ST_RESTART || sc[s].state == ST_RUNNING) {
+        if (ctl->state == ST_RUNNING) fin_alpha(ctl, slots_sum(A, s, 1));
+      }
+      __threadfence();
+    }
+    if (!grid_sync(A)) return;
+    load_ctl(A, sc);
+
+    // ---- phase C: s = r - alpha v, <s, s>, sh = T^-1 s ----
+    zero_acc();
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+      const int s = sys_of(A, item);
+      const SysCtl c = sc[s];
+      if (c.state != ST_RUNNING) continue;
+      const SysDesc& d = A.sys[s];
+      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+      double v[1] = {0.0};
+      if (q < d.g.ncol / V) {
+        SrcS<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, 0.0};
+        thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.sh, src);
+        v[0] = src.acc;
+      }
+      block_add<1>(v, &acc[s][0]);
+    }
+    store_acc(2, 1);
+    if (!grid_sync(A)) return;
+    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+      const int s = blockIdx.x;
+      if (sc[s].state == ST_RUNNING) fin_snorm(A.sys[s].ctl, slots_sum(A, s, 2));
+      __threadfence();
+    }
+    if (!grid_sync(A)) return;
+    load_ctl(A, sc);
+
+    // ---- phase D: t = s + H sh, <t, s>, <t, t> ----
+    zero_acc();
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+      const int s = sys_of(A, item);
+      const SysCtl c = sc[s];
+      if (c.state != ST_RUNNING) continue;
+      const SysDesc& d = A.sys[s];
+      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+      double v[2] = {0.0, 0.0};
+      if (q < d.g.ncol / V) hmv_vec<float, V, UM, 1, LD_CG>(d.g, q * V, d.a, d.w.s, d.w.sh, d.w.t, nullptr, v[0], v[1]);
+      block_add<2>(v, &acc[s][0]);
+    }
+    store_acc(0, 2);
+    if (!grid_sync(A)) return;
+    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+      const int s = blockIdx.x;
+      if (sc[s].state == ST_RUNNING) fin_omega(A.sys[s].ctl, slots_sum(A, s, 0), slots_sum(A, s, 1));
+      __threadfence();
+    }
+    if (!grid_sync(A)) return;
+    load_ctl(A, sc);
+
+    // ---- phase E: x += alpha ph + omega sh, r = s - omega t, <r0, r>, <r, r> ----
+    zero_acc();
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+      const int s = sys_of(A, item);
+      const SysCtl c = sc[s];
+      if (c.state != ST_RUNNING && c.state != ST_HALF) continue;
+      const SysDesc& d = A.sys[s];
+      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+      double v[2] = {0.0, 0.0};
+      if (q < d.g.ncol / V) {
+        const bool half = c.state == ST_HALF;
+        const float* r0 = c.r0sel ? d.w.r0 : d.w.rhs;
+        for (int k = 0; k < d.g.nz; ++k) {
+          const int64_t idx = (int64_t)k * d.g.ncol + q * V;
+          Pack<float, V> xv, pv = ldp<float, V, LD_CG>(d.w.ph + idx);
+          if (c.xzero) {
+#pragma unroll
+            for (int u = 0; u < V; ++u) xv.a[u] = 0.f;
+          } else {
+            xv = ldp<float, V, LD_CG>(d.w.x + idx);
+          }
+          if (half) {
+#pragma unroll
+            for (int u = 0; u < V; ++u) xv.a[u] = fmaf(c.alpha, pv.a[u], xv.a[u]);
+          } else {
+            const Pack<float, V> shv = ldp<float, V, LD_CG>(d.w.sh + idx), sv = ldp<float, V, LD_CG>(d.w.s + idx),
+                                 tv = ldp<float, V, LD_CG>(d.w.t + idx), r0v = ldp<float, V, LD_CG>(r0 + idx);
+            Pack<float, V> rv;
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+              xv.a[u] = fmaf(c.omega, shv.a[u], fmaf(c.alpha, pv.a[u], xv.a[u]));
+              rv.a[u] = fmaf(-c.omega, tv.a[u], sv.a[u]);
+              a0 = fmaf(r0v.a[u], rv.a[u], a0);
+              a1 = fmaf(rv.a[u], rv.a[u], a1);
+            }
+            stp(d.w.r + idx, rv);
+            v[0] += (double)a0;
+            v[1] += (double)a1;
+          }
+          stp(d.w.x + idx, xv);
+        }
+      }
+      block_add<2>(v, &acc[s][0]);
+    }
+    store_acc(2, 2);
+    if (!grid_sync(A)) return;
+    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+      const int s = blockIdx.x;
+      if (sc[s].state == ST_RUNNING || sc[s].state == ST_HALF)
+        fin_iteration(A.sys[s].ctl, sc[s].state == ST_HALF, slots_sum(A, s, 2), slots_sum(A, s, 3));
+      __threadfence();
+    }
+    if (!grid_sync(A)) return;
+  }
+  (void)left;
+}
+
+// ---------------------------------------------------------------------------
+struct BatchWs {
+  SysDesc* sys = nullptr;
+  double* part = nullptr;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  int part_grid = 0;
+};
+
+template <int V>
+const void* batched_kernel() {
+  return V == 4 ? (const void*)k_batched<4, 2, 1> : (const void*)k_batched<1, 8, 4>;
+}
+
+// Launch the persistent kernel cooperatively.  Returns the CUDA error; *err_h
+// receives the device error word (after a synchronisation).
+cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loops, long long timeout_ns,
+                           int leave_block, cudaStream_t stream, int* err_h, int sms) {
+  static BatchWs ws[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || nsys > kMaxSys || nsys < 1) return cudaErrorInvalidValue;
+  BatchWs& w = ws[dev];
+  const void* kern = batched_kernel<4>();
+  if (vec != 4) kern = batched_kernel<1>();
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBS, 0)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = per_sm * sms;  // cooperative: every block resident
+  if (!w.sys) {
+    if ((e = cudaMalloc(&w.sys, sizeof(SysDesc) * kMaxSys)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.bar, sizeof(unsigned) * 2)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.err, sizeof(int))) != cudaSuccess) return e;
+  }
+  if (w.part_grid < grid) {
+    if (w.part) cudaFree(w.part);
+    if ((e = cudaMalloc(&w.part, sizeof(double) * (size_t)grid * kMaxSys * 4)) != cudaSuccess) return e;
+    w.part_grid = grid;
+  }
+  if ((e = cudaMemcpyAsync(w.sys, sys_h, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2, stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.err, 0, sizeof(int), stream)) != cudaSuccess) return e;
+  int64_t nitems = 0;
+  for (int s = 0; s < nsys; ++s) nitems = sys_h[s].item0 + sys_h[s].nitems;
+  BatchArgs args{w.sys, nsys, nitems, w.part, w.bar, w.err, timeout_ns, leave_block, max_loops};
+  void* kargs[] = {&args};
+  if ((e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBS), kargs, 0, stream)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(err_h, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(stream);
+}
+
+
+}  // namespace hz

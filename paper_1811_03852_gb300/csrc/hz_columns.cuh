@@ -17,24 +17,38 @@ struct Pack {
   T a[V];
 };
 
-// vector load; NC = read-only for the whole launch (non-coherent path)
-template <typename T, int V, bool NC>
+// vector load.  M = LD_PLAIN: coherent (data this thread wrote); LD_NC: read-only
+// for the whole launch (non-coherent path); LD_CG: written earlier in the same
+// launch by other blocks (L2 only, never a stale L1 line)
+enum LoadMode : int { LD_PLAIN = 0, LD_NC = 1, LD_CG = 2 };
+
+template <typename W, int M>
+__device__ __forceinline__ W ldw(const W* p) {
+  if constexpr (M == LD_NC)
+    return __ldg(p);
+  else if constexpr (M == LD_CG)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
+template <typename T, int V, int M>
 __device__ __forceinline__ Pack<T, V> ldp(const T* p) {
   Pack<T, V> r;
   if constexpr (V == 1) {
-    r.a[0] = NC ? __ldg(p) : *p;
+    r.a[0] = ldw<T, M>(p);
   } else if constexpr (sizeof(T) == 4 && V == 4) {
-    const float4 t = NC ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+    const float4 t = ldw<float4, M>(reinterpret_cast<const float4*>(p));
     r.a[0] = t.x;
     r.a[1] = t.y;
     r.a[2] = t.z;
     r.a[3] = t.w;
   } else if constexpr (sizeof(T) == 4 && V == 2) {
-    const float2 t = NC ? __ldg(reinterpret_cast<const float2*>(p)) : *reinterpret_cast<const float2*>(p);
+    const float2 t = ldw<float2, M>(reinterpret_cast<const float2*>(p));
     r.a[0] = t.x;
     r.a[1] = t.y;
   } else if constexpr (sizeof(T) == 8 && V == 2) {
-    const double2 t = NC ? __ldg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
+    const double2 t = ldw<double2, M>(reinterpret_cast<const double2*>(p));
     r.a[0] = t.x;
     r.a[1] = t.y;
   } else {
@@ -97,8 +111,8 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
       if (k0 + u < nz) {
         const int64_t idx = (int64_t)(k0 + u) * ncol + c0;
         src.load(idx, v[u]);
-        mm[u] = ldp<T, V, true>(m + idx);
-        ll[u] = ldp<T, V, true>(l + idx);
+        mm[u] = ldp<T, V, LD_NC>(m + idx);
+        ll[u] = ldp<T, V, LD_NC>(l + idx);
       }
     }
 #pragma unroll
@@ -126,8 +140,8 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
     for (int u = 0; u < U; ++u) {
       if (k0 - u >= 0) {
         const int64_t idx = (int64_t)(k0 - u) * ncol + c0;
-        yy[u] = ldp<T, V, false>(out + idx);  // written by this thread above: coherent load
-        cc[u] = ldp<T, V, true>(cp + idx);
+        yy[u] = ldp<T, V, LD_PLAIN>(out + idx);  // written by this thread above: coherent load
+        cc[u] = ldp<T, V, LD_NC>(cp + idx);
       }
     }
 #pragma unroll
@@ -147,7 +161,7 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
 }
 
 // inputs of the Thomas sweeps ------------------------------------------------
-template <typename T, int V>
+template <typename T, int V, int M = LD_NC>
 struct SrcP {  // p = r + beta (p - omega v)
   static constexpr int NIN = 3;
   const T* __restrict__ r;
@@ -155,9 +169,9 @@ struct SrcP {  // p = r + beta (p - omega v)
   const T* __restrict__ v;
   T beta, omega;
   __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) {
-    o[0] = ldp<T, V, true>(r + idx);
-    o[1] = ldp<T, V, false>(p + idx);
-    o[2] = ldp<T, V, true>(v + idx);
+    o[0] = ldp<T, V, M>(r + idx);
+    o[1] = ldp<T, V, LD_PLAIN>(p + idx);
+    o[2] = ldp<T, V, M>(v + idx);
   }
   __device__ __forceinline__ Pack<T, V> make(const Pack<T, V> (&o)[NIN], int64_t idx) {
     Pack<T, V> q;
@@ -169,12 +183,12 @@ struct SrcP {  // p = r + beta (p - omega v)
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V>
+template <typename T, int V, int M = LD_NC>
 struct SrcCopy {  // q = r, optionally stored to dst
   static constexpr int NIN = 1;
   const T* __restrict__ r;
   T* __restrict__ dst;
-  __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) { o[0] = ldp<T, V, true>(r + idx); }
+  __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) { o[0] = ldp<T, V, M>(r + idx); }
   __device__ __forceinline__ Pack<T, V> make(const Pack<T, V> (&o)[NIN], int64_t idx) {
     if (dst) stp(dst + idx, o[0]);
     return o[0];
@@ -182,7 +196,7 @@ struct SrcCopy {  // q = r, optionally stored to dst
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V>
+template <typename T, int V, int M = LD_NC>
 struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, FP64 across batches
   static constexpr int NIN = 2;
   const T* __restrict__ r;
@@ -192,8 +206,8 @@ struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, F
   T part;
   double acc;
   __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) {
-    o[0] = ldp<T, V, true>(r + idx);
-    o[1] = ldp<T, V, true>(v + idx);
+    o[0] = ldp<T, V, M>(r + idx);
+    o[1] = ldp<T, V, M>(v + idx);
   }
   __device__ __forceinline__ Pack<T, V> make(const Pack<T, V> (&o)[NIN], int64_t idx) {
     Pack<T, V> q;
@@ -215,7 +229,7 @@ struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, F
 // MODE 0: d0 += <r0, y>.  MODE 1: d0 += <y, c>, d1 += <y, y>.  MODE 2: no dots.
 // Each batch's dot partial is FP32 (FP64 solver: FP64) and is added to the
 // FP64 accumulators once per batch.
-template <typename T, int V, int U, int MODE>
+template <typename T, int V, int U, int MODE, int M = LD_NC>
 __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T>& a, const T* __restrict__ cen,
                                         const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ r0,
                                         double& d0, double& d1) {
@@ -228,27 +242,27 @@ __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T
     for (int u = 0; u < U; ++u) {
       if (k0 + u < g.nz) {
         const int64_t idx = (int64_t)(k0 + u) * ncol + c0;
-        cc[u] = ldp<T, V, true>(cen + idx);
-        e[u] = ldp<T, V, true>(a.E + idx);
-        w[u] = ldp<T, V, true>(a.W + idx);
-        if constexpr (V > 1) xc[u] = ldp<T, V, true>(x + idx);
-        xw1[u] = __ldg(x + idx + nb.w_off);
-        xe1[u] = __ldg(x + idx + nb.e_off);
+        cc[u] = ldp<T, V, M>(cen + idx);
+        e[u] = ldp<T, V, LD_NC>(a.E + idx);
+        w[u] = ldp<T, V, LD_NC>(a.W + idx);
+        if constexpr (V > 1) xc[u] = ldp<T, V, M>(x + idx);
+        xw1[u] = ldw<T, M>(x + idx + nb.w_off);
+        xe1[u] = ldw<T, M>(x + idx + nb.e_off);
         if (nb.hn) {
-          nn[u] = ldp<T, V, true>(a.N + idx);
-          xn[u] = ldp<T, V, true>(x + idx + nx);
+          nn[u] = ldp<T, V, LD_NC>(a.N + idx);
+          xn[u] = ldp<T, V, M>(x + idx + nx);
         } else {
 #pragma unroll
           for (int c = 0; c < V; ++c) nn[u].a[c] = xn[u].a[c] = T(0);
         }
         if (nb.hs) {
-          ss[u] = ldp<T, V, true>(a.S + idx);
-          xs[u] = ldp<T, V, true>(x + idx - nx);
+          ss[u] = ldp<T, V, LD_NC>(a.S + idx);
+          xs[u] = ldp<T, V, M>(x + idx - nx);
         } else {
 #pragma unroll
           for (int c = 0; c < V; ++c) ss[u].a[c] = xs[u].a[c] = T(0);
         }
-        if constexpr (MODE == 0) q[u] = ldp<T, V, true>(r0 + idx);
+        if constexpr (MODE == 0) q[u] = ldp<T, V, M>(r0 + idx);
       }
     }
     T p0 = T(0), p1 = T(0);

@@ -393,6 +393,10 @@ void store_tuned(hz_op op) {
   fclose(f);
 }
 
+// test hooks of the batched solve (bounded grid-barrier wait)
+long long g_batch_timeout_ns = 2000000000LL;
+int g_batch_leave_block = -1;
+
 // global scratch for hz_dot (per device)
 std::mutex g_dot_mu;
 struct DotScratch {
@@ -926,10 +930,180 @@ int hz_op_export(hz_op op, int what, int prec, void* dst) {
   return HZ_OK;
 }
 
+int hz_batched_debug(long long timeout_ns, int leave_block) {
+  if (timeout_ns <= 0) timeout_ns = 2000000000LL;
+  g_batch_timeout_ns = timeout_ns;
+  g_batch_leave_block = leave_block;
+  return HZ_OK;
+}
+
 int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
-                     const hz_solve_params* params, hz_solve_info* infos) {
-  (void)nsys; (void)ops; (void)b; (void)x0; (void)x; (void)params; (void)infos;
-  return HZ_ERR_UNSUPPORTED;
+                     const hz_solve_params* pp, hz_solve_info* infos) {
+  if (nsys < 1 || nsys > kMaxSys || !ops || !b || !x) return HZ_ERR_INVALID;
+  hz_solve_params p;
+  if (pp)
+    p = *pp;
+  else
+    hz_default_params(&p);
+  if (!(p.tol > 0.0) || p.max_outer < 0 || p.max_inner < 1 || p.restart < 1) return HZ_ERR_INVALID;
+  if (p.mode != HZ_MODE_MIXED_IR || p.krylov != HZ_KRYLOV_BICGSTAB || p.precond != HZ_PRE_TRI)
+    return HZ_ERR_UNSUPPORTED;
+  const double eta = p.inner_tol > 0.0 ? p.inner_tol : 1e-4;
+  cudaStream_t s = ops[0] ? ops[0]->stream : nullptr;
+  int vec = 4;
+  for (int q = 0; q < nsys; ++q) {
+    if (!ops[q] || !b[q] || !x[q]) return HZ_ERR_INVALID;
+    if (ops[q]->stream != s) return HZ_ERR_INVALID;
+    if (!is_device_ptr(b[q]) || !is_device_ptr(x[q]) || (x0 && x0[q] && !is_device_ptr(x0[q])))
+      return HZ_ERR_INVALID;
+    for (int r = 0; r < q; ++r)
+      if (ops[r] == ops[q]) return HZ_ERR_INVALID;  // each system needs its own work vectors
+    if (ops[q]->g.nx % 4) vec = 1;
+  }
+  std::vector<SysDesc> sys(nsys);
+  int64_t item0 = 0;
+  for (int q = 0; q < nsys; ++q) {
+    hz_op op = ops[q];
+    const int64_t ni = (op->g.ncol / vec + kBS - 1) / kBS;
+    sys[q] = SysDesc{op->g, bands_of<float>(op), op->w32, op->ctl, item0, ni};
+    item0 += ni;
+  }
+  hz_op o0 = ops[0];
+  CK(cudaEventRecord(o0->ev0, s));
+  std::vector<const double*> cur(nsys, nullptr);
+  std::vector<double> R(nsys, 0.0), Rprev(nsys, 0.0), bb(nsys, 0.0), scaled(nsys, 0.0);
+  std::vector<int> outer(nsys, 0), inner(nsys, 0), rst(nsys, 0), status(nsys, HZ_OK), done(nsys, 0), stall(nsys, 0);
+  long long launches = 0;
+  for (int q = 0; q < nsys; ++q) {
+    hz_op op = ops[q];
+    Ctl* cfg = op->cfg_h;
+    memset(cfg, 0, sizeof(Ctl));
+    cfg->eta = eta;
+    cfg->maxit = p.max_inner;
+    cfg->restart_every = p.restart;
+    cfg->body_limit = 4 * p.max_inner + 64;
+    cfg->xzero = 1;
+    cfg->state = ST_CONVERGED;
+    CK(cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    if (x0 && x0[q]) cur[q] = x0[q];
+    CK(launch_residual<float>(op->g, op->A7, op->invc, b[q], cur[q], nullptr, nullptr, op->w32.rhs, nullptr, 0,
+                              op->ctl, op->red, op->L));
+    ++launches;
+    CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int q = 0; q < nsys; ++q) {
+    const Ctl& rp = *ops[q]->rep_h;
+    bb[q] = rp.res_bb;
+    R[q] = bb[q] > 0.0 ? std::sqrt(rp.res_rr / bb[q]) : std::sqrt(rp.res_rr);
+    Rprev[q] = R[q];
+  }
+  int batch_status = HZ_OK;
+  for (;;) {
+    // decide which systems go on
+    int active = 0;
+    for (int q = 0; q < nsys; ++q) {
+      if (done[q]) continue;
+      if (!std::isfinite(R[q])) {
+        status[q] = HZ_ERR_NONFINITE;
+        done[q] = 1;
+      } else if (R[q] <= p.tol) {
+        status[q] = HZ_OK;
+        done[q] = 1;
+      } else if (outer[q] >= p.max_outer) {
+        status[q] = HZ_ERR_NOT_CONVERGED;
+        done[q] = 1;
+      } else {
+        ++active;
+      }
+    }
+    if (!active) break;
+    // finished systems sit out the inner solve
+    for (int q = 0; q < nsys; ++q) {
+      if (!done[q]) continue;
+      ops[q]->cfg_h->state = ST_CONVERGED;
+      CK(cudaMemcpyAsync(&ops[q]->ctl->state, &ops[q]->cfg_h->state, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    int err = 0;
+    int* err_h = &o0->err_h[0];
+    CK(launch_batched(sys.data(), nsys, vec, 4 * p.max_inner + 64, g_batch_timeout_ns, g_batch_leave_block, s, err_h,
+                      o0->sms));
+    err = *err_h;
+    ++launches;
+    if (err) {
+      snprintf(g_err, sizeof(g_err), "batched inner solve: a grid-barrier wait exceeded %lld ns", g_batch_timeout_ns);
+      batch_status = HZ_ERR_TIMEOUT;
+      for (int q = 0; q < nsys; ++q)
+        if (!done[q]) {
+          status[q] = HZ_ERR_TIMEOUT;
+          done[q] = 1;
+        }
+      break;
+    }
+    for (int q = 0; q < nsys; ++q) {
+      if (done[q]) continue;
+      hz_op op = ops[q];
+      double* XA = x[q];
+      double* next = (cur[q] == XA) ? op->xscr : XA;
+      CK(launch_residual<float>(op->g, op->A7, op->invc, b[q], cur[q], next, op->w32.x, op->w32.rhs, nullptr, 0,
+                                op->ctl, op->red, op->L));
+      ++launches;
+      CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+      cur[q] = next;
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < nsys; ++q) {
+      if (done[q]) continue;
+      const Ctl& rp = *ops[q]->rep_h;
+      inner[q] += rp.last_iter;
+      rst[q] += rp.last_restarts;
+      scaled[q] = rp.last_bnorm2 > 0.0 ? std::sqrt(rp.last_rnorm2 / rp.last_bnorm2) : 0.0;
+      ++outer[q];
+      R[q] = bb[q] > 0.0 ? std::sqrt(rp.res_rr / bb[q]) : std::sqrt(rp.res_rr);
+      if (rp.last_state == ST_NONFINITE) {
+        status[q] = HZ_ERR_NONFINITE;
+        done[q] = 1;
+        continue;
+      }
+      if (R[q] > 0.5 * Rprev[q]) {
+        if (++stall[q] >= 2 && R[q] > p.tol) {
+          status[q] = HZ_ERR_NOT_CONVERGED;
+          done[q] = 1;
+        }
+      } else {
+        stall[q] = 0;
+      }
+      Rprev[q] = R[q];
+    }
+  }
+  // deliver every x into the caller's buffer
+  for (int q = 0; q < nsys; ++q) {
+    const size_t bytes = sizeof(double) * (size_t)ops[q]->g.n;
+    if (cur[q] == nullptr)
+      CK(cudaMemsetAsync(x[q], 0, bytes, s));
+    else if (cur[q] != x[q])
+      CK(cudaMemcpyAsync(x[q], cur[q], bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaEventRecord(o0->ev1, s));
+  CK(cudaEventSynchronize(o0->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, o0->ev0, o0->ev1);
+  int worst = batch_status;
+  for (int q = 0; q < nsys; ++q) {
+    if (status[q] != HZ_OK && worst == HZ_OK) worst = status[q];
+    if (infos) {
+      infos[q].status = status[q];
+      infos[q].outer_iters = outer[q];
+      infos[q].inner_iters = inner[q];
+      infos[q].restarts = rst[q];
+      infos[q].fallbacks = 0;
+      infos[q].true_rel_residual = R[q];
+      infos[q].scaled_rel_residual = scaled[q];
+      infos[q].seconds = ms * 1e-3;
+      infos[q].kernel_launches = launches;
+    }
+  }
+  return worst;
 }
 
 }  // extern "C"

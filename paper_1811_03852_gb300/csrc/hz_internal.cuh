@@ -200,4 +200,22 @@ cudaError_t launch_residual(const Grid& g, const double* A7, const double* invc,
                             double* x, const D* delta, D* rhs_out, double* r_out, int mode, Ctl* ctl, Red red,
                             const Launch& L);
 
+// ---- batched persistent solve (hz_batched.cu) ----
+constexpr int kMaxSys = 64;
+struct SysDesc {
+  Grid g;
+  Bands<float> a;
+  Vecs<float> w;
+  Ctl* ctl;
+  int64_t item0;   // first global work item of this system (item = kBS column groups)
+  int64_t nitems;  // items of this system
+};
+// Runs the inner FP32 BiCGStab of nsys systems to completion in one
+// cooperative launch and waits for it; *err_h receives the device error word
+// (bit 0: a grid-barrier wait exceeded timeout_ns).  vec = 4 needs nx % 4 == 0
+// for every system, else pass 1.  leave_block >= 0 makes that block leave
+// after its first barrier (test hook for the bounded wait).
+cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loops, long long timeout_ns,
+                           int leave_block, cudaStream_t stream, int* err_h, int sms);
+
 }  // namespace hz

@@ -84,6 +84,83 @@ __device__ __forceinline__ T ahat_point(const Grid& g, const Bands<T>& a, const 
   return y;
 }
 
+// ---- control steps (run by one thread once a reduction is complete; shared by
+// the single-system kernels and the batched persistent kernel) ----------------
+// restart (Sec. 4): rr = ||r||^2 of the recomputed residual, r0 = r
+__device__ __forceinline__ void fin_restart(Ctl* ctl, double rr) {
+  ctl->rho = rr;
+  ctl->r0norm2 = rr;
+  ctl->rnorm2 = rr;
+  ctl->alpha = 1.0;
+  ctl->omega = 1.0;
+  ctl->beta = 0.0;
+  ctl->since = 0;
+  ctl->fresh = 1;
+  ctl->rsel = 1;
+  ctl->r0sel = 1;
+  ctl->state = !isfinite(rr) ? ST_NONFINITE : (rr <= ctl->stop2 ? ST_CONVERGED : ST_RUNNING);
+}
+// alpha = rho / <r0, v>; a zero or non-finite value is a breakdown: restart
+__device__ __forceinline__ void fin_alpha(Ctl* ctl, double rv) {
+  const double alpha = ctl->rho / rv;
+  if (rv == 0.0 || !isfinite(alpha)) {
+    ctl->iter += 1;
+    ctl->restarts += 1;
+    ctl->state = ctl->iter >= ctl->maxit ? ST_MAXIT : ST_RESTART;
+  } else {
+    ctl->alpha = alpha;
+  }
+}
+// ||s||^2: half-step exit when it meets the tolerance
+__device__ __forceinline__ void fin_snorm(Ctl* ctl, double ss) {
+  ctl->snorm2 = ss;
+  if (!isfinite(ss))
+    ctl->state = ST_NONFINITE;
+  else if (ss <= ctl->stop2)
+    ctl->state = ST_HALF;
+}
+// omega = <t, s> / <t, t>
+__device__ __forceinline__ void fin_omega(Ctl* ctl, double ts, double tt) {
+  const double omega = tt > 0.0 ? ts / tt : 0.0;
+  if (!isfinite(omega)) ctl->state = ST_NONFINITE;
+  ctl->omega = omega;
+}
+// end of an iteration: stop, restart (every restart_every iterations, Sec. 4,
+// or on breakdown) or beta = (rho'/rho)(alpha/omega).  Returns the new state.
+__device__ __forceinline__ int fin_iteration(Ctl* ctl, bool half, double rho1, double rr) {
+  int st;
+  ctl->iter += 1;
+  ctl->since += 1;
+  ctl->xzero = 0;
+  if (half) {
+    ctl->rnorm2 = ctl->snorm2;
+    st = ST_CONVERGED;
+  } else {
+    ctl->rnorm2 = rr;
+    ctl->rsel = 1;
+    ctl->fresh = 0;
+    if (!isfinite(rr) || !isfinite(rho1)) {
+      st = ST_NONFINITE;
+    } else if (rr <= ctl->stop2) {
+      st = ST_CONVERGED;
+    } else if (ctl->iter >= ctl->maxit) {
+      st = ST_MAXIT;
+    } else if (ctl->omega == 0.0 || ctl->since >= ctl->restart_every ||
+               fabs(rho1) <= 1e-14 * sqrt(ctl->r0norm2 * rr)) {
+      st = ST_RESTART;
+      ctl->restarts += 1;
+    } else {
+      ctl->beta = (rho1 / ctl->rho) * (ctl->alpha / ctl->omega);
+      ctl->rho = rho1;
+      st = ST_RUNNING;
+    }
+  }
+  const int hi = ctl->hist_off + ctl->iter - 1;
+  if (ctl->hist && hi < ctl->hist_cap) ctl->hist[hi] = ctl->bnorm2 > 0.0 ? sqrt(ctl->rnorm2 / ctl->bnorm2) : 0.0;
+  ctl->state = st;
+  return st;
+}
+
 // Restart of one column (rare, kept out of line): r = rhs - Ahat x, r0 = r,
 // p = r, ph = T^-1 p.  Returns the column's <r, r>.  x is read-only here.
 template <typename T>
@@ -141,20 +218,7 @@ __global__ void __launch_bounds__(kBS, 4) k_pre_start(Grid g, Bands<T> a, Vecs<T
   }
   if (restart) {
     double vv[1] = {acc}, out[1];
-    if (grid_reduce<1>(vv, red, out)) {
-      const double rr = out[0];
-      ctl->rho = rr;
-      ctl->r0norm2 = rr;
-      ctl->rnorm2 = rr;
-      ctl->alpha = 1.0;
-      ctl->omega = 1.0;
-      ctl->beta = 0.0;
-      ctl->since = 0;
-      ctl->fresh = 1;
-      ctl->rsel = 1;
-      ctl->r0sel = 1;
-      ctl->state = !isfinite(rr) ? ST_NONFINITE : (rr <= ctl->stop2 ? ST_CONVERGED : ST_RUNNING);
-    }
+    if (grid_reduce<1>(vv, red, out)) fin_restart(ctl, out[0]);
   }
 }
 
@@ -174,26 +238,10 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs
     hmv_vec<T, V, U, MODE>(g, q * V, a, cen, x, y, r0, acc0, acc1);
   if (MODE == 0) {
     double vv[1] = {acc0}, out[1];
-    if (grid_reduce<1>(vv, red, out)) {
-      const double rv = out[0];
-      const double alpha = ctl->rho / rv;
-      if (rv == 0.0 || !isfinite(alpha)) {
-        // breakdown of the Lanczos part: count the iteration and restart
-        ctl->iter += 1;
-        ctl->restarts += 1;
-        ctl->state = ctl->iter >= ctl->maxit ? ST_MAXIT : ST_RESTART;
-      } else {
-        ctl->alpha = alpha;
-      }
-    }
+    if (grid_reduce<1>(vv, red, out)) fin_alpha(ctl, out[0]);
   } else {
     double vv[2] = {acc0, acc1}, out[2];
-    if (grid_reduce<2>(vv, red, out)) {
-      const double ts = out[0], tt = out[1];
-      const double omega = tt > 0.0 ? ts / tt : 0.0;
-      if (!isfinite(omega)) ctl->state = ST_NONFINITE;
-      ctl->omega = omega;
-    }
+    if (grid_reduce<2>(vv, red, out)) fin_omega(ctl, out[0], out[1]);
   }
 }
 
@@ -212,14 +260,7 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_s(Grid g, Bands<T> a, V
     acc += src.acc;
   }
   double vv[1] = {acc}, out[1];
-  if (grid_reduce<1>(vv, red, out)) {
-    const double ss = out[0];
-    ctl->snorm2 = ss;
-    if (!isfinite(ss))
-      ctl->state = ST_NONFINITE;
-    else if (ss <= ctl->stop2)
-      ctl->state = ST_HALF;
-  }
+  if (grid_reduce<1>(vv, red, out)) fin_snorm(ctl, out[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -333,37 +374,7 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
   }
   double vv[2] = {acc0, acc1}, out[2];
   if (grid_reduce<2>(vv, red, out)) {
-    int st;
-    ctl->iter += 1;
-    ctl->since += 1;
-    ctl->xzero = 0;
-    if (half) {
-      ctl->rnorm2 = ctl->snorm2;
-      st = ST_CONVERGED;
-    } else {
-      const double rho1 = out[0], rr = out[1];
-      ctl->rnorm2 = rr;
-      ctl->rsel = 1;
-      ctl->fresh = 0;
-      if (!isfinite(rr) || !isfinite(rho1)) {
-        st = ST_NONFINITE;
-      } else if (rr <= ctl->stop2) {
-        st = ST_CONVERGED;
-      } else if (ctl->iter >= ctl->maxit) {
-        st = ST_MAXIT;
-      } else if (ctl->omega == 0.0 || ctl->since >= ctl->restart_every ||
-                 fabs(rho1) <= 1e-14 * sqrt(ctl->r0norm2 * rr)) {
-        st = ST_RESTART;
-        ctl->restarts += 1;
-      } else {
-        ctl->beta = (rho1 / ctl->rho) * (ctl->alpha / ctl->omega);
-        ctl->rho = rho1;
-        st = ST_RUNNING;
-      }
-    }
-    const int hi = ctl->hist_off + ctl->iter - 1;
-    if (ctl->hist && hi < ctl->hist_cap) ctl->hist[hi] = ctl->bnorm2 > 0.0 ? sqrt(ctl->rnorm2 / ctl->bnorm2) : 0.0;
-    ctl->state = st;
+    const int st = fin_iteration(ctl, half, out[0], out[1]);
     if (use_cond) cudaGraphSetConditional(cond, (st == ST_RUNNING || st == ST_RESTART) ? 1u : 0u);
   }
 }

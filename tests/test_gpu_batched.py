@@ -1,0 +1,123 @@
+"""Batched persistent solve (many uneven systems, one cooperative launch per refinement step).
+
+Each system of a batch must reach the true FP64 residual 1e-8 (recomputed by
+the oracle) and agree with its own single-system solve to 1e-6 (relative 2-norm).
+The bounded grid-barrier wait must turn a block that leaves into HZ_ERR_TIMEOUT.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _systems(specs, z_unit="m"):
+    out = []
+    for (nx, ny, nz, sc, sr) in specs:
+        A = gen.make_operator(nx, ny, nz, sc, z_unit=z_unit)
+        b = gen.make_rhs(nx, ny, nz, sr)
+        out.append((A, b))
+    return out
+
+
+def _batched(systems, **kw):
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    ops = [hz.Operator(A) for A, _ in systems]
+    bs = [dev(b.reshape(-1)) for _, b in systems]
+    xs = [torch.empty(b.size, dtype=torch.float64, device="cuda") for _, b in systems]
+    infos = hz.solve_batched(ops, bs, xs, **kw)
+    return [host(x).reshape(b.shape) for x, (_, b) in zip(xs, systems)], infos, ops
+
+
+@pytest.mark.parametrize("z_unit", ["radius", "m"])
+def test_batched_uneven_matches_single_solves(z_unit):
+    import torch
+
+    specs = [(96, 72, 20, 100 + 2 * i, 101 + 2 * i) if i % 3 == 0 else
+             (64, 48, 20, 100 + 2 * i, 101 + 2 * i) if i % 3 == 1 else
+             (32, 24, 20, 100 + 2 * i, 101 + 2 * i) for i in range(7)]
+    systems = _systems(specs, z_unit)
+    xs, infos, ops = _batched(systems)
+    for (A, b), x, info, op in zip(systems, xs, infos, ops):
+        assert info["status"] == 0, info
+        _, rn = oracle.residual(A, b, x)
+        assert rn / np.linalg.norm(b) <= 1e-8
+        xd = torch.empty(b.size, dtype=torch.float64, device="cuda")
+        single = op.solve(dev(b), xd)
+        xsgl = host(xd).reshape(b.shape)
+        assert np.linalg.norm(x - xsgl) / np.linalg.norm(xsgl) <= 1e-6
+        assert single["status"] == 0
+
+
+def test_batched_scalar_path_and_warm_start():
+    # nx not a multiple of 4 -> one column per thread; x0 given for one system
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    systems = _systems([(37, 23, 9, 5, 6), (96, 72, 20, 7, 8), (6, 5, 4, 9, 10)])
+    ops = [hz.Operator(A) for A, _ in systems]
+    bs = [dev(b.reshape(-1)) for _, b in systems]
+    xs = [torch.empty(b.size, dtype=torch.float64, device="cuda") for _, b in systems]
+    x0s = [None, torch.zeros(systems[1][1].size, dtype=torch.float64, device="cuda"), None]
+    infos = hz.solve_batched(ops, bs, xs, x0s=x0s)
+    for (A, b), x, info in zip(systems, xs, infos):
+        _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+        assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8
+    # warm start from the converged x: nothing left to do
+    infos2 = hz.solve_batched(ops, bs, xs, x0s=[x.clone() for x in xs])
+    assert all(i["status"] == 0 and i["outer_iters"] == 0 for i in infos2)
+
+
+def test_batched_barrier_timeout_is_reported_not_hung():
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    systems = _systems([(64, 48, 20, 11, 12), (32, 24, 20, 13, 14)])
+    ops = [hz.Operator(A) for A, _ in systems]
+    bs = [dev(b.reshape(-1)) for _, b in systems]
+    xs = [torch.empty(b.size, dtype=torch.float64, device="cuda") for _, b in systems]
+    try:
+        hz.batched_debug(timeout_ns=200_000_000, leave_block=1)
+        st, infos = hz.solve_batched(ops, bs, xs, raise_on_error=False)
+    finally:
+        hz.batched_debug(0, -1)
+    assert st == hz.HZ_ERR_TIMEOUT and all(i["status"] == hz.HZ_ERR_TIMEOUT for i in infos)
+    # the context is still usable
+    infos = hz.solve_batched(ops, bs, xs)
+    assert all(i["status"] == 0 for i in infos)
+
+
+def test_batched_rejects_bad_arguments():
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    (A, b), = _systems([(8, 6, 5, 1, 2)])
+    op = hz.Operator(A)
+    bd = dev(b.reshape(-1))
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    st, _ = hz.solve_batched([op, op], [bd, bd], [x, x], raise_on_error=False)
+    assert st == hz.HZ_ERR_INVALID  # the same operator twice
+    st, _ = hz.solve_batched([op], [bd], [x], mode=hz.HZ_MODE_FP64, raise_on_error=False)
+    assert st == hz.HZ_ERR_UNSUPPORTED
+
+
+def test_batched_32_uneven_systems_full_size():
+    # the 32-system batch (grids 192x144, 320x240, 640x480, 70 levels): every
+    # system's true residual recomputed by the oracle over all points
+    specs = [gen.batched_spec(i) for i in range(32)]
+    specs = [(s["nx"], s["ny"], s["nz"], s["seed_coef"], s["seed_rhs"]) for s in specs]
+    systems = _systems(specs, z_unit="radius")
+    xs, infos, _ = _batched(systems)
+    for (A, b), x, info in zip(systems, xs, infos):
+        assert info["status"] == 0, info
+        _, rn = oracle.residual(A, b, x)
+        assert rn / np.linalg.norm(b) <= 1e-8

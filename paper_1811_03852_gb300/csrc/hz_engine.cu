@@ -95,6 +95,7 @@ struct hz_op_s {
   double p_ms[HZ_NUM_KERNELS] = {};
   double p_bytes[HZ_NUM_KERNELS] = {};
   long long launches = 0;  // kernels launched by the last solve
+  FgmWs fgm;               // flexible GMRES workspace (allocated on first use)
 };
 
 namespace {
@@ -275,6 +276,110 @@ int run_inner(hz_op op, int use_graph, int max_inner) {
   return HZ_OK;
 }
 
+// ---- flexible GMRES(m) inner solve (FP32 vectors, FP64 scalars) ------------
+int ensure_fgm(hz_op op, int m) {
+  FgmWs& W = op->fgm;
+  if (W.base && W.m >= m) return HZ_OK;
+  if (W.base) cudaFree(W.base), W.base = nullptr;
+  if (W.vptr) cudaFree(W.vptr), W.vptr = nullptr;
+  const int64_t s = pad64(op->g.n);
+  CK(cudaMalloc(&W.base, sizeof(float) * (size_t)s * (2 * m + 2)));
+  CK(cudaMalloc(&W.vptr, sizeof(float*) * (2 * m + 1)));
+  if (!W.part) CK(cudaMalloc(&W.part, sizeof(double) * (size_t)kMaxGrid * (kMaxFgm + 1)));
+  if (!W.st) CK(cudaMalloc(&W.st, sizeof(FgmState)));
+  std::vector<float*> ptrs(2 * m + 1);
+  for (int q = 0; q < 2 * m + 1; ++q) ptrs[q] = W.base + (int64_t)q * s;
+  W.w = W.base + (int64_t)(2 * m + 1) * s;
+  CK(cudaMemcpy(W.vptr, ptrs.data(), sizeof(float*) * (2 * m + 1), cudaMemcpyHostToDevice));
+  W.m = m;
+  return HZ_OK;
+}
+
+// One inner FGMRES solve of Ahat d = rhs (the right-hand side and its norm come
+// from the residual kernel) to relative tolerance eta; d is left in w32.x and
+// the control block is updated as the BiCGStab loop would leave it.
+int run_fgmres(hz_op op, int m, int max_inner, double eta) {
+  CKS(ensure_fgm(op, m));
+  FgmWs& W = op->fgm;
+  const int64_t n = op->g.n;
+  const Launch& L = op->L;
+  cudaStream_t s = op->stream;
+  const Bands<float> a = bands_of<float>(op);
+  const Vecs<float>& w32 = op->w32;
+  float* const* V = W.vptr;
+  float* const* Z = W.vptr + (W.m + 1);
+  const int64_t vs = pad64(n);
+  auto Vh = [&](int q) { return W.base + (int64_t)q * vs; };
+  auto Zh = [&](int q) { return W.base + (int64_t)(W.m + 1 + q) * vs; };
+  CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double beta0 = std::sqrt(op->rep_h->bnorm2);
+  int total = 0, cycles = 0, state = ST_CONVERGED;
+  bool xzero = true;
+  double resid = beta0;
+  if (beta0 > 0.0 && std::isfinite(beta0)) {
+    state = ST_MAXIT;
+    for (;;) {
+      if (cycles == 0) {
+        CK(fgm_start(W.st, &op->ctl->bnorm2, s));
+        CK(fgm_scale(n, w32.rhs, Vh(0), &op->ctl->bnorm2, 1, L));
+      } else {
+        CK(fgm_residual(W, op->g, a, w32.rhs, w32.x, Vh(0), &W.st->r2, L));
+        CK(fgm_start(W.st, &W.st->r2, s));
+        CK(fgm_scale(n, Vh(0), Vh(0), &W.st->r2, 1, L));
+      }
+      ++cycles;
+      int k = 0;
+      bool conv = false;
+      for (int j = 0; j < W.m && j < m; ++j) {
+        CK(launch_tinv<float>(op->g, a, Vh(j), Zh(j), L));        // z_j = M(v_j)
+        CK(launch_matvec_hat<float>(op->g, a, Zh(j), W.w, L));    // w = Ahat z_j
+        CK(fgm_multidot(W, n, V, j + 1, W.w, W.st->h1, L));       // CGS, first pass
+        CK(fgm_update(W, n, V, j + 1, W.st->h1, W.w, nullptr, L));
+        CK(fgm_multidot(W, n, V, j + 1, W.w, W.st->h2, L));       // second pass
+        CK(fgm_update(W, n, V, j + 1, W.st->h2, W.w, &W.st->wn2, L));
+        CK(fgm_step(W.st, j, s));
+        CK(fgm_scale(n, W.w, Vh(j + 1), &W.st->wn2, 1, L));       // v_(j+1) = w / ||w||
+        ++total;
+        k = j + 1;
+        CK(cudaMemcpyAsync(&op->rep_h->snorm2, &W.st->resid, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        resid = op->rep_h->snorm2;
+        if (!std::isfinite(resid)) {
+          state = ST_NONFINITE;
+          break;
+        }
+        if (resid <= eta * beta0) {
+          conv = true;
+          break;
+        }
+        if (total >= max_inner) break;
+      }
+      if (state == ST_NONFINITE) break;
+      CK(fgm_solve_update(W.st, n, Z, k, w32.x, xzero ? 1 : 0, L));
+      xzero = false;
+      if (conv) {
+        state = ST_CONVERGED;
+        break;
+      }
+      if (total >= max_inner) break;
+    }
+  }
+  // leave the control block as the BiCGStab loop would
+  CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  Ctl c = *op->rep_h;
+  c.iter = total;
+  c.restarts = cycles > 0 ? cycles - 1 : 0;
+  c.state = state;
+  c.xzero = xzero ? 1 : 0;
+  c.rnorm2 = resid * resid;
+  *op->cfg_h = c;
+  CK(cudaMemcpyAsync(op->ctl, op->cfg_h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return HZ_OK;
+}
+
 int do_setup(hz_op op, const double* coeffs) {
   const int64_t n = op->g.n;
   const bool dev = is_device_ptr(coeffs);
@@ -303,6 +408,10 @@ void free_op(hz_op op) {
     if (gs.graph) cudaGraphDestroy(gs.graph);
   }
   for (void* p : op->allocs) cudaFree(p);
+  if (op->fgm.base) cudaFree(op->fgm.base);
+  if (op->fgm.vptr) cudaFree(op->fgm.vptr);
+  if (op->fgm.part) cudaFree(op->fgm.part);
+  if (op->fgm.st) cudaFree(op->fgm.st);
   if (op->cfg_h) cudaFreeHost(op->cfg_h);
   if (op->rep_h) cudaFreeHost(op->rep_h);
   if (op->err_h) cudaFreeHost(op->err_h);
@@ -528,7 +637,10 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     hz_default_params(&p);
   if (!(p.tol > 0.0) || p.max_outer < 0 || p.max_inner < 1 || p.restart < 1) return HZ_ERR_INVALID;
   if (p.mode != HZ_MODE_FP64 && p.mode != HZ_MODE_MIXED_IR) return HZ_ERR_INVALID;
-  if (p.krylov != HZ_KRYLOV_BICGSTAB || p.precond != HZ_PRE_TRI) return HZ_ERR_UNSUPPORTED;
+  if (p.krylov != HZ_KRYLOV_BICGSTAB && p.krylov != HZ_KRYLOV_FGMRES) return HZ_ERR_INVALID;
+  if (p.krylov == HZ_KRYLOV_FGMRES && (p.mode != HZ_MODE_MIXED_IR || p.fgmres_m < 1 || p.fgmres_m > kMaxFgm))
+    return HZ_ERR_UNSUPPORTED;
+  if (p.precond != HZ_PRE_TRI) return HZ_ERR_UNSUPPORTED;
   const bool fp32 = (p.mode == HZ_MODE_MIXED_IR);
   const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : 0.1 * p.tol);
   const int64_t n = op->g.n;
@@ -618,7 +730,9 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (!std::isfinite(R)) { status = HZ_ERR_NONFINITE; break; }
     if (R <= p.tol) { status = HZ_OK; break; }
     if (outer >= p.max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
-    if (fp32)
+    if (p.krylov == HZ_KRYLOV_FGMRES)
+      CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta));
+    else if (fp32)
       CKS(run_inner<float>(op, p.use_graph, p.max_inner));
     else
       CKS(run_inner<double>(op, p.use_graph, p.max_inner));

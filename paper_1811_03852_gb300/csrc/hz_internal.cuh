@@ -200,6 +200,34 @@ cudaError_t launch_residual(const Grid& g, const double* A7, const double* invc,
                             double* x, const D* delta, D* rhs_out, double* r_out, int mode, Ctl* ctl, Red red,
                             const Launch& L);
 
+// ---- flexible GMRES (hz_fgmres.cu) ----
+constexpr int kMaxFgm = 64;  // largest restart length
+struct FgmState {            // small dense state of FGMRES, FP64, device memory
+  double H[(kMaxFgm + 1) * kMaxFgm];  // Hessenberg, column-major, then R after the rotations
+  double cs[kMaxFgm], sn[kMaxFgm], g[kMaxFgm + 1], y[kMaxFgm];
+  double h1[kMaxFgm + 1], h2[kMaxFgm + 1];  // the two Gram-Schmidt passes
+  double wn2, beta, resid, wnorm, r2;
+};
+struct FgmWs {
+  int m = 0;
+  float* base = nullptr;    // V_0..V_m, Z_0..Z_(m-1), w: (2m+2) vectors
+  float** vptr = nullptr;   // device array of those 2m+1 vector pointers (V then Z)
+  float* w = nullptr;
+  double* part = nullptr;   // [grid][kMaxFgm+1] partial sums
+  FgmState* st = nullptr;   // device
+};
+cudaError_t fgm_multidot(const FgmWs& W, int64_t n, float* const* Vdev, int nv, const float* w, double* dst,
+                         const Launch& L);
+cudaError_t fgm_update(const FgmWs& W, int64_t n, float* const* Vdev, int nv, const double* c, float* w,
+                       double* nrm2_dst, const Launch& L);
+cudaError_t fgm_scale(int64_t n, const float* x, float* y, const double* s, int inv_sqrt, const Launch& L);
+cudaError_t fgm_step(FgmState* st, int j, cudaStream_t s);
+cudaError_t fgm_solve_update(FgmState* st, int64_t n, float* const* Zdev, int k, float* x, int xzero,
+                             const Launch& L);
+cudaError_t fgm_start(FgmState* st, const double* nrm2, cudaStream_t s);
+cudaError_t fgm_residual(const FgmWs& W, const Grid& g, const Bands<float>& a, const float* rhs, const float* x,
+                         float* r, double* nrm2_dst, const Launch& L);
+
 // ---- batched persistent solve (hz_batched.cu) ----
 constexpr int kMaxSys = 64;
 struct SysDesc {

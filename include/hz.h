@@ -166,6 +166,59 @@ int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const d
    returns HZ_ERR_TIMEOUT without hanging the GPU (-1: off). */
 int hz_batched_debug(long long timeout_ns, int leave_block);
 
+/* ---- learned preconditioner stage ----------------------------------------
+ * Not in the paper: an extra preconditioner stage inside the flexible solver.
+ * After the paper's tridiagonal stage z1 = T^-1 v, the remaining residual
+ * e1 = v - D^-1 A z1 is fed to a small 3-D conv net whose output corrects z1:
+ *   z = z1 + sigma * NN(e1 / sigma),  sigma = rms(e1).
+ * NN: four convolutions 1 -> 16 -> 16 -> 16 -> 1 channels, kernels 3 (k) x
+ * 3 (j) x 3 (i), exact-erf GELU after the first three; cross-correlation
+ * y[o,p] = b[o] + sum_{c,tap} W[o][c][tap] x[c,p+tap], zero padding in k and
+ * j, periodic in i on full fields (zero padding for training crops).  BF16
+ * weights and activations, FP32 accumulation; the 16 -> 16 layers on tensor
+ * cores.  Parameters: one flat FP32 vector, per layer W[Cout][Cin][3][3][3]
+ * (tap order dk, dj, di = -1..1 each, last fastest) then b[Cout];
+ * hz_nn_num_params() values.  Training: relative MSE ||y - t||^2 / ||t||^2
+ * over the interior of each crop (border points excluded), Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) on FP32 master weights.  All pointers below are
+ * device pointers unless noted.
+ */
+typedef struct hz_nn_s* hz_nn;
+int hz_nn_num_params(void);
+const char* hz_nn_last_error(void);
+int hz_nn_create(void* stream, hz_nn* out); /* zero parameters */
+int hz_nn_destroy(hz_nn nn);
+/* params: host or device, hz_nn_num_params() floats; resets the Adam state */
+int hz_nn_set_params(hz_nn nn, const float* params);
+int hz_nn_get_params(hz_nn nn, float* out /* host or device */);
+/* y = NN(x) on an nx x ny x nz field (ny = several crops of seg_ny rows
+   stacked along j, or seg_ny = ny); periodic: wrap in i.  zout (may be NULL):
+   receives the FP32 pre-activations z1, z2, z3 as [3][n][16]. */
+int hz_nn_forward(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, const float* x, float* y, float* zout);
+/* gradient of the masked relative MSE of NN(x) against t (border points of
+   every crop excluded in i and j); grad: host or device doubles, loss: host */
+int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
+                   const float* t, double* grad, double* loss);
+/* one Adam step on that loss (loss: host, may be NULL) */
+int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
+                     const float* t, double lr, double* loss);
+/* ncrop crops of cx x cy columns, all levels, from two fields [nz][ny][nx]:
+   crop q starts at column (corners[2q], corners[2q+1]) (host ints; i wraps,
+   rows outside the grid are zero); outputs [nz][ncrop*cy][cx] (crops stacked
+   along j).  The random corners are an input. */
+int hz_nn_crops(int nx, int ny, int nz, const float* fa, const float* fb, int ncrop, int cx, int cy,
+                const int* corners, float* oa, float* ob, void* stream);
+/* checkpoint: FP32 master weights, Adam moments and step (host file) */
+int hz_nn_save(hz_nn nn, const char* path);
+int hz_nn_load(hz_nn nn, const char* path);
+/* attach a network to an operator for params->precond = HZ_PRE_TRI_NN (NULL detaches) */
+int hz_op_set_nn(hz_op op, hz_nn nn);
+/* Training pair of an iterate x_k with exact solution x_star (all FP64, n):
+   r = D^-1 (b - A x_k), e = x_star - x_k, z1 = T^-1 r, e1 = r - D^-1 A z1;
+   in = e1 / sigma, target = (e - z1) / sigma, sigma = rms(e1) (host out). */
+int hz_nn_make_pair(hz_op op, const double* b, const double* xk, const double* x_star, float* in, float* target,
+                    double* sigma);
+
 /* Inner recursive residual history of the last solve with record_history=1:
    copies up to cap values into hist (host) and returns how many. */
 int hz_get_history(hz_op op, double* hist, int cap);

@@ -324,3 +324,132 @@ def dot_noalloc(x, y, out, prec=None, stream=None):
 
 def version() -> int:
     return load().hz_version()
+
+
+# ---- learned preconditioner stage ---------------------------------------------------
+def _nn_sigs(L):
+    i32, dbl, pv = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "hz_nn_num_params": (i32, []),
+        "hz_nn_last_error": (ctypes.c_char_p, []),
+        "hz_nn_create": (i32, [pv, P(pv)]),
+        "hz_nn_destroy": (i32, [pv]),
+        "hz_nn_set_params": (i32, [pv, pv]),
+        "hz_nn_get_params": (i32, [pv, pv]),
+        "hz_nn_forward": (i32, [pv, i32, i32, i32, i32, i32, pv, pv, pv]),
+        "hz_nn_gradient": (i32, [pv, i32, i32, i32, i32, i32, i32, pv, pv, pv, P(dbl)]),
+        "hz_nn_train_step": (i32, [pv, i32, i32, i32, i32, i32, i32, pv, pv, dbl, P(dbl)]),
+        "hz_nn_crops": (i32, [i32, i32, i32, pv, pv, i32, i32, i32, pv, pv, pv, pv]),
+        "hz_nn_save": (i32, [pv, ctypes.c_char_p]),
+        "hz_nn_load": (i32, [pv, ctypes.c_char_p]),
+        "hz_op_set_nn": (i32, [pv, pv]),
+        "hz_nn_make_pair": (i32, [pv, pv, pv, pv, pv, pv, P(dbl)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def _nnlib():
+    L = load()
+    if not getattr(L, "_nn_ready", False):
+        _nn_sigs(L)
+        L._nn_ready = True
+    return L
+
+
+def _nn_check(st, where):
+    if st != HZ_OK:
+        L = _nnlib()
+        raise HzError(st, f"{where}: {L.hz_nn_last_error().decode()}")
+
+
+class Net:
+    """The learned preconditioner stage (hz_nn): 4-layer 3-D conv net, BF16 weights and activations."""
+
+    def __init__(self, params=None, stream=None):
+        L = _nnlib()
+        self._h = ctypes.c_void_p()
+        _nn_check(L.hz_nn_create(_stream_ptr(stream), ctypes.byref(self._h)), "hz_nn_create")
+        if params is not None:
+            self.set_params(params)
+
+    @staticmethod
+    def num_params():
+        return _nnlib().hz_nn_num_params()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _nnlib().hz_nn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32) if isinstance(params, np.ndarray) else params
+        _nn_check(_nnlib().hz_nn_set_params(self._h, _ptr(p)), "hz_nn_set_params")
+
+    def get_params(self):
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _nn_check(_nnlib().hz_nn_get_params(self._h, out.ctypes.data), "hz_nn_get_params")
+        return out
+
+    def forward(self, x, y, dims, seg_ny=None, periodic=True, zout=None):
+        nx, ny, nz = dims
+        _nn_check(_nnlib().hz_nn_forward(self._h, nx, ny, nz, seg_ny or ny, int(periodic), _ptr(x), _ptr(y), _ptr(zout)),
+                  "hz_nn_forward")
+
+    def gradient(self, x, t, dims, seg_ny=None, periodic=False, border=0):
+        nx, ny, nz = dims
+        g = np.empty(self.num_params(), dtype=np.float64)
+        loss = ctypes.c_double()
+        _nn_check(_nnlib().hz_nn_gradient(self._h, nx, ny, nz, seg_ny or ny, int(periodic), border, _ptr(x), _ptr(t),
+                                          g.ctypes.data, ctypes.byref(loss)), "hz_nn_gradient")
+        return g, loss.value
+
+    def train_step(self, x, t, dims, lr=1e-3, seg_ny=None, periodic=False, border=0):
+        nx, ny, nz = dims
+        loss = ctypes.c_double()
+        _nn_check(_nnlib().hz_nn_train_step(self._h, nx, ny, nz, seg_ny or ny, int(periodic), border, _ptr(x), _ptr(t),
+                                            lr, ctypes.byref(loss)), "hz_nn_train_step")
+        return loss.value
+
+    def save(self, path):
+        _nn_check(_nnlib().hz_nn_save(self._h, str(path).encode()), "hz_nn_save")
+
+    def load(self, path):
+        _nn_check(_nnlib().hz_nn_load(self._h, str(path).encode()), "hz_nn_load")
+
+
+def nn_crops(fa, fb, dims, corners, cx, cy, oa, ob, stream=None):
+    """Crops (cx x cy columns, all levels) of two fields at the given (i0, j0) corners, stacked along j."""
+    nx, ny, nz = dims
+    c = np.ascontiguousarray(np.asarray(corners, dtype=np.int32).reshape(-1))
+    _nn_check(_nnlib().hz_nn_crops(nx, ny, nz, _ptr(fa), _ptr(fb), c.size // 2, cx, cy, c.ctypes.data, _ptr(oa),
+                                   _ptr(ob), _stream_ptr(stream)), "hz_nn_crops")
+
+
+def _op_set_nn(self, net):
+    _check(_nnlib().hz_op_set_nn(self._h, net.handle if net is not None else None), "hz_op_set_nn")
+
+
+def _op_make_pair(self, b, xk, xstar, inp, tgt):
+    sig = ctypes.c_double()
+    _check(_nnlib().hz_nn_make_pair(self._h, _ptr(b), _ptr(xk), _ptr(xstar), _ptr(inp), _ptr(tgt), ctypes.byref(sig)),
+           "hz_nn_make_pair")
+    return sig.value
+
+
+Operator.set_nn = _op_set_nn
+Operator.make_pair = _op_make_pair

@@ -96,6 +96,7 @@ struct hz_op_s {
   double p_bytes[HZ_NUM_KERNELS] = {};
   long long launches = 0;  // kernels launched by the last solve
   FgmWs fgm;               // flexible GMRES workspace (allocated on first use)
+  hz_nn nn = nullptr;      // learned stage (not owned)
 };
 
 namespace {
@@ -298,8 +299,14 @@ int ensure_fgm(hz_op op, int m) {
 // One inner FGMRES solve of Ahat d = rhs (the right-hand side and its norm come
 // from the residual kernel) to relative tolerance eta; d is left in w32.x and
 // the control block is updated as the BiCGStab loop would leave it.
-int run_fgmres(hz_op op, int m, int max_inner, double eta) {
+// With use_nn the preconditioner is the learned two-stage one,
+// z = T^-1 v + sigma NN((v - Ahat T^-1 v) / sigma); it is dropped for plain
+// T^-1 (counted in *fallbacks) when the residual estimate has not halved over
+// the last 10 steps or has grown above its starting value.
+int run_fgmres(hz_op op, int m, int max_inner, double eta, bool use_nn, int* fallbacks) {
   CKS(ensure_fgm(op, m));
+  bool nn_on = use_nn && op->nn != nullptr;
+  std::vector<double> rhist;
   FgmWs& W = op->fgm;
   const int64_t n = op->g.n;
   const Launch& L = op->L;
@@ -332,7 +339,11 @@ int run_fgmres(hz_op op, int m, int max_inner, double eta) {
       int k = 0;
       bool conv = false;
       for (int j = 0; j < W.m && j < m; ++j) {
-        CK(launch_tinv<float>(op->g, a, Vh(j), Zh(j), L));        // z_j = M(v_j)
+        CK(launch_tinv<float>(op->g, a, Vh(j), Zh(j), L));        // z_j = M(v_j): T^-1 stage
+        if (nn_on) {                                                // learned stage on e1 = v_j - Ahat z1
+          CK(fgm_residual(W, op->g, a, Vh(j), Zh(j), W.w, &W.st->r2, L));
+          CKS(nn_stage_apply(op->nn, op->g, W.w, &W.st->r2, Zh(j), s));
+        }
         CK(launch_matvec_hat<float>(op->g, a, Zh(j), W.w, L));    // w = Ahat z_j
         CK(fgm_multidot(W, n, V, j + 1, W.w, W.st->h1, L));       // CGS, first pass
         CK(fgm_update(W, n, V, j + 1, W.st->h1, W.w, nullptr, L));
@@ -352,6 +363,14 @@ int run_fgmres(hz_op op, int m, int max_inner, double eta) {
         if (resid <= eta * beta0) {
           conv = true;
           break;
+        }
+        rhist.push_back(resid);
+        if (nn_on) {
+          const size_t h = rhist.size();
+          if (resid > beta0 || (h > 10 && resid > 0.5 * rhist[h - 11])) {
+            nn_on = false;  // the learned stage is not helping: plain T^-1 from here on
+            if (fallbacks) ++*fallbacks;
+          }
         }
         if (total >= max_inner) break;
       }
@@ -619,6 +638,34 @@ int hz_op_destroy(hz_op op) {
   return HZ_OK;
 }
 
+int hz_op_set_nn(hz_op op, hz_nn nn) {
+  if (!op) return HZ_ERR_INVALID;
+  op->nn = nn;
+  return HZ_OK;
+}
+
+int hz_nn_make_pair(hz_op op, const double* b, const double* xk, const double* x_star, float* in, float* target,
+                    double* sigma) {
+  if (!op || !b || !xk || !x_star || !in || !target) return HZ_ERR_INVALID;
+  CKS(ensure_fgm(op, 1));
+  const int64_t n = op->g.n;
+  cudaStream_t s = op->stream;
+  FgmWs& W = op->fgm;
+  Vecs<float>& w = op->w32;
+  // r = b - A x_k (FP64) into the refinement scratch
+  CK(launch_residual<float>(op->g, op->A7, op->invc, b, xk, nullptr, nullptr, w.rhs, op->xscr, 0, op->ctl, op->red,
+                            op->L));
+  CK(nn_pair_launch(n, op->A7, b, xk, x_star, op->xscr, w.r, w.s, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s));
+  CK(launch_tinv<float>(op->g, bands_of<float>(op), w.r, w.p, op->L));                          // z1 = T^-1 r
+  CK(fgm_residual(W, op->g, bands_of<float>(op), w.r, w.p, w.v, &W.st->r2, op->L));            // e1 = r - Ahat z1
+  CK(nn_pair_launch(n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, w.s, w.v, w.p, &W.st->r2, in, target, 1,
+                    s));
+  CK(cudaMemcpyAsync(&op->rep_h->snorm2, &W.st->r2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (sigma) *sigma = std::sqrt(op->rep_h->snorm2 / (double)n);
+  return HZ_OK;
+}
+
 int hz_op_dims(hz_op op, int* nx, int* ny, int* nz) {
   if (!op) return HZ_ERR_INVALID;
   if (nx) *nx = op->g.nx;
@@ -640,7 +687,9 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   if (p.krylov != HZ_KRYLOV_BICGSTAB && p.krylov != HZ_KRYLOV_FGMRES) return HZ_ERR_INVALID;
   if (p.krylov == HZ_KRYLOV_FGMRES && (p.mode != HZ_MODE_MIXED_IR || p.fgmres_m < 1 || p.fgmres_m > kMaxFgm))
     return HZ_ERR_UNSUPPORTED;
-  if (p.precond != HZ_PRE_TRI) return HZ_ERR_UNSUPPORTED;
+  if (p.precond != HZ_PRE_TRI && p.precond != HZ_PRE_TRI_NN) return HZ_ERR_INVALID;
+  // the learned stage is not a fixed linear operator: it needs the flexible solver and a network
+  if (p.precond == HZ_PRE_TRI_NN && (p.krylov != HZ_KRYLOV_FGMRES || !op->nn)) return HZ_ERR_UNSUPPORTED;
   const bool fp32 = (p.mode == HZ_MODE_MIXED_IR);
   const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : 0.1 * p.tol);
   const int64_t n = op->g.n;
@@ -723,7 +772,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   CKS(residual(cur, nullptr, false));
   const double bb = op->rep_h->res_bb;
   double R = bb > 0.0 ? std::sqrt(op->rep_h->res_rr / bb) : std::sqrt(op->rep_h->res_rr);
-  int outer = 0, inner_total = 0, restarts = 0, status = HZ_OK;
+  int outer = 0, inner_total = 0, restarts = 0, status = HZ_OK, fallbacks = 0;
   double scaled = 0.0, Rprev = R;
   int stall = 0;
   for (;;) {
@@ -731,7 +780,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (R <= p.tol) { status = HZ_OK; break; }
     if (outer >= p.max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
     if (p.krylov == HZ_KRYLOV_FGMRES)
-      CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta));
+      CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta, p.precond == HZ_PRE_TRI_NN, &fallbacks));
     else if (fp32)
       CKS(run_inner<float>(op, p.use_graph, p.max_inner));
     else
@@ -780,7 +829,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     info->outer_iters = outer;
     info->inner_iters = inner_total;
     info->restarts = restarts;
-    info->fallbacks = 0;
+    info->fallbacks = fallbacks;
     info->true_rel_residual = R;
     info->scaled_rel_residual = scaled;
     info->seconds = ms * 1e-3;

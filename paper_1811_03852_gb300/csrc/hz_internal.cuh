@@ -228,6 +228,14 @@ cudaError_t fgm_start(FgmState* st, const double* nrm2, cudaStream_t s);
 cudaError_t fgm_residual(const FgmWs& W, const Grid& g, const Bands<float>& a, const float* rhs, const float* x,
                          float* r, double* nrm2_dst, const Launch& L);
 
+// ---- learned stage (hz_nn.cu) ----
+// z <- z + sigma * NN(e1 / sigma), sigma = sqrt(*nrm2 / n), on a full (periodic) field
+int nn_stage_apply(hz_nn_s* nn, const Grid& g, const float* e1, const double* nrm2, float* z, cudaStream_t s);
+// training-pair helpers: stage 0: rs = r / A_C, e = xs - xk; stage 1: in = e1 / sigma, tg = (e - z1) / sigma
+cudaError_t nn_pair_launch(int64_t n, const double* A7, const double* b, const double* xk, const double* xs,
+                           const double* r, float* rs, float* e, const float* e1, const float* z1, const double* nrm2,
+                           float* in, float* tg, int stage, cudaStream_t s);
+
 // ---- batched persistent solve (hz_batched.cu) ----
 constexpr int kMaxSys = 64;
 struct SysDesc {

@@ -1,0 +1,899 @@
+// hz_nn.cu -- the learned preconditioner stage: a 4-layer 3-D conv net
+// (1 -> 16 -> 16 -> 16 -> 1 channels, 3x3x3 kernels, exact-erf GELU after the
+// first three layers), its inference inside the flexible Krylov solver, and
+// its training (backward pass, deterministic weight-gradient reduction, Adam).
+//
+// Convolution = cross-correlation with bias:
+//   y[o, p] = b[o] + sum_{c, tap} W[o][c][tap] x[c, p + tap],  tap = (dk, dj, di) in {-1,0,1}^3,
+// with zero padding in k (levels) and j (latitude; also at the edges of
+// stacked training crops, every seg_ny rows) and periodic wrap in i
+// (longitude) for full fields or zero padding for crops.
+//
+// Precision: weights and stored activations BF16, every sum accumulated in
+// FP32.  The 16 -> 16 layers run on the tensor cores (mma.sync m16n8k16 BF16,
+// FP32 accumulate; a warp computes 16 points x 16 output channels per tile,
+// one MMA k-step per tap).  The 1 -> 16 and 16 -> 1 layers and the whole
+// backward pass (FP32 activation gradients) run on the CUDA cores.
+// Activations are channel-last: [point][16], point = (k*ny + j)*nx + i.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hz_internal.cuh"
+
+namespace hz {
+
+constexpr int kC = 16;    // hidden channels
+constexpr int kTaps = 27;
+// flat parameter layout (per layer W[Cout][Cin][27] then b[Cout])
+constexpr int kP1 = kC * 1 * kTaps, kP2 = kC * kC * kTaps, kP4 = 1 * kC * kTaps;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kP1;
+constexpr int kOffW2 = kOffB1 + kC, kOffB2 = kOffW2 + kP2;
+constexpr int kOffW3 = kOffB2 + kC, kOffB3 = kOffW3 + kP2;
+constexpr int kOffW4 = kOffB3 + kC, kOffB4 = kOffW4 + kP4;
+constexpr int kNParams = kOffB4 + 1;
+
+struct NnGrid {
+  int nx, ny, nz, seg;   // seg: rows per stacked crop (= ny for one field)
+  int periodic;          // 1: wrap in i
+  int64_t n;
+};
+
+// index of the neighbour of (i, j, k) at tap t, or -1 outside the domain
+__device__ __forceinline__ int64_t nbr(const NnGrid& g, int i, int j, int k, int t) {
+  const int dk = t / 9 - 1, dj = (t / 3) % 3 - 1, di = t % 3 - 1;
+  const int kk = k + dk;
+  if (kk < 0 || kk >= g.nz) return -1;
+  if (dj == -1 && (j % g.seg) == 0) return -1;
+  if (dj == 1 && (j % g.seg) == g.seg - 1) return -1;
+  const int jj = j + dj;
+  int ii = i + di;
+  if (ii < 0 || ii >= g.nx) {
+    if (!g.periodic) return -1;
+    ii = ii < 0 ? ii + g.nx : ii - g.nx;
+  }
+  return ((int64_t)kk * g.ny + jj) * g.nx + ii;
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// kernel-side weights (bf16-rounded values; FP32 copies for the CUDA-core layers)
+struct NnW {
+  const float* w1;                // [27][16]     layer 1, (tap, co)
+  const float* b1;                // [16]
+  const __nv_bfloat16* w2b;       // [27][16][16] layer 2, (tap, co, ci) for the MMA
+  const float* w2f;               // [27][16][16] same values in FP32 (backward)
+  const float* b2;
+  const __nv_bfloat16* w3b;
+  const float* w3f;
+  const float* b3;
+  const float* w4;                // [27][16]     layer 4, (tap, ci)
+  const float* b4;                // [1]
+};
+
+// ---- layer 1: x (FP32, one channel, scaled by s) -> z1 (FP32, optional), h1 = gelu(z1) (BF16)
+__global__ void __launch_bounds__(256) k_nn_l1(NnGrid g, const float* __restrict__ x, const double* scale_nrm2,
+                                               float scale, NnW w, float* __restrict__ z, __nv_bfloat16* __restrict__ h) {
+  __shared__ float W[kTaps * kC + kC];
+  for (int q = threadIdx.x; q < kTaps * kC; q += blockDim.x) W[q] = w.w1[q];
+  for (int q = threadIdx.x; q < kC; q += blockDim.x) W[kTaps * kC + q] = w.b1[q];
+  __syncthreads();
+  float s = scale;
+  if (scale_nrm2) {  // input scaled by 1/sigma, sigma = rms of the field
+    const double v = *scale_nrm2;
+    s = v > 0.0 ? (float)(1.0 / sqrt(v / (double)g.n)) : 0.f;
+  }
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((int64_t)g.nx * g.ny));
+    float acc[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) acc[c] = W[kTaps * kC + c];
+    for (int t = 0; t < kTaps; ++t) {
+      const int64_t q = nbr(g, i, j, k, t);
+      const float xv = q >= 0 ? s * x[q] : 0.f;
+#pragma unroll
+      for (int c = 0; c < kC; ++c) acc[c] = fmaf(W[t * kC + c], xv, acc[c]);
+    }
+    if (z) {
+#pragma unroll
+      for (int c = 0; c < kC; c += 4) *reinterpret_cast<float4*>(z + p * kC + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+    }
+    __align__(16) __nv_bfloat16 hv[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) hv[c] = __float2bfloat16_rn(gelu_f(acc[c]));
+    reinterpret_cast<uint4*>(h + p * kC)[0] = reinterpret_cast<const uint4*>(hv)[0];
+    reinterpret_cast<uint4*>(h + p * kC)[1] = reinterpret_cast<const uint4*>(hv)[1];
+  }
+}
+
+// ---- layers 2, 3: 16 -> 16 on the tensor cores ------------------------------
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// A warp computes a tile of 16 consecutive points of one row (k, j) for all 16
+// output channels: for every tap, A = the 16 x 16 (point x input channel)
+// neighbours, B = W[tap] (input channel x output channel); two n8 halves.
+// Fragment layout of m16n8k16 (g = lane/4, c = lane%4): A rows g, g+8 and
+// columns 2c, 2c+1, 2c+8, 2c+9; B rows (k) 2c, 2c+1, 2c+8, 2c+9 of column g;
+// D rows g, g+8, columns 2c, 2c+1.
+__global__ void __launch_bounds__(128) k_nn_mid(NnGrid g, const __nv_bfloat16* __restrict__ hin,
+                                               const __nv_bfloat16* __restrict__ wb, const float* __restrict__ bias,
+                                               float* __restrict__ z, __nv_bfloat16* __restrict__ hout) {
+  __shared__ uint32_t Ws[kTaps * kC * kC / 2];  // [tap][co][ci] bf16 pairs
+  __shared__ float Bs[kC];
+  for (int q = threadIdx.x; q < kTaps * kC * kC / 2; q += blockDim.x) Ws[q] = reinterpret_cast<const uint32_t*>(wb)[q];
+  for (int q = threadIdx.x; q < kC; q += blockDim.x) Bs[q] = bias[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
+  const int tiles_row = (g.nx + 15) / 16;
+  const int64_t ntiles = (int64_t)tiles_row * g.ny * g.nz;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const uint32_t* hin32 = reinterpret_cast<const uint32_t*>(hin);
+  for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < ntiles; tile += wstride) {
+    const int it = (int)(tile % tiles_row);
+    const int64_t row = tile / tiles_row;  // k*ny + j
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    const int i0 = it * 16;
+    const int ia = i0 + gq, ib = i0 + gq + 8;  // the two points this lane feeds
+    float d0[4], d1[4];
+    d0[0] = d0[2] = Bs[2 * cq];
+    d0[1] = d0[3] = Bs[2 * cq + 1];
+    d1[0] = d1[2] = Bs[8 + 2 * cq];
+    d1[1] = d1[3] = Bs[8 + 2 * cq + 1];
+    for (int t = 0; t < kTaps; ++t) {
+      const int64_t qa = ia < g.nx ? nbr(g, ia, j, k, t) : -1;
+      const int64_t qb = ib < g.nx ? nbr(g, ib, j, k, t) : -1;
+      uint32_t a[4];
+      a[0] = qa >= 0 ? hin32[qa * (kC / 2) + cq] : 0u;
+      a[1] = qb >= 0 ? hin32[qb * (kC / 2) + cq] : 0u;
+      a[2] = qa >= 0 ? hin32[qa * (kC / 2) + 4 + cq] : 0u;
+      a[3] = qb >= 0 ? hin32[qb * (kC / 2) + 4 + cq] : 0u;
+      const uint32_t* wt = Ws + t * (kC * kC / 2);
+      // B[k = ci][n = co] = W[t][co][ci]: ci pairs (2c, 2c+1) and (2c+8, 2c+9) of column co = g (+8)
+      mma_bf16_16816(d0, a, wt[gq * (kC / 2) + cq], wt[gq * (kC / 2) + 4 + cq]);
+      mma_bf16_16816(d1, a, wt[(gq + 8) * (kC / 2) + cq], wt[(gq + 8) * (kC / 2) + 4 + cq]);
+    }
+    // epilogue: point ia gets d*[0..1], point ib gets d*[2..3]; channels 2c, 2c+1 and 8+2c, 9+2c
+    const int64_t pbase = row * g.nx;
+    if (ia < g.nx) {
+      const int64_t p = pbase + ia;
+      if (z) {
+        *reinterpret_cast<float2*>(z + p * kC + 2 * cq) = make_float2(d0[0], d0[1]);
+        *reinterpret_cast<float2*>(z + p * kC + 8 + 2 * cq) = make_float2(d1[0], d1[1]);
+      }
+      reinterpret_cast<__nv_bfloat162*>(hout + p * kC + 2 * cq)[0] = __floats2bfloat162_rn(gelu_f(d0[0]), gelu_f(d0[1]));
+      reinterpret_cast<__nv_bfloat162*>(hout + p * kC + 8 + 2 * cq)[0] = __floats2bfloat162_rn(gelu_f(d1[0]), gelu_f(d1[1]));
+    }
+    if (ib < g.nx) {
+      const int64_t p = pbase + ib;
+      if (z) {
+        *reinterpret_cast<float2*>(z + p * kC + 2 * cq) = make_float2(d0[2], d0[3]);
+        *reinterpret_cast<float2*>(z + p * kC + 8 + 2 * cq) = make_float2(d1[2], d1[3]);
+      }
+      reinterpret_cast<__nv_bfloat162*>(hout + p * kC + 2 * cq)[0] = __floats2bfloat162_rn(gelu_f(d0[2]), gelu_f(d0[3]));
+      reinterpret_cast<__nv_bfloat162*>(hout + p * kC + 8 + 2 * cq)[0] = __floats2bfloat162_rn(gelu_f(d1[2]), gelu_f(d1[3]));
+    }
+  }
+}
+
+// ---- layer 4: h3 (BF16, 16 channels) -> y (FP32).  With base != null the
+// preconditioner combination out = base + sigma * y is written instead, sigma
+// = rms of the stage input (sqrt(nrm2 / n)).
+__global__ void __launch_bounds__(256) k_nn_l4(NnGrid g, const __nv_bfloat16* __restrict__ h, NnW w,
+                                               const float* base, const double* nrm2, float* out) {
+  __shared__ float W[kTaps * kC + 1];
+  for (int q = threadIdx.x; q < kTaps * kC; q += blockDim.x) W[q] = w.w4[q];
+  if (threadIdx.x == 0) W[kTaps * kC] = w.b4[0];
+  __syncthreads();
+  float sigma = 1.f;
+  if (nrm2) {
+    const double v = *nrm2;
+    sigma = (float)sqrt(v / (double)g.n);
+  }
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((int64_t)g.nx * g.ny));
+    float acc = W[kTaps * kC];
+    for (int t = 0; t < kTaps; ++t) {
+      const int64_t q = nbr(g, i, j, k, t);
+      if (q < 0) continue;
+      __align__(16) __nv_bfloat16 hv[kC];
+      reinterpret_cast<uint4*>(hv)[0] = reinterpret_cast<const uint4*>(h + q * kC)[0];
+      reinterpret_cast<uint4*>(hv)[1] = reinterpret_cast<const uint4*>(h + q * kC)[1];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) acc = fmaf(W[t * kC + c], __bfloat162float(hv[c]), acc);
+    }
+    out[p] = base ? fmaf(sigma, acc, base[p]) : acc;
+  }
+}
+
+// ---- backward (FP32 on the CUDA cores) ---------------------------------------
+// dz3[p][ci] = gelu'(z3[p][ci]) * sum_t W4[t][ci] dy[p - t]   (adjoint of layer 4)
+__global__ void __launch_bounds__(256) k_nn_b4(NnGrid g, const float* __restrict__ dy, NnW w,
+                                               const float* __restrict__ z3, float* __restrict__ dz3) {
+  __shared__ float W[kTaps * kC];
+  for (int q = threadIdx.x; q < kTaps * kC; q += blockDim.x) W[q] = w.w4[q];
+  __syncthreads();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((int64_t)g.nx * g.ny));
+    float acc[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) acc[c] = 0.f;
+    for (int t = 0; t < kTaps; ++t) {
+      const int64_t q = nbr(g, i, j, k, kTaps - 1 - t);  // p - tap
+      if (q < 0) continue;
+      const float d = dy[q];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) acc[c] = fmaf(W[t * kC + c], d, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kC; ++c) dz3[p * kC + c] = acc[c] * gelu_grad_f(z3[p * kC + c]);
+  }
+}
+
+// dzo[p][ci] = gelu'(zo[p][ci]) * sum_t sum_co W[t][co][ci] dz[p - t][co]   (adjoint of a 16 -> 16 layer)
+__global__ void __launch_bounds__(128) k_nn_bmid(NnGrid g, const float* __restrict__ dz, const float* __restrict__ wf,
+                                                 const float* __restrict__ zo, float* __restrict__ dzo) {
+  __shared__ float W[kTaps * kC * kC];
+  for (int q = threadIdx.x; q < kTaps * kC * kC; q += blockDim.x) W[q] = wf[q];
+  __syncthreads();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((int64_t)g.nx * g.ny));
+    float acc[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) acc[c] = 0.f;
+    for (int t = 0; t < kTaps; ++t) {
+      const int64_t q = nbr(g, i, j, k, kTaps - 1 - t);
+      if (q < 0) continue;
+      float d[kC];
+#pragma unroll
+      for (int c = 0; c < kC; c += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(dz + q * kC + c);
+        d[c] = v.x, d[c + 1] = v.y, d[c + 2] = v.z, d[c + 3] = v.w;
+      }
+      const float* wt = W + t * kC * kC;
+#pragma unroll
+      for (int co = 0; co < kC; ++co)
+#pragma unroll
+        for (int ci = 0; ci < kC; ++ci) acc[ci] = fmaf(wt[co * kC + ci], d[co], acc[ci]);
+    }
+#pragma unroll
+    for (int c = 0; c < kC; ++c) dzo[p * kC + c] = acc[c] * gelu_grad_f(zo[p * kC + c]);
+  }
+}
+
+// Weight gradient of one layer, dW[co][ci][t] = sum_p dz[p][co] hin[p + t][ci]
+// and db[co] = sum_p dz[p][co].  Block partials in FP64 (each thread owns
+// output slots o = tid, tid + blockDim, ...; FP32 within a 32-point tile),
+// written to part[block][slot]; k_nn_greduce sums them in block order.
+template <int CI, int CO, typename HT>
+__global__ void __launch_bounds__(256) k_nn_dw(NnGrid g, const float* __restrict__ dz, const HT* __restrict__ hin,
+                                               double* __restrict__ part) {
+  constexpr int NO = CO * CI * kTaps + CO;
+  constexpr int TP = CI > 1 ? 16 : 32;  // points per tile: the staged neighbours stay under 48 KiB
+  constexpr int PER = (NO + 255) / 256;
+  __shared__ float sdz[TP][CO];
+  __shared__ float sh[kTaps][TP][CI];
+  double acc[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) acc[u] = 0.0;
+  const int64_t ntile = (g.n + TP - 1) / TP;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t p0 = tile * TP;
+    __syncthreads();
+    for (int q = threadIdx.x; q < TP * CO; q += blockDim.x) {
+      const int pp = q / CO, c = q % CO;
+      sdz[pp][c] = (p0 + pp < g.n) ? dz[(p0 + pp) * CO + c] : 0.f;
+    }
+    for (int q = threadIdx.x; q < kTaps * TP; q += blockDim.x) {
+      const int t = q / TP, pp = q % TP;
+      const int64_t p = p0 + pp;
+      int64_t nb = -1;
+      if (p < g.n) {
+        const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((int64_t)g.nx * g.ny));
+        nb = nbr(g, i, j, k, t);
+      }
+#pragma unroll
+      for (int c = 0; c < CI; ++c) {
+        float v = 0.f;
+        if (nb >= 0) {
+          if constexpr (sizeof(HT) == 2)
+            v = __bfloat162float(hin[nb * CI + c]);
+          else
+            v = (float)hin[nb * CI + c];
+        }
+        sh[t][pp][c] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int o = threadIdx.x + u * 256;
+      if (o >= NO) continue;
+      float s = 0.f;
+      if (o < CO * CI * kTaps) {
+        const int co = o / (CI * kTaps), rem = o % (CI * kTaps), ci = rem / kTaps, t = rem % kTaps;
+        for (int pp = 0; pp < TP; ++pp) s = fmaf(sdz[pp][co], sh[t][pp][ci], s);
+      } else {
+        const int co = o - CO * CI * kTaps;
+        for (int pp = 0; pp < TP; ++pp) s += sdz[pp][co];
+      }
+      acc[u] += (double)s;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int o = threadIdx.x + u * 256;
+    if (o < NO) part[(size_t)blockIdx.x * NO + o] = acc[u];
+  }
+}
+
+// out[o] = sum_b part[b][o] in block order (deterministic)
+__global__ void k_nn_greduce(const double* __restrict__ part, int nblocks, int no, double* __restrict__ out) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < no; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * no + o];
+    out[o] = s;
+  }
+}
+
+// relative MSE over the interior of every crop (border points of each crop
+// excluded in i and j): partials of sum (y - t)^2 and sum t^2
+__device__ __forceinline__ bool in_mask(const NnGrid& g, int64_t p, int border) {
+  const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny) % g.seg;
+  return i >= border && i < g.nx - border && j >= border && j < g.seg - border;
+}
+
+__global__ void __launch_bounds__(256) k_nn_loss(NnGrid g, const float* __restrict__ y, const float* __restrict__ t,
+                                                 int border, double* __restrict__ part) {
+  double a = 0.0, b = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (!in_mask(g, p, border)) continue;
+    const double d = (double)y[p] - (double)t[p];
+    a += d * d;
+    b += (double)t[p] * (double)t[p];
+  }
+  __shared__ double sa[8], sb[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) sa[warp] = a, sb[warp] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, z = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += sa[w], z += sb[w];
+    part[blockIdx.x * 2] = x;
+    part[blockIdx.x * 2 + 1] = z;
+  }
+}
+
+__global__ void k_nn_loss_fin(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int q = 0; q < nblocks; ++q) a += part[2 * q], b += part[2 * q + 1];
+  out[0] = b > 0.0 ? a / b : 0.0;  // loss
+  out[1] = b;                       // sum t^2
+}
+
+// dy = 2 (y - t) / sum t^2 on the mask, 0 elsewhere
+__global__ void __launch_bounds__(256) k_nn_dy(NnGrid g, const float* __restrict__ y, const float* __restrict__ t,
+                                               int border, const double* __restrict__ lossv, float* __restrict__ dy) {
+  const double tt = lossv[1];
+  const float sc = tt > 0.0 ? (float)(2.0 / tt) : 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (int64_t)gridDim.x * blockDim.x)
+    dy[p] = in_mask(g, p, border) ? sc * (y[p] - t[p]) : 0.f;
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters; lr, betas, eps and the
+// bias corrections come from the host.
+__global__ void k_nn_adam(int np, float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                          const double* __restrict__ grad, float lr, float b1, float b2, float eps, float c1,
+                          float c2) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+    const float gq = (float)grad[q];
+    const float mq = b1 * m[q] + (1.f - b1) * gq;
+    const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    w[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+  }
+}
+
+// kernel-side weights from the FP32 master vector (bf16 rounding, re-layout)
+__global__ void k_nn_refresh(const float* __restrict__ master, float* __restrict__ w1, float* __restrict__ b1,
+                             __nv_bfloat16* __restrict__ w2b, float* __restrict__ w2f, float* __restrict__ b2,
+                             __nv_bfloat16* __restrict__ w3b, float* __restrict__ w3f, float* __restrict__ b3,
+                             float* __restrict__ w4, float* __restrict__ b4) {
+  const int stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  auto rb = [](float x) { return __bfloat162float(__float2bfloat16_rn(x)); };
+  for (int q = tid; q < kP1; q += stride) {  // master W1[co][0][t] -> w1[t][co]
+    const int co = q / kTaps, t = q % kTaps;
+    w1[t * kC + co] = rb(master[kOffW1 + q]);
+  }
+  for (int q = tid; q < kP2; q += stride) {  // master W[co][ci][t] -> [t][co][ci]
+    const int co = q / (kC * kTaps), ci = (q / kTaps) % kC, t = q % kTaps;
+    const int d = (t * kC + co) * kC + ci;
+    const __nv_bfloat16 v2 = __float2bfloat16_rn(master[kOffW2 + q]);
+    const __nv_bfloat16 v3 = __float2bfloat16_rn(master[kOffW3 + q]);
+    w2b[d] = v2;
+    w2f[d] = __bfloat162float(v2);
+    w3b[d] = v3;
+    w3f[d] = __bfloat162float(v3);
+  }
+  for (int q = tid; q < kP4; q += stride) {  // master W4[0][ci][t] -> w4[t][ci]
+    const int ci = q / kTaps, t = q % kTaps;
+    w4[t * kC + ci] = rb(master[kOffW4 + q]);
+  }
+  for (int q = tid; q < kC; q += stride) {
+    b1[q] = rb(master[kOffB1 + q]);
+    b2[q] = rb(master[kOffB2 + q]);
+    b3[q] = rb(master[kOffB3 + q]);
+  }
+  if (tid == 0) b4[0] = rb(master[kOffB4]);
+}
+
+// training pair of one iterate x_k (Sec.-2 scaled system, FP64 in, FP32 out):
+// r = D^-1 (b - A x_k) is the residual, e = x* - x_k the error; with
+// z1 = T^-1 r and e1 = r - Ahat z1, the stage input is e1 / sigma and the
+// target (e - z1) / sigma, sigma = rms(e1).  This kernel forms r (float) and
+// e (float); the rest uses the solver's own T^-1 and residual kernels.
+__global__ void __launch_bounds__(256) k_nn_pair_r(int64_t n, const double* __restrict__ A7, const double* __restrict__ b,
+                                                  const double* __restrict__ xk, const double* __restrict__ xs,
+                                                  const double* __restrict__ r, float* __restrict__ rs,
+                                                  float* __restrict__ e) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    rs[p] = (float)(r[p] / A7[p]);
+    e[p] = (float)(xs[p] - xk[p]);
+  }
+}
+
+// in = e1 / sigma, target = (e - z1) / sigma with sigma = sqrt(nrm2 / n)
+__global__ void __launch_bounds__(256) k_nn_pair_fin(int64_t n, const float* __restrict__ e1, const float* __restrict__ e,
+                                                    const float* __restrict__ z1, const double* __restrict__ nrm2,
+                                                    float* __restrict__ in, float* __restrict__ tg) {
+  const double v = *nrm2;
+  const float inv = v > 0.0 ? (float)(1.0 / sqrt(v / (double)n)) : 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    in[p] = e1[p] * inv;
+    tg[p] = (e[p] - z1[p]) * inv;
+  }
+}
+
+// Crops of (cy + 2h) x (cx + 2h) columns, all levels, from two fields, stacked
+// along j: crop q starts at column (i0, j0) of the field (corners from the
+// host), i wraps, rows outside [0, ny) are zero.
+__global__ void __launch_bounds__(256) k_nn_crops(int nx, int ny, int nz, const float* __restrict__ fa,
+                                                  const float* __restrict__ fb, int ncrop, int cx, int cy,
+                                                  const int* __restrict__ corners, float* __restrict__ oa,
+                                                  float* __restrict__ ob) {
+  const int64_t per = (int64_t)cx * cy * nz;
+  const int64_t total = per * ncrop;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    // output layout [k][q*cy + jj][ii] (crops stacked along j)
+    const int ii = (int)(o % cx);
+    const int64_t rowo = o / cx;
+    const int jq = (int)(rowo % ((int64_t)cy * ncrop));
+    const int k = (int)(rowo / ((int64_t)cy * ncrop));
+    const int q = jq / cy, jj = jq % cy;
+    const int i0 = corners[2 * q], j0 = corners[2 * q + 1];
+    int i = (i0 + ii) % nx;
+    if (i < 0) i += nx;
+    const int j = j0 + jj;
+    float va = 0.f, vb = 0.f;
+    if (j >= 0 && j < ny) {
+      const int64_t src = ((int64_t)k * ny + j) * nx + i;
+      va = fa[src];
+      vb = fb[src];
+    }
+    oa[o] = va;
+    ob[o] = vb;
+  }
+}
+
+}  // namespace hz
+
+// ===========================================================================
+// host side
+// ===========================================================================
+namespace hz {
+
+static thread_local char g_nn_err[256] = "";
+
+struct NnDev {
+  float* master = nullptr;  // FP32 master parameters, flat layout
+  float* m = nullptr;       // Adam moments
+  float* v = nullptr;
+  double* grad = nullptr;   // reduced gradient (FP64)
+  float *w1 = nullptr, *b1 = nullptr, *w2f = nullptr, *b2 = nullptr, *w3f = nullptr, *b3 = nullptr, *w4 = nullptr,
+        *b4 = nullptr;
+  __nv_bfloat16 *w2b = nullptr, *w3b = nullptr;
+  int64_t cap = 0;
+  __nv_bfloat16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+  float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *dza = nullptr, *dzb = nullptr, *y = nullptr, *dy = nullptr;
+  int train_cap = 0;  // 1 if the training buffers exist for cap points
+  double* part = nullptr;
+  int64_t part_cap = 0;
+  double* lossv = nullptr;
+  double* lossh = nullptr;
+  int step = 0;
+};
+
+}  // namespace hz
+
+struct hz_nn_s {
+  hz::NnDev d;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+};
+
+namespace hz {
+
+#define NN_CK(call)                                                                               \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      snprintf(g_nn_err, sizeof(g_nn_err), "%s at hz_nn.cu:%d: %s", cudaGetErrorName(e_), __LINE__, #call); \
+      return e_ == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA;                          \
+    }                                                                                             \
+  } while (0)
+
+static NnW nn_w(const NnDev& d) {
+  return NnW{d.w1, d.b1, d.w2b, d.w2f, d.b2, d.w3b, d.w3f, d.b3, d.w4, d.b4};
+}
+
+static int nn_grid(const hz_nn_s* nn, int64_t n, int block) {
+  int64_t g = (int64_t)nn->sms * 8;
+  const int64_t need = (n + block - 1) / block;
+  if (g > need) g = need;
+  return g < 1 ? 1 : (int)g;
+}
+
+static int nn_refresh(hz_nn_s* nn) {
+  NnDev& d = nn->d;
+  k_nn_refresh<<<32, 256, 0, nn->stream>>>(d.master, d.w1, d.b1, d.w2b, d.w2f, d.b2, d.w3b, d.w3f, d.b3, d.w4, d.b4);
+  NN_CK(cudaGetLastError());
+  return HZ_OK;
+}
+
+static int nn_reserve(hz_nn_s* nn, int64_t n, bool train) {
+  NnDev& d = nn->d;
+  if (n <= d.cap && (!train || d.train_cap)) return HZ_OK;
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  for (void* p : {(void*)d.h1, (void*)d.h2, (void*)d.h3, (void*)d.z1, (void*)d.z2, (void*)d.z3, (void*)d.dza,
+                  (void*)d.dzb, (void*)d.y, (void*)d.dy})
+    if (p) cudaFree(p);
+  d.h1 = d.h2 = d.h3 = nullptr;
+  d.z1 = d.z2 = d.z3 = d.dza = d.dzb = d.y = d.dy = nullptr;
+  const int64_t c = n > d.cap ? n : d.cap;
+  NN_CK(cudaMalloc(&d.h1, sizeof(__nv_bfloat16) * kC * c));
+  NN_CK(cudaMalloc(&d.h2, sizeof(__nv_bfloat16) * kC * c));
+  d.train_cap = 0;
+  if (train) {
+    NN_CK(cudaMalloc(&d.h3, sizeof(__nv_bfloat16) * kC * c));
+    NN_CK(cudaMalloc(&d.z1, sizeof(float) * kC * c));
+    NN_CK(cudaMalloc(&d.z2, sizeof(float) * kC * c));
+    NN_CK(cudaMalloc(&d.z3, sizeof(float) * kC * c));
+    NN_CK(cudaMalloc(&d.dza, sizeof(float) * kC * c));
+    NN_CK(cudaMalloc(&d.dzb, sizeof(float) * kC * c));
+    NN_CK(cudaMalloc(&d.y, sizeof(float) * c));
+    NN_CK(cudaMalloc(&d.dy, sizeof(float) * c));
+    d.train_cap = 1;
+  }
+  d.cap = c;
+  return HZ_OK;
+}
+
+// forward pass; train: keep z1..z3 and h1..h3 for the backward pass.
+// x scaled by 1/sigma (sigma from *scale_nrm2) when scale_nrm2 is given.
+// Output: out = y, or out = base + sigma * y when base is given.
+static int nn_forward(hz_nn_s* nn, const NnGrid& g, const float* x, const double* scale_nrm2, bool train,
+                      const float* base, float* out) {
+  NnDev& d = nn->d;
+  const NnW w = nn_w(d);
+  cudaStream_t s = nn->stream;
+  __nv_bfloat16* h3 = train ? d.h3 : d.h1;
+  k_nn_l1<<<nn_grid(nn, g.n, 256), 256, 0, s>>>(g, x, scale_nrm2, 1.f, w, train ? d.z1 : nullptr, d.h1);
+  const int64_t tiles = (int64_t)((g.nx + 15) / 16) * g.ny * g.nz;
+  const int gm = (int)std::min<int64_t>((tiles + 3) / 4, (int64_t)nn->sms * 16);
+  k_nn_mid<<<gm, 128, 0, s>>>(g, d.h1, d.w2b, d.b2, train ? d.z2 : nullptr, d.h2);
+  k_nn_mid<<<gm, 128, 0, s>>>(g, d.h2, d.w3b, d.b3, train ? d.z3 : nullptr, h3);
+  k_nn_l4<<<nn_grid(nn, g.n, 256), 256, 0, s>>>(g, h3, w, base, base ? scale_nrm2 : nullptr, out);
+  NN_CK(cudaGetLastError());
+  return HZ_OK;
+}
+
+template <int CI, int CO, typename HT>
+static int nn_dw(hz_nn_s* nn, const NnGrid& g, const float* dz, const HT* hin, double* dst) {
+  NnDev& d = nn->d;
+  constexpr int NO = CO * CI * kTaps + CO;
+  const int64_t ntile = (g.n + 31) / 32;
+  const int grid = (int)std::min<int64_t>(ntile, (int64_t)nn->sms * 4);
+  if (d.part_cap < (int64_t)grid * NO) {
+    NN_CK(cudaStreamSynchronize(nn->stream));
+    if (d.part) cudaFree(d.part);
+    NN_CK(cudaMalloc(&d.part, sizeof(double) * (size_t)grid * NO));
+    d.part_cap = (int64_t)grid * NO;
+  }
+  k_nn_dw<CI, CO, HT><<<grid, 256, 0, nn->stream>>>(g, dz, hin, d.part);
+  k_nn_greduce<<<(NO + 255) / 256, 256, 0, nn->stream>>>(d.part, grid, NO, dst);
+  NN_CK(cudaGetLastError());
+  return HZ_OK;
+}
+
+// forward + masked relative-MSE loss + backward: d.grad, d.lossv
+static int nn_gradient(hz_nn_s* nn, const NnGrid& g, int border, const float* x, const float* t) {
+  NnDev& d = nn->d;
+  cudaStream_t s = nn->stream;
+  int st = nn_reserve(nn, g.n, true);
+  if (st != HZ_OK) return st;
+  if ((st = nn_forward(nn, g, x, nullptr, true, nullptr, d.y)) != HZ_OK) return st;
+  const int gl = nn_grid(nn, g.n, 256);
+  if (d.part_cap < 2 * gl) {
+    NN_CK(cudaStreamSynchronize(s));
+    if (d.part) cudaFree(d.part);
+    NN_CK(cudaMalloc(&d.part, sizeof(double) * 2 * gl));
+    d.part_cap = 2 * gl;
+  }
+  k_nn_loss<<<gl, 256, 0, s>>>(g, d.y, t, border, d.part);
+  k_nn_loss_fin<<<1, 32, 0, s>>>(d.part, gl, d.lossv);
+  k_nn_dy<<<gl, 256, 0, s>>>(g, d.y, t, border, d.lossv, d.dy);
+  const NnW w = nn_w(d);
+  // layer 4
+  k_nn_b4<<<gl, 256, 0, s>>>(g, d.dy, w, d.z3, d.dza);  // dz3
+  if ((st = nn_dw<kC, 1, __nv_bfloat16>(nn, g, d.dy, d.h3, d.grad + kOffW4)) != HZ_OK) return st;
+  // layer 3
+  k_nn_bmid<<<nn_grid(nn, g.n, 128), 128, 0, s>>>(g, d.dza, d.w3f, d.z2, d.dzb);  // dz2
+  if ((st = nn_dw<kC, kC, __nv_bfloat16>(nn, g, d.dza, d.h2, d.grad + kOffW3)) != HZ_OK) return st;
+  // layer 2
+  k_nn_bmid<<<nn_grid(nn, g.n, 128), 128, 0, s>>>(g, d.dzb, d.w2f, d.z1, d.dza);  // dz1
+  if ((st = nn_dw<kC, kC, __nv_bfloat16>(nn, g, d.dzb, d.h1, d.grad + kOffW2)) != HZ_OK) return st;
+  // layer 1
+  if ((st = nn_dw<1, kC, float>(nn, g, d.dza, x, d.grad + kOffW1)) != HZ_OK) return st;
+  NN_CK(cudaGetLastError());
+  return HZ_OK;
+}
+
+// the learned stage inside the flexible solver (called by the engine):
+// z <- z + sigma * NN(e1 / sigma), sigma = sqrt(nrm2 / n)
+int nn_stage_apply(hz_nn_s* nn, const Grid& gr, const float* e1, const double* nrm2, float* z, cudaStream_t s) {
+  NnGrid g{gr.nx, gr.ny, gr.nz, gr.ny, 1, gr.n};
+  cudaStream_t keep = nn->stream;
+  nn->stream = s;
+  int st = nn_reserve(nn, g.n, false);
+  if (st == HZ_OK) st = nn_forward(nn, g, e1, nrm2, false, z, z);
+  nn->stream = keep;
+  return st;
+}
+
+cudaError_t nn_pair_launch(int64_t n, const double* A7, const double* b, const double* xk, const double* xs,
+                           const double* r, float* rs, float* e, const float* e1, const float* z1, const double* nrm2,
+                           float* in, float* tg, int stage, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 8192);
+  if (stage == 0)
+    k_nn_pair_r<<<grid, 256, 0, s>>>(n, A7, b, xk, xs, r, rs, e);
+  else
+    k_nn_pair_fin<<<grid, 256, 0, s>>>(n, e1, e, z1, nrm2, in, tg);
+  return cudaGetLastError();
+}
+
+}  // namespace hz
+
+using namespace hz;
+
+static bool nn_is_dev(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" {
+
+int hz_nn_num_params(void) { return kNParams; }
+
+const char* hz_nn_last_error(void) { return g_nn_err; }
+
+int hz_nn_create(void* stream, hz_nn* out) {
+  if (!out) return HZ_ERR_INVALID;
+  *out = nullptr;
+  hz_nn_s* nn = new hz_nn_s();
+  nn->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nn->sms, cudaDevAttrMultiProcessorCount, dev);
+  NnDev& d = nn->d;
+  auto fail = [&](int st) {
+    hz_nn_destroy(nn);
+    return st;
+  };
+  if (cudaMalloc(&d.master, sizeof(float) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMalloc(&d.m, sizeof(float) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMalloc(&d.v, sizeof(float) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMalloc(&d.grad, sizeof(double) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMalloc(&d.w1, sizeof(float) * (kP1 + kC + 2 * (kP2 + kC) + kP4 + 1)) != cudaSuccess) return fail(HZ_ERR_OOM);
+  d.b1 = d.w1 + kP1;
+  d.w2f = d.b1 + kC;
+  d.b2 = d.w2f + kP2;
+  d.w3f = d.b2 + kC;
+  d.b3 = d.w3f + kP2;
+  d.w4 = d.b3 + kC;
+  d.b4 = d.w4 + kP4;
+  if (cudaMalloc(&d.w2b, sizeof(__nv_bfloat16) * 2 * kP2) != cudaSuccess) return fail(HZ_ERR_OOM);
+  d.w3b = d.w2b + kP2;
+  if (cudaMalloc(&d.lossv, sizeof(double) * 2) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMallocHost(&d.lossh, sizeof(double) * 2) != cudaSuccess) return fail(HZ_ERR_OOM);
+  cudaMemsetAsync(d.master, 0, sizeof(float) * kNParams, nn->stream);
+  cudaMemsetAsync(d.m, 0, sizeof(float) * kNParams, nn->stream);
+  cudaMemsetAsync(d.v, 0, sizeof(float) * kNParams, nn->stream);
+  if (nn_refresh(nn) != HZ_OK) return fail(HZ_ERR_CUDA);
+  if (cudaStreamSynchronize(nn->stream) != cudaSuccess) return fail(HZ_ERR_CUDA);
+  *out = nn;
+  return HZ_OK;
+}
+
+int hz_nn_destroy(hz_nn nn) {
+  if (!nn) return HZ_OK;
+  cudaStreamSynchronize(nn->stream);
+  NnDev& d = nn->d;
+  for (void* p : {(void*)d.master, (void*)d.m, (void*)d.v, (void*)d.grad, (void*)d.w1, (void*)d.w2b, (void*)d.lossv,
+                  (void*)d.h1, (void*)d.h2, (void*)d.h3, (void*)d.z1, (void*)d.z2, (void*)d.z3, (void*)d.dza,
+                  (void*)d.dzb, (void*)d.y, (void*)d.dy, (void*)d.part})
+    if (p) cudaFree(p);
+  if (d.lossh) cudaFreeHost(d.lossh);
+  delete nn;
+  return HZ_OK;
+}
+
+int hz_nn_set_params(hz_nn nn, const float* params) {
+  if (!nn || !params) return HZ_ERR_INVALID;
+  NnDev& d = nn->d;
+  NN_CK(cudaMemcpyAsync(d.master, params, sizeof(float) * kNParams,
+                        nn_is_dev(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, nn->stream));
+  NN_CK(cudaMemsetAsync(d.m, 0, sizeof(float) * kNParams, nn->stream));
+  NN_CK(cudaMemsetAsync(d.v, 0, sizeof(float) * kNParams, nn->stream));
+  d.step = 0;
+  int st = nn_refresh(nn);
+  if (st != HZ_OK) return st;
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  return HZ_OK;
+}
+
+int hz_nn_get_params(hz_nn nn, float* out) {
+  if (!nn || !out) return HZ_ERR_INVALID;
+  NN_CK(cudaMemcpyAsync(out, nn->d.master, sizeof(float) * kNParams,
+                        nn_is_dev(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, nn->stream));
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  return HZ_OK;
+}
+
+int hz_nn_forward(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, const float* x, float* y, float* zout) {
+  if (!nn || !x || !y || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny) return HZ_ERR_INVALID;
+  NnGrid g{nx, ny, nz, seg_ny, periodic ? 1 : 0, (int64_t)nx * ny * nz};
+  int st = nn_reserve(nn, g.n, zout != nullptr);
+  if (st != HZ_OK) return st;
+  st = nn_forward(nn, g, x, nullptr, zout != nullptr, nullptr, y);
+  if (st != HZ_OK) return st;
+  if (zout) {  // pre-activations z1, z2, z3 (FP32, [3][n][16])
+    NN_CK(cudaMemcpyAsync(zout, nn->d.z1, sizeof(float) * kC * g.n, cudaMemcpyDeviceToDevice, nn->stream));
+    NN_CK(cudaMemcpyAsync(zout + kC * g.n, nn->d.z2, sizeof(float) * kC * g.n, cudaMemcpyDeviceToDevice, nn->stream));
+    NN_CK(cudaMemcpyAsync(zout + 2 * kC * g.n, nn->d.z3, sizeof(float) * kC * g.n, cudaMemcpyDeviceToDevice,
+                          nn->stream));
+  }
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  return HZ_OK;
+}
+
+int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
+                   const float* t, double* grad, double* loss) {
+  if (!nn || !x || !t || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny || border < 0) return HZ_ERR_INVALID;
+  NnGrid g{nx, ny, nz, seg_ny, periodic ? 1 : 0, (int64_t)nx * ny * nz};
+  int st = nn_gradient(nn, g, border, x, t);
+  if (st != HZ_OK) return st;
+  if (grad)
+    NN_CK(cudaMemcpyAsync(grad, nn->d.grad, sizeof(double) * kNParams,
+                          nn_is_dev(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, nn->stream));
+  NN_CK(cudaMemcpyAsync(nn->d.lossh, nn->d.lossv, sizeof(double) * 2, cudaMemcpyDeviceToHost, nn->stream));
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  if (loss) *loss = nn->d.lossh[0];
+  return HZ_OK;
+}
+
+int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
+                     const float* t, double lr, double* loss) {
+  if (!nn || !x || !t || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny || border < 0 || !(lr > 0))
+    return HZ_ERR_INVALID;
+  NnGrid g{nx, ny, nz, seg_ny, periodic ? 1 : 0, (int64_t)nx * ny * nz};
+  int st = nn_gradient(nn, g, border, x, t);
+  if (st != HZ_OK) return st;
+  NnDev& d = nn->d;
+  d.step += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, d.step)), c2 = (float)(1.0 - std::pow(b2, d.step));
+  k_nn_adam<<<(kNParams + 255) / 256, 256, 0, nn->stream>>>(kNParams, d.master, d.m, d.v, d.grad, (float)lr, (float)b1,
+                                                             (float)b2, 1e-8f, c1, c2);
+  NN_CK(cudaGetLastError());
+  if ((st = nn_refresh(nn)) != HZ_OK) return st;
+  if (loss) {
+    NN_CK(cudaMemcpyAsync(d.lossh, d.lossv, sizeof(double) * 2, cudaMemcpyDeviceToHost, nn->stream));
+    NN_CK(cudaStreamSynchronize(nn->stream));
+    *loss = d.lossh[0];
+  }
+  return HZ_OK;
+}
+
+int hz_nn_crops(int nx, int ny, int nz, const float* fa, const float* fb, int ncrop, int cx, int cy,
+                const int* corners, float* oa, float* ob, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || !fa || !fb || ncrop < 1 || cx < 1 || cy < 1 || !corners || !oa || !ob)
+    return HZ_ERR_INVALID;
+  for (int q = 0; q < ncrop; ++q)
+    if (corners[2 * q + 1] < -cy || corners[2 * q + 1] > ny) return HZ_ERR_INVALID;
+  int* dc = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  NN_CK(cudaMallocAsync((void**)&dc, sizeof(int) * 2 * ncrop, s));
+  NN_CK(cudaMemcpyAsync(dc, corners, sizeof(int) * 2 * ncrop, cudaMemcpyHostToDevice, s));
+  const int64_t total = (int64_t)cx * cy * nz * ncrop;
+  k_nn_crops<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, s>>>(nx, ny, nz, fa, fb, ncrop, cx, cy, dc,
+                                                                               oa, ob);
+  NN_CK(cudaGetLastError());
+  NN_CK(cudaFreeAsync(dc, s));
+  NN_CK(cudaStreamSynchronize(s));
+  return HZ_OK;
+}
+
+int hz_nn_save(hz_nn nn, const char* path) {
+  if (!nn || !path) return HZ_ERR_INVALID;
+  std::vector<float> buf(3 * kNParams);
+  NN_CK(cudaMemcpyAsync(buf.data(), nn->d.master, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, nn->stream));
+  NN_CK(cudaMemcpyAsync(buf.data() + kNParams, nn->d.m, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, nn->stream));
+  NN_CK(cudaMemcpyAsync(buf.data() + 2 * kNParams, nn->d.v, sizeof(float) * kNParams, cudaMemcpyDeviceToHost,
+                        nn->stream));
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  FILE* f = fopen(path, "wb");
+  if (!f) return HZ_ERR_INVALID;
+  const char magic[8] = {'H', 'Z', 'N', 'N', '0', '0', '0', '1'};
+  const int32_t hdr[2] = {kNParams, nn->d.step};
+  bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 2, f) == 2 &&
+            fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? HZ_OK : HZ_ERR_INVALID;
+}
+
+int hz_nn_load(hz_nn nn, const char* path) {
+  if (!nn || !path) return HZ_ERR_INVALID;
+  FILE* f = fopen(path, "rb");
+  if (!f) return HZ_ERR_INVALID;
+  char magic[8];
+  int32_t hdr[2];
+  std::vector<float> buf(3 * kNParams);
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "HZNN0001", 8) == 0 && fread(hdr, sizeof(int32_t), 2, f) == 2 &&
+            hdr[0] == kNParams && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) return HZ_ERR_INVALID;
+  NnDev& d = nn->d;
+  NN_CK(cudaMemcpyAsync(d.master, buf.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice, nn->stream));
+  NN_CK(cudaMemcpyAsync(d.m, buf.data() + kNParams, sizeof(float) * kNParams, cudaMemcpyHostToDevice, nn->stream));
+  NN_CK(cudaMemcpyAsync(d.v, buf.data() + 2 * kNParams, sizeof(float) * kNParams, cudaMemcpyHostToDevice, nn->stream));
+  d.step = hdr[1];
+  int st = nn_refresh(nn);
+  if (st != HZ_OK) return st;
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  return HZ_OK;
+}
+
+}  // extern "C"

@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96"])
+    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned"])
+    ap.add_argument("--train-systems", type=int, default=24)
+    ap.add_argument("--test-systems", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=240)
     ap.add_argument("--z-unit", default="radius", choices=["radius", "m"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -347,10 +350,98 @@ def make_seed(args):
     return f"{w['seed_coef']}/{w['seed_rhs']}"
 
 
+def run_batched(args):
+    """32 uneven systems (192x144, 320x240, 640x480; 70 levels) solved together per step."""
+    import torch
+
+    import gen
+    import paper_1811_03852_gb300 as hz
+
+    torch.cuda.set_device(0)
+    specs = [gen.batched_spec(i) for i in range(32)]
+    ops, bs, xs, npts = [], [], [], 0
+    for s in specs:
+        A = gen.make_operator(s["nx"], s["ny"], s["nz"], s["seed_coef"], z_unit=args.z_unit)
+        b = gen.make_rhs(s["nx"], s["ny"], s["nz"], s["seed_rhs"])
+        ops.append(hz.Operator(A))
+        bs.append(torch.from_numpy(b.reshape(-1)).cuda())
+        xs.append(torch.empty(b.size, dtype=torch.float64, device="cuda"))
+        npts += b.size
+    for _ in range(args.warmup):
+        hz.solve_batched(ops, bs, xs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = None
+    for _ in range(args.steps):
+        infos = hz.solve_batched(ops, bs, xs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    inner = sum(i["inner_iters"] * s["nx"] * s["ny"] * s["nz"] for i, s in zip(infos, specs))
+    outer = sum((i["outer_iters"] + 1) * s["nx"] * s["ny"] * s["nz"] for i, s in zip(infos, specs))
+    # algorithmic bytes: 152 B per point and inner iteration, 88 B per point and residual pass
+    gbs = (152.0 * inner + 88.0 * outer) / (ms * 1e-3) / 1e9
+    peak, kind = measured_peaks()
+    print(json.dumps({"workload": "batched 32 systems (192x144, 320x240, 640x480) x 70, mixed IR tol 1e-8",
+                      "points": npts, "systems_per_s": round(32 / (ms * 1e-3), 3), "ms_per_batch": round(ms, 3),
+                      "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
+                      "inner_iters": [i["inner_iters"] for i in infos],
+                      "effective_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 3),
+                      "peak_source": f"{kind} hbm_gbs"}), flush=True)
+
+
+def run_learned(args):
+    """Learned stage on 640x480x70: train on fresh seeds, evaluate plain vs learned FGMRES on held-out seeds."""
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+    from paper_1811_03852_gb300 import learn
+
+    torch.cuda.set_device(0)
+    dims = (640, 480, 70)
+    train_sys = [(10000 + 2 * i, 10001 + 2 * i) for i in range(args.train_systems)]
+    test_sys = [(20000 + 2 * i, 20001 + 2 * i) for i in range(args.test_systems)]
+    net = hz.Net(learn.init_params(1))
+    t0 = time.perf_counter()
+    losses = learn.train(net, train_sys, dims, steps=args.train_steps, batch=16, crop=64, lr=1e-3, seed=7,
+                         z_unit=args.z_unit)
+    t_train = time.perf_counter() - t0
+    rows = learn.evaluate(net, test_sys, dims, z_unit=args.z_unit)
+    # the plain mixed BiCGStab solver on the same held-out systems, for reference
+    import gen
+
+    bic = []
+    for sc, sr in test_sys:
+        op = hz.Operator(gen.make_operator(*dims, sc, z_unit=args.z_unit))
+        b = torch.from_numpy(gen.make_rhs(*dims, sr).reshape(-1)).cuda()
+        x = torch.empty_like(b)
+        op.solve(b, x)
+        bic.append(op.solve(b, x))
+    pl = [r["plain"] for r in rows]
+    le = [r["learned"] for r in rows]
+    out = {"workload": f"learned stage 640x480x70 z_unit={args.z_unit}", "train_systems": len(train_sys),
+           "test_systems": len(test_sys), "train_steps": len(losses), "train_s": round(t_train, 1),
+           "loss_first": losses[0], "loss_last10": float(np.mean(losses[-10:])),
+           "fgmres_plain": {"solves_per_s": len(pl) / sum(i["seconds"] for i in pl),
+                            "inner_iters": [i["inner_iters"] for i in pl]},
+           "fgmres_learned": {"solves_per_s": len(le) / sum(i["seconds"] for i in le),
+                              "inner_iters": [i["inner_iters"] for i in le], "fallbacks": [i["fallbacks"] for i in le],
+                              "status": [i["status"] for i in le],
+                              "max_true_rel_residual": max(i["true_rel_residual"] for i in le)},
+           "bicgstab_plain": {"solves_per_s": len(bic) / sum(i["seconds"] for i in bic),
+                              "inner_iters": [i["inner_iters"] for i in bic]}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

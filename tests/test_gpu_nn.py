@@ -235,11 +235,12 @@ def test_zero_network_equals_plain_preconditioner():
     import paper_1811_03852_gb300 as hz
 
     A, b = gen.make_system(48, 24, 10, 5, 6, z_unit="m")
-    net = hz.Net()  # all parameters zero: the stage adds nothing
+    net = hz.Net()  # all parameters zero: the stage adds nothing (z = z1 exactly)
     x1, i1 = _fgmres_nn(A, b, net)
     x0, i0 = _fgmres_nn(A, b, None)
-    assert i1["status"] == 0 and i1["inner_iters"] == i0["inner_iters"] and i1["fallbacks"] == 0
-    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-12
+    # same iterates; the stall test may still switch the (useless) stage off
+    assert i1["status"] == 0 and i1["inner_iters"] == i0["inner_iters"]
+    assert np.array_equal(x1, x0)
 
 
 def test_bad_network_falls_back_and_still_converges():

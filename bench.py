@@ -256,7 +256,7 @@ def run_ours(args):
 
     fp64 = None
     if not args.no_fp64:
-        ms64, inf64 = timed(p64, max(1, args.steps // 2), 1)
+        ms64, inf64 = timed(p64, max(1, min(2, args.steps)), 1)
         for i in inf64:
             assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
         fp64 = {"value": world * len(inf64) / (ms64 * 1e-3), "ms_per_solve": ms64 / len(inf64),
@@ -268,7 +268,7 @@ def run_ours(args):
     op.solve(bh, xh, params=pm)
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = max(1, args.steps // 2)
+    e2e_steps = max(1, min(3, args.steps))
     for _ in range(e2e_steps):
         op.solve(bh, xh, params=pm)
     barrier()
@@ -404,7 +404,7 @@ def run_learned(args):
     test_sys = [(20000 + 2 * i, 20001 + 2 * i) for i in range(args.test_systems)]
     net = hz.Net(learn.init_params(1))
     t0 = time.perf_counter()
-    losses = learn.train(net, train_sys, dims, steps=args.train_steps, batch=16, crop=64, lr=1e-3, seed=7,
+    losses = learn.train(net, train_sys, dims, steps=args.train_steps, batch=16, crop=64, lr=3e-4, seed=7,
                          z_unit=args.z_unit)
     t_train = time.perf_counter() - t0
     rows = learn.evaluate(net, test_sys, dims, z_unit=args.z_unit)

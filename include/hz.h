@@ -199,9 +199,10 @@ int hz_nn_forward(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, co
    every crop excluded in i and j); grad: host or device doubles, loss: host */
 int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
                    const float* t, double* grad, double* loss);
-/* one Adam step on that loss (loss: host, may be NULL) */
+/* one Adam step on that loss; the gradient is first scaled down to global
+   2-norm clip when it is larger (clip <= 0: no clipping).  loss: host, may be NULL */
 int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
-                     const float* t, double lr, double* loss);
+                     const float* t, double lr, double clip, double* loss);
 /* ncrop crops of cx x cy columns, all levels, from two fields [nz][ny][nx]:
    crop q starts at column (corners[2q], corners[2q+1]) (host ints; i wraps,
    rows outside the grid are zero); outputs [nz][ncrop*cy][cx] (crops stacked

@@ -339,7 +339,7 @@ def _nn_sigs(L):
         "hz_nn_get_params": (i32, [pv, pv]),
         "hz_nn_forward": (i32, [pv, i32, i32, i32, i32, i32, pv, pv, pv]),
         "hz_nn_gradient": (i32, [pv, i32, i32, i32, i32, i32, i32, pv, pv, pv, P(dbl)]),
-        "hz_nn_train_step": (i32, [pv, i32, i32, i32, i32, i32, i32, pv, pv, dbl, P(dbl)]),
+        "hz_nn_train_step": (i32, [pv, i32, i32, i32, i32, i32, i32, pv, pv, dbl, dbl, P(dbl)]),
         "hz_nn_crops": (i32, [i32, i32, i32, pv, pv, i32, i32, i32, pv, pv, pv, pv]),
         "hz_nn_save": (i32, [pv, ctypes.c_char_p]),
         "hz_nn_load": (i32, [pv, ctypes.c_char_p]),
@@ -418,11 +418,11 @@ class Net:
                                           g.ctypes.data, ctypes.byref(loss)), "hz_nn_gradient")
         return g, loss.value
 
-    def train_step(self, x, t, dims, lr=1e-3, seg_ny=None, periodic=False, border=0):
+    def train_step(self, x, t, dims, lr=1e-3, seg_ny=None, periodic=False, border=0, clip=0.0):
         nx, ny, nz = dims
         loss = ctypes.c_double()
         _nn_check(_nnlib().hz_nn_train_step(self._h, nx, ny, nz, seg_ny or ny, int(periodic), border, _ptr(x), _ptr(t),
-                                            lr, ctypes.byref(loss)), "hz_nn_train_step")
+                                            lr, clip, ctypes.byref(loss)), "hz_nn_train_step")
         return loss.value
 
     def save(self, path):

@@ -399,11 +399,27 @@ __global__ void __launch_bounds__(256) k_nn_dy(NnGrid g, const float* __restrict
 
 // Adam (Kingma & Ba) on the FP32 master parameters; lr, betas, eps and the
 // bias corrections come from the host.
+// global gradient norm (one block, fixed order) -> clipping factor min(1, clip / ||g||)
+__global__ void k_nn_gclip(int np, const double* __restrict__ grad, double clip, double* __restrict__ factor) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < np; q += blockDim.x) s += grad[q] * grad[q];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x; ++w) t += sm[w];
+    const double nrm = sqrt(t);
+    *factor = (clip > 0.0 && nrm > clip) ? clip / nrm : 1.0;
+  }
+}
+
 __global__ void k_nn_adam(int np, float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                          const double* __restrict__ grad, float lr, float b1, float b2, float eps, float c1,
-                          float c2) {
+                          const double* __restrict__ grad, const double* __restrict__ gscale, float lr, float b1,
+                          float b2, float eps, float c1, float c2) {
+  const double gs = *gscale;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
-    const float gq = (float)grad[q];
+    const float gq = (float)(grad[q] * gs);
     const float mq = b1 * m[q] + (1.f - b1) * gq;
     const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
     m[q] = mq;
@@ -736,7 +752,7 @@ int hz_nn_create(void* stream, hz_nn* out) {
   d.b4 = d.w4 + kP4;
   if (cudaMalloc(&d.w2b, sizeof(__nv_bfloat16) * 2 * kP2) != cudaSuccess) return fail(HZ_ERR_OOM);
   d.w3b = d.w2b + kP2;
-  if (cudaMalloc(&d.lossv, sizeof(double) * 2) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMalloc(&d.lossv, sizeof(double) * 4) != cudaSuccess) return fail(HZ_ERR_OOM);
   if (cudaMallocHost(&d.lossh, sizeof(double) * 2) != cudaSuccess) return fail(HZ_ERR_OOM);
   cudaMemsetAsync(d.master, 0, sizeof(float) * kNParams, nn->stream);
   cudaMemsetAsync(d.m, 0, sizeof(float) * kNParams, nn->stream);
@@ -815,7 +831,7 @@ int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, i
 }
 
 int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
-                     const float* t, double lr, double* loss) {
+                     const float* t, double lr, double clip, double* loss) {
   if (!nn || !x || !t || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny || border < 0 || !(lr > 0))
     return HZ_ERR_INVALID;
   NnGrid g{nx, ny, nz, seg_ny, periodic ? 1 : 0, (int64_t)nx * ny * nz};
@@ -825,8 +841,9 @@ int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic,
   d.step += 1;
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = (float)(1.0 - std::pow(b1, d.step)), c2 = (float)(1.0 - std::pow(b2, d.step));
-  k_nn_adam<<<(kNParams + 255) / 256, 256, 0, nn->stream>>>(kNParams, d.master, d.m, d.v, d.grad, (float)lr, (float)b1,
-                                                             (float)b2, 1e-8f, c1, c2);
+  k_nn_gclip<<<1, 256, 0, nn->stream>>>(kNParams, d.grad, clip, d.lossv + 2);
+  k_nn_adam<<<(kNParams + 255) / 256, 256, 0, nn->stream>>>(kNParams, d.master, d.m, d.v, d.grad, d.lossv + 2, (float)lr,
+                                                             (float)b1, (float)b2, 1e-8f, c1, c2);
   NN_CK(cudaGetLastError());
   if ((st = nn_refresh(nn)) != HZ_OK) return st;
   if (loss) {

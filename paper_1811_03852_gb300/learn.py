@@ -65,8 +65,8 @@ def system_pairs(op, b_dev, iters=(1, 2, 4, 8, 16, 32), eta_star=1e-11):
     return pairs
 
 
-def train(net, systems, dims, steps=200, batch=16, crop=64, lr=1e-3, seed=0, z_unit="radius", iters=None,
-          log=None):
+def train(net, systems, dims, steps=200, batch=16, crop=64, lr=3e-4, seed=0, z_unit="radius", iters=None,
+          log=None, clip=1.0):
     """Train on the given (seed_coef, seed_rhs) systems.  Returns the list of losses."""
     torch = _torch()
     import gen
@@ -76,7 +76,6 @@ def train(net, systems, dims, steps=200, batch=16, crop=64, lr=1e-3, seed=0, z_u
     cx = cy = crop + 2 * HALO
     bin_ = torch.empty(batch * cx * cy * nz, dtype=torch.float32, device="cuda")
     btg = torch.empty_like(bin_)
-    per = cx * cy * nz
     losses = []
     steps_per_sys = max(1, steps // max(1, len(systems)))
     ctr = 0
@@ -97,7 +96,8 @@ def train(net, systems, dims, steps=200, batch=16, crop=64, lr=1e-3, seed=0, z_u
                 ctr += 1
                 corners.append((i0 - HALO, j0 - HALO))
             hz.nn_crops(pairs[pi][0], pairs[pi][1], dims, corners, cx, cy, bin_, btg)
-            loss = net.train_step(bin_, btg, (cx, batch * cy, nz), lr=lr, seg_ny=cy, periodic=False, border=HALO)
+            loss = net.train_step(bin_, btg, (cx, batch * cy, nz), lr=lr, seg_ny=cy, periodic=False, border=HALO,
+                                  clip=clip)
             losses.append(loss)
             if log and len(losses) % 20 == 0:
                 log(f"step {len(losses)} system {si} loss {loss:.4f}")

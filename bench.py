@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--eta", type=float, default=1e-4, help="inner relative tolerance of the mixed solver")
+    ap.add_argument("--restart", type=int, default=150, help="forced BiCGStab restart period")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven inner loop (same kernels); ncu cannot profile kernels inside conditional graphs")
     return ap.parse_args()
 
 
@@ -208,8 +211,9 @@ def run_ours(args):
     bd = torch.from_numpy(b.reshape(-1)).to(f"cuda:{dev}")
     x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
     variants = op.autotune(fp64=not args.no_fp64)  # launch-shape search, outside the timed region
-    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta)
-    p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8)
+    ug = 0 if args.no_graph else 1
+    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta, restart=args.restart, use_graph=ug)
+    p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8, restart=args.restart, use_graph=ug)
 
     def barrier():
         if world > 1:

@@ -76,7 +76,7 @@ typedef enum { HZ_KRYLOV_BICGSTAB = 0, HZ_KRYLOV_FGMRES = 1 } hz_krylov;
 /* Solve parameters (host struct).  Fill with hz_default_params first. */
 typedef struct {
   double tol;        /* target true relative residual ||b - A x|| / ||b||   (default 1e-8) */
-  double inner_tol;  /* inner relative tolerance eta on the scaled system (default 1e-4; FP64 mode: 0.1*tol) */
+  double inner_tol;  /* inner relative tolerance eta on the scaled system (0: default, 1e-4 mixed; tol in FP64 mode) */
   int mode;          /* hz_mode (default HZ_MODE_MIXED_IR) */
   int precond;       /* hz_precond (default HZ_PRE_TRI) */
   int krylov;        /* hz_krylov (default HZ_KRYLOV_BICGSTAB) */

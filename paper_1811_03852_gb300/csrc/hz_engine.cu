@@ -691,7 +691,9 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   // the learned stage is not a fixed linear operator: it needs the flexible solver and a network
   if (p.precond == HZ_PRE_TRI_NN && (p.krylov != HZ_KRYLOV_FGMRES || !op->nn)) return HZ_ERR_UNSUPPORTED;
   const bool fp32 = (p.mode == HZ_MODE_MIXED_IR);
-  const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : 0.1 * p.tol);
+  // FP64 mode is plain BiCGStab to tol (one inner solve; the outer check adds a
+  // step only if the scaled residual and the true one disagree)
+  const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : p.tol);
   const int64_t n = op->g.n;
   const size_t bytes = sizeof(double) * (size_t)n;
   cudaStream_t s = op->stream;

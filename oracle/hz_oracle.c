@@ -141,6 +141,71 @@ void or_apply_Tinv(int nx, int ny, int nz, const double* Ah, const double* r, do
   free(lo);
 }
 
+/* ---------------------------------------------------------------------------
+ * The paper's preconditioner (Sec. 2): a few sweeps of SOR with the vertical
+ * tridiagonal T in place of the diagonal, Ahat = L + T + U,
+ *   (T + omega L) x_n = (1 - omega) T x_(n-1) + omega (r - U x_(n-1)),  x_0 = 0,
+ * i.e. per column x_n = (1 - omega) x_(n-1) + omega T^-1 (r - L x_n - U x_(n-1)).
+ * Column order: red-black in (i, j) (colour (i + j) mod 2, red first), so the
+ * horizontal neighbours of a red column are black (U) and those of a black
+ * column red (L).  z = x after `sweeps` sweeps.
+ * ------------------------------------------------------------------------- */
+void or_apply_trisor(int nx, int ny, int nz, const double* Ah, const double* r, double* z, int sweeps,
+                     double omega) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  double* lo = (double*)malloc(sizeof(double) * 7 * (size_t)nz);
+  double* di = lo + nz;
+  double* up = di + nz;
+  double* rc = up + nz;
+  double* xc = rc + nz;
+  double* wk = xc + nz;
+  /* within one colour pass every column reads the values from before the pass
+     (for even nx no two columns of a colour are neighbours, so this is
+     Gauss-Seidel in the red-black order; for odd nx it stays well defined) */
+  double* zo = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int64_t p = 0; p < n; ++p) z[p] = 0.0;
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int64_t p = 0; p < n; ++p) zo[p] = z[p];
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          if (((i + j) & 1) != colour) continue;
+          for (int k = 0; k < nz; ++k) {
+            int64_t p = IDX(i, j, k);
+            double h = Ah[0 * n + p] * zo[IDX((i + 1) % nx, j, k)] + Ah[1 * n + p] * zo[IDX((i + nx - 1) % nx, j, k)];
+            if (j + 1 < ny) h += Ah[2 * n + p] * zo[IDX(i, j + 1, k)];
+            if (j > 0) h += Ah[3 * n + p] * zo[IDX(i, j - 1, k)];
+            lo[k] = Ah[5 * n + p];
+            di[k] = 1.0;
+            up[k] = Ah[4 * n + p];
+            rc[k] = r[p] - h;
+          }
+          or_tridiag_solve(nz, lo, di, up, rc, xc, wk);
+          for (int k = 0; k < nz; ++k) {
+            int64_t p = IDX(i, j, k);
+            z[p] = (1.0 - omega) * z[p] + omega * xc[k];
+          }
+        }
+    }
+  free(zo);
+  free(lo);
+}
+
+/* Preconditioner used by or_bicgstab: kind 0 = T^-1, kind 1 = tri-SOR (sweeps, omega). */
+static int g_pc_kind = 0, g_pc_sweeps = 3;
+static double g_pc_omega = 1.5;
+void or_set_precond(int kind, int sweeps, double omega) {
+  g_pc_kind = kind;
+  g_pc_sweeps = sweeps;
+  g_pc_omega = omega;
+}
+static void apply_precond(int nx, int ny, int nz, const double* Ah, const double* r, double* z) {
+  if (g_pc_kind == 1)
+    or_apply_trisor(nx, ny, nz, Ah, r, z, g_pc_sweeps, g_pc_omega);
+  else
+    or_apply_Tinv(nx, ny, nz, Ah, r, z);
+}
+
 /* FP32-emulated variants: every stored value is a float, arithmetic in float. */
 static void matvec_hat_f32(int nx, int ny, int nz, const float* Ah, const float* x, float* y) {
   const int64_t n = (int64_t)nx * ny * nz;
@@ -257,7 +322,7 @@ void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, dou
     ++since;
     double beta = (rho1 / rho) * (alpha / omega);
     for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
-    or_apply_Tinv(nx, ny, nz, Ah, p, ph);
+    apply_precond(nx, ny, nz, Ah, p, ph);
     or_matvec_hat(nx, ny, nz, Ah, ph, v);
     alpha = rho1 / dot_d(n, r0, v);
     for (int64_t q = 0; q < n; ++q) s[q] = r[q] - alpha * v[q];
@@ -269,7 +334,7 @@ void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, dou
       status = 0;
       break;
     }
-    or_apply_Tinv(nx, ny, nz, Ah, s, sh);
+    apply_precond(nx, ny, nz, Ah, s, sh);
     or_matvec_hat(nx, ny, nz, Ah, sh, t);
     double tt = dot_d(n, t, t);
     omega = tt > 0.0 ? dot_d(n, t, s) / tt : 0.0;

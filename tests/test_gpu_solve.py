@@ -182,7 +182,8 @@ def test_full_size_640x480x70_true_residual(mode):
     assert info["status"] == 0
     _, rn = oracle.residual(A, b, x)
     assert rn / np.linalg.norm(b) <= 1e-8
-    assert abs(rn / np.linalg.norm(b) - info["true_rel_residual"]) <= 1e-3 * info["true_rel_residual"]
+    # the two residuals agree up to the rounding floor of b - A x (about 1e-15 relative here)
+    assert abs(rn / np.linalg.norm(b) - info["true_rel_residual"]) <= 1e-3 * info["true_rel_residual"] + 1e-14
 
 
 def test_full_size_n1280_true_residual():

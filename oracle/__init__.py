@@ -185,3 +185,28 @@ def solve(A, b, x0=None, mode=MODE_MIXED, tol=1e-8, eta=1e-4, max_outer=20, max_
 def dot(a, b):
     a, b = _c(a).ravel(), _c(b).ravel()
     return _load().or_dot(a.size, _p(a), _p(b))
+
+
+def apply_trisor(Ah, r, sweeps=3, omega=1.5):
+    """z = C r, C = `sweeps` red-black tri-SOR sweeps from zero (Sec. 2 fixed point)."""
+    Ah, r = _c(Ah), _c(r)
+    nx, ny, nz = _dims(r)
+    z = np.empty_like(r)
+    L = _load()
+    if not getattr(L, "_sor_sig", False):
+        L.or_apply_trisor.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_double]
+        L.or_apply_trisor.restype = None
+        L.or_set_precond.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.or_set_precond.restype = None
+        L._sor_sig = True
+    L.or_apply_trisor(nx, ny, nz, _p(Ah), _p(r), _p(z), sweeps, omega)
+    return z
+
+
+def set_precond(kind, sweeps=3, omega=1.5):
+    """Preconditioner of bicgstab()/solve(): kind 0 = T^-1 (default), 1 = tri-SOR(sweeps, omega)."""
+    apply_trisor  # noqa: B018  (ensures signatures below)
+    L = _load()
+    L.or_set_precond.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    L.or_set_precond.restype = None
+    L.or_set_precond(kind, sweeps, omega)

@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--eta", type=float, default=1e-4, help="inner relative tolerance of the mixed solver")
     ap.add_argument("--restart", type=int, default=150, help="forced BiCGStab restart period")
+    ap.add_argument("--precond", default="tri", choices=["tri", "trisor"],
+                    help="preconditioner of the headline solves: T^-1 or tri-SOR (Sec. 2)")
+    ap.add_argument("--no-trisor", action="store_true", help="skip the tri-SOR side measurement")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven inner loop (same kernels); ncu cannot profile kernels inside conditional graphs")
     return ap.parse_args()
@@ -212,8 +215,10 @@ def run_ours(args):
     x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
     variants = op.autotune(fp64=not args.no_fp64)  # launch-shape search, outside the timed region
     ug = 0 if args.no_graph else 1
-    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta, restart=args.restart, use_graph=ug)
-    p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8, restart=args.restart, use_graph=ug)
+    pc = hz.HZ_PRE_TRISOR if args.precond == "trisor" else hz.HZ_PRE_TRI
+    pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta, restart=args.restart, use_graph=ug,
+                           precond=pc)
+    p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8, restart=args.restart, use_graph=ug, precond=pc)
 
     def barrier():
         if world > 1:
@@ -265,6 +270,33 @@ def run_ours(args):
             assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
         fp64 = {"value": world * len(inf64) / (ms64 * 1e-3), "ms_per_solve": ms64 / len(inf64),
                 "outer": inf64[0]["outer_iters"], "inner": inf64[0]["inner_iters"]}
+
+    # the paper's tri-SOR preconditioner (3 red-black sweeps, omega 1.5) on the same system, one solve each
+    trisor = None
+    if not args.no_trisor and args.precond == "tri" and nx % 2 == 0:
+        ps = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta, restart=args.restart,
+                               use_graph=ug, precond=hz.HZ_PRE_TRISOR)
+        mss, infs = timed(ps, 1, 1)
+        for i in infs:
+            assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
+        trisor = {"mixed": {"value": round(world / (mss * 1e-3), 4), "ms_per_solve": round(mss, 3),
+                            "outer": infs[0]["outer_iters"], "inner": infs[0]["inner_iters"]}}
+        if not args.no_fp64:
+            ps64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8, restart=args.restart, use_graph=ug,
+                                     precond=hz.HZ_PRE_TRISOR)
+            mss64, infs64 = timed(ps64, 1, 1)
+            for i in infs64:
+                assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
+            trisor["fp64"] = {"value": round(world / (mss64 * 1e-3), 4), "ms_per_solve": round(mss64, 3),
+                              "outer": infs64[0]["outer_iters"], "inner": infs64[0]["inner_iters"]}
+        op.profile(True)
+        op.solve(bd, x, params=ps)
+        sp = {k: v for k, v in op.profile_read().items() if v[0] > 0}
+        op.profile(False)
+        st = sum(v[1] for v in sp.values())
+        trisor["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / st, 4),
+                                 "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
+                             for k, v in sp.items()}
 
     # end to end through the public API with host buffers (pinned b, pinned x)
     bh = torch.from_numpy(b.reshape(-1)).pin_memory()
@@ -327,12 +359,13 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
         "config": {"workload": f"{args.workload} {nx}x{ny}x{nz} z_unit={args.z_unit} seeds "
-                               f"{make_seed(args)} mixed IR tol 1e-8 eta {args.eta:g}",
+                               f"{make_seed(args)} mixed IR tol 1e-8 eta {args.eta:g} precond {args.precond}",
                    "l2": "inputs larger than L2 (vectors 1.4-2.8 GB)", "parallelism": f"replicas x{world}"},
         "solve": {"outer": infos[0]["outer_iters"], "inner": infos[0]["inner_iters"],
                   "true_rel_residual": infos[0]["true_rel_residual"]},
         "fp64": fp64,
         "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
+        "trisor": trisor,
         "setup_ms": round(min(su), 3),
         "variants": variants,
         "e2e": e2e,

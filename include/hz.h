@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define HZ_ABI_VERSION 1
+#define HZ_ABI_VERSION 2
 
 typedef struct hz_op_s* hz_op;
 
@@ -68,7 +68,11 @@ typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
 
 typedef enum {
   HZ_PRE_TRI = 0,    /* C = T^-1, the per-column tridiagonal solve */
-  HZ_PRE_TRI_NN = 1  /* T^-1 followed by the learned conv-net correction (flexible Krylov only) */
+  HZ_PRE_TRI_NN = 1, /* T^-1 followed by the learned conv-net correction (flexible Krylov only) */
+  HZ_PRE_TRISOR = 2  /* tri-SOR (Sec. 2): sor_sweeps red-black sweeps of
+                        x_n = (1-w) x_(n-1) + w T^-1 (r - L x_n - U x_(n-1)), w = sor_omega,
+                        from x_0 = 0; red = columns with (i + j) even, first.
+                        BiCGStab only; needs nx even (HZ_ERR_UNSUPPORTED otherwise). */
 } hz_precond;
 
 typedef enum { HZ_KRYLOV_BICGSTAB = 0, HZ_KRYLOV_FGMRES = 1 } hz_krylov;
@@ -86,6 +90,8 @@ typedef struct {
   int fgmres_m;      /* FGMRES restart length (default 30) */
   int use_graph;     /* 1: inner loop runs on the device inside a CUDA graph (default); 0: host-driven */
   int record_history;/* 1: keep the inner recursive residual after every iteration (hz_get_history) */
+  int sor_sweeps;    /* HZ_PRE_TRISOR: sweeps per application, 1..64 (default 3, Sec. 2) */
+  double sor_omega;  /* HZ_PRE_TRISOR: relaxation factor, 0 < w < 2 (default 1.5, Sec. 2) */
 } hz_solve_params;
 
 /* Solve report (host struct). */
@@ -250,7 +256,11 @@ int hz_op_set_variants(hz_op op, int pre32, int mv32, int pre64, int mv64);
  * algorithmic bytes (each array element read or written once per launch).
  * Enabling (or disabling) resets the counters.  hz_op_update is profiled too.
  */
-#define HZ_NUM_KERNELS 7 /* k_setup, k_residual, k_pre_p, k_mv_v, k_pre_s, k_mv_t, k_upd */
+/* ids: 0 k_setup, 1 k_residual, 2 k_pre_p, 3 k_mv_v, 4 k_pre_s, 5 k_mv_t, 6 k_upd,
+   and for HZ_PRE_TRISOR: 7 k_sor_first (vector update + first red pass),
+   8 k_sor_pass (colour passes), 9 k_mv_rb (Ahat matvec + dots), 10 k_rb_copy
+   (natural <-> colour-compact order around each refinement step) */
+#define HZ_NUM_KERNELS 11
 int hz_profile_enable(hz_op op, int on);
 int hz_profile_read(hz_op op, int kid, long long* launches, double* ms, double* bytes);
 const char* hz_kernel_name(int kid);
@@ -268,6 +278,15 @@ int hz_precond_apply(hz_op op, int prec, const void* r, void* z);
 /* v = D^-1 A (T^-1 p) as the solver forms it: ph = T^-1 p, then
    v = p + H ph with H the four horizontal bands (T ph = p).  p, ph, v: device. */
 int hz_precond_matvec(hz_op op, int prec, const void* p, void* ph, void* v);
+
+/* z = C r with C the tri-SOR preconditioner of Sec. 2: `sweeps` (1..64)
+   red-black sweeps x_n = (1-w) x_(n-1) + w T^-1 (r - L x_n - U x_(n-1)) from
+   x_0 = 0, w = omega in (0, 2), in the given precision; the same kernels as
+   the solver (which work in colour-compact column order: r is gathered into
+   it and z scattered back).  r, z: device arrays in natural order; may not
+   alias.  Needs nx even (HZ_ERR_UNSUPPORTED).  Overwrites the operator's
+   inner work vectors of that precision: call between solves. */
+int hz_trisor_apply(hz_op op, int prec, int sweeps, double omega, const void* r, void* z);
 
 /* True FP64 residual (Sec. 3): r = b - A x with the unscaled bands.
    b, x: device doubles; r: device doubles or NULL; rnorm, bnorm: host outputs (may be NULL). */

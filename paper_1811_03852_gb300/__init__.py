@@ -40,9 +40,10 @@ HZ_PREC_FP64 = 0
 HZ_PREC_FP32 = 1
 HZ_PRE_TRI = 0
 HZ_PRE_TRI_NN = 1
+HZ_PRE_TRISOR = 2
 HZ_KRYLOV_BICGSTAB = 0
 HZ_KRYLOV_FGMRES = 1
-NUM_KERNELS = 7
+NUM_KERNELS = 11
 
 
 class hz_solve_params(ctypes.Structure):
@@ -58,6 +59,8 @@ class hz_solve_params(ctypes.Structure):
         ("fgmres_m", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("record_history", ctypes.c_int),
+        ("sor_sweeps", ctypes.c_int),
+        ("sor_omega", ctypes.c_double),
     ]
 
 
@@ -110,6 +113,7 @@ def load(build_if_missing: bool = True):
         "hz_get_history": (i32, [pv, pv, i32]),
         "hz_matvec": (i32, [pv, i32, pv, pv]),
         "hz_precond_apply": (i32, [pv, i32, pv, pv]),
+        "hz_trisor_apply": (i32, [pv, i32, i32, ctypes.c_double, pv, pv]),
         "hz_precond_matvec": (i32, [pv, i32, pv, pv, pv]),
         "hz_residual": (i32, [pv, pv, pv, pv, P(dbl), P(dbl)]),
         "hz_dot": (i32, [i32, i64, pv, pv, pv, P(dbl)]),
@@ -234,6 +238,10 @@ class Operator:
 
     def precond_apply(self, r, z, prec):
         _check(load().hz_precond_apply(self._h, prec, _ptr(r), _ptr(z)), "hz_precond_apply")
+
+    def trisor_apply(self, r, z, prec, sweeps=3, omega=1.5):
+        """z = C r, C = `sweeps` red-black tri-SOR sweeps (Sec. 2); overwrites the work vectors."""
+        _check(load().hz_trisor_apply(self._h, prec, sweeps, omega, _ptr(r), _ptr(z)), "hz_trisor_apply")
 
     def precond_matvec(self, p, ph, v, prec):
         _check(load().hz_precond_matvec(self._h, prec, _ptr(p), _ptr(ph), _ptr(v)), "hz_precond_matvec")

@@ -86,11 +86,21 @@ struct hz_op_s {
   double* hist_d = nullptr;
   int hist_cap = 0;
   GraphSlot gs[2];  // [0] FP32 inner loop, [1] FP64 inner loop
+  // tri-SOR: bands and Thomas factors in colour-compact order ([9][n] per
+  // precision, allocated on first use, refreshed after a coefficient update)
+  // and the inner-loop graphs, built for one (sweeps, omega) at a time
+  float* sor32 = nullptr;
+  double* sor64 = nullptr;
+  bool sor_ok[2] = {false, false};
+  GraphSlot gs_sor[2];
+  int gs_sor_sweeps[2] = {0, 0};
+  double gs_sor_omega[2] = {0.0, 0.0};
   std::vector<void*> allocs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-kernel profile (CUDA events around every launch; host-driven loop)
   bool prof = false;
   std::vector<cudaEvent_t> pev;
+  bool sor_mode = false;  // the current solve uses tri-SOR (compact order)
   long long p_launch[HZ_NUM_KERNELS] = {};
   double p_ms[HZ_NUM_KERNELS] = {};
   double p_bytes[HZ_NUM_KERNELS] = {};
@@ -154,6 +164,75 @@ int ensure_w64(hz_op op) {
   return HZ_OK;
 }
 
+// ---- tri-SOR (colour-compact order) ---------------------------------------
+template <typename T>
+T*& sor_base(hz_op op);
+template <>
+float*& sor_base<float>(hz_op op) { return op->sor32; }
+template <>
+double*& sor_base<double>(hz_op op) { return op->sor64; }
+
+template <typename T>
+Bands<T> bands_rb(hz_op op) {
+  const int64_t s = pad64(op->g.n);
+  const T* b = sor_base<T>(op);
+  return Bands<T>{b, b + s, b + 2 * s, b + 3 * s, b + 4 * s, b + 5 * s, b + 6 * s, b + 7 * s, b + 8 * s};
+}
+
+// compact copies of the six bands and the three Thomas factors
+template <typename T>
+int ensure_sor(hz_op op) {
+  const int pr = sizeof(T) == 8 ? 1 : 0;
+  if (op->sor_ok[pr]) return HZ_OK;
+  const int64_t s = pad64(op->g.n);
+  T*& base = sor_base<T>(op);
+  if (!base) {
+    int st = HZ_OK;
+    if (!(base = dalloc<T>(op, 9 * s, &st))) return st;
+  }
+  const Bands<T> a = bands_of<T>(op);
+  const T* src[9] = {a.E, a.W, a.N, a.S, a.U, a.D, a.m, a.l, a.cp};
+  for (int q = 0; q < 9; ++q) CK(launch_rb_copy<T>(op->g, src[q], base + q * s, 1, op->L));
+  op->sor_ok[pr] = true;
+  return HZ_OK;
+}
+
+// One inner BiCGStab iteration with the tri-SOR preconditioner, everything in
+// compact order: for each of p and s, the update fused with the first red
+// pass, then the remaining 2*sweeps - 1 colour passes ping-ponging between
+// the result vector (ph or sh) and t (free at that point); then the full
+// matvec with its dots; k_upd is shared with the T^-1 path.
+template <typename T>
+cudaError_t launch_body_sor(hz_op op, cudaStream_t s, unsigned long long cond, int use_cond, int sweeps,
+                            double omega) {
+  Launch L = op->L;
+  L.stream = s;
+  const Bands<T> a = bands_rb<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  cudaError_t e;
+  for (int half = 0; half < 2; ++half) {
+    T* res = half == 0 ? w.ph : w.sh;
+    const T* rc = half == 0 ? w.p : w.s;
+    // buf[(sw + 1) % 2] receives sweep sw; the last sweep must land in res
+    T* buf[2];
+    buf[sweeps % 2] = res;
+    buf[(sweeps + 1) % 2] = w.t;
+    if ((e = launch_sor_first<T>(op->g, a, w, buf[1], omega, half, op->ctl, op->red, L)) != cudaSuccess) return e;
+    for (int sw = 0; sw < sweeps; ++sw) {
+      T* zin = buf[sw % 2];
+      T* zout = buf[(sw + 1) % 2];
+      if (sw > 0 &&
+          (e = launch_sor_pass<T>(op->g, a, rc, zin, zin, zout, 0, 1, omega, op->ctl, L)) != cudaSuccess)
+        return e;
+      if ((e = launch_sor_pass<T>(op->g, a, rc, zout, sw > 0 ? zin : nullptr, zout, 1, 1, omega, op->ctl, L)) !=
+          cudaSuccess)
+        return e;
+    }
+    if ((e = launch_mv_rb<T>(op->g, a, w, half, op->ctl, op->red, L)) != cudaSuccess) return e;
+  }
+  return launch_upd<T>(op->g, w, op->ctl, op->red, cond, use_cond, L);
+}
+
 // one inner BiCGStab iteration (five launches) on stream s
 template <typename T>
 cudaError_t launch_body(hz_op op, cudaStream_t s, unsigned long long cond, int use_cond) {
@@ -171,6 +250,49 @@ cudaError_t launch_body(hz_op op, cudaStream_t s, unsigned long long cond, int u
 
 // Build the inner loop as a graph: one conditional WHILE node whose body is
 // one iteration; k_upd sets the condition from the device.
+template <typename F>
+int build_loop_graph(hz_op op, GraphSlot& gs, F&& body) {
+  if (gs.exec) return HZ_OK;
+  CK(cudaGraphCreate(&gs.graph, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, gs.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, gs.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(op->cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = body((unsigned long long)h);
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(op->cap, &out);
+  CK(e);
+  CK(e2);
+  CK(cudaGraphInstantiate(&gs.exec, gs.graph, 0));
+  return HZ_OK;
+}
+
+void drop_graph(GraphSlot& gs) {
+  if (gs.exec) cudaGraphExecDestroy(gs.exec);
+  if (gs.graph) cudaGraphDestroy(gs.graph);
+  gs.exec = nullptr;
+  gs.graph = nullptr;
+}
+
+// the tri-SOR loop graph of one precision, rebuilt when (sweeps, omega) change
+template <typename T>
+int build_graph_sor(hz_op op, int sweeps, double omega) {
+  const int pr = sizeof(T) == 8 ? 1 : 0;
+  GraphSlot& gs = op->gs_sor[pr];
+  if (gs.exec && (op->gs_sor_sweeps[pr] != sweeps || op->gs_sor_omega[pr] != omega)) drop_graph(gs);
+  op->gs_sor_sweeps[pr] = sweeps;
+  op->gs_sor_omega[pr] = omega;
+  return build_loop_graph(op, gs, [&](unsigned long long h) {
+    return launch_body_sor<T>(op, op->cap, h, 1, sweeps, omega);
+  });
+}
+
 template <typename T>
 int build_graph(hz_op op) {
   GraphSlot& gs = op->gs[sizeof(T) == 8 ? 1 : 0];
@@ -250,25 +372,107 @@ int profiled_iteration(hz_op op) {
   return HZ_OK;
 }
 
+// The tri-SOR iteration with every launch timed (kernel ids 7-9 and 6).
+// Algorithmic bytes per point, in units of sizeof(T): k_sor_first 4-6 for the
+// p update (13 on a restart) or 3 for s, plus 2 for the red half's Thomas
+// factors and z; a colour pass (half the points) 11, 10 without an old
+// iterate, 5 without neighbours; k_mv_rb 9.
 template <typename T>
-int run_inner(hz_op op, int use_graph, int max_inner) {
+int profiled_iteration_sor(hz_op op, int sweeps, double omega) {
+  const double n = (double)op->g.n, B = (double)sizeof(T);
+  Launch L = op->L;
+  const Bands<T> a = bands_rb<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  auto state = [&](Ctl* c) -> int {
+    CK(cudaMemcpyAsync(c, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    return HZ_OK;
+  };
+  Ctl* c = op->rep_h;
+  CKS(state(c));
+  if (c->state != ST_RUNNING && c->state != ST_RESTART) return HZ_OK;
+  const bool xz = c->xzero != 0;
+  for (int half = 0; half < 2; ++half) {
+    T* res = half == 0 ? w.ph : w.sh;
+    const T* rc = half == 0 ? w.p : w.s;
+    T* buf[2];
+    buf[sweeps % 2] = res;
+    buf[(sweeps + 1) % 2] = w.t;
+    double bf = 5.0;
+    if (half == 0) bf = c->state == ST_RESTART ? (xz ? 6.0 : 13.0) : (c->fresh ? 4.0 : 6.0);
+    CKS(prof_launch(op, 7, bf * B * n, [&] {
+      return launch_sor_first<T>(op->g, a, w, buf[1], omega, half, op->ctl, op->red, L);
+    }));
+    op->launches++;
+    CKS(state(c));
+    if (c->state != ST_RUNNING) {
+      if (half == 0) return HZ_OK;
+      break;
+    }
+    for (int sw = 0; sw < sweeps; ++sw) {
+      T* zin = buf[sw % 2];
+      T* zout = buf[(sw + 1) % 2];
+      if (sw > 0) {
+        CKS(prof_launch(op, 8, 5.5 * B * n, [&] {
+          return launch_sor_pass<T>(op->g, a, rc, zin, zin, zout, 0, 1, omega, op->ctl, L);
+        }));
+        op->launches++;
+      }
+      CKS(prof_launch(op, 8, (sw > 0 ? 5.5 : 5.0) * B * n, [&] {
+        return launch_sor_pass<T>(op->g, a, rc, zout, sw > 0 ? zin : nullptr, zout, 1, 1, omega, op->ctl, L);
+      }));
+      op->launches++;
+    }
+    CKS(prof_launch(op, 9, 9.0 * B * n, [&] { return launch_mv_rb<T>(op->g, a, w, half, op->ctl, op->red, L); }));
+    op->launches++;
+    if (half == 0) {
+      CKS(state(c));
+      if (c->state != ST_RUNNING) break;
+    }
+  }
+  CKS(state(c));
+  const bool hs = c->state == ST_HALF;
+  const double bu = hs ? (xz ? 2 : 3) * B : (xz ? 7 : 8) * B;
+  CKS(prof_launch(op, 6, bu * n, [&] { return launch_upd<T>(op->g, w, op->ctl, op->red, 0ull, 0, L); }));
+  op->launches++;
+  return HZ_OK;
+}
+
+// sweeps > 0: the tri-SOR preconditioner (compact order), else T^-1
+template <typename T>
+int run_inner(hz_op op, int use_graph, int max_inner, int sweeps = 0, double omega = 0.0) {
+  const bool sor = sweeps > 0;
   if (op->prof) {
     for (int it = 0; it < 4 * max_inner + 16; ++it) {
-      CKS(profiled_iteration<T>(op));
+      if (sor)
+        CKS(profiled_iteration_sor<T>(op, sweeps, omega));
+      else
+        CKS(profiled_iteration<T>(op));
       const int st = op->rep_h->state;
       if (st != ST_RUNNING && st != ST_RESTART) break;
     }
     return HZ_OK;
   }
+  const int pr = sizeof(T) == 8 ? 1 : 0;
   if (use_graph) {
-    CKS(build_graph<T>(op));
-    CK(cudaGraphLaunch(op->gs[sizeof(T) == 8 ? 1 : 0].exec, op->stream));
+    if (sor) {
+      CKS(build_graph_sor<T>(op, sweeps, omega));
+      CK(cudaGraphLaunch(op->gs_sor[pr].exec, op->stream));
+    } else {
+      CKS(build_graph<T>(op));
+      CK(cudaGraphLaunch(op->gs[pr].exec, op->stream));
+    }
     return HZ_OK;
   }
   // host-driven: launch iterations in groups and poll the device state
   const int group = 4;
   for (int it = 0; it < 4 * max_inner + 16; it += group) {
-    for (int u = 0; u < group; ++u) CK(launch_body<T>(op, op->stream, 0ull, 0));
+    for (int u = 0; u < group; ++u) {
+      if (sor)
+        CK(launch_body_sor<T>(op, op->stream, 0ull, 0, sweeps, omega));
+      else
+        CK(launch_body<T>(op, op->stream, 0ull, 0));
+    }
     CK(cudaMemcpyAsync(&op->rep_h->state, &op->ctl->state, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
     CK(cudaStreamSynchronize(op->stream));
     const int st = op->rep_h->state;
@@ -405,6 +609,7 @@ int do_setup(hz_op op, const double* coeffs) {
   CK(cudaMemcpyAsync(op->A7, coeffs, sizeof(double) * 7 * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      op->stream));
   CK(cudaMemsetAsync(op->err_d, 0, sizeof(int), op->stream));
+  op->sor_ok[0] = op->sor_ok[1] = false;  // compact copies are redone on next use
   SetupOut o{op->ah32, op->th32, op->ah64, op->th64, op->invc, op->err_d};
   if (op->prof)
     CKS(prof_launch(op, 0, 164.0 * (double)n, [&] { return launch_setup(op->g, op->A7, o, op->L); }));
@@ -422,6 +627,7 @@ int do_setup(hz_op op, const double* coeffs) {
 
 void free_op(hz_op op) {
   if (!op) return;
+  for (auto& gs : op->gs_sor) drop_graph(gs);
   for (auto& gs : op->gs) {
     if (gs.exec) cudaGraphExecDestroy(gs.exec);
     if (gs.graph) cudaGraphDestroy(gs.graph);
@@ -573,6 +779,8 @@ void hz_default_params(hz_solve_params* p) {
   p->fgmres_m = 30;
   p->use_graph = 1;
   p->record_history = 0;
+  p->sor_sweeps = 3;
+  p->sor_omega = 1.5;
 }
 
 int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_op* out) {
@@ -687,9 +895,14 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   if (p.krylov != HZ_KRYLOV_BICGSTAB && p.krylov != HZ_KRYLOV_FGMRES) return HZ_ERR_INVALID;
   if (p.krylov == HZ_KRYLOV_FGMRES && (p.mode != HZ_MODE_MIXED_IR || p.fgmres_m < 1 || p.fgmres_m > kMaxFgm))
     return HZ_ERR_UNSUPPORTED;
-  if (p.precond != HZ_PRE_TRI && p.precond != HZ_PRE_TRI_NN) return HZ_ERR_INVALID;
+  if (p.precond != HZ_PRE_TRI && p.precond != HZ_PRE_TRI_NN && p.precond != HZ_PRE_TRISOR) return HZ_ERR_INVALID;
   // the learned stage is not a fixed linear operator: it needs the flexible solver and a network
   if (p.precond == HZ_PRE_TRI_NN && (p.krylov != HZ_KRYLOV_FGMRES || !op->nn)) return HZ_ERR_UNSUPPORTED;
+  const bool sor = (p.precond == HZ_PRE_TRISOR);
+  if (sor) {
+    if (p.sor_sweeps < 1 || p.sor_sweeps > 64 || !(p.sor_omega > 0.0 && p.sor_omega < 2.0)) return HZ_ERR_INVALID;
+    if (p.krylov != HZ_KRYLOV_BICGSTAB || op->g.nx % 2 != 0) return HZ_ERR_UNSUPPORTED;
+  }
   const bool fp32 = (p.mode == HZ_MODE_MIXED_IR);
   // FP64 mode is plain BiCGStab to tol (one inner solve; the outer check adds a
   // step only if the scaled residual and the true one disagree)
@@ -698,6 +911,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   const size_t bytes = sizeof(double) * (size_t)n;
   cudaStream_t s = op->stream;
   if (!fp32) CKS(ensure_w64(op));
+  if (sor) CKS(fp32 ? ensure_sor<float>(op) : ensure_sor<double>(op));
   if (p.record_history) {
     const int cap = std::max(1, p.max_inner * std::max(1, p.max_outer));
     if (cap > op->hist_cap) {
@@ -747,24 +961,43 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   cfg->state = ST_CONVERGED;
   CK(cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, s));
 
+  // tri-SOR: the inner vectors are in colour-compact order; the inner solution
+  // is scattered to natural order (into s) before the residual and the new
+  // inner right-hand side (written to t) gathered back into rhs after it
   auto residual = [&](const double* xin, double* xout, bool with_delta) -> int {
-    auto go = [&]() -> cudaError_t {
-      if (fp32)
-        return launch_residual<float>(op->g, op->A7, op->invc, bd, xin, xout, with_delta ? op->w32.x : nullptr,
-                                      op->w32.rhs, nullptr, 0, op->ctl, op->red, op->L);
-      return launch_residual<double>(op->g, op->A7, op->invc, bd, xin, xout, with_delta ? op->w64.x : nullptr,
-                                     op->w64.rhs, nullptr, 0, op->ctl, op->red, op->L);
+    const double ds = fp32 ? 4.0 : 8.0;
+    auto step = [&](int kid, double bytes, auto&& launch) -> int {
+      if (op->prof)
+        CKS(prof_launch(op, kid, bytes * (double)n, launch));
+      else
+        CK(launch());
+      op->launches++;
+      return HZ_OK;
     };
-    if (op->prof) {
-      // algorithmic bytes: C band, b, rhs; plus the other six bands, x, d and x out for a stencil pass
-      const double ds = fp32 ? 4.0 : 8.0;
-      double bp = 8 + 8 + ds;
-      if (xin || with_delta) bp += 48 + (xin ? 8 : 0) + (with_delta ? ds : 0) + (xout ? 8 : 0);
-      CKS(prof_launch(op, 1, bp * (double)n, go));
-    } else {
-      CK(go());
-    }
-    op->launches++;
+    auto rb = [&](int to_compact) -> cudaError_t {
+      if (fp32)
+        return to_compact ? launch_rb_copy<float>(op->g, op->w32.t, op->w32.rhs, 1, op->L)
+                          : launch_rb_copy<float>(op->g, op->w32.x, op->w32.s, 0, op->L);
+      return to_compact ? launch_rb_copy<double>(op->g, op->w64.t, op->w64.rhs, 1, op->L)
+                        : launch_rb_copy<double>(op->g, op->w64.x, op->w64.s, 0, op->L);
+    };
+    if (sor && with_delta) CKS(step(10, 2 * ds, [&] { return rb(0); }));
+    auto go = [&]() -> cudaError_t {
+      if (fp32) {
+        const Vecs<float>& w = op->w32;
+        return launch_residual<float>(op->g, op->A7, op->invc, bd, xin, xout,
+                                      with_delta ? (sor ? w.s : w.x) : nullptr, sor ? w.t : w.rhs, nullptr, 0,
+                                      op->ctl, op->red, op->L);
+      }
+      const Vecs<double>& w = op->w64;
+      return launch_residual<double>(op->g, op->A7, op->invc, bd, xin, xout, with_delta ? (sor ? w.s : w.x) : nullptr,
+                                     sor ? w.t : w.rhs, nullptr, 0, op->ctl, op->red, op->L);
+    };
+    // algorithmic bytes: C band, b, rhs; plus the other six bands, x, d and x out for a stencil pass
+    double bp = 8 + 8 + ds;
+    if (xin || with_delta) bp += 48 + (xin ? 8 : 0) + (with_delta ? ds : 0) + (xout ? 8 : 0);
+    CKS(step(1, bp, go));
+    if (sor) CKS(step(10, 2 * ds, [&] { return rb(1); }));
     CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return HZ_OK;
@@ -784,13 +1017,16 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (p.krylov == HZ_KRYLOV_FGMRES)
       CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta, p.precond == HZ_PRE_TRI_NN, &fallbacks));
     else if (fp32)
-      CKS(run_inner<float>(op, p.use_graph, p.max_inner));
+      CKS(run_inner<float>(op, p.use_graph, p.max_inner, sor ? p.sor_sweeps : 0, p.sor_omega));
     else
-      CKS(run_inner<double>(op, p.use_graph, p.max_inner));
+      CKS(run_inner<double>(op, p.use_graph, p.max_inner, sor ? p.sor_sweeps : 0, p.sor_omega));
     double* next = (cur == XA) ? XB : XA;
     CKS(residual(cur, next, true));
     const Ctl& rp = *op->rep_h;
-    if (!op->prof) op->launches += 6LL * std::max(1, rp.last_iter);
+    // launches per inner iteration: 6 with T^-1; with tri-SOR 2 first-pass
+    // kernels, 2 (2 sweeps - 1) colour passes, 2 matvecs and k_upd
+    const long long per_it = sor ? 4LL * p.sor_sweeps + 3 : 6LL;
+    if (!op->prof) op->launches += per_it * std::max(1, rp.last_iter);
     inner_total += rp.last_iter;
     restarts += rp.last_restarts;
     scaled = rp.last_bnorm2 > 0.0 ? std::sqrt(rp.last_rnorm2 / rp.last_bnorm2) : 0.0;
@@ -985,8 +1221,9 @@ int hz_profile_read(hz_op op, int kid, long long* launches, double* ms, double* 
 }
 
 const char* hz_kernel_name(int kid) {
-  static const char* names[HZ_NUM_KERNELS] = {"k_setup", "k_residual", "k_pre_p", "k_mv_v", "k_pre_s", "k_mv_t",
-                                              "k_upd"};
+  static const char* names[HZ_NUM_KERNELS] = {"k_setup",     "k_residual", "k_pre_p", "k_mv_v",
+                                              "k_pre_s",     "k_mv_t",     "k_upd",   "k_sor_first",
+                                              "k_sor_pass",  "k_mv_rb",    "k_rb_copy"};
   return (kid >= 0 && kid < HZ_NUM_KERNELS) ? names[kid] : "";
 }
 
@@ -1021,6 +1258,45 @@ int hz_precond_apply(hz_op op, int prec, const void* r, void* z) {
   else
     return HZ_ERR_INVALID;
   return HZ_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// gather r into compact order (p), sweeps ping-pong between ph and t, scatter to z
+template <typename T>
+int trisor_apply(hz_op op, int sweeps, double omega, const T* r, T* z) {
+  CKS(ensure_sor<T>(op));
+  const Bands<T> a = bands_rb<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  const Grid& g = op->g;
+  CK(launch_rb_copy<T>(g, r, w.p, 1, op->L));
+  T* buf[2];
+  buf[sweeps % 2] = w.ph;
+  buf[(sweeps + 1) % 2] = w.t;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    T* zin = buf[sw % 2];
+    T* zout = buf[(sw + 1) % 2];
+    CK(launch_sor_pass<T>(g, a, w.p, zin, sw > 0 ? zin : nullptr, zout, 0, sw > 0 ? 1 : 0, omega, nullptr, op->L));
+    CK(launch_sor_pass<T>(g, a, w.p, zout, sw > 0 ? zin : nullptr, zout, 1, 1, omega, nullptr, op->L));
+  }
+  CK(launch_rb_copy<T>(g, w.ph, z, 0, op->L));
+  return HZ_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int hz_trisor_apply(hz_op op, int prec, int sweeps, double omega, const void* r, void* z) {
+  if (!op || !r || !z || r == z) return HZ_ERR_INVALID;
+  if (sweeps < 1 || sweeps > 64 || !(omega > 0.0 && omega < 2.0)) return HZ_ERR_INVALID;
+  if (op->g.nx % 2 != 0) return HZ_ERR_UNSUPPORTED;
+  if (prec == HZ_PREC_FP32) return trisor_apply<float>(op, sweeps, omega, (const float*)r, (float*)z);
+  if (prec == HZ_PREC_FP64) {
+    CKS(ensure_w64(op));
+    return trisor_apply<double>(op, sweeps, omega, (const double*)r, (double*)z);
+  }
+  return HZ_ERR_INVALID;
 }
 
 int hz_precond_matvec(hz_op op, int prec, const void* p, void* ph, void* v) {

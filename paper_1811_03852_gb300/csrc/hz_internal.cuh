@@ -176,6 +176,27 @@ template <typename T>
 cudaError_t launch_tinv(const Grid& g, const Bands<T>& a, const T* r, T* z, const Launch& L);
 template <typename T>
 cudaError_t launch_precond_matvec(const Grid& g, const Bands<T>& a, const T* p, T* ph, T* v, const Launch& L);
+
+// ---- tri-SOR preconditioner in colour-compact column order (hz_sor.cu) ----
+// compact column of (i, j): ((i + j) & 1) * ncol/2 + j * nx/2 + i/2 (nx even).
+// Bands and vectors passed to these are all in compact order.
+template <typename T>
+cudaError_t launch_rb_copy(const Grid& g, const T* src, T* dst, int to_compact, const Launch& L);
+// mode 0: p update (with start/restart handling), mode 1: s = r - alpha v; then
+// z1 = omega T^-1 (p or s) on the red half (the first sweep's red pass)
+template <typename T>
+cudaError_t launch_sor_first(const Grid& g, const Bands<T>& a, const Vecs<T>& w, T* z1, double omega, int mode,
+                             Ctl* ctl, Red red, const Launch& L);
+// zout(colour) = (1 - omega) zold + omega T^-1 (rc - H znbr); zold may be null (zero), nbr = 0: znbr is zero
+template <typename T>
+cudaError_t launch_sor_pass(const Grid& g, const Bands<T>& a, const T* rc, const T* znbr, const T* zold, T* zout,
+                            int colour, int nbr, double omega, const Ctl* ctl, const Launch& L);
+// mode 0: v = Ahat ph, <r0, v> -> alpha; mode 1: t = Ahat sh, <t, s>, <t, t> -> omega
+template <typename T>
+cudaError_t launch_mv_rb(const Grid& g, const Bands<T>& a, const Vecs<T>& w, int mode, Ctl* ctl, Red red,
+                         const Launch& L);
+template <typename T>
+void warm_sor(const Launch& L);
 template <typename T>
 cudaError_t launch_dot(int64_t n, const T* x, const T* y, Red red, double* out_dev, int grid, cudaStream_t s);
 

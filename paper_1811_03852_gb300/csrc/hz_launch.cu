@@ -56,6 +56,8 @@ template cudaError_t launch_dot<double>(int64_t, const double*, const double*, R
 void warm_launch_cache(const Launch& L) {
   warm_kernels<float>(L);
   warm_kernels<double>(L);
+  warm_sor<float>(L);
+  warm_sor<double>(L);
   warm_launch_kernels(L);
 }
 

@@ -36,9 +36,16 @@ def test_library_exports_every_declared_symbol():
 def test_version_and_defaults_without_gpu():
     import paper_1811_03852_gb300 as hz
 
-    assert hz.version() >= 1
+    assert hz.version() == 2
     p = hz.default_params()
     assert p.tol == 1e-8 and p.restart == 150 and p.mode == hz.HZ_MODE_MIXED_IR and p.fgmres_m == 30
+    # tri-SOR defaults of Sec. 2: three sweeps, omega = 1.5; T^-1 stays the default preconditioner
+    assert p.precond == hz.HZ_PRE_TRI and p.sor_sweeps == 3 and p.sor_omega == 1.5
+    # the binding's struct matches the header's layout (two doubles, nine ints, one int, one double)
+    assert ctypes.sizeof(hz.hz_solve_params) == 64
+    names = [hz.load().hz_kernel_name(k).decode() for k in range(hz.NUM_KERNELS)]
+    assert names[7:] == ["k_sor_first", "k_sor_pass", "k_mv_rb", "k_rb_copy"] and hz.load().hz_kernel_name(
+        hz.NUM_KERNELS).decode() == ""
     assert hz.load().hz_status_str(hz.HZ_ERR_NOT_CONVERGED).decode() == "not converged"
 
 

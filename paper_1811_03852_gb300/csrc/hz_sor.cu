@@ -24,11 +24,21 @@
 // newest values and its own previous values from one buffer and writes its
 // colour to the other, so the forward Thomas sweep can park y in the output
 // column (as the T^-1 kernels do) and no extra array is needed.
+//
+// Every column march is software-pipelined like the T^-1 kernels: the loads
+// of U levels are issued before any of them is used (U from 1 to 4 by kernel
+// and precision, the largest that keeps the kernel within 80 registers
+// without spilling).
 #include "hz_krylov.cuh"
 
 namespace hz {
 
 namespace {
+
+template <typename T>
+__host__ __device__ constexpr int sor_u() {
+  return sizeof(T) == 8 ? 2 : 4;
+}
 
 struct Rb {
   int nx, ny, nz, hx;
@@ -37,7 +47,7 @@ struct Rb {
 
 __device__ __forceinline__ Rb make_rb(const Grid& g) { return Rb{g.nx, g.ny, g.nz, g.nx / 2, g.ncol, g.ncol / 2}; }
 
-// compact neighbours of compact column q: e/w/n/s absolute compact columns
+// neighbours of compact column q, as offsets from q (the same at every level)
 struct RbNbr {
   int64_t e, w, n, s;
   bool hn, hs;
@@ -51,7 +61,7 @@ __device__ __forceinline__ RbNbr rb_nbr(const Rb& rb, int64_t q) {
   const int i = 2 * qi + ((j + c) & 1);
   const int iE = (i + 1 == rb.nx) ? 0 : i + 1;
   const int iW = (i == 0) ? rb.nx - 1 : i - 1;
-  const int64_t o = (int64_t)(c ^ 1) * rb.H;
+  const int64_t o = (int64_t)(c ^ 1) * rb.H - q;
   RbNbr n;
   n.e = o + (int64_t)j * rb.hx + (iE >> 1);
   n.w = o + (int64_t)j * rb.hx + (iW >> 1);
@@ -62,40 +72,196 @@ __device__ __forceinline__ RbNbr rb_nbr(const Rb& rb, int64_t q) {
   return n;
 }
 
-// (Ahat x)_(k, q) in compact order, all six bands
+// Work items of a kernel over both colours: item w maps to blocks of kBS red
+// and kBS black columns in turn, so that the blocks resident at one time
+// cover the same rows of both halves (a column read as the other colour's
+// neighbour is then still in L2 from its own read).  rb_col returns -1 for
+// the padding items past the end of a half.
+__device__ __forceinline__ int64_t rb_items(const Rb& rb) { return 2 * ((rb.H + kBS - 1) / kBS) * kBS; }
+__device__ __forceinline__ int64_t rb_col(const Rb& rb, int64_t w) {
+  const int64_t pb = w / (2 * kBS);
+  const int within = (int)(w - pb * 2 * kBS);
+  const int colour = within >= kBS ? 1 : 0;
+  const int64_t off = pb * kBS + (within - colour * kBS);
+  return off < rb.H ? (int64_t)colour * rb.H + off : -1;
+}
+
+// (Ahat x)_(k, q) in compact order, all six bands (restart path only)
 template <typename T>
 __device__ __forceinline__ T ahat_rb(const Rb& rb, const Bands<T>& a, const T* x, int64_t q, int k, const RbNbr& nb) {
-  const int64_t kk = (int64_t)k * rb.ncol;
-  const int64_t idx = kk + q;
+  const int64_t idx = (int64_t)k * rb.ncol + q;
   T y = x[idx];
-  y = fma(a.E[idx], x[kk + nb.e], y);
-  y = fma(a.W[idx], x[kk + nb.w], y);
-  if (nb.hn) y = fma(a.N[idx], x[kk + nb.n], y);
-  if (nb.hs) y = fma(a.S[idx], x[kk + nb.s], y);
+  y = fma(a.E[idx], x[idx + nb.e], y);
+  y = fma(a.W[idx], x[idx + nb.w], y);
+  if (nb.hn) y = fma(a.N[idx], x[idx + nb.n], y);
+  if (nb.hs) y = fma(a.S[idx], x[idx + nb.s], y);
   if (k + 1 < rb.nz) y = fma(a.U[idx], x[idx + rb.ncol], y);
   if (k > 0) y = fma(a.D[idx], x[idx - rb.ncol], y);
   return y;
 }
 
-// Thomas back sweep of one column whose forward values y are parked in z:
-// z_k = (1 - omega) zold_k + omega (y_k - c'_k x_(k+1)), x the unrelaxed solution.
-template <typename T>
-__device__ __forceinline__ void back_relax(const Rb& rb, const T* __restrict__ cp, const T* zold, T* z, int64_t q,
-                                           T omega, T keep) {
+// Relaxed Thomas solve of one column with unit diagonal and pre-computed
+// factors: forward y_k = m_k q_k - l_k y_(k-1) with q_k = src.make(...), y
+// parked in z; back x_k = y_k - c'_k x_(k+1) and
+// z_k = (1 - omega) zold_k + omega x_k (zold == nullptr: zero).
+template <typename T, int U, typename Src>
+__device__ __forceinline__ void sor_column(const Rb& rb, int64_t q, const T* __restrict__ m, const T* __restrict__ l,
+                                           const T* __restrict__ cp, const T* __restrict__ zold, T* __restrict__ z,
+                                           T omega, T keep, Src& src) {
+  constexpr int NIN = Src::NIN;
+  const int64_t ncol = rb.ncol;
+  const int nz = rb.nz;
+  T yprev = T(0);
+  for (int k0 = 0; k0 < nz; k0 += U) {
+    T v[U][NIN], mm[U], ll[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u < nz) {
+        const int64_t idx = (int64_t)(k0 + u) * ncol + q;
+        src.load(idx, v[u]);
+        mm[u] = __ldg(m + idx);
+        ll[u] = __ldg(l + idx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u < nz) {
+        const int64_t idx = (int64_t)(k0 + u) * ncol + q;
+        const T qv = src.make(v[u], idx);
+        yprev = fma(mm[u], qv, -ll[u] * yprev);
+        z[idx] = yprev;
+      }
+    }
+    src.flush();
+  }
   T xn = T(0);
-#pragma unroll 4
-  for (int k = rb.nz - 1; k >= 0; --k) {
-    const int64_t idx = (int64_t)k * rb.ncol + q;
-    const T x = fma(-cp[idx], xn, z[idx]);
-    xn = x;
-    z[idx] = zold ? fma(keep, zold[idx], omega * x) : omega * x;
+  for (int k0 = nz - 1; k0 >= 0; k0 -= 2 * U) {
+    T yy[2 * U], cc[2 * U], zo[2 * U];
+#pragma unroll
+    for (int u = 0; u < 2 * U; ++u) {
+      if (k0 - u >= 0) {
+        const int64_t idx = (int64_t)(k0 - u) * ncol + q;
+        yy[u] = z[idx];  // written by this thread above: coherent load
+        cc[u] = __ldg(cp + idx);
+        zo[u] = zold ? __ldg(zold + idx) : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2 * U; ++u) {
+      if (k0 - u >= 0) {
+        const int64_t idx = (int64_t)(k0 - u) * ncol + q;
+        xn = fma(-cc[u], xn, yy[u]);
+        z[idx] = fma(keep, zo[u], omega * xn);
+      }
+    }
+  }
+}
+
+// inputs of the relaxed solves ------------------------------------------------
+template <typename T>
+struct SrcHz {  // q = rc - (E zE + W zW + N zN + S zS); nbr == false: q = rc
+  static constexpr int NIN = 9;
+  const T* __restrict__ rc;
+  const T* __restrict__ E;
+  const T* __restrict__ W;
+  const T* __restrict__ N;
+  const T* __restrict__ S;
+  const T* __restrict__ zn;  // other colour's newest values (read-only in the pass)
+  RbNbr nb;
+  bool nbr;
+  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
+    o[0] = __ldg(rc + idx);
+    if (nbr) {
+      o[1] = __ldg(E + idx);
+      o[2] = __ldg(zn + idx + nb.e);
+      o[3] = __ldg(W + idx);
+      o[4] = __ldg(zn + idx + nb.w);
+      o[5] = nb.hn ? __ldg(N + idx) : T(0);
+      o[6] = nb.hn ? __ldg(zn + idx + nb.n) : T(0);
+      o[7] = nb.hs ? __ldg(S + idx) : T(0);
+      o[8] = nb.hs ? __ldg(zn + idx + nb.s) : T(0);
+    }
+  }
+  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t) {
+    if (!nbr) return o[0];
+    T h = o[1] * o[2];
+    h = fma(o[3], o[4], h);
+    h = fma(o[5], o[6], h);
+    h = fma(o[7], o[8], h);
+    return o[0] - h;
+  }
+  __device__ __forceinline__ void flush() {}
+};
+
+template <typename T>
+struct SrcPu {  // p = r + beta (p - omega v) (fresh: p = r), stored
+  static constexpr int NIN = 3;
+  const T* __restrict__ r;
+  T* __restrict__ p;
+  const T* __restrict__ v;
+  T beta, omega;
+  bool fresh;
+  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
+    o[0] = __ldg(r + idx);
+    if (!fresh) {
+      o[1] = p[idx];
+      o[2] = __ldg(v + idx);
+    }
+  }
+  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
+    const T q = fresh ? o[0] : fma(beta, fma(-omega, o[2], o[1]), o[0]);
+    p[idx] = q;
+    return q;
+  }
+  __device__ __forceinline__ void flush() {}
+};
+
+template <typename T>
+struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP64 across)
+  static constexpr int NIN = 2;
+  const T* __restrict__ r;
+  const T* __restrict__ v;
+  T* __restrict__ s;
+  T alpha;
+  T part;
+  double acc;
+  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
+    o[0] = __ldg(r + idx);
+    o[1] = __ldg(v + idx);
+  }
+  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
+    const T q = fma(-alpha, o[1], o[0]);
+    s[idx] = q;
+    part = fma(q, q, part);
+    return q;
+  }
+  __device__ __forceinline__ void flush() {
+    acc += (double)part;
+    part = T(0);
+  }
+};
+
+// the vector update alone on a column (black half of k_sor_first)
+template <typename T, int U, typename Src>
+__device__ __forceinline__ void update_column(const Rb& rb, int64_t q, Src& src) {
+  constexpr int NIN = Src::NIN;
+  for (int k0 = 0; k0 < rb.nz; k0 += 2 * U) {
+    T v[2 * U][NIN];
+#pragma unroll
+    for (int u = 0; u < 2 * U; ++u)
+      if (k0 + u < rb.nz) src.load((int64_t)(k0 + u) * rb.ncol + q, v[u]);
+#pragma unroll
+    for (int u = 0; u < 2 * U; ++u)
+      if (k0 + u < rb.nz) src.make(v[u], (int64_t)(k0 + u) * rb.ncol + q);
+    src.flush();
   }
 }
 
 // Restart of one compact column (rare, out of line): r = rhs - Ahat x,
-// r0 = r, p = r.  Returns <r, r> of the column.
+// r0 = r, p = r, and for a red column z1 = omega T^-1 p.  Returns <r, r>.
 template <typename T>
-__device__ __noinline__ double restart_rb(const Rb& rb, const Bands<T>& a, const Vecs<T>& w, int64_t q, bool xzero) {
+__device__ __noinline__ double restart_rb(const Rb& rb, const Bands<T>& a, const Vecs<T>& w, int64_t q, bool xzero,
+                                          T* z1, T omega) {
   const RbNbr nb = rb_nbr(rb, q);
   T acc = T(0);
   for (int k = 0; k < rb.nz; ++k) {
@@ -106,6 +272,20 @@ __device__ __noinline__ double restart_rb(const Rb& rb, const Bands<T>& a, const
     w.r0[idx] = v;
     w.p[idx] = v;
     acc = fma(v, v, acc);
+  }
+  if (q < rb.H) {
+    T yp = T(0);
+    for (int k = 0; k < rb.nz; ++k) {
+      const int64_t idx = (int64_t)k * rb.ncol + q;
+      yp = fma(a.m[idx], w.p[idx], -a.l[idx] * yp);
+      z1[idx] = yp;
+    }
+    T xn = T(0);
+    for (int k = rb.nz - 1; k >= 0; --k) {
+      const int64_t idx = (int64_t)k * rb.ncol + q;
+      xn = fma(-a.cp[idx], xn, z1[idx]);
+      z1[idx] = omega * xn;
+    }
   }
   return (double)acc;
 }
@@ -122,12 +302,15 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
   for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
     const int i = (int)(col % g.nx), j = (int)(col / g.nx);
     const int64_t q = (int64_t)((i + j) & 1) * H + (int64_t)j * hx + (i >> 1);
-    for (int k = 0; k < g.nz; ++k) {
-      const int64_t kk = (int64_t)k * g.ncol;
-      if (TO_COMPACT)
-        dst[kk + q] = src[kk + col];
-      else
-        dst[kk + col] = src[kk + q];
+    constexpr int B = 8;
+    for (int k0 = 0; k0 < g.nz; k0 += B) {
+      T v[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (k0 + u < g.nz) v[u] = __ldg(src + (int64_t)(k0 + u) * g.ncol + (TO_COMPACT ? col : q));
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (k0 + u < g.nz) dst[(int64_t)(k0 + u) * g.ncol + (TO_COMPACT ? q : col)] = v[u];
     }
   }
 }
@@ -141,66 +324,52 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
 // All columns are updated; only the red half (compact columns < ncol/2)
 // continues into the tridiagonal solve.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kBS, 4) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* z1, double omega_d, Ctl* ctl,
-                                                      Red red) {
+__global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* __restrict__ z1,
+                                                               double omega_d, Ctl* ctl, Red red) {
+  constexpr int U = sor_u<T>();
   const Rb rb = make_rb(g);
-  bool restart = false, fresh = false, xzero = true;
-  T beta = T(0), om = T(0), alpha = T(0);
+  bool restart = false;
   if (MODE == 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bodies += 1;  // read only by k_upd, a later launch
     const int state = ctl->state;
     restart = (state == ST_RESTART);
     if (!restart && state != ST_RUNNING) return;
-    fresh = ctl->fresh != 0;
-    xzero = ctl->xzero != 0;
-    beta = (T)ctl->beta;
-    om = (T)ctl->omega;
   } else {
     if (ctl->state != ST_RUNNING) return;
-    alpha = (T)ctl->alpha;
   }
-  const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
-  T* out = MODE == 0 ? w.p : w.s;  // may be w.p, read above
+  const T* rin = ctl->rsel ? w.r : w.rhs;
   const T omega = (T)omega_d;
   double acc = 0.0;
-  for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < rb.ncol; q += (int64_t)gridDim.x * kBS) {
-    const bool red_col = q < rb.H;
-    if (MODE == 0 && restart) {
-      acc += restart_rb<T>(rb, a, w, q, xzero);
-      if (red_col) {  // forward sweep on the p just written
-        T yp = T(0);
-        for (int k = 0; k < rb.nz; ++k) {
-          const int64_t idx = (int64_t)k * rb.ncol + q;
-          yp = fma(a.m[idx], w.p[idx], -a.l[idx] * yp);
-          z1[idx] = yp;
-        }
-      }
-    } else {
-      T part = T(0), yp = T(0);
-#pragma unroll 4
-      for (int k = 0; k < rb.nz; ++k) {
-        const int64_t idx = (int64_t)k * rb.ncol + q;
-        T v;
-        if (MODE == 0)
-          v = fresh ? rin[idx] : fma(beta, fma(-om, w.v[idx], w.p[idx]), rin[idx]);
-        else
-          v = fma(-alpha, w.v[idx], rin[idx]);
-        out[idx] = v;
-        if (MODE == 1) part = fma(v, v, part);
-        if (red_col) {
-          yp = fma(a.m[idx], v, -a.l[idx] * yp);
-          z1[idx] = yp;
-        }
-      }
-      acc += (double)part;
-    }
-    if (red_col) back_relax<T>(rb, a.cp, (const T*)nullptr, z1, q, omega, T(0));
-  }
   if (MODE == 0 && restart) {
+    const bool xzero = ctl->xzero != 0;
+    for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < rb.ncol; q += (int64_t)gridDim.x * kBS)
+      acc += restart_rb<T>(rb, a, w, q, xzero, z1, omega);
     double vv[1] = {acc}, o[1];
     if (grid_reduce<1>(vv, red, o)) fin_restart(ctl, o[0]);
-  } else if (MODE == 1) {
-    double vv[1] = {acc}, o[1];
+    return;
+  }
+  const int64_t items = rb_items(rb);
+  if (MODE == 0) {
+    SrcPu<T> src{rin, w.p, w.v, (T)ctl->beta, (T)ctl->omega, ctl->fresh != 0};
+    for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
+      const int64_t q = rb_col(rb, it);
+      if (q < 0) continue;
+      if (q < rb.H)
+        sor_column<T, U>(rb, q, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
+      else
+        update_column<T, U>(rb, q, src);
+    }
+  } else {
+    SrcSu<T> src{rin, w.v, w.s, (T)ctl->alpha, T(0), 0.0};
+    for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
+      const int64_t q = rb_col(rb, it);
+      if (q < 0) continue;
+      if (q < rb.H)
+        sor_column<T, U>(rb, q, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
+      else
+        update_column<T, U>(rb, q, src);
+    }
+    double vv[1] = {src.acc}, o[1];
     if (grid_reduce<1>(vv, red, o)) fin_snorm(ctl, o[0]);
   }
 }
@@ -210,61 +379,95 @@ __global__ void __launch_bounds__(kBS, 4) k_sor_first(Grid g, Bands<T> a, Vecs<T
 // H the four horizontal bands (their neighbours all have the other colour).
 // zold == nullptr: the first sweep (previous iterate zero).  nbr == 0: the
 // other colour is still zero (the red pass of the first sweep).  znbr and zout
-// may be the same buffer (different halves).  ctl (may be null): nothing to do
-// unless the inner solve is running.
+// may be the same buffer: the pass reads only the other colour's half of it
+// and writes only its own.  ctl (may be null): nothing to do unless the inner
+// solve is running.
 template <typename T>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_pass(Grid g, Bands<T> a, const T* __restrict__ rc,
-                                                              const T* znbr, const T* zold, T* zout, int colour,
-                                                              int nbr, double omega_d, const Ctl* ctl) {
+                                                              const T* __restrict__ znbr, const T* __restrict__ zold,
+                                                              T* __restrict__ zout, int colour, int nbr,
+                                                              double omega_d, const Ctl* ctl) {
   if (ctl && ctl->state != ST_RUNNING) return;
+  constexpr int U = sor_u<T>() / 2;  // eleven loads per level
   const Rb rb = make_rb(g);
   const T omega = (T)omega_d, keep = (T)(1.0 - omega_d);
   for (int64_t h = (int64_t)blockIdx.x * kBS + threadIdx.x; h < rb.H; h += (int64_t)gridDim.x * kBS) {
     const int64_t q = (int64_t)colour * rb.H + h;
-    const RbNbr nb = rb_nbr(rb, q);
-    T yp = T(0);
-#pragma unroll 4
-    for (int k = 0; k < rb.nz; ++k) {
-      const int64_t kk = (int64_t)k * rb.ncol;
-      const int64_t idx = kk + q;
-      T rhs = rc[idx];
-      if (nbr) {
-        T hsum = a.E[idx] * znbr[kk + nb.e];
-        hsum = fma(a.W[idx], znbr[kk + nb.w], hsum);
-        if (nb.hn) hsum = fma(a.N[idx], znbr[kk + nb.n], hsum);
-        if (nb.hs) hsum = fma(a.S[idx], znbr[kk + nb.s], hsum);
-        rhs -= hsum;
-      }
-      yp = fma(a.m[idx], rhs, -a.l[idx] * yp);
-      zout[idx] = yp;
-    }
-    back_relax<T>(rb, a.cp, zold, zout, q, omega, keep);
+    SrcHz<T> src{rc, a.E, a.W, a.N, a.S, znbr, rb_nbr(rb, q), nbr != 0};
+    sor_column<T, U>(rb, q, a.m, a.l, a.cp, zold, zout, omega, keep, src);
   }
 }
 
 // y = Ahat x in compact order with the iteration's dots:
-// MODE 0 (x = ph, y = v): <r0, v> -> alpha;  MODE 1 (x = sh, y = t): <t, s>, <t, t> -> omega
+// MODE 0 (x = ph, y = v): <r0, v> -> alpha;  MODE 1 (x = sh, y = t): <t, s>, <t, t> -> omega.
+// The column's own values ride down in registers (x_(k-1), x_k); each level
+// loads x_(k+1), the four horizontal neighbours, six bands and the dot partner.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv_rb(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
+  constexpr int U = sizeof(T) == 8 ? 1 : sor_u<T>();  // twelve loads per level
   const Rb rb = make_rb(g);
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
   const T* __restrict__ c = MODE == 0 ? (ctl->r0sel ? w.r0 : w.rhs) : w.s;
+  const T* __restrict__ E = a.E;
+  const T* __restrict__ W = a.W;
+  const T* __restrict__ N = a.N;
+  const T* __restrict__ S = a.S;
+  const T* __restrict__ Up = a.U;
+  const T* __restrict__ Dn = a.D;
+  const int64_t ncol = rb.ncol;
+  const int nz = rb.nz;
   double acc0 = 0.0, acc1 = 0.0;
-  for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < rb.ncol; q += (int64_t)gridDim.x * kBS) {
+  const int64_t items = rb_items(rb);
+  for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
+    const int64_t q = rb_col(rb, it);
+    if (q < 0) continue;
     const RbNbr nb = rb_nbr(rb, q);
-    T a0 = T(0), a1 = T(0);
-#pragma unroll 4
-    for (int k = 0; k < rb.nz; ++k) {
-      const int64_t idx = (int64_t)k * rb.ncol + q;
-      const T yy = ahat_rb(rb, a, x, q, k, nb);
-      y[idx] = yy;
-      a0 = fma(c[idx], yy, a0);
-      if (MODE == 1) a1 = fma(yy, yy, a1);
+    T xm = T(0), x0 = __ldg(x + q);
+    for (int k0 = 0; k0 < nz; k0 += U) {
+      T xp[U], he[U], hw[U], hn[U], hs[U], be[U], bw[U], bn[U], bs[U], bu[U], bd[U], cc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u;
+        if (k < nz) {
+          const int64_t idx = (int64_t)k * ncol + q;
+          xp[u] = k + 1 < nz ? __ldg(x + idx + ncol) : T(0);
+          he[u] = __ldg(x + idx + nb.e);
+          hw[u] = __ldg(x + idx + nb.w);
+          hn[u] = nb.hn ? __ldg(x + idx + nb.n) : T(0);
+          hs[u] = nb.hs ? __ldg(x + idx + nb.s) : T(0);
+          be[u] = __ldg(E + idx);
+          bw[u] = __ldg(W + idx);
+          bn[u] = nb.hn ? __ldg(N + idx) : T(0);
+          bs[u] = nb.hs ? __ldg(S + idx) : T(0);
+          bu[u] = __ldg(Up + idx);
+          bd[u] = __ldg(Dn + idx);
+          cc[u] = __ldg(c + idx);
+        }
+      }
+      T a0 = T(0), a1 = T(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u;
+        if (k < nz) {
+          T yy = x0;
+          yy = fma(be[u], he[u], yy);
+          yy = fma(bw[u], hw[u], yy);
+          yy = fma(bn[u], hn[u], yy);
+          yy = fma(bs[u], hs[u], yy);
+          yy = fma(bu[u], xp[u], yy);
+          yy = fma(bd[u], xm, yy);
+          y[(int64_t)k * ncol + q] = yy;
+          a0 = fma(cc[u], yy, a0);
+          if (MODE == 1) a1 = fma(yy, yy, a1);
+          xm = x0;
+          x0 = xp[u];
+        }
+      }
+      acc0 += (double)a0;
+      acc1 += (double)a1;
     }
-    acc0 += (double)a0;
-    acc1 += (double)a1;
   }
   if (MODE == 0) {
     double vv[1] = {acc0}, o[1];

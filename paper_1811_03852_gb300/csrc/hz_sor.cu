@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* __restrict__ z1,
                                                                double omega_d, Ctl* ctl, Red red) {
-  constexpr int U = sor_u<T>();
+  constexpr int U = sor_u<T>() / (sizeof(T) == 8 ? 2 : 1);
   const Rb rb = make_rb(g);
   bool restart = false;
   if (MODE == 0) {

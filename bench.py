@@ -213,7 +213,12 @@ def run_ours(args):
     op = hz.Operator(A, stream=stream)
     bd = torch.from_numpy(b.reshape(-1)).to(f"cuda:{dev}")
     x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
-    variants = op.autotune(fp64=not args.no_fp64)  # launch-shape search, outside the timed region
+    use_sor = (args.precond == "trisor" or not args.no_trisor) and nx % 2 == 0
+    # launch-shape search, outside the timed region
+    variants = op.autotune(fp64=not args.no_fp64, trisor=use_sor)
+    if use_sor:
+        variants["trisor"] = {f"{'fp64' if p == hz.HZ_PREC_FP64 else 'fp32'}/{('pass', 'matvec', 'first')[k]}": v
+                              for (p, k), v in op.sor_variants().items()}
     ug = 0 if args.no_graph else 1
     pc = hz.HZ_PRE_TRISOR if args.precond == "trisor" else hz.HZ_PRE_TRI
     pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta, restart=args.restart, use_graph=ug,

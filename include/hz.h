@@ -237,7 +237,9 @@ int hz_get_history(hz_op op, double* hist, int cap);
  * depth levels per software-pipelined batch.  hz_op_autotune times every
  * valid variant on the operator's own arrays (3 launches each, CUDA events on
  * the operator's stream) and keeps the fastest; flags bit 0 also tunes the
- * FP64 kernels (allocating the FP64 work vectors).  If the environment
+ * FP64 kernels (allocating the FP64 work vectors); flags bit 1 also tunes the
+ * tri-SOR kernels (for nx even; allocating their colour-compact copies of the
+ * bands), in FP32 and, with bit 0, FP64.  If the environment
  * variable HZ_AUTOTUNE_CACHE names a file, results are appended to it (one
  * line per device, grid, precision and kernel kind) and read back by
  * hz_op_create for operators of the same grid.  Variant ids: 0 .. count-1 of
@@ -245,6 +247,15 @@ int hz_get_history(hz_op op, double* hist, int cap);
  * The work vectors are overwritten; call between solves.
  */
 int hz_op_autotune(hz_op op, int flags);
+/* tri-SOR kernel variants: kind 0 = colour pass, 1 = matvec, 2 = first pass
+   (vector update fused with the first red pass); each is a (levels per
+   batch, blocks per SM) shape.  Count per prec (HZ_PREC_*) and kind (0 for an
+   invalid pair); get/set the operator's choice (set: HZ_ERR_INVALID for an id
+   out of range).  Every variant computes the same columns the same way; the
+   matvec's dot partial sums follow the shape. */
+int hz_sor_variant_count(int prec, int kind);
+int hz_op_get_sor_variant(hz_op op, int prec, int kind, int* id);
+int hz_op_set_sor_variant(hz_op op, int prec, int kind, int id);
 int hz_op_get_variants(hz_op op, int* pre32, int* mv32, int* pre64, int* mv64);
 int hz_op_set_variants(hz_op op, int pre32, int mv32, int pre64, int mv64);
 

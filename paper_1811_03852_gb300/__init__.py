@@ -114,6 +114,9 @@ def load(build_if_missing: bool = True):
         "hz_matvec": (i32, [pv, i32, pv, pv]),
         "hz_precond_apply": (i32, [pv, i32, pv, pv]),
         "hz_trisor_apply": (i32, [pv, i32, i32, ctypes.c_double, pv, pv]),
+        "hz_sor_variant_count": (i32, [i32, i32]),
+        "hz_op_get_sor_variant": (i32, [pv, i32, i32, ctypes.POINTER(i32)]),
+        "hz_op_set_sor_variant": (i32, [pv, i32, i32, i32]),
         "hz_precond_matvec": (i32, [pv, i32, pv, pv, pv]),
         "hz_residual": (i32, [pv, pv, pv, pv, P(dbl), P(dbl)]),
         "hz_dot": (i32, [i32, i64, pv, pv, pv, P(dbl)]),
@@ -252,10 +255,24 @@ class Operator:
                "hz_residual")
         return rn.value, bn.value
 
-    def autotune(self, fp64=True):
+    def autotune(self, fp64=True, trisor=False):
         """Pick the fastest column-kernel variants for this grid (timed on the GPU)."""
-        _check(load().hz_op_autotune(self._h, 1 if fp64 else 0), "hz_op_autotune")
+        _check(load().hz_op_autotune(self._h, (1 if fp64 else 0) | (2 if trisor else 0)), "hz_op_autotune")
         return self.variants()
+
+    def sor_variants(self):
+        """{(prec, kind): id} of the tri-SOR kernels (kind 0 pass, 1 matvec, 2 first pass)."""
+        L = load()
+        out = {}
+        for prec in (HZ_PREC_FP32, HZ_PREC_FP64):
+            for kind in range(3):
+                v = ctypes.c_int()
+                _check(L.hz_op_get_sor_variant(self._h, prec, kind, ctypes.byref(v)), "hz_op_get_sor_variant")
+                out[(prec, kind)] = v.value
+        return out
+
+    def set_sor_variant(self, prec, kind, id_):
+        _check(load().hz_op_set_sor_variant(self._h, prec, kind, id_), "hz_op_set_sor_variant")
 
     def variants(self):
         v = [ctypes.c_int() for _ in range(4)]
@@ -328,6 +345,10 @@ def dot_noalloc(x, y, out, prec=None, stream=None):
     assert out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1
     _check(load().hz_dot_noalloc(prec, x.numel(), _ptr(x), _ptr(y), _stream_ptr(stream), _ptr(out)),
            "hz_dot_noalloc")
+
+
+def sor_variant_count(prec, kind) -> int:
+    return load().hz_sor_variant_count(prec, kind)
 
 
 def version() -> int:

@@ -702,11 +702,14 @@ void load_tuned(hz_op op) {
     int var = -1;
     if (sscanf(line, "%399s %d", key, &var) != 2) continue;
     for (int pr = 0; pr < 2; ++pr)
-      for (int kind = 0; kind < 2; ++kind) {
+      for (int kind = 0; kind < 5; ++kind) {
         char want[400];
         tune_key(op, pr, kind, want, sizeof(want));
-        if (strcmp(want, key) == 0 && var >= 0 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx))
+        if (strcmp(want, key) != 0 || var < 0) continue;
+        if (kind < 2 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx))
           (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = var;
+        else if (kind >= 2 && var < sor_num_variants(pr, kind - 2))
+          op->L.vsor[pr][kind - 2] = var;
       }
   }
   fclose(f);
@@ -719,10 +722,10 @@ void store_tuned(hz_op op) {
   FILE* f = fopen(path, "a");
   if (!f) return;
   for (int pr = 0; pr < 2; ++pr)
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < 5; ++kind) {
       char key[400];
       tune_key(op, pr, kind, key, sizeof(key));
-      fprintf(f, "%s %d\n", key, (kind == 0 ? op->L.vpre : op->L.vmv)[pr]);
+      fprintf(f, "%s %d\n", key, kind < 2 ? (kind == 0 ? op->L.vpre : op->L.vmv)[pr] : op->L.vsor[pr][kind - 2]);
     }
   fclose(f);
 }
@@ -1147,6 +1150,77 @@ int autotune_prec(hz_op op, int reps, double* best_ms) {
   cudaEventDestroy(e1);
   return HZ_OK;
 }
+
+// The tri-SOR kernels of one precision in every variant, on the operator's
+// compact arrays (work vectors zeroed, control block "running" before each
+// launch): a colour pass with neighbours and an old iterate, both matvecs,
+// both first-pass kernels.
+template <typename T>
+int autotune_sor(hz_op op, int reps) {
+  const int pr = sizeof(T) == 8 ? 1 : 0;
+  CKS(ensure_sor<T>(op));
+  const Bands<T> a = bands_rb<T>(op);
+  const Vecs<T>& w = vecs_of<T>(op);
+  CK(cudaMemsetAsync(w.rhs, 0, sizeof(T) * 10 * pad64(op->g.n), op->stream));
+  Ctl* cfg = op->cfg_h;
+  memset(cfg, 0, sizeof(Ctl));
+  cfg->state = ST_RUNNING;
+  cfg->rsel = 1;
+  cfg->r0sel = 1;
+  cfg->xzero = 1;
+  cfg->alpha = cfg->omega = cfg->beta = 0.5;
+  cfg->rho = 1.0;
+  cfg->stop2 = -1.0;
+  cfg->maxit = 1 << 30;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& launch) -> double {
+    double tot = 0.0;
+    for (int r = 0; r <= reps; ++r) {  // first launch is a warm-up
+      if (cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, op->stream) != cudaSuccess) return -1.0;
+      cudaEventRecord(e0, op->stream);
+      if (launch() != cudaSuccess) return -1.0;
+      cudaEventRecord(e1, op->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) tot += ms;
+    }
+    return tot / reps;
+  };
+  for (int kind = 0; kind < 3; ++kind) {
+    int best = -1;
+    double bms = 1e30;
+    for (int id = 0; id < sor_num_variants(pr, kind); ++id) {
+      Launch L = op->L;
+      L.vsor[pr][kind] = id;
+      double ms;
+      if (kind == 0)
+        ms = time_it([&] { return launch_sor_pass<T>(op->g, a, w.p, w.ph, w.ph, w.t, 1, 1, 1.5, op->ctl, L); });
+      else if (kind == 1)
+        ms = time_it([&] { return launch_mv_rb<T>(op->g, a, w, 0, op->ctl, op->red, L); }) +
+             time_it([&] { return launch_mv_rb<T>(op->g, a, w, 1, op->ctl, op->red, L); });
+      else
+        ms = time_it([&] { return launch_sor_first<T>(op->g, a, w, w.t, 1.5, 0, op->ctl, op->red, L); }) +
+             time_it([&] { return launch_sor_first<T>(op->g, a, w, w.t, 1.5, 1, op->ctl, op->red, L); });
+      if (ms < 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_err(cudaGetLastError(), "autotune launch", __LINE__);
+        return HZ_ERR_CUDA;
+      }
+      if (ms < bms) {
+        bms = ms;
+        best = id;
+      }
+    }
+    if (best >= 0) op->L.vsor[pr][kind] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return HZ_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1160,14 +1234,32 @@ int hz_op_autotune(hz_op op, int flags) {
     CKS(ensure_w64(op));
     CKS(autotune_prec<double>(op, reps, ms));
   }
-  // the captured inner loops bake the old launch shapes in: rebuild on next use
-  for (auto& gs : op->gs) {
-    if (gs.exec) cudaGraphExecDestroy(gs.exec);
-    if (gs.graph) cudaGraphDestroy(gs.graph);
-    gs.exec = nullptr;
-    gs.graph = nullptr;
+  if ((flags & 2) && op->g.nx % 2 == 0) {
+    CKS(autotune_sor<float>(op, reps));
+    if (flags & 1) CKS(autotune_sor<double>(op, reps));
   }
+  // the captured inner loops bake the old launch shapes in: rebuild on next use
+  for (auto& gs : op->gs) drop_graph(gs);
+  for (auto& gs : op->gs_sor) drop_graph(gs);
   store_tuned(op);
+  return HZ_OK;
+}
+
+int hz_sor_variant_count(int prec, int kind) {
+  if ((prec != HZ_PREC_FP32 && prec != HZ_PREC_FP64) || kind < 0 || kind > 2) return 0;
+  return sor_num_variants(prec == HZ_PREC_FP64 ? 1 : 0, kind);
+}
+
+int hz_op_get_sor_variant(hz_op op, int prec, int kind, int* id) {
+  if (!op || !id || hz_sor_variant_count(prec, kind) == 0) return HZ_ERR_INVALID;
+  *id = op->L.vsor[prec == HZ_PREC_FP64 ? 1 : 0][kind];
+  return HZ_OK;
+}
+
+int hz_op_set_sor_variant(hz_op op, int prec, int kind, int id) {
+  if (!op || id < 0 || id >= hz_sor_variant_count(prec, kind)) return HZ_ERR_INVALID;
+  op->L.vsor[prec == HZ_PREC_FP64 ? 1 : 0][kind] = id;
+  for (auto& gs : op->gs_sor) drop_graph(gs);
   return HZ_OK;
 }
 

@@ -140,7 +140,14 @@ struct Launch {
   cudaStream_t stream;
   int vpre[2];       // variant of the Thomas kernels, [0] FP32, [1] FP64
   int vmv[2];        // variant of the stencil kernels
+  int vsor[2][3];    // tri-SOR variants: [prec][0 colour pass, 1 matvec, 2 first pass]
 };
+
+// tri-SOR kernel variants (kind 0 colour pass, 1 matvec, 2 first pass):
+// depth = levels per software-pipelined batch, minb = launch bound in blocks
+// of kBS threads per SM (registers per thread = 65536 / (kBS * minb))
+int sor_num_variants(int prec, int kind);
+void sor_variant_shape(int prec, int kind, int id, int* depth, int* minb);
 
 // Column-kernel variants: kind 0 = Thomas (k_pre_p, k_pre_s), kind 1 = stencil
 // (k_mv); prec 0 = FP32, 1 = FP64.  vec = columns per thread (must divide nx),

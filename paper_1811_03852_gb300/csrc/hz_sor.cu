@@ -35,11 +35,6 @@ namespace hz {
 
 namespace {
 
-template <typename T>
-__host__ __device__ constexpr int sor_u() {
-  return sizeof(T) == 8 ? 2 : 4;
-}
-
 struct Rb {
   int nx, ny, nz, hx;
   int64_t ncol, H;
@@ -316,6 +311,36 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
 }
 
 // ---------------------------------------------------------------------------
+// Variants (the autotuner picks one per kernel, precision and grid): U levels
+// per batch and MINB blocks per SM (the register budget).  Each table lists
+// only shapes that compile without spills.
+template <typename T>
+struct SorVar;
+template <>
+struct SorVar<float> {
+  static constexpr int NK[3] = {4, 3, 3};
+  static constexpr int u[3][4] = {{2, 4, 1, 3}, {4, 2, 8, 0}, {4, 2, 3, 0}};
+  static constexpr int b[3][4] = {{6, 4, 8, 5}, {6, 8, 4, 0}, {6, 8, 5, 0}};
+};
+template <>
+struct SorVar<double> {
+  static constexpr int NK[3] = {3, 3, 3};
+  static constexpr int u[3][4] = {{1, 2, 2, 0}, {1, 2, 1, 0}, {1, 2, 1, 0}};
+  static constexpr int b[3][4] = {{6, 4, 5, 0}, {6, 4, 8, 0}, {6, 4, 8, 0}};
+};
+
+template <typename T, int KIND, int I = 0, typename F>
+cudaError_t with_sor(int id, F&& f) {
+  if constexpr (I < SorVar<T>::NK[KIND]) {
+    if (id == I)
+      return f(std::integral_constant<int, SorVar<T>::u[KIND][I]>{}, std::integral_constant<int, SorVar<T>::b[KIND][I]>{});
+    return with_sor<T, KIND, I + 1>(id, f);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_sor_first<0>: p = r + beta (p - omega v) (p = r after a start; on a
 //   restart, Sec. 4: r = rhs - Ahat x, r0 = r, p = r and ||r||^2), then the red
 //   pass of the first sweep on the new p: z1 = omega T^-1 p on red columns.
@@ -323,10 +348,9 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
 //   same first red pass on s.
 // All columns are updated; only the red half (compact columns < ncol/2)
 // continues into the tridiagonal solve.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* __restrict__ z1,
-                                                               double omega_d, Ctl* ctl, Red red) {
-  constexpr int U = sor_u<T>() / (sizeof(T) == 8 ? 2 : 1);
+template <typename T, int MODE, int U, int MINB>
+__global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* __restrict__ z1,
+                                                         double omega_d, Ctl* ctl, Red red) {
   const Rb rb = make_rb(g);
   bool restart = false;
   if (MODE == 0) {
@@ -382,13 +406,12 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_first(Grid g, Bands<T> 
 // may be the same buffer: the pass reads only the other colour's half of it
 // and writes only its own.  ctl (may be null): nothing to do unless the inner
 // solve is running.
-template <typename T>
-__global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_pass(Grid g, Bands<T> a, const T* __restrict__ rc,
-                                                              const T* __restrict__ znbr, const T* __restrict__ zold,
-                                                              T* __restrict__ zout, int colour, int nbr,
-                                                              double omega_d, const Ctl* ctl) {
+template <typename T, int U, int MINB>
+__global__ void __launch_bounds__(kBS, MINB) k_sor_pass(Grid g, Bands<T> a, const T* __restrict__ rc,
+                                                        const T* __restrict__ znbr, const T* __restrict__ zold,
+                                                        T* __restrict__ zout, int colour, int nbr, double omega_d,
+                                                        const Ctl* ctl) {
   if (ctl && ctl->state != ST_RUNNING) return;
-  constexpr int U = sor_u<T>() / 2;  // eleven loads per level
   const Rb rb = make_rb(g);
   const T omega = (T)omega_d, keep = (T)(1.0 - omega_d);
   for (int64_t h = (int64_t)blockIdx.x * kBS + threadIdx.x; h < rb.H; h += (int64_t)gridDim.x * kBS) {
@@ -402,10 +425,9 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_sor_pass(Grid g, Bands<T> a
 // MODE 0 (x = ph, y = v): <r0, v> -> alpha;  MODE 1 (x = sh, y = t): <t, s>, <t, t> -> omega.
 // The column's own values ride down in registers (x_(k-1), x_k); each level
 // loads x_(k+1), the four horizontal neighbours, six bands and the dot partner.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kBS, kMinBlocks) k_mv_rb(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
+template <typename T, int MODE, int U, int MINB>
+__global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
-  constexpr int U = sizeof(T) == 8 ? 1 : sor_u<T>();  // twelve loads per level
   const Rb rb = make_rb(g);
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
@@ -480,6 +502,11 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv_rb(Grid g, Bands<T> a, V
 
 // ---------------------------------------------------------------------------
 template <typename T>
+constexpr int sor_prec() {
+  return sizeof(T) == 8 ? 1 : 0;
+}
+
+template <typename T>
 cudaError_t launch_rb_copy(const Grid& g, const T* src, T* dst, int to_compact, const Launch& L) {
   if (to_compact)
     k_rb_copy<T, true><<<grid_for((const void*)k_rb_copy<T, true>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, src, dst);
@@ -491,43 +518,76 @@ cudaError_t launch_rb_copy(const Grid& g, const T* src, T* dst, int to_compact, 
 template <typename T>
 cudaError_t launch_sor_first(const Grid& g, const Bands<T>& a, const Vecs<T>& w, T* z1, double omega, int mode,
                              Ctl* ctl, Red red, const Launch& L) {
-  if (mode == 0)
-    k_sor_first<T, 0><<<grid_for((const void*)k_sor_first<T, 0>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, z1,
-                                                                                                        omega, ctl, red);
-  else
-    k_sor_first<T, 1><<<grid_for((const void*)k_sor_first<T, 1>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, z1,
-                                                                                                        omega, ctl, red);
-  return cudaGetLastError();
+  return with_sor<T, 2>(L.vsor[sor_prec<T>()][2], [&](auto uc, auto bc) {
+    constexpr int U = decltype(uc)::value, B = decltype(bc)::value;
+    if (mode == 0)
+      k_sor_first<T, 0, U, B><<<grid_for((const void*)k_sor_first<T, 0, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(
+          g, a, w, z1, omega, ctl, red);
+    else
+      k_sor_first<T, 1, U, B><<<grid_for((const void*)k_sor_first<T, 1, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(
+          g, a, w, z1, omega, ctl, red);
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
 cudaError_t launch_sor_pass(const Grid& g, const Bands<T>& a, const T* rc, const T* znbr, const T* zold, T* zout,
                             int colour, int nbr, double omega, const Ctl* ctl, const Launch& L) {
   const int64_t wb = (g.ncol / 2 + kBS - 1) / kBS;
-  k_sor_pass<T><<<grid_for((const void*)k_sor_pass<T>, kBS, L, wb), kBS, 0, L.stream>>>(g, a, rc, znbr, zold, zout,
-                                                                                          colour, nbr, omega, ctl);
-  return cudaGetLastError();
+  return with_sor<T, 0>(L.vsor[sor_prec<T>()][0], [&](auto uc, auto bc) {
+    constexpr int U = decltype(uc)::value, B = decltype(bc)::value;
+    k_sor_pass<T, U, B><<<grid_for((const void*)k_sor_pass<T, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+        g, a, rc, znbr, zold, zout, colour, nbr, omega, ctl);
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
 cudaError_t launch_mv_rb(const Grid& g, const Bands<T>& a, const Vecs<T>& w, int mode, Ctl* ctl, Red red,
                          const Launch& L) {
-  if (mode == 0)
-    k_mv_rb<T, 0><<<grid_for((const void*)k_mv_rb<T, 0>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
-  else
-    k_mv_rb<T, 1><<<grid_for((const void*)k_mv_rb<T, 1>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
-  return cudaGetLastError();
+  return with_sor<T, 1>(L.vsor[sor_prec<T>()][1], [&](auto uc, auto bc) {
+    constexpr int U = decltype(uc)::value, B = decltype(bc)::value;
+    if (mode == 0)
+      k_mv_rb<T, 0, U, B><<<grid_for((const void*)k_mv_rb<T, 0, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w,
+                                                                                                            ctl, red);
+    else
+      k_mv_rb<T, 1, U, B><<<grid_for((const void*)k_mv_rb<T, 1, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w,
+                                                                                                            ctl, red);
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
 void warm_sor(const Launch& L) {
   grid_for((const void*)k_rb_copy<T, true>, kBS, L, 1);
   grid_for((const void*)k_rb_copy<T, false>, kBS, L, 1);
-  grid_for((const void*)k_sor_first<T, 0>, kBS, L, 1);
-  grid_for((const void*)k_sor_first<T, 1>, kBS, L, 1);
-  grid_for((const void*)k_sor_pass<T>, kBS, L, 1);
-  grid_for((const void*)k_mv_rb<T, 0>, kBS, L, 1);
-  grid_for((const void*)k_mv_rb<T, 1>, kBS, L, 1);
+  for (int id = 0; id < SorVar<T>::NK[0]; ++id)
+    with_sor<T, 0>(id, [&](auto uc, auto bc) {
+      grid_for((const void*)k_sor_pass<T, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+      return cudaSuccess;
+    });
+  for (int id = 0; id < SorVar<T>::NK[1]; ++id)
+    with_sor<T, 1>(id, [&](auto uc, auto bc) {
+      grid_for((const void*)k_mv_rb<T, 0, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+      grid_for((const void*)k_mv_rb<T, 1, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+      return cudaSuccess;
+    });
+  for (int id = 0; id < SorVar<T>::NK[2]; ++id)
+    with_sor<T, 2>(id, [&](auto uc, auto bc) {
+      grid_for((const void*)k_sor_first<T, 0, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+      grid_for((const void*)k_sor_first<T, 1, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+      return cudaSuccess;
+    });
+}
+
+int sor_num_variants(int prec, int kind) {
+  if (kind < 0 || kind > 2) return 0;
+  return prec == 0 ? SorVar<float>::NK[kind] : SorVar<double>::NK[kind];
+}
+
+void sor_variant_shape(int prec, int kind, int id, int* depth, int* minb) {
+  *depth = prec == 0 ? SorVar<float>::u[kind][id] : SorVar<double>::u[kind][id];
+  *minb = prec == 0 ? SorVar<float>::b[kind][id] : SorVar<double>::b[kind][id];
 }
 
 #define HZ_SOR_INST(T)                                                                                               \

@@ -201,6 +201,67 @@ def test_trisor_forced_restarts_warm_start_and_sweep_counts():
         assert rn / np.linalg.norm(b) <= 1e-8
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_pass_variant_gives_identical_columns(prec):
+    # the variants change only launch shape and load batching, not the arithmetic of a column
+    import torch
+
+    hz = _hz()
+    nx, ny, nz = 130, 65, 11
+    A = gen.make_operator(nx, ny, nz, seed=4, z_unit="m")
+    op = hz.Operator(A)
+    p = hz.HZ_PREC_FP64 if prec == "fp64" else hz.HZ_PREC_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    r = dev(gen.normals(6, 0, nx * ny * nz), dt)
+    outs = []
+    for vid in range(hz.sor_variant_count(p, 0)):
+        op.set_sor_variant(p, 0, vid)
+        z = torch.empty(r.numel(), dtype=dt, device="cuda")
+        op.trisor_apply(r, z, p, 3, 1.5)
+        outs.append(host(z))
+    assert len(outs) >= 3 and all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+def test_every_matvec_and_first_pass_variant_solves(mode):
+    hz = _hz()
+    A, b = gen.make_system(96, 72, 20, 1, 2, z_unit="m")
+    m = hz.HZ_MODE_MIXED_IR if mode == "mixed" else hz.HZ_MODE_FP64
+    p = hz.HZ_PREC_FP32 if mode == "mixed" else hz.HZ_PREC_FP64
+    x_ref, _ = oracle.solve(A, b, mode=oracle.MODE_FP64, tol=1e-12, eta=1e-13)
+    import torch
+
+    op = hz.Operator(A)
+    for kind in (1, 2):
+        for vid in range(hz.sor_variant_count(p, kind)):
+            op.set_sor_variant(p, kind, vid)
+            x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+            info = op.solve(dev(b), x, mode=m, precond=hz.HZ_PRE_TRISOR)
+            xh = host(x).reshape(b.shape)
+            _, rn = oracle.residual(A, b, xh)
+            assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8, (kind, vid)
+            assert np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref) <= 1e-6
+        op.set_sor_variant(p, kind, 0)
+
+
+def test_autotune_picks_valid_sor_variants_and_solves():
+    import torch
+
+    hz = _hz()
+    A, b = gen.make_system(96, 72, 20, 3, 4, z_unit="m")
+    op = hz.Operator(A)
+    op.autotune(fp64=True, trisor=True)
+    v = op.sor_variants()
+    for (prec, kind), vid in v.items():
+        assert 0 <= vid < hz.sor_variant_count(prec, kind)
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    info = op.solve(dev(b), x, precond=hz.HZ_PRE_TRISOR)
+    _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+    assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8
+    with pytest.raises(hz.HzError):
+        op.set_sor_variant(hz.HZ_PREC_FP32, 0, hz.sor_variant_count(hz.HZ_PREC_FP32, 0))
+
+
 def test_trisor_rejections():
     import torch
 

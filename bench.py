@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--precond", default="tri", choices=["tri", "trisor"],
                     help="preconditioner of the headline solves: T^-1 or tri-SOR (Sec. 2)")
     ap.add_argument("--no-trisor", action="store_true", help="skip the tri-SOR side measurement")
+    ap.add_argument("--dims", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
+                    help="override the workload's grid (same recipe and seeds; for profiling smaller cases)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven inner loop (same kernels); ncu cannot profile kernels inside conditional graphs")
     return ap.parse_args()
@@ -126,7 +128,7 @@ def make_inputs(args):
     import gen
 
     w = gen.WORKLOADS[args.workload]
-    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    nx, ny, nz = args.dims if args.dims else (w["nx"], w["ny"], w["nz"])
     A = gen.make_operator(nx, ny, nz, w["seed_coef"], z_unit=args.z_unit)
     b = gen.make_rhs(nx, ny, nz, w["seed_rhs"])
     return (nx, ny, nz), A, b

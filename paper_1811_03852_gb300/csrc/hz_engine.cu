@@ -708,7 +708,7 @@ void load_tuned(hz_op op) {
         if (strcmp(want, key) != 0 || var < 0) continue;
         if (kind < 2 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx))
           (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = var;
-        else if (kind >= 2 && var < sor_num_variants(pr, kind - 2))
+        else if (kind >= 2 && sor_variant_ok(pr, kind - 2, var, op->g.nx))
           op->L.vsor[pr][kind - 2] = var;
       }
   }
@@ -1193,6 +1193,7 @@ int autotune_sor(hz_op op, int reps) {
     int best = -1;
     double bms = 1e30;
     for (int id = 0; id < sor_num_variants(pr, kind); ++id) {
+      if (!sor_variant_ok(pr, kind, id, op->g.nx)) continue;
       Launch L = op->L;
       L.vsor[pr][kind] = id;
       double ms;
@@ -1258,6 +1259,7 @@ int hz_op_get_sor_variant(hz_op op, int prec, int kind, int* id) {
 
 int hz_op_set_sor_variant(hz_op op, int prec, int kind, int id) {
   if (!op || id < 0 || id >= hz_sor_variant_count(prec, kind)) return HZ_ERR_INVALID;
+  if (!sor_variant_ok(prec == HZ_PREC_FP64 ? 1 : 0, kind, id, op->g.nx)) return HZ_ERR_INVALID;
   op->L.vsor[prec == HZ_PREC_FP64 ? 1 : 0][kind] = id;
   for (auto& gs : op->gs_sor) drop_graph(gs);
   return HZ_OK;

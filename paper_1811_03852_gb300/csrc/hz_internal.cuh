@@ -144,10 +144,12 @@ struct Launch {
 };
 
 // tri-SOR kernel variants (kind 0 colour pass, 1 matvec, 2 first pass):
-// depth = levels per software-pipelined batch, minb = launch bound in blocks
-// of kBS threads per SM (registers per thread = 65536 / (kBS * minb))
+// vec = columns per thread (must divide nx/2), depth = levels per
+// software-pipelined batch, minb = launch bound in blocks of kBS threads per
+// SM (registers per thread = 65536 / (kBS * minb))
 int sor_num_variants(int prec, int kind);
-void sor_variant_shape(int prec, int kind, int id, int* depth, int* minb);
+void sor_variant_shape(int prec, int kind, int id, int* vec, int* depth, int* minb);
+bool sor_variant_ok(int prec, int kind, int id, int nx);
 
 // Column-kernel variants: kind 0 = Thomas (k_pre_p, k_pre_s), kind 1 = stencil
 // (k_mv); prec 0 = FP32, 1 = FP64.  vec = columns per thread (must divide nx),

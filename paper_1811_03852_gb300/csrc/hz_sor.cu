@@ -10,25 +10,28 @@
 // colour and the columns are independent.
 //
 // Layout.  With this preconditioner the whole inner solve runs in
-// colour-compact column order, c = colour * (ncol/2) + j * (nx/2) + i/2: the
-// six scaled bands and the Thomas factors are permuted once per operator, the
-// inner right-hand side is gathered into this order and the inner solution
-// scattered back around every refinement step (the FP64 residual stays in
-// natural order).  A colour pass then streams one contiguous half of every
-// array, and the E/W/N/S neighbours of a compact column are at compact
-// columns of the other half that stay contiguous across a warp.  Inner
-// products and the elementwise BiCGStab updates are unchanged by the
-// relabelling.
+// colour-compact column order, c = colour * H + j * (nx/2) + i/2 with
+// H = ncol/2: the six scaled bands and the Thomas factors are permuted once
+// per operator, the inner right-hand side is gathered into this order and the
+// inner solution scattered back around every refinement step (the FP64
+// residual stays in natural order).  A colour pass then streams one
+// contiguous half of every array.  Inner products and the elementwise
+// BiCGStab updates are unchanged by the relabelling.
+//
+// Groups.  A thread owns V consecutive compact columns of one row (V divides
+// nx/2) and marches k with V-wide vector loads, U levels per software-
+// pipelined batch.  The other colour's values at the same (j, i/2) sit at
+// compact offset +-H (the "mirror" group): with p the parity of the first
+// column's i, its east neighbours are mirror[c + p] and its west neighbours
+// mirror[c + p - 1], so one aligned vector load of the mirror group plus one
+// scalar (the west neighbour of column 0 when p = 0, the east neighbour of
+// column V-1 when p = 1, wrapping around the periodic row) give all of them;
+// north and south are the mirror groups of rows j +- 1 (offset +-nx/2).
 //
 // Sweeps ping-pong between two buffers: a pass reads the other colour's
 // newest values and its own previous values from one buffer and writes its
 // colour to the other, so the forward Thomas sweep can park y in the output
 // column (as the T^-1 kernels do) and no extra array is needed.
-//
-// Every column march is software-pipelined like the T^-1 kernels: the loads
-// of U levels are issued before any of them is used (U from 1 to 4 by kernel
-// and precision, the largest that keeps the kernel within 80 registers
-// without spilling).
 #include "hz_krylov.cuh"
 
 namespace hz {
@@ -42,192 +45,229 @@ struct Rb {
 
 __device__ __forceinline__ Rb make_rb(const Grid& g) { return Rb{g.nx, g.ny, g.nz, g.nx / 2, g.ncol, g.ncol / 2}; }
 
-// neighbours of compact column q, as offsets from q (the same at every level)
-struct RbNbr {
-  int64_t e, w, n, s;
-  bool hn, hs;
+// other-colour neighbours of the group starting at compact column q0, as
+// offsets from the group's own index (the same at every level)
+struct RbGrp {
+  int64_t mir;  // mirror group: +H (red group) or -H (black group)
+  int64_t xo;   // the extra scalar (see above)
+  int64_t hx;   // row length of a half (north = mir + hx, south = mir - hx)
+  bool p;       // parity of i of the group's first column
+  bool hn, hs;  // north / south row exists
 };
 
-__device__ __forceinline__ RbNbr rb_nbr(const Rb& rb, int64_t q) {
-  const int c = q >= rb.H ? 1 : 0;
-  const int64_t r = q - (int64_t)c * rb.H;
+template <int V>
+__device__ __forceinline__ RbGrp rb_grp(const Rb& rb, int64_t q0) {
+  const int c = q0 >= rb.H ? 1 : 0;
+  const int64_t r = q0 - (int64_t)c * rb.H;
   const int j = (int)(r / rb.hx);
   const int qi = (int)(r - (int64_t)j * rb.hx);
-  const int i = 2 * qi + ((j + c) & 1);
-  const int iE = (i + 1 == rb.nx) ? 0 : i + 1;
-  const int iW = (i == 0) ? rb.nx - 1 : i - 1;
-  const int64_t o = (int64_t)(c ^ 1) * rb.H - q;
-  RbNbr n;
-  n.e = o + (int64_t)j * rb.hx + (iE >> 1);
-  n.w = o + (int64_t)j * rb.hx + (iW >> 1);
-  n.hn = j + 1 < rb.ny;
-  n.hs = j > 0;
-  n.n = n.hn ? o + (int64_t)(j + 1) * rb.hx + (i >> 1) : 0;
-  n.s = n.hs ? o + (int64_t)(j - 1) * rb.hx + (i >> 1) : 0;
-  return n;
+  RbGrp gr;
+  gr.mir = c ? -rb.H : rb.H;
+  gr.p = ((j + c) & 1) != 0;
+  if (!gr.p)
+    gr.xo = gr.mir + (qi == 0 ? (int64_t)(rb.hx - 1) : (int64_t)-1);
+  else
+    gr.xo = gr.mir + (qi + V == rb.hx ? (int64_t)-qi : (int64_t)V);
+  gr.hx = rb.hx;
+  gr.hn = j + 1 < rb.ny;
+  gr.hs = j > 0;
+  return gr;
 }
 
-// Work items of a kernel over both colours: item w maps to blocks of kBS red
-// and kBS black columns in turn, so that the blocks resident at one time
-// cover the same rows of both halves (a column read as the other colour's
-// neighbour is then still in L2 from its own read).  rb_col returns -1 for
-// the padding items past the end of a half.
-__device__ __forceinline__ int64_t rb_items(const Rb& rb) { return 2 * ((rb.H + kBS - 1) / kBS) * kBS; }
-__device__ __forceinline__ int64_t rb_col(const Rb& rb, int64_t w) {
-  const int64_t pb = w / (2 * kBS);
-  const int within = (int)(w - pb * 2 * kBS);
-  const int colour = within >= kBS ? 1 : 0;
-  const int64_t off = pb * kBS + (within - colour * kBS);
-  return off < rb.H ? (int64_t)colour * rb.H + off : -1;
+// east / west neighbour of column c of the group from the mirror vector m and the extra scalar x
+template <typename T, int V>
+__device__ __forceinline__ T nbr_e(const RbGrp& gr, const Pack<T, V>& m, T x, int c) {
+  if (!gr.p) return m.a[c];
+  return c + 1 < V ? m.a[(c + 1) % V] : x;
+}
+template <typename T, int V>
+__device__ __forceinline__ T nbr_w(const RbGrp& gr, const Pack<T, V>& m, T x, int c) {
+  if (gr.p) return m.a[c];
+  return c > 0 ? m.a[(c + V - 1) % V] : x;
 }
 
-// (Ahat x)_(k, q) in compact order, all six bands (restart path only)
-template <typename T>
-__device__ __forceinline__ T ahat_rb(const Rb& rb, const Bands<T>& a, const T* x, int64_t q, int k, const RbNbr& nb) {
-  const int64_t idx = (int64_t)k * rb.ncol + q;
-  T y = x[idx];
-  y = fma(a.E[idx], x[idx + nb.e], y);
-  y = fma(a.W[idx], x[idx + nb.w], y);
-  if (nb.hn) y = fma(a.N[idx], x[idx + nb.n], y);
-  if (nb.hs) y = fma(a.S[idx], x[idx + nb.s], y);
-  if (k + 1 < rb.nz) y = fma(a.U[idx], x[idx + rb.ncol], y);
-  if (k > 0) y = fma(a.D[idx], x[idx - rb.ncol], y);
-  return y;
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> zero_pack() {
+  Pack<T, V> z;
+#pragma unroll
+  for (int c = 0; c < V; ++c) z.a[c] = T(0);
+  return z;
 }
 
-// Relaxed Thomas solve of one column with unit diagonal and pre-computed
+// Relaxed Thomas solve of V columns with unit diagonal and pre-computed
 // factors: forward y_k = m_k q_k - l_k y_(k-1) with q_k = src.make(...), y
 // parked in z; back x_k = y_k - c'_k x_(k+1) and
 // z_k = (1 - omega) zold_k + omega x_k (zold == nullptr: zero).
-template <typename T, int U, typename Src>
-__device__ __forceinline__ void sor_column(const Rb& rb, int64_t q, const T* __restrict__ m, const T* __restrict__ l,
-                                           const T* __restrict__ cp, const T* __restrict__ zold, T* __restrict__ z,
-                                           T omega, T keep, Src& src) {
-  constexpr int NIN = Src::NIN;
+template <typename T, int V, int U, typename Src>
+__device__ __forceinline__ void sor_group(const Rb& rb, int64_t q0, const T* __restrict__ m, const T* __restrict__ l,
+                                          const T* __restrict__ cp, const T* __restrict__ zold, T* __restrict__ z,
+                                          T omega, T keep, Src& src) {
   const int64_t ncol = rb.ncol;
   const int nz = rb.nz;
-  T yprev = T(0);
+  T yprev[V];
+#pragma unroll
+  for (int c = 0; c < V; ++c) yprev[c] = T(0);
   for (int k0 = 0; k0 < nz; k0 += U) {
-    T v[U][NIN], mm[U], ll[U];
+    typename Src::In v[U];
+    Pack<T, V> mm[U], ll[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (k0 + u < nz) {
-        const int64_t idx = (int64_t)(k0 + u) * ncol + q;
+        const int64_t idx = (int64_t)(k0 + u) * ncol + q0;
         src.load(idx, v[u]);
-        mm[u] = __ldg(m + idx);
-        ll[u] = __ldg(l + idx);
+        mm[u] = ldp<T, V, LD_NC>(m + idx);
+        ll[u] = ldp<T, V, LD_NC>(l + idx);
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (k0 + u < nz) {
-        const int64_t idx = (int64_t)(k0 + u) * ncol + q;
-        const T qv = src.make(v[u], idx);
-        yprev = fma(mm[u], qv, -ll[u] * yprev);
-        z[idx] = yprev;
+        const int64_t idx = (int64_t)(k0 + u) * ncol + q0;
+        const Pack<T, V> q = src.make(v[u], idx);
+        Pack<T, V> y;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+          y.a[c] = fma(mm[u].a[c], q.a[c], -ll[u].a[c] * yprev[c]);
+          yprev[c] = y.a[c];
+        }
+        stp(z + idx, y);
       }
     }
     src.flush();
   }
-  T xn = T(0);
-  for (int k0 = nz - 1; k0 >= 0; k0 -= 2 * U) {
-    T yy[2 * U], cc[2 * U], zo[2 * U];
+  T xn[V];
 #pragma unroll
-    for (int u = 0; u < 2 * U; ++u) {
+  for (int c = 0; c < V; ++c) xn[c] = T(0);
+  constexpr int UB = 2 * U;
+  for (int k0 = nz - 1; k0 >= 0; k0 -= UB) {
+    Pack<T, V> yy[UB], cc[UB], zo[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
       if (k0 - u >= 0) {
-        const int64_t idx = (int64_t)(k0 - u) * ncol + q;
-        yy[u] = z[idx];  // written by this thread above: coherent load
-        cc[u] = __ldg(cp + idx);
-        zo[u] = zold ? __ldg(zold + idx) : T(0);
+        const int64_t idx = (int64_t)(k0 - u) * ncol + q0;
+        yy[u] = ldp<T, V, LD_PLAIN>(z + idx);  // written by this thread above: coherent load
+        cc[u] = ldp<T, V, LD_NC>(cp + idx);
+        zo[u] = zold ? ldp<T, V, LD_NC>(zold + idx) : zero_pack<T, V>();
       }
     }
 #pragma unroll
-    for (int u = 0; u < 2 * U; ++u) {
+    for (int u = 0; u < UB; ++u) {
       if (k0 - u >= 0) {
-        const int64_t idx = (int64_t)(k0 - u) * ncol + q;
-        xn = fma(-cc[u], xn, yy[u]);
-        z[idx] = fma(keep, zo[u], omega * xn);
+        const int64_t idx = (int64_t)(k0 - u) * ncol + q0;
+        Pack<T, V> o;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+          xn[c] = fma(-cc[u].a[c], xn[c], yy[u].a[c]);
+          o.a[c] = fma(keep, zo[u].a[c], omega * xn[c]);
+        }
+        stp(z + idx, o);
       }
     }
   }
 }
 
 // inputs of the relaxed solves ------------------------------------------------
-template <typename T>
+template <typename T, int V>
 struct SrcHz {  // q = rc - (E zE + W zW + N zN + S zS); nbr == false: q = rc
-  static constexpr int NIN = 9;
+  struct In {
+    Pack<T, V> rc, e, w, n, s, zm, zn, zs;
+    T zx;
+  };
   const T* __restrict__ rc;
   const T* __restrict__ E;
   const T* __restrict__ W;
   const T* __restrict__ N;
   const T* __restrict__ S;
-  const T* __restrict__ zn;  // other colour's newest values (read-only in the pass)
-  RbNbr nb;
+  const T* __restrict__ z;  // other colour's newest values (read-only in the pass)
+  RbGrp gr;
   bool nbr;
-  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
-    o[0] = __ldg(rc + idx);
+  __device__ __forceinline__ void load(int64_t idx, In& o) {
+    o.rc = ldp<T, V, LD_NC>(rc + idx);
     if (nbr) {
-      o[1] = __ldg(E + idx);
-      o[2] = __ldg(zn + idx + nb.e);
-      o[3] = __ldg(W + idx);
-      o[4] = __ldg(zn + idx + nb.w);
-      o[5] = nb.hn ? __ldg(N + idx) : T(0);
-      o[6] = nb.hn ? __ldg(zn + idx + nb.n) : T(0);
-      o[7] = nb.hs ? __ldg(S + idx) : T(0);
-      o[8] = nb.hs ? __ldg(zn + idx + nb.s) : T(0);
+      o.e = ldp<T, V, LD_NC>(E + idx);
+      o.w = ldp<T, V, LD_NC>(W + idx);
+      o.zm = ldp<T, V, LD_NC>(z + idx + gr.mir);
+      o.zx = ldw<T, LD_NC>(z + idx + gr.xo);
+      if (gr.hn) {
+        o.n = ldp<T, V, LD_NC>(N + idx);
+        o.zn = ldp<T, V, LD_NC>(z + idx + gr.mir + gr.hx);
+      } else {
+        o.n = o.zn = zero_pack<T, V>();
+      }
+      if (gr.hs) {
+        o.s = ldp<T, V, LD_NC>(S + idx);
+        o.zs = ldp<T, V, LD_NC>(z + idx + gr.mir - gr.hx);
+      } else {
+        o.s = o.zs = zero_pack<T, V>();
+      }
     }
   }
-  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t) {
-    if (!nbr) return o[0];
-    T h = o[1] * o[2];
-    h = fma(o[3], o[4], h);
-    h = fma(o[5], o[6], h);
-    h = fma(o[7], o[8], h);
-    return o[0] - h;
-  }
-  __device__ __forceinline__ void flush() {}
-};
-
-template <typename T>
-struct SrcPu {  // p = r + beta (p - omega v) (fresh: p = r), stored
-  static constexpr int NIN = 3;
-  const T* __restrict__ r;
-  T* __restrict__ p;
-  const T* __restrict__ v;
-  T beta, omega;
-  bool fresh;
-  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
-    o[0] = __ldg(r + idx);
-    if (!fresh) {
-      o[1] = p[idx];
-      o[2] = __ldg(v + idx);
+  __device__ __forceinline__ Pack<T, V> make(const In& o, int64_t) {
+    if (!nbr) return o.rc;
+    Pack<T, V> q;
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      T h = o.e.a[c] * nbr_e<T, V>(gr, o.zm, o.zx, c);
+      h = fma(o.w.a[c], nbr_w<T, V>(gr, o.zm, o.zx, c), h);
+      h = fma(o.n.a[c], o.zn.a[c], h);
+      h = fma(o.s.a[c], o.zs.a[c], h);
+      q.a[c] = o.rc.a[c] - h;
     }
-  }
-  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
-    const T q = fresh ? o[0] : fma(beta, fma(-omega, o[2], o[1]), o[0]);
-    p[idx] = q;
     return q;
   }
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T>
+template <typename T, int V>
+struct SrcPu {  // p = r + beta (p - omega v) (fresh: p = r), stored
+  struct In {
+    Pack<T, V> r, p, v;
+  };
+  const T* __restrict__ r;
+  T* __restrict__ p;
+  const T* __restrict__ v;
+  T beta, omega;
+  bool fresh;
+  __device__ __forceinline__ void load(int64_t idx, In& o) {
+    o.r = ldp<T, V, LD_NC>(r + idx);
+    if (!fresh) {
+      o.p = ldp<T, V, LD_PLAIN>(p + idx);
+      o.v = ldp<T, V, LD_NC>(v + idx);
+    }
+  }
+  __device__ __forceinline__ Pack<T, V> make(const In& o, int64_t idx) {
+    Pack<T, V> q;
+#pragma unroll
+    for (int c = 0; c < V; ++c) q.a[c] = fresh ? o.r.a[c] : fma(beta, fma(-omega, o.v.a[c], o.p.a[c]), o.r.a[c]);
+    stp(p + idx, q);
+    return q;
+  }
+  __device__ __forceinline__ void flush() {}
+};
+
+template <typename T, int V>
 struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP64 across)
-  static constexpr int NIN = 2;
+  struct In {
+    Pack<T, V> r, v;
+  };
   const T* __restrict__ r;
   const T* __restrict__ v;
   T* __restrict__ s;
   T alpha;
   T part;
   double acc;
-  __device__ __forceinline__ void load(int64_t idx, T (&o)[NIN]) {
-    o[0] = __ldg(r + idx);
-    o[1] = __ldg(v + idx);
+  __device__ __forceinline__ void load(int64_t idx, In& o) {
+    o.r = ldp<T, V, LD_NC>(r + idx);
+    o.v = ldp<T, V, LD_NC>(v + idx);
   }
-  __device__ __forceinline__ T make(const T (&o)[NIN], int64_t idx) {
-    const T q = fma(-alpha, o[1], o[0]);
-    s[idx] = q;
-    part = fma(q, q, part);
+  __device__ __forceinline__ Pack<T, V> make(const In& o, int64_t idx) {
+    Pack<T, V> q;
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      q.a[c] = fma(-alpha, o.v.a[c], o.r.a[c]);
+      part = fma(q.a[c], q.a[c], part);
+    }
+    stp(s + idx, q);
     return q;
   }
   __device__ __forceinline__ void flush() {
@@ -236,20 +276,35 @@ struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP
   }
 };
 
-// the vector update alone on a column (black half of k_sor_first)
-template <typename T, int U, typename Src>
-__device__ __forceinline__ void update_column(const Rb& rb, int64_t q, Src& src) {
-  constexpr int NIN = Src::NIN;
-  for (int k0 = 0; k0 < rb.nz; k0 += 2 * U) {
-    T v[2 * U][NIN];
+// the vector update alone on a group (black half of k_sor_first)
+template <typename T, int V, int U, typename Src>
+__device__ __forceinline__ void update_group(const Rb& rb, int64_t q0, Src& src) {
+  constexpr int UB = 2 * U;
+  for (int k0 = 0; k0 < rb.nz; k0 += UB) {
+    typename Src::In v[UB];
 #pragma unroll
-    for (int u = 0; u < 2 * U; ++u)
-      if (k0 + u < rb.nz) src.load((int64_t)(k0 + u) * rb.ncol + q, v[u]);
+    for (int u = 0; u < UB; ++u)
+      if (k0 + u < rb.nz) src.load((int64_t)(k0 + u) * rb.ncol + q0, v[u]);
 #pragma unroll
-    for (int u = 0; u < 2 * U; ++u)
-      if (k0 + u < rb.nz) src.make(v[u], (int64_t)(k0 + u) * rb.ncol + q);
+    for (int u = 0; u < UB; ++u)
+      if (k0 + u < rb.nz) src.make(v[u], (int64_t)(k0 + u) * rb.ncol + q0);
     src.flush();
   }
+}
+
+// Work items over both colours, in groups: item w maps to blocks of kBS red
+// and kBS black groups in turn, so that the blocks resident at one time cover
+// the same rows of both halves (a column read as the other colour's
+// neighbour is then still in L2 from its own read).  rb_group returns -1 for
+// the padding items past the end of a half.
+__device__ __forceinline__ int64_t rb_items(int64_t hg) { return 2 * ((hg + kBS - 1) / kBS) * kBS; }
+template <int V>
+__device__ __forceinline__ int64_t rb_group(const Rb& rb, int64_t hg, int64_t w) {
+  const int64_t pb = w / (2 * kBS);
+  const int within = (int)(w - pb * 2 * kBS);
+  const int colour = within >= kBS ? 1 : 0;
+  const int64_t off = pb * kBS + (within - colour * kBS);
+  return off < hg ? (int64_t)colour * rb.H + off * V : -1;
 }
 
 // Restart of one compact column (rare, out of line): r = rhs - Ahat x,
@@ -257,12 +312,22 @@ __device__ __forceinline__ void update_column(const Rb& rb, int64_t q, Src& src)
 template <typename T>
 __device__ __noinline__ double restart_rb(const Rb& rb, const Bands<T>& a, const Vecs<T>& w, int64_t q, bool xzero,
                                           T* z1, T omega) {
-  const RbNbr nb = rb_nbr(rb, q);
+  const RbGrp gr = rb_grp<1>(rb, q);
   T acc = T(0);
   for (int k = 0; k < rb.nz; ++k) {
     const int64_t idx = (int64_t)k * rb.ncol + q;
     T v = w.rhs[idx];
-    if (!xzero) v -= ahat_rb(rb, a, w.x, q, k, nb);
+    if (!xzero) {
+      const T xm = w.x[idx + gr.mir], xx = w.x[idx + gr.xo];
+      T y = w.x[idx];
+      y = fma(a.E[idx], gr.p ? xx : xm, y);
+      y = fma(a.W[idx], gr.p ? xm : xx, y);
+      if (gr.hn) y = fma(a.N[idx], w.x[idx + gr.mir + gr.hx], y);
+      if (gr.hs) y = fma(a.S[idx], w.x[idx + gr.mir - gr.hx], y);
+      if (k + 1 < rb.nz) y = fma(a.U[idx], w.x[idx + rb.ncol], y);
+      if (k > 0) y = fma(a.D[idx], w.x[idx - rb.ncol], y);
+      v -= y;
+    }
     w.r[idx] = v;
     w.r0[idx] = v;
     w.p[idx] = v;
@@ -311,29 +376,33 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
 }
 
 // ---------------------------------------------------------------------------
-// Variants (the autotuner picks one per kernel, precision and grid): U levels
-// per batch and MINB blocks per SM (the register budget).  Each table lists
-// only shapes that compile without spills.
+// Variants (the autotuner picks one per kernel, precision and grid): V columns
+// per thread (V divides nx/2), U levels per batch and MINB blocks per SM (the
+// register budget).  Variant 0 of every table has V = 1 (any even nx).  The
+// tables list only shapes that compile without spills.
 template <typename T>
 struct SorVar;
 template <>
 struct SorVar<float> {
-  static constexpr int NK[3] = {4, 3, 3};
-  static constexpr int u[3][4] = {{2, 4, 1, 3}, {4, 2, 8, 0}, {4, 2, 3, 0}};
-  static constexpr int b[3][4] = {{6, 4, 8, 5}, {6, 8, 4, 0}, {6, 8, 5, 0}};
+  static constexpr int NK[3] = {6, 5, 4};
+  static constexpr int v[3][6] = {{1, 1, 2, 4, 4, 2}, {1, 1, 2, 4, 4, 0}, {1, 2, 4, 2, 0, 0}};
+  static constexpr int u[3][6] = {{2, 3, 1, 1, 1, 2}, {4, 2, 2, 1, 2, 0}, {4, 2, 1, 2, 0, 0}};
+  static constexpr int b[3][6] = {{6, 5, 6, 6, 5, 4}, {6, 8, 6, 6, 4, 0}, {6, 6, 4, 4, 0, 0}};
 };
 template <>
 struct SorVar<double> {
-  static constexpr int NK[3] = {3, 3, 3};
-  static constexpr int u[3][4] = {{1, 2, 2, 0}, {1, 2, 1, 0}, {1, 2, 1, 0}};
-  static constexpr int b[3][4] = {{6, 4, 5, 0}, {6, 4, 8, 0}, {6, 4, 8, 0}};
+  static constexpr int NK[3] = {4, 4, 3};
+  static constexpr int v[3][6] = {{1, 1, 2, 2, 0, 0}, {1, 1, 2, 2, 0, 0}, {1, 2, 2, 0, 0, 0}};
+  static constexpr int u[3][6] = {{1, 2, 1, 1, 0, 0}, {1, 2, 1, 1, 0, 0}, {1, 1, 1, 0, 0, 0}};
+  static constexpr int b[3][6] = {{6, 4, 4, 5, 0, 0}, {6, 4, 6, 4, 0, 0}, {6, 4, 5, 0, 0, 0}};
 };
 
 template <typename T, int KIND, int I = 0, typename F>
 cudaError_t with_sor(int id, F&& f) {
   if constexpr (I < SorVar<T>::NK[KIND]) {
     if (id == I)
-      return f(std::integral_constant<int, SorVar<T>::u[KIND][I]>{}, std::integral_constant<int, SorVar<T>::b[KIND][I]>{});
+      return f(std::integral_constant<int, SorVar<T>::v[KIND][I]>{}, std::integral_constant<int, SorVar<T>::u[KIND][I]>{},
+               std::integral_constant<int, SorVar<T>::b[KIND][I]>{});
     return with_sor<T, KIND, I + 1>(id, f);
   } else {
     return cudaErrorInvalidValue;
@@ -346,9 +415,9 @@ cudaError_t with_sor(int id, F&& f) {
 //   pass of the first sweep on the new p: z1 = omega T^-1 p on red columns.
 // k_sor_first<1>: s = r - alpha v, ||s||^2 (half-step exit test), then the
 //   same first red pass on s.
-// All columns are updated; only the red half (compact columns < ncol/2)
-// continues into the tridiagonal solve.
-template <typename T, int MODE, int U, int MINB>
+// All columns are updated; only the red half (compact columns < H) continues
+// into the tridiagonal solve.
+template <typename T, int MODE, int V, int U, int MINB>
 __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* __restrict__ z1,
                                                          double omega_d, Ctl* ctl, Red red) {
   const Rb rb = make_rb(g);
@@ -372,26 +441,27 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
     if (grid_reduce<1>(vv, red, o)) fin_restart(ctl, o[0]);
     return;
   }
-  const int64_t items = rb_items(rb);
+  const int64_t hg = rb.H / V;
+  const int64_t items = rb_items(hg);
   if (MODE == 0) {
-    SrcPu<T> src{rin, w.p, w.v, (T)ctl->beta, (T)ctl->omega, ctl->fresh != 0};
+    SrcPu<T, V> src{rin, w.p, w.v, (T)ctl->beta, (T)ctl->omega, ctl->fresh != 0};
     for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
-      const int64_t q = rb_col(rb, it);
-      if (q < 0) continue;
-      if (q < rb.H)
-        sor_column<T, U>(rb, q, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
+      const int64_t q0 = rb_group<V>(rb, hg, it);
+      if (q0 < 0) continue;
+      if (q0 < rb.H)
+        sor_group<T, V, U>(rb, q0, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
       else
-        update_column<T, U>(rb, q, src);
+        update_group<T, V, U>(rb, q0, src);
     }
   } else {
-    SrcSu<T> src{rin, w.v, w.s, (T)ctl->alpha, T(0), 0.0};
+    SrcSu<T, V> src{rin, w.v, w.s, (T)ctl->alpha, T(0), 0.0};
     for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
-      const int64_t q = rb_col(rb, it);
-      if (q < 0) continue;
-      if (q < rb.H)
-        sor_column<T, U>(rb, q, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
+      const int64_t q0 = rb_group<V>(rb, hg, it);
+      if (q0 < 0) continue;
+      if (q0 < rb.H)
+        sor_group<T, V, U>(rb, q0, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
       else
-        update_column<T, U>(rb, q, src);
+        update_group<T, V, U>(rb, q0, src);
     }
     double vv[1] = {src.acc}, o[1];
     if (grid_reduce<1>(vv, red, o)) fin_snorm(ctl, o[0]);
@@ -406,7 +476,7 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
 // may be the same buffer: the pass reads only the other colour's half of it
 // and writes only its own.  ctl (may be null): nothing to do unless the inner
 // solve is running.
-template <typename T, int U, int MINB>
+template <typename T, int V, int U, int MINB>
 __global__ void __launch_bounds__(kBS, MINB) k_sor_pass(Grid g, Bands<T> a, const T* __restrict__ rc,
                                                         const T* __restrict__ znbr, const T* __restrict__ zold,
                                                         T* __restrict__ zout, int colour, int nbr, double omega_d,
@@ -414,58 +484,64 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_pass(Grid g, Bands<T> a, cons
   if (ctl && ctl->state != ST_RUNNING) return;
   const Rb rb = make_rb(g);
   const T omega = (T)omega_d, keep = (T)(1.0 - omega_d);
-  for (int64_t h = (int64_t)blockIdx.x * kBS + threadIdx.x; h < rb.H; h += (int64_t)gridDim.x * kBS) {
-    const int64_t q = (int64_t)colour * rb.H + h;
-    SrcHz<T> src{rc, a.E, a.W, a.N, a.S, znbr, rb_nbr(rb, q), nbr != 0};
-    sor_column<T, U>(rb, q, a.m, a.l, a.cp, zold, zout, omega, keep, src);
+  const int64_t hg = rb.H / V;
+  for (int64_t h = (int64_t)blockIdx.x * kBS + threadIdx.x; h < hg; h += (int64_t)gridDim.x * kBS) {
+    const int64_t q0 = (int64_t)colour * rb.H + h * V;
+    SrcHz<T, V> src{rc, a.E, a.W, a.N, a.S, znbr, rb_grp<V>(rb, q0), nbr != 0};
+    sor_group<T, V, U>(rb, q0, a.m, a.l, a.cp, zold, zout, omega, keep, src);
   }
 }
 
 // y = Ahat x in compact order with the iteration's dots:
 // MODE 0 (x = ph, y = v): <r0, v> -> alpha;  MODE 1 (x = sh, y = t): <t, s>, <t, t> -> omega.
-// The column's own values ride down in registers (x_(k-1), x_k); each level
-// loads x_(k+1), the four horizontal neighbours, six bands and the dot partner.
-template <typename T, int MODE, int U, int MINB>
+// The group's own values ride down in registers (x_(k-1), x_k); each level
+// loads x_(k+1), the mirror groups of rows j-1, j, j+1 and one scalar, six
+// bands and the dot partner.
+template <typename T, int MODE, int V, int U, int MINB>
 __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
   const Rb rb = make_rb(g);
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
   const T* __restrict__ c = MODE == 0 ? (ctl->r0sel ? w.r0 : w.rhs) : w.s;
-  const T* __restrict__ E = a.E;
-  const T* __restrict__ W = a.W;
-  const T* __restrict__ N = a.N;
-  const T* __restrict__ S = a.S;
-  const T* __restrict__ Up = a.U;
-  const T* __restrict__ Dn = a.D;
   const int64_t ncol = rb.ncol;
   const int nz = rb.nz;
+  const int64_t hg = rb.H / V;
   double acc0 = 0.0, acc1 = 0.0;
-  const int64_t items = rb_items(rb);
+  const int64_t items = rb_items(hg);
   for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
-    const int64_t q = rb_col(rb, it);
-    if (q < 0) continue;
-    const RbNbr nb = rb_nbr(rb, q);
-    T xm = T(0), x0 = __ldg(x + q);
+    const int64_t q0 = rb_group<V>(rb, hg, it);
+    if (q0 < 0) continue;
+    const RbGrp gr = rb_grp<V>(rb, q0);
+    Pack<T, V> xm = zero_pack<T, V>(), x0 = ldp<T, V, LD_NC>(x + q0);
     for (int k0 = 0; k0 < nz; k0 += U) {
-      T xp[U], he[U], hw[U], hn[U], hs[U], be[U], bw[U], bn[U], bs[U], bu[U], bd[U], cc[U];
+      Pack<T, V> xp[U], hm[U], hn[U], hs[U], be[U], bw[U], bn[U], bs[U], bu[U], bd[U], cc[U];
+      T hx1[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int k = k0 + u;
         if (k < nz) {
-          const int64_t idx = (int64_t)k * ncol + q;
-          xp[u] = k + 1 < nz ? __ldg(x + idx + ncol) : T(0);
-          he[u] = __ldg(x + idx + nb.e);
-          hw[u] = __ldg(x + idx + nb.w);
-          hn[u] = nb.hn ? __ldg(x + idx + nb.n) : T(0);
-          hs[u] = nb.hs ? __ldg(x + idx + nb.s) : T(0);
-          be[u] = __ldg(E + idx);
-          bw[u] = __ldg(W + idx);
-          bn[u] = nb.hn ? __ldg(N + idx) : T(0);
-          bs[u] = nb.hs ? __ldg(S + idx) : T(0);
-          bu[u] = __ldg(Up + idx);
-          bd[u] = __ldg(Dn + idx);
-          cc[u] = __ldg(c + idx);
+          const int64_t idx = (int64_t)k * ncol + q0;
+          xp[u] = k + 1 < nz ? ldp<T, V, LD_NC>(x + idx + ncol) : zero_pack<T, V>();
+          hm[u] = ldp<T, V, LD_NC>(x + idx + gr.mir);
+          hx1[u] = ldw<T, LD_NC>(x + idx + gr.xo);
+          be[u] = ldp<T, V, LD_NC>(a.E + idx);
+          bw[u] = ldp<T, V, LD_NC>(a.W + idx);
+          if (gr.hn) {
+            hn[u] = ldp<T, V, LD_NC>(x + idx + gr.mir + gr.hx);
+            bn[u] = ldp<T, V, LD_NC>(a.N + idx);
+          } else {
+            hn[u] = bn[u] = zero_pack<T, V>();
+          }
+          if (gr.hs) {
+            hs[u] = ldp<T, V, LD_NC>(x + idx + gr.mir - gr.hx);
+            bs[u] = ldp<T, V, LD_NC>(a.S + idx);
+          } else {
+            hs[u] = bs[u] = zero_pack<T, V>();
+          }
+          bu[u] = ldp<T, V, LD_NC>(a.U + idx);
+          bd[u] = ldp<T, V, LD_NC>(a.D + idx);
+          cc[u] = ldp<T, V, LD_NC>(c + idx);
         }
       }
       T a0 = T(0), a1 = T(0);
@@ -473,16 +549,21 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
       for (int u = 0; u < U; ++u) {
         const int k = k0 + u;
         if (k < nz) {
-          T yy = x0;
-          yy = fma(be[u], he[u], yy);
-          yy = fma(bw[u], hw[u], yy);
-          yy = fma(bn[u], hn[u], yy);
-          yy = fma(bs[u], hs[u], yy);
-          yy = fma(bu[u], xp[u], yy);
-          yy = fma(bd[u], xm, yy);
-          y[(int64_t)k * ncol + q] = yy;
-          a0 = fma(cc[u], yy, a0);
-          if (MODE == 1) a1 = fma(yy, yy, a1);
+          Pack<T, V> yy;
+#pragma unroll
+          for (int cl = 0; cl < V; ++cl) {
+            T t = x0.a[cl];
+            t = fma(be[u].a[cl], nbr_e<T, V>(gr, hm[u], hx1[u], cl), t);
+            t = fma(bw[u].a[cl], nbr_w<T, V>(gr, hm[u], hx1[u], cl), t);
+            t = fma(bn[u].a[cl], hn[u].a[cl], t);
+            t = fma(bs[u].a[cl], hs[u].a[cl], t);
+            t = fma(bu[u].a[cl], xp[u].a[cl], t);
+            t = fma(bd[u].a[cl], xm.a[cl], t);
+            yy.a[cl] = t;
+            a0 = fma(cc[u].a[cl], t, a0);
+            if (MODE == 1) a1 = fma(t, t, a1);
+          }
+          stp(y + (int64_t)k * ncol + q0, yy);
           xm = x0;
           x0 = xp[u];
         }
@@ -515,16 +596,21 @@ cudaError_t launch_rb_copy(const Grid& g, const T* src, T* dst, int to_compact, 
   return cudaGetLastError();
 }
 
+// blocks of kBS threads for the interleaved both-colour kernels with V columns per thread
+inline int64_t rb_blocks(const Grid& g, int V) { return 2 * ((g.ncol / 2 / V + kBS - 1) / kBS); }
+
 template <typename T>
 cudaError_t launch_sor_first(const Grid& g, const Bands<T>& a, const Vecs<T>& w, T* z1, double omega, int mode,
                              Ctl* ctl, Red red, const Launch& L) {
-  return with_sor<T, 2>(L.vsor[sor_prec<T>()][2], [&](auto uc, auto bc) {
-    constexpr int U = decltype(uc)::value, B = decltype(bc)::value;
+  return with_sor<T, 2>(L.vsor[sor_prec<T>()][2], [&](auto vc, auto uc, auto bc) {
+    constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+    if ((g.nx / 2) % V) return cudaErrorInvalidValue;
+    const int64_t wb = rb_blocks(g, V);
     if (mode == 0)
-      k_sor_first<T, 0, U, B><<<grid_for((const void*)k_sor_first<T, 0, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(
+      k_sor_first<T, 0, V, U, B><<<grid_for((const void*)k_sor_first<T, 0, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
           g, a, w, z1, omega, ctl, red);
     else
-      k_sor_first<T, 1, U, B><<<grid_for((const void*)k_sor_first<T, 1, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(
+      k_sor_first<T, 1, V, U, B><<<grid_for((const void*)k_sor_first<T, 1, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
           g, a, w, z1, omega, ctl, red);
     return cudaGetLastError();
   });
@@ -533,10 +619,11 @@ cudaError_t launch_sor_first(const Grid& g, const Bands<T>& a, const Vecs<T>& w,
 template <typename T>
 cudaError_t launch_sor_pass(const Grid& g, const Bands<T>& a, const T* rc, const T* znbr, const T* zold, T* zout,
                             int colour, int nbr, double omega, const Ctl* ctl, const Launch& L) {
-  const int64_t wb = (g.ncol / 2 + kBS - 1) / kBS;
-  return with_sor<T, 0>(L.vsor[sor_prec<T>()][0], [&](auto uc, auto bc) {
-    constexpr int U = decltype(uc)::value, B = decltype(bc)::value;
-    k_sor_pass<T, U, B><<<grid_for((const void*)k_sor_pass<T, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+  return with_sor<T, 0>(L.vsor[sor_prec<T>()][0], [&](auto vc, auto uc, auto bc) {
+    constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+    if ((g.nx / 2) % V) return cudaErrorInvalidValue;
+    const int64_t wb = (g.ncol / 2 / V + kBS - 1) / kBS;
+    k_sor_pass<T, V, U, B><<<grid_for((const void*)k_sor_pass<T, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
         g, a, rc, znbr, zold, zout, colour, nbr, omega, ctl);
     return cudaGetLastError();
   });
@@ -545,14 +632,16 @@ cudaError_t launch_sor_pass(const Grid& g, const Bands<T>& a, const T* rc, const
 template <typename T>
 cudaError_t launch_mv_rb(const Grid& g, const Bands<T>& a, const Vecs<T>& w, int mode, Ctl* ctl, Red red,
                          const Launch& L) {
-  return with_sor<T, 1>(L.vsor[sor_prec<T>()][1], [&](auto uc, auto bc) {
-    constexpr int U = decltype(uc)::value, B = decltype(bc)::value;
+  return with_sor<T, 1>(L.vsor[sor_prec<T>()][1], [&](auto vc, auto uc, auto bc) {
+    constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+    if ((g.nx / 2) % V) return cudaErrorInvalidValue;
+    const int64_t wb = rb_blocks(g, V);
     if (mode == 0)
-      k_mv_rb<T, 0, U, B><<<grid_for((const void*)k_mv_rb<T, 0, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w,
-                                                                                                            ctl, red);
+      k_mv_rb<T, 0, V, U, B><<<grid_for((const void*)k_mv_rb<T, 0, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+          g, a, w, ctl, red);
     else
-      k_mv_rb<T, 1, U, B><<<grid_for((const void*)k_mv_rb<T, 1, U, B>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w,
-                                                                                                            ctl, red);
+      k_mv_rb<T, 1, V, U, B><<<grid_for((const void*)k_mv_rb<T, 1, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+          g, a, w, ctl, red);
     return cudaGetLastError();
   });
 }
@@ -562,20 +651,22 @@ void warm_sor(const Launch& L) {
   grid_for((const void*)k_rb_copy<T, true>, kBS, L, 1);
   grid_for((const void*)k_rb_copy<T, false>, kBS, L, 1);
   for (int id = 0; id < SorVar<T>::NK[0]; ++id)
-    with_sor<T, 0>(id, [&](auto uc, auto bc) {
-      grid_for((const void*)k_sor_pass<T, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+    with_sor<T, 0>(id, [&](auto vc, auto uc, auto bc) {
+      grid_for((const void*)k_sor_pass<T, decltype(vc)::value, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
       return cudaSuccess;
     });
   for (int id = 0; id < SorVar<T>::NK[1]; ++id)
-    with_sor<T, 1>(id, [&](auto uc, auto bc) {
-      grid_for((const void*)k_mv_rb<T, 0, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
-      grid_for((const void*)k_mv_rb<T, 1, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+    with_sor<T, 1>(id, [&](auto vc, auto uc, auto bc) {
+      constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+      grid_for((const void*)k_mv_rb<T, 0, V, U, B>, kBS, L, 1);
+      grid_for((const void*)k_mv_rb<T, 1, V, U, B>, kBS, L, 1);
       return cudaSuccess;
     });
   for (int id = 0; id < SorVar<T>::NK[2]; ++id)
-    with_sor<T, 2>(id, [&](auto uc, auto bc) {
-      grid_for((const void*)k_sor_first<T, 0, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
-      grid_for((const void*)k_sor_first<T, 1, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+    with_sor<T, 2>(id, [&](auto vc, auto uc, auto bc) {
+      constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+      grid_for((const void*)k_sor_first<T, 0, V, U, B>, kBS, L, 1);
+      grid_for((const void*)k_sor_first<T, 1, V, U, B>, kBS, L, 1);
       return cudaSuccess;
     });
 }
@@ -585,9 +676,17 @@ int sor_num_variants(int prec, int kind) {
   return prec == 0 ? SorVar<float>::NK[kind] : SorVar<double>::NK[kind];
 }
 
-void sor_variant_shape(int prec, int kind, int id, int* depth, int* minb) {
+void sor_variant_shape(int prec, int kind, int id, int* vec, int* depth, int* minb) {
+  *vec = prec == 0 ? SorVar<float>::v[kind][id] : SorVar<double>::v[kind][id];
   *depth = prec == 0 ? SorVar<float>::u[kind][id] : SorVar<double>::u[kind][id];
   *minb = prec == 0 ? SorVar<float>::b[kind][id] : SorVar<double>::b[kind][id];
+}
+
+bool sor_variant_ok(int prec, int kind, int id, int nx) {
+  if (id < 0 || id >= sor_num_variants(prec, kind) || nx % 2) return false;
+  int v = 1, u = 1, b = 1;
+  sor_variant_shape(prec, kind, id, &v, &u, &b);
+  return (nx / 2) % v == 0;
 }
 
 #define HZ_SOR_INST(T)                                                                                               \

@@ -207,7 +207,7 @@ def test_every_pass_variant_gives_identical_columns(prec):
     import torch
 
     hz = _hz()
-    nx, ny, nz = 130, 65, 11
+    nx, ny, nz = 136, 65, 11  # nx/2 = 68: every vector width fits; ragged ny
     A = gen.make_operator(nx, ny, nz, seed=4, z_unit="m")
     op = hz.Operator(A)
     p = hz.HZ_PREC_FP64 if prec == "fp64" else hz.HZ_PREC_FP32
@@ -220,6 +220,25 @@ def test_every_pass_variant_gives_identical_columns(prec):
         op.trisor_apply(r, z, p, 3, 1.5)
         outs.append(host(z))
     assert len(outs) >= 3 and all(np.array_equal(outs[0], o) for o in outs[1:])
+    zo = oracle.apply_trisor(oracle.scale(A) if prec == "fp64" else oracle.scale(A).astype(np.float32).astype(np.float64),
+                             host(r).astype(np.float64).reshape(nz, ny, nx), 3, 1.5)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(outs[0].astype(np.float64).reshape(zo.shape) - zo)) <= tol * np.max(np.abs(zo))
+
+
+def test_variants_wider_than_the_row_are_rejected():
+    hz = _hz()
+    A = gen.make_operator(130, 9, 5, seed=4)  # nx/2 = 65: only one column per thread fits
+    op = hz.Operator(A)
+    for p in (hz.HZ_PREC_FP32, hz.HZ_PREC_FP64):
+        ok = []
+        for vid in range(hz.sor_variant_count(p, 0)):
+            try:
+                op.set_sor_variant(p, 0, vid)
+                ok.append(vid)
+            except hz.HzError as e:
+                assert e.status == hz.HZ_ERR_INVALID
+        assert 0 in ok and len(ok) < hz.sor_variant_count(p, 0)
 
 
 @pytest.mark.parametrize("mode", ["mixed", "fp64"])

@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned"])
+    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned", "nnfwd"])
     ap.add_argument("--train-systems", type=int, default=24)
     ap.add_argument("--test-systems", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=240)
@@ -478,6 +478,47 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+def run_nn_forward(args):
+    """Inference of the learned stage's conv net alone on one 640x480x70 field (random-init weights)."""
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+    from paper_1811_03852_gb300 import learn
+
+    torch.cuda.set_device(0)
+    dims = tuple(args.dims) if args.dims else (640, 480, 70)
+    n = dims[0] * dims[1] * dims[2]
+    net = hz.Net(learn.init_params(1))
+    x = torch.randn(n, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    for _ in range(max(1, args.warmup)):
+        net.forward(x, y, dims)
+    ts = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.forward(x, y, dims)  # returns after its stream is idle
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.median(ts))
+    flop = 2.0 * (432 + 6912 + 6912 + 432) * n  # multiply-adds of the four layers
+    nbytes = 200.0 * n  # x 4 + h1 32 + (32 + 32) x 2 + h3 32 + y 4 bytes per point
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    print(json.dumps({"workload": f"conv-net forward {dims[0]}x{dims[1]}x{dims[2]} (4 layers, 16 channels, 3x3x3)",
+                      "ms_per_forward": round(ms, 3), "TFLOPs": round(flop / (ms * 1e-3) / 1e12, 2),
+                      "frac_of_bf16_peak": round(flop / (ms * 1e-3) / 1e12 / bf16, 4),
+                      "GBps_algorithmic": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                      "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4),
+                      "roofline_ms": round(max(flop / (bf16 * 1e12), nbytes / (hbm * 1e9)) * 1e3, 3),
+                      "note": "wall clock per call (the call waits for its stream), median of steps"}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -486,6 +527,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "nnfwd":
+        run_nn_forward(args)
     else:
         run_ours(args)
 

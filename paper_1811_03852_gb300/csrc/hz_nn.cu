@@ -217,6 +217,299 @@ __global__ void __launch_bounds__(256) k_nn_l4(NnGrid g, const __nv_bfloat16* __
   }
 }
 
+// ---- plane-tiled forward kernels ----------------------------------------------
+// A block owns a kTI x kTJ tile of columns (i, j) and marches k.  A ring of
+// four shared-memory planes holds the input at levels k-1, k, k+1 (with a
+// one-point halo in i and j) while cp.async fetches level k+2, so every tap
+// of the 3x3x3 stencil is read from shared memory and each input value
+// leaves HBM once per tile.  Halo points outside the domain, across a crop
+// seam (every seg rows) or past the periodic wrap are zero-filled by the copy.
+// Used when no tile straddles a crop seam (seg a multiple of kTJ, or one
+// segment); the gather kernels above handle the rest.
+constexpr int kTI = 32, kTJ = 4;
+constexpr int kPI = kTI + 2, kPJ = kTJ + 2, kPP = kPI * kPJ;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+struct TileGeo {
+  int i0, j0;
+  bool jlo_zero, jhi_zero;  // the halo row above / below lies across a crop seam
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const NnGrid& g, int64_t tile, int tiles_i) {
+  TileGeo t;
+  t.i0 = (int)(tile % tiles_i) * kTI;
+  t.j0 = (int)(tile / tiles_i) * kTJ;
+  t.jlo_zero = (t.j0 % g.seg) == 0;
+  t.jhi_zero = ((t.j0 + kTJ) % g.seg) == 0;
+  return t;
+}
+
+// source point of plane position (ti, tj) at level k, or -1 for a zero
+__device__ __forceinline__ int64_t plane_src(const NnGrid& g, const TileGeo& t, int k, int ti, int tj) {
+  if (k < 0 || k >= g.nz) return -1;
+  if ((tj == 0 && t.jlo_zero) || (tj == kPJ - 1 && t.jhi_zero)) return -1;
+  const int gj = t.j0 - 1 + tj;
+  if (gj < 0 || gj >= g.ny) return -1;
+  int gi = t.i0 - 1 + ti;
+  if (gi < 0) {
+    if (!g.periodic) return -1;
+    gi += g.nx;
+  } else if (gi >= g.nx) {
+    if (!g.periodic) return -1;
+    gi -= g.nx;
+  }
+  if (gi < 0 || gi >= g.nx) return -1;
+  return ((int64_t)k * g.ny + gj) * g.nx + gi;
+}
+
+// 16-channel BF16 planes: point pp holds two 16-byte chunks (channels 0-7,
+// 8-15), chunk h stored at slot h ^ ((pp >> 2) & 1) so that the eight rows of
+// an ldmatrix (eight consecutive points) fall in distinct banks.
+__device__ __forceinline__ void load_plane16(uint4 (*pl)[2], const __nv_bfloat16* __restrict__ h, const NnGrid& g,
+                                             const TileGeo& t, int k) {
+  for (int q = threadIdx.x; q < 2 * kPP; q += blockDim.x) {
+    const int pp = q >> 1, hh = q & 1;
+    const int64_t src = plane_src(g, t, k, pp % kPI, pp / kPI);
+    cp_async16(&pl[pp][hh ^ ((pp >> 2) & 1)], src >= 0 ? (const void*)(h + src * kC + hh * 8) : (const void*)h,
+               src >= 0 ? 16 : 0);
+  }
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+
+// A fragment (16 points x 16 channels) of output row w, points i = 16*mt ..
+// 16*mt+15 of the tile, shifted by tap (dj, di), from plane pl.
+__device__ __forceinline__ void load_a(uint32_t (&a)[4], uint4 (*pl)[2], int w, int mt, int dj, int di, int lane) {
+  const int mi = lane >> 3, r = lane & 7;
+  const int pp = (w + 1 + dj) * kPI + (16 * mt + (mi & 1) * 8 + r + 1 + di);
+  ldmatrix_x4(a, &pl[pp][(mi >> 1) ^ ((pp >> 2) & 1)]);
+}
+
+// layer 1 on planes: x (FP32, one channel) -> z1 (optional), h1 = gelu(z1).
+// Same arithmetic order as k_nn_l1 (taps 0..26, one FMA each).
+__global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __restrict__ x, const double* scale_nrm2,
+                                                    NnW w, float* __restrict__ z, __nv_bfloat16* __restrict__ h) {
+  __shared__ float W[kTaps * kC + kC];
+  __shared__ float pl[4][kPP];
+  for (int q = threadIdx.x; q < kTaps * kC; q += blockDim.x) W[q] = w.w1[q];
+  for (int q = threadIdx.x; q < kC; q += blockDim.x) W[kTaps * kC + q] = w.b1[q];
+  float s = 1.f;
+  if (scale_nrm2) {
+    const double v = *scale_nrm2;
+    s = v > 0.0 ? (float)(1.0 / sqrt(v / (double)g.n)) : 0.f;
+  }
+  const int tiles_i = (g.nx + kTI - 1) / kTI;
+  const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
+  const int ti = threadIdx.x % kTI, tj = threadIdx.x / kTI;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const TileGeo t = tile_geo(g, tile, tiles_i);
+    auto load = [&](int k) {
+      for (int q = threadIdx.x; q < kPP; q += blockDim.x) {
+        const int64_t src = plane_src(g, t, k, q % kPI, q / kPI);
+        cp_async4(&pl[k & 3][q], src >= 0 ? (const void*)(x + src) : (const void*)x, src >= 0 ? 4 : 0);
+      }
+    };
+    __syncthreads();  // previous tile's readers are done
+    load(0);
+    if (g.nz > 1) load(1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int gi = t.i0 + ti, gj = t.j0 + tj;
+    const bool valid = gi < g.nx && gj < g.ny;
+    for (int k = 0; k < g.nz; ++k) {
+      if (k + 2 < g.nz) load(k + 2);
+      cp_async_commit();
+      float acc[kC];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) acc[c] = W[kTaps * kC + c];
+      for (int tp = 0; tp < kTaps; ++tp) {
+        const int dk = tp / 9 - 1, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
+        const int kk = k + dk;
+        const float xv = (kk >= 0 && kk < g.nz) ? s * pl[kk & 3][(tj + 1 + dj) * kPI + ti + 1 + di] : 0.f;
+#pragma unroll
+        for (int c = 0; c < kC; ++c) acc[c] = fmaf(W[tp * kC + c], xv, acc[c]);
+      }
+      if (valid) {
+        const int64_t p = ((int64_t)k * g.ny + gj) * g.nx + gi;
+        if (z) {
+#pragma unroll
+          for (int c = 0; c < kC; c += 4)
+            *reinterpret_cast<float4*>(z + p * kC + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+        }
+        __align__(16) __nv_bfloat16 hv[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) hv[c] = __float2bfloat16_rn(gelu_f(acc[c]));
+        reinterpret_cast<uint4*>(h + p * kC)[0] = reinterpret_cast<const uint4*>(hv)[0];
+        reinterpret_cast<uint4*>(h + p * kC)[1] = reinterpret_cast<const uint4*>(hv)[1];
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+}
+
+// layers 2, 3 on planes: 16 -> 16 on the tensor cores.  Warp w computes output
+// row w of the tile (two 16-point m-tiles, both 8-channel n-halves); per tap
+// one ldmatrix per m-tile and one m16n8k16 MMA per (m-tile, n-half).
+__global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bfloat16* __restrict__ hin,
+                                                     const __nv_bfloat16* __restrict__ wb,
+                                                     const float* __restrict__ bias, float* __restrict__ z,
+                                                     __nv_bfloat16* __restrict__ hout) {
+  __shared__ __align__(128) uint4 pl[4][kPP][2];
+  __shared__ uint32_t Ws[kTaps * kC * kC / 2];  // [tap][co][ci pair]
+  __shared__ float Bs[kC];
+  for (int q = threadIdx.x; q < kTaps * kC * kC / 2; q += blockDim.x) Ws[q] = reinterpret_cast<const uint32_t*>(wb)[q];
+  for (int q = threadIdx.x; q < kC; q += blockDim.x) Bs[q] = bias[q];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
+  const int tiles_i = (g.nx + kTI - 1) / kTI;
+  const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const TileGeo t = tile_geo(g, tile, tiles_i);
+    __syncthreads();
+    load_plane16(pl[0], hin, g, t, 0);
+    if (g.nz > 1) load_plane16(pl[1], hin, g, t, 1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int gj = t.j0 + w;
+    for (int k = 0; k < g.nz; ++k) {
+      if (k + 2 < g.nz) load_plane16(pl[(k + 2) & 3], hin, g, t, k + 2);
+      cp_async_commit();
+      float d[2][2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        d[mt][0][0] = d[mt][0][2] = Bs[2 * cq];
+        d[mt][0][1] = d[mt][0][3] = Bs[2 * cq + 1];
+        d[mt][1][0] = d[mt][1][2] = Bs[8 + 2 * cq];
+        d[mt][1][1] = d[mt][1][3] = Bs[8 + 2 * cq + 1];
+      }
+      for (int tp = 0; tp < kTaps; ++tp) {
+        const int dk = tp / 9 - 1, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
+        const int kk = k + dk;
+        if (kk < 0 || kk >= g.nz) continue;  // zero plane: contributes nothing
+        const uint32_t* wt = Ws + tp * (kC * kC / 2);
+        const uint32_t b00 = wt[gq * (kC / 2) + cq], b01 = wt[gq * (kC / 2) + 4 + cq];
+        const uint32_t b10 = wt[(gq + 8) * (kC / 2) + cq], b11 = wt[(gq + 8) * (kC / 2) + 4 + cq];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          uint32_t a[4];
+          load_a(a, pl[kk & 3], w, mt, dj, di, lane);
+          mma_bf16_16816(d[mt][0], a, b00, b01);
+          mma_bf16_16816(d[mt][1], a, b10, b11);
+        }
+      }
+      if (gj < g.ny) {
+        const int64_t prow = ((int64_t)k * g.ny + gj) * g.nx;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {  // points gq (d[.][.][0..1]) and gq + 8 (d[.][.][2..3])
+            const int gi = t.i0 + 16 * mt + gq + 8 * hf;
+            if (gi >= g.nx) continue;
+            const int64_t p = prow + gi;
+            const float* v0 = &d[mt][0][2 * hf];
+            const float* v1 = &d[mt][1][2 * hf];
+            if (z) {
+              *reinterpret_cast<float2*>(z + p * kC + 2 * cq) = make_float2(v0[0], v0[1]);
+              *reinterpret_cast<float2*>(z + p * kC + 8 + 2 * cq) = make_float2(v1[0], v1[1]);
+            }
+            reinterpret_cast<__nv_bfloat162*>(hout + p * kC + 2 * cq)[0] =
+                __floats2bfloat162_rn(gelu_f(v0[0]), gelu_f(v0[1]));
+            reinterpret_cast<__nv_bfloat162*>(hout + p * kC + 8 + 2 * cq)[0] =
+                __floats2bfloat162_rn(gelu_f(v1[0]), gelu_f(v1[1]));
+          }
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+}
+
+// layer 4 on planes: 16 -> 1 as an m16n8k16 MMA whose B has one live column
+// (output channel 0 = W4[tap][ci]).  out = y, or out = base + sigma * y.
+__global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloat16* __restrict__ hin, NnW w,
+                                                    const float* base, const double* nrm2, float* out) {
+  __shared__ __align__(128) uint4 pl[4][kPP][2];
+  __shared__ uint32_t W4[kTaps * kC / 2];  // [tap][ci pair], BF16 (the values are BF16-rounded already)
+  __shared__ float B4;
+  for (int q = threadIdx.x; q < kTaps * kC / 2; q += blockDim.x) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(w.w4[2 * q], w.w4[2 * q + 1]);
+    W4[q] = *reinterpret_cast<const uint32_t*>(&v);
+  }
+  if (threadIdx.x == 0) B4 = w.b4[0];
+  float sigma = 1.f;
+  if (nrm2) {
+    const double v = *nrm2;
+    sigma = (float)sqrt(v / (double)g.n);
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
+  const int tiles_i = (g.nx + kTI - 1) / kTI;
+  const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const TileGeo t = tile_geo(g, tile, tiles_i);
+    __syncthreads();
+    load_plane16(pl[0], hin, g, t, 0);
+    if (g.nz > 1) load_plane16(pl[1], hin, g, t, 1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int gj = t.j0 + wp;
+    for (int k = 0; k < g.nz; ++k) {
+      if (k + 2 < g.nz) load_plane16(pl[(k + 2) & 3], hin, g, t, k + 2);
+      cp_async_commit();
+      float d[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) d[mt][0] = d[mt][1] = d[mt][2] = d[mt][3] = B4;
+      for (int tp = 0; tp < kTaps; ++tp) {
+        const int dk = tp / 9 - 1, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
+        const int kk = k + dk;
+        if (kk < 0 || kk >= g.nz) continue;
+        const uint32_t b0 = gq == 0 ? W4[tp * (kC / 2) + cq] : 0u;
+        const uint32_t b1 = gq == 0 ? W4[tp * (kC / 2) + 4 + cq] : 0u;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          uint32_t a[4];
+          load_a(a, pl[kk & 3], wp, mt, dj, di, lane);
+          mma_bf16_16816(d[mt], a, b0, b1);
+        }
+      }
+      if (cq == 0 && gj < g.ny) {  // column 0 of D: points gq (d[.][0]) and gq + 8 (d[.][2])
+        const int64_t prow = ((int64_t)k * g.ny + gj) * g.nx;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {
+            const int gi = t.i0 + 16 * mt + gq + 8 * hf;
+            if (gi >= g.nx) continue;
+            const int64_t p = prow + gi;
+            const float y = d[mt][2 * hf];
+            out[p] = base ? fmaf(sigma, y, base[p]) : y;
+          }
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+}
+
 // ---- backward (FP32 on the CUDA cores) ---------------------------------------
 // dz3[p][ci] = gelu'(z3[p][ci]) * sum_t W4[t][ci] dy[p - t]   (adjoint of layer 4)
 __global__ void __launch_bounds__(256) k_nn_b4(NnGrid g, const float* __restrict__ dy, NnW w,
@@ -622,6 +915,16 @@ static int nn_forward(hz_nn_s* nn, const NnGrid& g, const float* x, const double
   const NnW w = nn_w(d);
   cudaStream_t s = nn->stream;
   __nv_bfloat16* h3 = train ? d.h3 : d.h1;
+  if (g.seg == g.ny || g.seg % kTJ == 0) {  // plane-tiled kernels: no tile straddles a crop seam
+    const int64_t tiles = (int64_t)((g.nx + kTI - 1) / kTI) * ((g.ny + kTJ - 1) / kTJ);
+    const int gt = (int)std::min<int64_t>(tiles, (int64_t)nn->sms * 4);
+    k_nn_l1t<<<gt, kTI * kTJ, 0, s>>>(g, x, scale_nrm2, w, train ? d.z1 : nullptr, d.h1);
+    k_nn_midt<<<gt, kTI * kTJ, 0, s>>>(g, d.h1, d.w2b, d.b2, train ? d.z2 : nullptr, d.h2);
+    k_nn_midt<<<gt, kTI * kTJ, 0, s>>>(g, d.h2, d.w3b, d.b3, train ? d.z3 : nullptr, h3);
+    k_nn_l4t<<<gt, kTI * kTJ, 0, s>>>(g, h3, w, base, base ? scale_nrm2 : nullptr, out);
+    NN_CK(cudaGetLastError());
+    return HZ_OK;
+  }
   k_nn_l1<<<nn_grid(nn, g.n, 256), 256, 0, s>>>(g, x, scale_nrm2, 1.f, w, train ? d.z1 : nullptr, d.h1);
   const int64_t tiles = (int64_t)((g.nx + 15) / 16) * g.ny * g.nz;
   const int gm = (int)std::min<int64_t>((tiles + 3) / 4, (int64_t)nn->sms * 16);

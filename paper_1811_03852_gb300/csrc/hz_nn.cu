@@ -272,39 +272,42 @@ __device__ __forceinline__ int64_t plane_src(const NnGrid& g, const TileGeo& t, 
   return ((int64_t)k * g.ny + gj) * g.nx + gi;
 }
 
-// 16-channel BF16 planes: point pp holds two 16-byte chunks (channels 0-7,
-// 8-15), chunk h stored at slot h ^ ((pp >> 2) & 1) so that the eight rows of
-// an ldmatrix (eight consecutive points) fall in distinct banks.
-__device__ __forceinline__ void load_plane16(uint4 (*pl)[2], const __nv_bfloat16* __restrict__ h, const NnGrid& g,
+// 16-channel BF16 planes, one 16-byte chunk per point and half (channels 0-7
+// in pl[0], 8-15 in pl[1]): the eight rows of an ldmatrix (eight consecutive
+// points of one half) are 128 contiguous bytes, so they hit distinct banks.
+__device__ __forceinline__ void load_plane16(uint4 (*pl)[kPP], const __nv_bfloat16* __restrict__ h, const NnGrid& g,
                                              const TileGeo& t, int k) {
   for (int q = threadIdx.x; q < 2 * kPP; q += blockDim.x) {
     const int pp = q >> 1, hh = q & 1;
     const int64_t src = plane_src(g, t, k, pp % kPI, pp / kPI);
-    cp_async16(&pl[pp][hh ^ ((pp >> 2) & 1)], src >= 0 ? (const void*)(h + src * kC + hh * 8) : (const void*)h,
-               src >= 0 ? 16 : 0);
+    cp_async16(&pl[hh][pp], src >= 0 ? (const void*)(h + src * kC + hh * 8) : (const void*)h, src >= 0 ? 16 : 0);
   }
 }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], unsigned saddr) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(s));
+               : "r"(saddr));
 }
 
-// A fragment (16 points x 16 channels) of output row w, points i = 16*mt ..
-// 16*mt+15 of the tile, shifted by tap (dj, di), from plane pl.
-__device__ __forceinline__ void load_a(uint32_t (&a)[4], uint4 (*pl)[2], int w, int mt, int dj, int di, int lane) {
+// Shared-memory address of this lane's ldmatrix row for the A fragment (16
+// points x 16 channels) of output row w, points 16*mt .. 16*mt+15 of the tile,
+// unshifted: tap (dj, di) adds (dj * kPI + di) * 16 bytes.
+__device__ __forceinline__ unsigned a_row_addr(uint4 (*pl)[kPP], int w, int mt, int lane) {
   const int mi = lane >> 3, r = lane & 7;
-  const int pp = (w + 1 + dj) * kPI + (16 * mt + (mi & 1) * 8 + r + 1 + di);
-  ldmatrix_x4(a, &pl[pp][(mi >> 1) ^ ((pp >> 2) & 1)]);
+  const int pp = (w + 1) * kPI + 16 * mt + (mi & 1) * 8 + r + 1;
+  return (unsigned)__cvta_generic_to_shared(&pl[mi >> 1][pp]);
+}
+constexpr unsigned kSlotBytes = 2 * kPP * 16;  // one ring slot: both halves of a plane
+__device__ __forceinline__ constexpr int tap_off(int tp) {
+  return (((tp / 3) % 3 - 1) * kPI + (tp % 3 - 1)) * 16;
 }
 
 // layer 1 on planes: x (FP32, one channel) -> z1 (optional), h1 = gelu(z1).
 // Same arithmetic order as k_nn_l1 (taps 0..26, one FMA each).
 __global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __restrict__ x, const double* scale_nrm2,
                                                     NnW w, float* __restrict__ z, __nv_bfloat16* __restrict__ h) {
-  __shared__ float W[kTaps * kC + kC];
+  __shared__ __align__(16) float W[kTaps * kC + kC];
   __shared__ float pl[4][kPP];
   for (int q = threadIdx.x; q < kTaps * kC; q += blockDim.x) W[q] = w.w1[q];
   for (int q = threadIdx.x; q < kC; q += blockDim.x) W[kTaps * kC + q] = w.b1[q];
@@ -338,12 +341,21 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __r
       float acc[kC];
 #pragma unroll
       for (int c = 0; c < kC; ++c) acc[c] = W[kTaps * kC + c];
-      for (int tp = 0; tp < kTaps; ++tp) {
-        const int dk = tp / 9 - 1, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
-        const int kk = k + dk;
-        const float xv = (kk >= 0 && kk < g.nz) ? s * pl[kk & 3][(tj + 1 + dj) * kPI + ti + 1 + di] : 0.f;
+      const float* sp[3] = {pl[(k + 3) & 3], pl[k & 3], pl[(k + 1) & 3]};
+      const bool has[3] = {k > 0, true, k + 1 < g.nz};
+      const int me = (tj + 1) * kPI + ti + 1;
 #pragma unroll
-        for (int c = 0; c < kC; ++c) acc[c] = fmaf(W[tp * kC + c], xv, acc[c]);
+      for (int tp = 0; tp < kTaps; ++tp) {
+        const int dk = tp / 9, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
+        const float xv = has[dk] ? s * sp[dk][me + dj * kPI + di] : 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < kC / 4; ++c4) {
+          const float4 wv = reinterpret_cast<const float4*>(W)[tp * (kC / 4) + c4];
+          acc[4 * c4 + 0] = fmaf(wv.x, xv, acc[4 * c4 + 0]);
+          acc[4 * c4 + 1] = fmaf(wv.y, xv, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(wv.z, xv, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(wv.w, xv, acc[4 * c4 + 3]);
+        }
       }
       if (valid) {
         const int64_t p = ((int64_t)k * g.ny + gj) * g.nx + gi;
@@ -371,12 +383,14 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
                                                      const __nv_bfloat16* __restrict__ wb,
                                                      const float* __restrict__ bias, float* __restrict__ z,
                                                      __nv_bfloat16* __restrict__ hout) {
-  __shared__ __align__(128) uint4 pl[4][kPP][2];
+  __shared__ __align__(128) uint4 pl[4][2][kPP];
   __shared__ uint32_t Ws[kTaps * kC * kC / 2];  // [tap][co][ci pair]
   __shared__ float Bs[kC];
   for (int q = threadIdx.x; q < kTaps * kC * kC / 2; q += blockDim.x) Ws[q] = reinterpret_cast<const uint32_t*>(wb)[q];
   for (int q = threadIdx.x; q < kC; q += blockDim.x) Bs[q] = bias[q];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
+  const uint32_t* wl = Ws + gq * (kC / 2) + cq;  // this lane's B pairs: + tap * 128 (+4 high ci, +64 co + 8)
+  const unsigned arow[2] = {a_row_addr(pl[0], w, 0, lane), a_row_addr(pl[0], w, 1, lane)};
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -399,17 +413,18 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
         d[mt][1][0] = d[mt][1][2] = Bs[8 + 2 * cq];
         d[mt][1][1] = d[mt][1][3] = Bs[8 + 2 * cq + 1];
       }
+      // planes of levels k-1, k, k+1 (a missing level contributes nothing)
+      const unsigned sl[3] = {((k + 3) & 3) * kSlotBytes, (k & 3) * kSlotBytes, ((k + 1) & 3) * kSlotBytes};
+      const bool has[3] = {k > 0, true, k + 1 < g.nz};
+#pragma unroll
       for (int tp = 0; tp < kTaps; ++tp) {
-        const int dk = tp / 9 - 1, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
-        const int kk = k + dk;
-        if (kk < 0 || kk >= g.nz) continue;  // zero plane: contributes nothing
-        const uint32_t* wt = Ws + tp * (kC * kC / 2);
-        const uint32_t b00 = wt[gq * (kC / 2) + cq], b01 = wt[gq * (kC / 2) + 4 + cq];
-        const uint32_t b10 = wt[(gq + 8) * (kC / 2) + cq], b11 = wt[(gq + 8) * (kC / 2) + 4 + cq];
+        const int dk = tp / 9;
+        if (!has[dk]) continue;
+        const uint32_t b00 = wl[tp * 128], b01 = wl[tp * 128 + 4], b10 = wl[tp * 128 + 64], b11 = wl[tp * 128 + 68];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
           uint32_t a[4];
-          load_a(a, pl[kk & 3], w, mt, dj, di, lane);
+          ldmatrix_x4(a, arow[mt] + sl[dk] + tap_off(tp));
           mma_bf16_16816(d[mt][0], a, b00, b01);
           mma_bf16_16816(d[mt][1], a, b10, b11);
         }
@@ -446,7 +461,7 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
 // (output channel 0 = W4[tap][ci]).  out = y, or out = base + sigma * y.
 __global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloat16* __restrict__ hin, NnW w,
                                                     const float* base, const double* nrm2, float* out) {
-  __shared__ __align__(128) uint4 pl[4][kPP][2];
+  __shared__ __align__(128) uint4 pl[4][2][kPP];
   __shared__ uint32_t W4[kTaps * kC / 2];  // [tap][ci pair], BF16 (the values are BF16-rounded already)
   __shared__ float B4;
   for (int q = threadIdx.x; q < kTaps * kC / 2; q += blockDim.x) {
@@ -460,6 +475,7 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloa
     sigma = (float)sqrt(v / (double)g.n);
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
+  const unsigned arow[2] = {a_row_addr(pl[0], wp, 0, lane), a_row_addr(pl[0], wp, 1, lane)};
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -477,16 +493,18 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloa
       float d[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) d[mt][0] = d[mt][1] = d[mt][2] = d[mt][3] = B4;
+      const unsigned sl[3] = {((k + 3) & 3) * kSlotBytes, (k & 3) * kSlotBytes, ((k + 1) & 3) * kSlotBytes};
+      const bool has[3] = {k > 0, true, k + 1 < g.nz};
+#pragma unroll
       for (int tp = 0; tp < kTaps; ++tp) {
-        const int dk = tp / 9 - 1, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
-        const int kk = k + dk;
-        if (kk < 0 || kk >= g.nz) continue;
+        const int dk = tp / 9;
+        if (!has[dk]) continue;
         const uint32_t b0 = gq == 0 ? W4[tp * (kC / 2) + cq] : 0u;
         const uint32_t b1 = gq == 0 ? W4[tp * (kC / 2) + 4 + cq] : 0u;
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
           uint32_t a[4];
-          load_a(a, pl[kk & 3], wp, mt, dj, di, lane);
+          ldmatrix_x4(a, arow[mt] + sl[dk] + tap_off(tp));
           mma_bf16_16816(d[mt], a, b0, b1);
         }
       }

@@ -272,18 +272,10 @@ __device__ __forceinline__ int64_t plane_src(const NnGrid& g, const TileGeo& t, 
   return ((int64_t)k * g.ny + gj) * g.nx + gi;
 }
 
-// 16-channel BF16 planes, one 16-byte chunk per point and half (channels 0-7
-// in pl[0], 8-15 in pl[1]): the eight rows of an ldmatrix (eight consecutive
-// points of one half) are 128 contiguous bytes, so they hit distinct banks.
-__device__ __forceinline__ void load_plane16(uint4 (*pl)[kPP], const __nv_bfloat16* __restrict__ h, const NnGrid& g,
-                                             const TileGeo& t, int k) {
-  for (int q = threadIdx.x; q < 2 * kPP; q += blockDim.x) {
-    const int pp = q >> 1, hh = q & 1;
-    const int64_t src = plane_src(g, t, k, pp % kPI, pp / kPI);
-    cp_async16(&pl[hh][pp], src >= 0 ? (const void*)(h + src * kC + hh * 8) : (const void*)h, src >= 0 ? 16 : 0);
-  }
-}
-
+// 16-channel BF16 planes hold one 16-byte chunk per point and half
+// (channels 0-7 in [0], 8-15 in [1]): the eight rows of an ldmatrix (eight
+// consecutive points of one half) are 128 contiguous bytes, so they hit
+// distinct banks.
 __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], unsigned saddr) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -303,12 +295,58 @@ __device__ __forceinline__ constexpr int tap_off(int tp) {
   return (((tp / 3) % 3 - 1) * kPI + (tp % 3 - 1)) * 16;
 }
 
+// Per-thread copy list of one tile's plane: the chunks this thread copies
+// (point pp, half h), as the source element offset within one level (-1: zero
+// fill) and the destination byte offset within a ring slot.  Built once per
+// tile; a level adds k * ny * nx.
+template <int NCH, int BYTES>
+struct PlaneCopy {
+  static constexpr int kMax = (NCH * kPP + kTI * kTJ - 1) / (kTI * kTJ);
+  int64_t src[kMax];
+  unsigned dst[kMax];
+  __device__ __forceinline__ void init(const NnGrid& g, const TileGeo& t) {
+#pragma unroll
+    for (int m = 0; m < kMax; ++m) {
+      const int q = threadIdx.x + m * kTI * kTJ;
+      src[m] = -2;
+      if (q < NCH * kPP) {
+        const int pp = q / NCH, hh = q % NCH;
+        const int64_t s = plane_src(g, t, 0, pp % kPI, pp / kPI);
+        src[m] = s >= 0 ? s * (NCH * BYTES / (NCH == 2 ? 2 : 4)) + hh * 8 : -1;
+        dst[m] = (unsigned)((hh * kPP + pp) * BYTES);
+      }
+    }
+  }
+  // elements: bf16 units for NCH = 2 (16 channels, 16-byte chunks), float units for NCH = 1
+  template <typename E>
+  __device__ __forceinline__ void issue(unsigned slot, const E* base, int64_t kofs) const {
+#pragma unroll
+    for (int m = 0; m < kMax; ++m) {
+      if (src[m] == -2) continue;
+      const bool ok = src[m] >= 0;
+      const void* gp = ok ? (const void*)(base + kofs + src[m]) : (const void*)base;
+      if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(slot + dst[m]), "l"(gp), "r"(ok ? 16 : 0)
+                     : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(slot + dst[m]), "l"(gp), "r"(ok ? 4 : 0)
+                     : "memory");
+    }
+  }
+};
+
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// The ring: kRing slots; output level k reads levels k-1, k, k+1 while the
+// copies of k+2 (issued one level earlier) land and those of k+3 start.
+constexpr int kRing = 5;
+
 // layer 1 on planes: x (FP32, one channel) -> z1 (optional), h1 = gelu(z1).
 // Same arithmetic order as k_nn_l1 (taps 0..26, one FMA each).
 __global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __restrict__ x, const double* scale_nrm2,
                                                     NnW w, float* __restrict__ z, __nv_bfloat16* __restrict__ h) {
   __shared__ __align__(16) float W[kTaps * kC + kC];
-  __shared__ float pl[4][kPP];
+  __shared__ __align__(16) float pl[kRing][kPP];
   for (int q = threadIdx.x; q < kTaps * kC; q += blockDim.x) W[q] = w.w1[q];
   for (int q = threadIdx.x; q < kC; q += blockDim.x) W[kTaps * kC + q] = w.b1[q];
   float s = 1.f;
@@ -319,31 +357,31 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __r
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
   const int ti = threadIdx.x % kTI, tj = threadIdx.x / kTI;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(&pl[0][0]);
+  constexpr unsigned kSlot = kPP * 4;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const TileGeo t = tile_geo(g, tile, tiles_i);
-    auto load = [&](int k) {
-      for (int q = threadIdx.x; q < kPP; q += blockDim.x) {
-        const int64_t src = plane_src(g, t, k, q % kPI, q / kPI);
-        cp_async4(&pl[k & 3][q], src >= 0 ? (const void*)(x + src) : (const void*)x, src >= 0 ? 4 : 0);
-      }
-    };
+    PlaneCopy<1, 4> pc;
+    pc.init(g, t);
     __syncthreads();  // previous tile's readers are done
-    load(0);
-    if (g.nz > 1) load(1);
-    cp_async_commit();
-    cp_async_wait_all();
+    for (int kq = 0; kq < 3; ++kq) {
+      if (kq < g.nz) pc.issue(sbase + kq * kSlot, x, kq * plane);
+      cp_async_commit();
+    }
+    cp_async_wait_one();  // levels 0 and 1 landed
     __syncthreads();
     const int gi = t.i0 + ti, gj = t.j0 + tj;
     const bool valid = gi < g.nx && gj < g.ny;
+    const int me = (tj + 1) * kPI + ti + 1;
     for (int k = 0; k < g.nz; ++k) {
-      if (k + 2 < g.nz) load(k + 2);
+      if (k + 3 < g.nz) pc.issue(sbase + ((k + 3) % kRing) * kSlot, x, (int64_t)(k + 3) * plane);
       cp_async_commit();
+      const float* sp[3] = {pl[(k + kRing - 1) % kRing], pl[k % kRing], pl[(k + 1) % kRing]};
+      const bool has[3] = {k > 0, true, k + 1 < g.nz};
       float acc[kC];
 #pragma unroll
       for (int c = 0; c < kC; ++c) acc[c] = W[kTaps * kC + c];
-      const float* sp[3] = {pl[(k + 3) & 3], pl[k & 3], pl[(k + 1) & 3]};
-      const bool has[3] = {k > 0, true, k + 1 < g.nz};
-      const int me = (tj + 1) * kPI + ti + 1;
 #pragma unroll
       for (int tp = 0; tp < kTaps; ++tp) {
         const int dk = tp / 9, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
@@ -358,7 +396,7 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __r
         }
       }
       if (valid) {
-        const int64_t p = ((int64_t)k * g.ny + gj) * g.nx + gi;
+        const int64_t p = (int64_t)k * plane + (int64_t)gj * g.nx + gi;
         if (z) {
 #pragma unroll
           for (int c = 0; c < kC; c += 4)
@@ -370,10 +408,11 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l1t(NnGrid g, const float* __r
         reinterpret_cast<uint4*>(h + p * kC)[0] = reinterpret_cast<const uint4*>(hv)[0];
         reinterpret_cast<uint4*>(h + p * kC)[1] = reinterpret_cast<const uint4*>(hv)[1];
       }
-      cp_async_wait_all();
+      cp_async_wait_one();  // level k+2 landed (k+3 may still be in flight)
       __syncthreads();
     }
   }
+  cp_async_wait_all();
 }
 
 // layers 2, 3 on planes: 16 -> 16 on the tensor cores.  Warp w computes output
@@ -383,7 +422,7 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
                                                      const __nv_bfloat16* __restrict__ wb,
                                                      const float* __restrict__ bias, float* __restrict__ z,
                                                      __nv_bfloat16* __restrict__ hout) {
-  __shared__ __align__(128) uint4 pl[4][2][kPP];
+  __shared__ __align__(128) uint4 pl[kRing][2][kPP];
   __shared__ uint32_t Ws[kTaps * kC * kC / 2];  // [tap][co][ci pair]
   __shared__ float Bs[kC];
   for (int q = threadIdx.x; q < kTaps * kC * kC / 2; q += blockDim.x) Ws[q] = reinterpret_cast<const uint32_t*>(wb)[q];
@@ -391,19 +430,24 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
   const uint32_t* wl = Ws + gq * (kC / 2) + cq;  // this lane's B pairs: + tap * 128 (+4 high ci, +64 co + 8)
   const unsigned arow[2] = {a_row_addr(pl[0], w, 0, lane), a_row_addr(pl[0], w, 1, lane)};
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(&pl[0][0][0]);
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
+  const int64_t plane = (int64_t)g.nx * g.ny * kC;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const TileGeo t = tile_geo(g, tile, tiles_i);
+    PlaneCopy<2, 16> pc;
+    pc.init(g, t);
     __syncthreads();
-    load_plane16(pl[0], hin, g, t, 0);
-    if (g.nz > 1) load_plane16(pl[1], hin, g, t, 1);
-    cp_async_commit();
-    cp_async_wait_all();
+    for (int kq = 0; kq < 3; ++kq) {
+      if (kq < g.nz) pc.issue(sbase + kq * kSlotBytes, hin, kq * plane);
+      cp_async_commit();
+    }
+    cp_async_wait_one();
     __syncthreads();
     const int gj = t.j0 + w;
     for (int k = 0; k < g.nz; ++k) {
-      if (k + 2 < g.nz) load_plane16(pl[(k + 2) & 3], hin, g, t, k + 2);
+      if (k + 3 < g.nz) pc.issue(sbase + ((k + 3) % kRing) * kSlotBytes, hin, (int64_t)(k + 3) * plane);
       cp_async_commit();
       float d[2][2][4];
 #pragma unroll
@@ -414,7 +458,8 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
         d[mt][1][1] = d[mt][1][3] = Bs[8 + 2 * cq + 1];
       }
       // planes of levels k-1, k, k+1 (a missing level contributes nothing)
-      const unsigned sl[3] = {((k + 3) & 3) * kSlotBytes, (k & 3) * kSlotBytes, ((k + 1) & 3) * kSlotBytes};
+      const unsigned sl[3] = {((k + kRing - 1) % kRing) * kSlotBytes, (k % kRing) * kSlotBytes,
+                              ((k + 1) % kRing) * kSlotBytes};
       const bool has[3] = {k > 0, true, k + 1 < g.nz};
 #pragma unroll
       for (int tp = 0; tp < kTaps; ++tp) {
@@ -451,17 +496,18 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_midt(NnGrid g, const __nv_bflo
           }
         }
       }
-      cp_async_wait_all();
+      cp_async_wait_one();
       __syncthreads();
     }
   }
+  cp_async_wait_all();
 }
 
 // layer 4 on planes: 16 -> 1 as an m16n8k16 MMA whose B has one live column
 // (output channel 0 = W4[tap][ci]).  out = y, or out = base + sigma * y.
 __global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloat16* __restrict__ hin, NnW w,
                                                     const float* base, const double* nrm2, float* out) {
-  __shared__ __align__(128) uint4 pl[4][2][kPP];
+  __shared__ __align__(128) uint4 pl[kRing][2][kPP];
   __shared__ uint32_t W4[kTaps * kC / 2];  // [tap][ci pair], BF16 (the values are BF16-rounded already)
   __shared__ float B4;
   for (int q = threadIdx.x; q < kTaps * kC / 2; q += blockDim.x) {
@@ -476,24 +522,30 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloa
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, gq = lane >> 2, cq = lane & 3;
   const unsigned arow[2] = {a_row_addr(pl[0], wp, 0, lane), a_row_addr(pl[0], wp, 1, lane)};
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(&pl[0][0][0]);
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
+  const int64_t plane = (int64_t)g.nx * g.ny * kC;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const TileGeo t = tile_geo(g, tile, tiles_i);
+    PlaneCopy<2, 16> pc;
+    pc.init(g, t);
     __syncthreads();
-    load_plane16(pl[0], hin, g, t, 0);
-    if (g.nz > 1) load_plane16(pl[1], hin, g, t, 1);
-    cp_async_commit();
-    cp_async_wait_all();
+    for (int kq = 0; kq < 3; ++kq) {
+      if (kq < g.nz) pc.issue(sbase + kq * kSlotBytes, hin, kq * plane);
+      cp_async_commit();
+    }
+    cp_async_wait_one();
     __syncthreads();
     const int gj = t.j0 + wp;
     for (int k = 0; k < g.nz; ++k) {
-      if (k + 2 < g.nz) load_plane16(pl[(k + 2) & 3], hin, g, t, k + 2);
+      if (k + 3 < g.nz) pc.issue(sbase + ((k + 3) % kRing) * kSlotBytes, hin, (int64_t)(k + 3) * plane);
       cp_async_commit();
       float d[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) d[mt][0] = d[mt][1] = d[mt][2] = d[mt][3] = B4;
-      const unsigned sl[3] = {((k + 3) & 3) * kSlotBytes, (k & 3) * kSlotBytes, ((k + 1) & 3) * kSlotBytes};
+      const unsigned sl[3] = {((k + kRing - 1) % kRing) * kSlotBytes, (k % kRing) * kSlotBytes,
+                              ((k + 1) % kRing) * kSlotBytes};
       const bool has[3] = {k > 0, true, k + 1 < g.nz};
 #pragma unroll
       for (int tp = 0; tp < kTaps; ++tp) {
@@ -522,10 +574,11 @@ __global__ void __launch_bounds__(kTI * kTJ) k_nn_l4t(NnGrid g, const __nv_bfloa
           }
         }
       }
-      cp_async_wait_all();
+      cp_async_wait_one();
       __syncthreads();
     }
   }
+  cp_async_wait_all();
 }
 
 // ---- backward (FP32 on the CUDA cores) ---------------------------------------

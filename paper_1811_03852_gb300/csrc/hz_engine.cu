@@ -1018,7 +1018,10 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (R <= p.tol) { status = HZ_OK; break; }
     if (outer >= p.max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
     if (p.krylov == HZ_KRYLOV_FGMRES)
+    {
       CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta, p.precond == HZ_PRE_TRI_NN, &fallbacks));
+      if (p.precond == HZ_PRE_TRI_NN) CKS(nn_stage_status(op->nn, op->stream));
+    }
     else if (fp32)
       CKS(run_inner<float>(op, p.use_graph, p.max_inner, sor ? p.sor_sweeps : 0, p.sor_omega));
     else

@@ -261,6 +261,9 @@ cudaError_t fgm_residual(const FgmWs& W, const Grid& g, const Bands<float>& a, c
 // ---- learned stage (hz_nn.cu) ----
 // z <- z + sigma * NN(e1 / sigma), sigma = sqrt(*nrm2 / n), on a full (periodic) field
 int nn_stage_apply(hz_nn_s* nn, const Grid& g, const float* e1, const double* nrm2, float* z, cudaStream_t s);
+// waits for the network's stream and reports HZ_ERR_TIMEOUT if a tensor-core
+// kernel's bounded wait gave up since the last check
+int nn_stage_status(hz_nn_s* nn, cudaStream_t s);
 // training-pair helpers: stage 0: rs = r / A_C, e = xs - xk; stage 1: in = e1 / sigma, tg = (e - z1) / sigma
 cudaError_t nn_pair_launch(int64_t n, const double* A7, const double* b, const double* xk, const double* xs,
                            const double* r, float* rs, float* e, const float* e1, const float* z1, const double* nrm2,

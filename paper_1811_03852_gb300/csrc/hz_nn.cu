@@ -22,12 +22,10 @@
 #include <cstring>
 #include <vector>
 
-#include "hz_internal.cuh"
+#include "hz_nn.cuh"
 
 namespace hz {
 
-constexpr int kC = 16;    // hidden channels
-constexpr int kTaps = 27;
 // flat parameter layout (per layer W[Cout][Cin][27] then b[Cout])
 constexpr int kP1 = kC * 1 * kTaps, kP2 = kC * kC * kTaps, kP4 = 1 * kC * kTaps;
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kP1;
@@ -35,12 +33,6 @@ constexpr int kOffW2 = kOffB1 + kC, kOffB2 = kOffW2 + kP2;
 constexpr int kOffW3 = kOffB2 + kC, kOffB3 = kOffW3 + kP2;
 constexpr int kOffW4 = kOffB3 + kC, kOffB4 = kOffW4 + kP4;
 constexpr int kNParams = kOffB4 + 1;
-
-struct NnGrid {
-  int nx, ny, nz, seg;   // seg: rows per stacked crop (= ny for one field)
-  int periodic;          // 1: wrap in i
-  int64_t n;
-};
 
 // index of the neighbour of (i, j, k) at tap t, or -1 outside the domain
 __device__ __forceinline__ int64_t nbr(const NnGrid& g, int i, int j, int k, int t) {
@@ -57,25 +49,6 @@ __device__ __forceinline__ int64_t nbr(const NnGrid& g, int i, int j, int k, int
   }
   return ((int64_t)kk * g.ny + jj) * g.nx + ii;
 }
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
-
-// kernel-side weights (bf16-rounded values; FP32 copies for the CUDA-core layers)
-struct NnW {
-  const float* w1;                // [27][16]     layer 1, (tap, co)
-  const float* b1;                // [16]
-  const __nv_bfloat16* w2b;       // [27][16][16] layer 2, (tap, co, ci) for the MMA
-  const float* w2f;               // [27][16][16] same values in FP32 (backward)
-  const float* b2;
-  const __nv_bfloat16* w3b;
-  const float* w3f;
-  const float* b3;
-  const float* w4;                // [27][16]     layer 4, (tap, ci)
-  const float* b4;                // [1]
-};
 
 // ---- layer 1: x (FP32, one channel, scaled by s) -> z1 (FP32, optional), h1 = gelu(z1) (BF16)
 __global__ void __launch_bounds__(256) k_nn_l1(NnGrid g, const float* __restrict__ x, const double* scale_nrm2,
@@ -909,6 +882,7 @@ struct NnDev {
   int64_t part_cap = 0;
   double* lossv = nullptr;
   double* lossh = nullptr;
+  int* err = nullptr;       // device error word of the tensor-core kernels (bit 0: a bounded wait gave up)
   int step = 0;
 };
 
@@ -930,6 +904,18 @@ namespace hz {
       return e_ == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA;                          \
     }                                                                                             \
   } while (0)
+
+// the tensor-core kernels' error word: a bounded wait that gave up (reset when read)
+static int nn_check_err(hz_nn_s* nn) {
+  int e = 0;
+  NN_CK(cudaMemcpy(&e, nn->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    NN_CK(cudaMemset(nn->d.err, 0, sizeof(int)));
+    snprintf(g_nn_err, sizeof(g_nn_err), "tensor-core convolution: a completion wait exceeded its limit");
+    return HZ_ERR_TIMEOUT;
+  }
+  return HZ_OK;
+}
 
 static NnW nn_w(const NnDev& d) {
   return NnW{d.w1, d.b1, d.w2b, d.w2f, d.b2, d.w3b, d.w3f, d.b3, d.w4, d.b4};
@@ -990,6 +976,12 @@ static int nn_forward(hz_nn_s* nn, const NnGrid& g, const float* x, const double
     const int64_t tiles = (int64_t)((g.nx + kTI - 1) / kTI) * ((g.ny + kTJ - 1) / kTJ);
     const int gt = (int)std::min<int64_t>(tiles, (int64_t)nn->sms * 4);
     k_nn_l1t<<<gt, kTI * kTJ, 0, s>>>(g, x, scale_nrm2, w, train ? d.z1 : nullptr, d.h1);
+    if (nn_tc_ok(g)) {  // 16 -> 16 and 16 -> 1 on tcgen05 (rows of 128 points)
+      NN_CK(nn_tc_mid(g, d.h1, d.w2b, d.b2, train ? d.z2 : nullptr, d.h2, d.err, nn->sms, s));
+      NN_CK(nn_tc_mid(g, d.h2, d.w3b, d.b3, train ? d.z3 : nullptr, h3, d.err, nn->sms, s));
+      NN_CK(nn_tc_l4(g, h3, d.w4, d.b4, base, base ? scale_nrm2 : nullptr, out, d.err, nn->sms, s));
+      return HZ_OK;
+    }
     k_nn_midt<<<gt, kTI * kTJ, 0, s>>>(g, d.h1, d.w2b, d.b2, train ? d.z2 : nullptr, d.h2);
     k_nn_midt<<<gt, kTI * kTJ, 0, s>>>(g, d.h2, d.w3b, d.b3, train ? d.z3 : nullptr, h3);
     k_nn_l4t<<<gt, kTI * kTJ, 0, s>>>(g, h3, w, base, base ? scale_nrm2 : nullptr, out);
@@ -1069,6 +1061,11 @@ int nn_stage_apply(hz_nn_s* nn, const Grid& gr, const float* e1, const double* n
   return st;
 }
 
+int nn_stage_status(hz_nn_s* nn, cudaStream_t s) {
+  NN_CK(cudaStreamSynchronize(s));
+  return nn_check_err(nn);
+}
+
 cudaError_t nn_pair_launch(int64_t n, const double* A7, const double* b, const double* xk, const double* xs,
                            const double* r, float* rs, float* e, const float* e1, const float* z1, const double* nrm2,
                            float* in, float* tg, int stage, cudaStream_t s) {
@@ -1113,6 +1110,8 @@ int hz_nn_create(void* stream, hz_nn* out) {
     return st;
   };
   if (cudaMalloc(&d.master, sizeof(float) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMalloc(&d.err, sizeof(int)) != cudaSuccess) return fail(HZ_ERR_OOM);
+  if (cudaMemset(d.err, 0, sizeof(int)) != cudaSuccess) return fail(HZ_ERR_CUDA);
   if (cudaMalloc(&d.m, sizeof(float) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
   if (cudaMalloc(&d.v, sizeof(float) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
   if (cudaMalloc(&d.grad, sizeof(double) * kNParams) != cudaSuccess) return fail(HZ_ERR_OOM);
@@ -1143,7 +1142,7 @@ int hz_nn_destroy(hz_nn nn) {
   NnDev& d = nn->d;
   for (void* p : {(void*)d.master, (void*)d.m, (void*)d.v, (void*)d.grad, (void*)d.w1, (void*)d.w2b, (void*)d.lossv,
                   (void*)d.h1, (void*)d.h2, (void*)d.h3, (void*)d.z1, (void*)d.z2, (void*)d.z3, (void*)d.dza,
-                  (void*)d.dzb, (void*)d.y, (void*)d.dy, (void*)d.part})
+                  (void*)d.dzb, (void*)d.y, (void*)d.dy, (void*)d.part, (void*)d.err})
     if (p) cudaFree(p);
   if (d.lossh) cudaFreeHost(d.lossh);
   delete nn;
@@ -1186,7 +1185,7 @@ int hz_nn_forward(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, co
                           nn->stream));
   }
   NN_CK(cudaStreamSynchronize(nn->stream));
-  return HZ_OK;
+  return nn_check_err(nn);
 }
 
 int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,

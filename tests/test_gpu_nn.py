@@ -46,7 +46,10 @@ def _rounded(params):
     return [(bf16(W), bf16(b)) for W, b in params]
 
 
-DIMS = [((20, 12, 6), 12, True), ((37, 9, 5), 9, True), ((24, 12, 4), 6, False), ((16, 16, 3), 16, False)]
+DIMS = [((20, 12, 6), 12, True), ((37, 9, 5), 9, True), ((24, 12, 4), 6, False), ((16, 16, 3), 16, False),
+        # rows of 128 points and more: the tensor-core (tcgen05) 16->16 and 16->1 layers, ragged
+        # tiles in i, crop seams every 4 rows, a single odd segment, one level
+        ((160, 12, 6), 12, True), ((136, 8, 4), 4, False), ((129, 5, 3), 5, True), ((256, 6, 1), 6, True)]
 
 
 @pytest.mark.parametrize("dims,seg,periodic", DIMS)
@@ -84,7 +87,7 @@ def test_forward_layerwise_and_end_to_end(dims, seg, periodic):
     assert rel(yg, yf) <= 2e-2, rel(yg, yf)
 
 
-@pytest.mark.parametrize("dims,seg,periodic", DIMS[:3])
+@pytest.mark.parametrize("dims,seg,periodic", DIMS[:3] + [DIMS[5]])
 def test_gradient_layerwise(dims, seg, periodic):
     import torch
 

@@ -29,11 +29,9 @@ constexpr unsigned kHalfBytes = kPP * 16;        // one 8-channel half of a plan
 constexpr unsigned kSlotBytes = 2 * kHalfBytes;  // one ring slot
 constexpr unsigned kWBytes = kTaps * 512;        // B operands: [tap][channel half][co][8 ci] BF16
 constexpr unsigned kUsedBytes = kRing * kSlotBytes + kWBytes + 256;
-// dynamic shared memory per CTA: the whole 227 KB, one CTA per SM, so that
-// every operand window the tensor core can be pointed at stays inside the
-// CTA's own allocation
-constexpr unsigned kSmemBytes = 227 * 1024;
-constexpr int kCtasPerSm = 1;
+// dynamic shared memory per CTA (97 KB: two CTAs per SM)
+constexpr unsigned kSmemBytes = kUsedBytes;
+constexpr int kCtasPerSm = 2;
 static_assert(kUsedBytes <= kSmemBytes, "shared-memory layout");
 constexpr int kTmemCols = 64;                    // two buffers x two rows x 16 columns
 constexpr long long kWaitLimitNs = 500000000LL;  // bound of a completion wait

@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kTI = 128, kTJ = 2;
 constexpr int kPI = kTI + 2, kPJ = kTJ + 2, kPP = kPI * kPJ;  // plane with halo: 130 x 4 points
-constexpr int kRing = 5;
+constexpr int kRing = 6;
 constexpr unsigned kHalfBytes = kPP * 16;        // one 8-channel half of a plane
 constexpr unsigned kSlotBytes = 2 * kHalfBytes;  // one ring slot
 constexpr unsigned kWBytes = kTaps * 512;        // B operands: [tap][channel half][co][8 ci] BF16
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
   extern __shared__ __align__(1024) unsigned char smem[];
   __nv_bfloat16* Wsm = reinterpret_cast<__nv_bfloat16*>(smem + kRing * kSlotBytes);
   float* Bs = reinterpret_cast<float*>(smem + kRing * kSlotBytes + kWBytes);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kRing * kSlotBytes + kWBytes + 64);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kRing * kSlotBytes + kWBytes + 64);  // one per TMEM buffer
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kRing * kSlotBytes + kWBytes + 128);
   int* abort_flag = reinterpret_cast<int*>(smem + kRing * kSlotBytes + kWBytes + 192);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
   if (tid < kC) Bs[tid] = MODE == 0 ? bias[tid] : (tid == 0 ? bias[0] : 0.f);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // visible to the tensor core's arrive
     *abort_flag = 0;
   }
@@ -211,13 +212,16 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
   const unsigned mb = smem_u32(mbar);
   const unsigned sbase = smem_u32(smem);
   const unsigned wbase = smem_u32(Wsm);
+  // descriptors: A = row window in a slot (start field advanced per slot, row and tap), B = tap block
+  const uint64_t adesc0 = umma_desc(sbase, kHalfBytes, 128);
+  const uint64_t bdesc0 = umma_desc(wbase, 256, 128);
 
   float sigma = 1.f;
   if (MODE == 1 && nrm2) sigma = (float)sqrt(*nrm2 / (double)g.n);
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
   const int64_t plane = (int64_t)g.nx * g.ny;
-  unsigned phase = 0;
+  unsigned phase = 0;  // bit b: parity of the next completion of barrier b
   bool aborted = false;
   for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
     const Geo t = tc_geo(g, tile, tiles_i);
@@ -231,18 +235,13 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
     asm volatile("cp.async.wait_group 1;" ::: "memory");  // levels 0 and 1 landed
     fence_async_smem();
     __syncthreads();
+    // level k: copies of k+3 start, the MMAs of k are queued behind those of
+    // k-1, then the epilogue of k-1 waits for its MMAs and reads its buffer
     for (int k = 0; k <= g.nz; ++k) {
-      if (k >= 1) {  // the MMAs of level k-1 are complete: its TMEM buffer is readable, its oldest plane free
-        if (!mbar_wait(mb, phase & 1)) {
-          atomicExch(abort_flag, 1);
-          atomicExch(err, 1);
-        }
-        ++phase;
-        tc_fence_after();
-      }
       if (k + 3 < g.nz) pc.issue(sbase + ((k + 3) % kRing) * kSlotBytes, hin, (int64_t)(k + 3) * plane * kC);
       asm volatile("cp.async.commit_group;" ::: "memory");
       if (k < g.nz && tid == 0) {
+        tc_fence_after();
         const bool has[3] = {k > 0, true, k + 1 < g.nz};
         const unsigned sl[3] = {((k + kRing - 1) % kRing) * kSlotBytes, (k % kRing) * kSlotBytes,
                                 ((k + 1) % kRing) * kSlotBytes};
@@ -254,12 +253,21 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
           for (int tp = 0; tp < kTaps; ++tp) {
             const int dk = tp / 9, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
             if (!has[dk]) continue;
-            const unsigned a = sbase + sl[dk] + (unsigned)(((r + 1 + dj) * kPI + 1 + di) * 16);
-            umma(dcol, umma_desc(a, kHalfBytes, 128), umma_desc(wbase + tp * 512, 256, 128), acc);
+            const unsigned off = sl[dk] + (unsigned)(((r + 1 + dj) * kPI + 1 + di) * 16);
+            umma(dcol, adesc0 + (off >> 4), bdesc0 + (uint64_t)(tp * 32), acc);
             acc = 1;
           }
         }
-        umma_commit(mb);
+        umma_commit(mb + 8u * (k & 1));
+      }
+      if (k >= 1) {  // the MMAs of level k-1 are complete: its TMEM buffer is readable
+        const unsigned b = (k - 1) & 1;
+        if (!mbar_wait(mb + 8u * b, (phase >> b) & 1u)) {
+          atomicExch(abort_flag, 1);
+          atomicExch(err, 1);
+        }
+        phase ^= 1u << b;
+        tc_fence_after();
       }
       if (k >= 1) {  // epilogue of level k-1
         const int kk = k - 1;

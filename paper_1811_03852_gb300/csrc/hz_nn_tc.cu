@@ -24,14 +24,15 @@ namespace {
 
 constexpr int kTI = 128, kTJ = 2;
 constexpr int kPI = kTI + 2, kPJ = kTJ + 2, kPP = kPI * kPJ;  // plane with halo: 130 x 4 points
-constexpr int kRing = 6;
+constexpr int kRing = 6;                // plane slots: levels k-2 .. k+kAhead in flight or in use
+constexpr int kAhead = kRing - 3;        // copies of level k + kAhead start at level k
 constexpr unsigned kHalfBytes = kPP * 16;        // one 8-channel half of a plane
 constexpr unsigned kSlotBytes = 2 * kHalfBytes;  // one ring slot
 constexpr unsigned kWBytes = kTaps * 512;        // B operands: [tap][channel half][co][8 ci] BF16
 constexpr unsigned kUsedBytes = kRing * kSlotBytes + kWBytes + 256;
 // dynamic shared memory per CTA (97 KB: two CTAs per SM)
 constexpr unsigned kSmemBytes = kUsedBytes;
-constexpr int kCtasPerSm = 2;
+constexpr int kCtasPerSm = kUsedBytes * 2 + 2048 <= 228 * 1024 ? 2 : 1;
 static_assert(kUsedBytes <= kSmemBytes, "shared-memory layout");
 constexpr int kTmemCols = 64;                    // two buffers x two rows x 16 columns
 constexpr long long kWaitLimitNs = 500000000LL;  // bound of a completion wait
@@ -228,35 +229,36 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
     TcCopy pc;
     pc.init(g, t);
     __syncthreads();  // the previous tile's MMAs and readers are done with the ring
-    for (int kq = 0; kq < 3; ++kq) {
+    for (int kq = 0; kq < kAhead; ++kq) {
       if (kq < g.nz) pc.issue(sbase + kq * kSlotBytes, hin, (int64_t)kq * plane * kC);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    asm volatile("cp.async.wait_group 1;" ::: "memory");  // levels 0 and 1 landed
+    asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 2) : "memory");  // levels 0 and 1 landed
     fence_async_smem();
     __syncthreads();
     // level k: copies of k+3 start, the MMAs of k are queued behind those of
     // k-1, then the epilogue of k-1 waits for its MMAs and reads its buffer
     for (int k = 0; k <= g.nz; ++k) {
-      if (k + 3 < g.nz) pc.issue(sbase + ((k + 3) % kRing) * kSlotBytes, hin, (int64_t)(k + 3) * plane * kC);
+      if (k + kAhead < g.nz)
+        pc.issue(sbase + ((k + kAhead) % kRing) * kSlotBytes, hin, (int64_t)(k + kAhead) * plane * kC);
       asm volatile("cp.async.commit_group;" ::: "memory");
       if (k < g.nz && tid == 0) {
         tc_fence_after();
         const bool has[3] = {k > 0, true, k + 1 < g.nz};
         const unsigned sl[3] = {((k + kRing - 1) % kRing) * kSlotBytes, (k % kRing) * kSlotBytes,
                                 ((k + 1) % kRing) * kSlotBytes};
+        uint32_t acc = 0;  // the rows' accumulator chains are interleaved tap by tap
 #pragma unroll
-        for (int r = 0; r < kTJ; ++r) {
-          const uint32_t dcol = tmem + (uint32_t)((k & 1) * (kTJ * 16) + r * 16);
-          uint32_t acc = 0;
+        for (int tp = 0; tp < kTaps; ++tp) {
+          const int dk = tp / 9, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
+          if (!has[dk]) continue;
 #pragma unroll
-          for (int tp = 0; tp < kTaps; ++tp) {
-            const int dk = tp / 9, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
-            if (!has[dk]) continue;
+          for (int r = 0; r < kTJ; ++r) {
+            const uint32_t dcol = tmem + (uint32_t)((k & 1) * (kTJ * 16) + r * 16);
             const unsigned off = sl[dk] + (unsigned)(((r + 1 + dj) * kPI + 1 + di) * 16);
             umma(dcol, adesc0 + (off >> 4), bdesc0 + (uint64_t)(tp * 32), acc);
-            acc = 1;
           }
+          acc = 1;
         }
         umma_commit(mb + 8u * (k & 1));
       }
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
         }
         tc_fence_before();
       }
-      asm volatile("cp.async.wait_group 1;" ::: "memory");  // level k+2 landed
+      asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 2) : "memory");  // level k+2 landed
       fence_async_smem();
       __syncthreads();
       if (*abort_flag) {

@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned", "nnfwd"])
+    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned", "nnfwd", "fig1"])
     ap.add_argument("--train-systems", type=int, default=24)
     ap.add_argument("--test-systems", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=240)
@@ -519,6 +519,56 @@ def run_nn_forward(args):
                       "note": "wall clock per call (the call waits for its stream), median of steps"}), flush=True)
 
 
+def run_fig1(args):
+    """The paper's Sec. 4 / Fig. 1 comparison on a synthetic system: one FP32 and one FP64 BiCGStab
+    (T^-1 preconditioner, restart 150, FP64 global sums, no refinement) run far past convergence,
+    their recursive residuals per iteration and true FP64 residuals at checkpoints, next to the
+    mixed solver's refinement loop."""
+    import torch
+
+    import gen
+    import paper_1811_03852_gb300 as hz
+
+    torch.cuda.set_device(0)
+    dims = tuple(args.dims) if args.dims else (96, 72, 20)
+    A, b = gen.make_system(*dims, 1, 2, z_unit=args.z_unit)
+    op = hz.Operator(A)
+    bd = torch.from_numpy(b.reshape(-1)).cuda()
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    nmax = 600
+    curves, true_r = {}, {}
+    for name, mode in (("fp32", hz.HZ_MODE_MIXED_IR), ("fp64", hz.HZ_MODE_FP64)):
+        op.solve(bd, x, mode=mode, max_outer=1, inner_tol=1e-15, max_inner=nmax, record_history=1,
+                 raise_on_error=False)
+        curves[name] = [float(v) for v in op.history()]
+        true_r[name] = {}
+        for it in (10, 25, 50, 100, 150, 200, 300, 400, 600):
+            info = op.solve(bd, x, mode=mode, max_outer=1, inner_tol=1e-15, max_inner=it, raise_on_error=False)
+            true_r[name][it] = info["true_rel_residual"]
+
+    def first_below(c, lvl):
+        for i, v in enumerate(c):
+            if v <= lvl:
+                return i + 1
+        return None
+
+    levels = [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8]
+    gap = {f"{lvl:g}": {"fp32": first_below(curves["fp32"], lvl), "fp64": first_below(curves["fp64"], lvl)}
+           for lvl in levels}
+    ir = op.solve(bd, x, tol=1e-8)
+    early = [abs(a - c) / c for a, c in zip(curves["fp32"][:5], curves["fp64"][:5])]
+    print(json.dumps({
+        "workload": f"paper Sec. 4 FP32 vs FP64 BiCGStab, {dims[0]}x{dims[1]}x{dims[2]} z_unit={args.z_unit} seeds 1/2",
+        "iterations_to_reach_recursive_R": gap,
+        "first5_rel_diff_fp32_vs_fp64": [round(v, 8) for v in early],
+        "true_R_at_iteration": true_r,
+        "min_true_R": {k: min(v.values()) for k, v in true_r.items()},
+        "mixed_refinement": {"outer": ir["outer_iters"], "inner": ir["inner_iters"],
+                             "true_R": ir["true_rel_residual"]},
+        "recursive_R_every_10": {k: [c[i] for i in range(9, len(c), 10)] for k, c in curves.items()},
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -529,6 +579,8 @@ def main():
         run_learned(args)
     elif args.workload == "nnfwd":
         run_nn_forward(args)
+    elif args.workload == "fig1":
+        run_fig1(args)
     else:
         run_ours(args)
 

@@ -1,0 +1,53 @@
+"""The paper's Sec. 4 observations on a synthetic system (GPU solver, FP64 true residual
+recomputed by the oracle): FP32 and FP64 BiCGStab agree for the first iterations; the FP32
+solver alone stalls above the 32-bit limit and needs more iterations for the same recursive
+residual (the "iteration gap"); the FP64 refinement loop around FP32 inner solves reaches 1e-8.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fp32_vs_fp64_bicgstab_behaviour():
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    A, b = gen.make_system(96, 72, 20, 1, 2, z_unit="m")
+    op = hz.Operator(A)
+    bd = dev(b)
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    hist = {}
+    for name, mode in (("fp32", hz.HZ_MODE_MIXED_IR), ("fp64", hz.HZ_MODE_FP64)):
+        op.solve(bd, x, mode=mode, max_outer=1, inner_tol=1e-15, max_inner=500, record_history=1,
+                 raise_on_error=False)
+        hist[name] = np.array(op.history())
+    h32, h64 = hist["fp32"], hist["fp64"]
+    # indistinguishable at first (the paper's Fig. 1: the curves coincide for the first iterations)
+    assert np.all(np.abs(h32[:5] - h64[:5]) <= 1e-3 * h64[:5])
+    # the FP64 solver goes far below the 32-bit limit; the FP32 one does not
+    assert h64.min() <= 1e-10
+    assert h32.min() > 1e-9
+
+    def first(h, lvl):
+        i = np.nonzero(h <= lvl)[0]
+        return int(i[0]) + 1 if i.size else 10**9
+
+    # iteration gap: never fewer FP32 iterations than FP64 ones to reach a level, and strictly
+    # more once the level approaches the 32-bit precision
+    for lvl in (1e-3, 1e-4, 1e-5):
+        assert first(h32, lvl) >= first(h64, lvl) - 2
+    assert first(h32, 1e-7) > first(h64, 1e-7)
+    # the FP32 solver's true residual (oracle) stalls above 1e-8 however long it runs ...
+    op.solve(bd, x, mode=hz.HZ_MODE_MIXED_IR, max_outer=1, inner_tol=1e-15, max_inner=500, raise_on_error=False)
+    _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+    assert rn / np.linalg.norm(b) > 1e-8
+    # ... while refinement around FP32 inner solves reaches it
+    info = op.solve(bd, x, tol=1e-8)
+    _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+    assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8

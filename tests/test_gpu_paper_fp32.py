@@ -37,9 +37,11 @@ def test_fp32_vs_fp64_bicgstab_behaviour():
         i = np.nonzero(h <= lvl)[0]
         return int(i[0]) + 1 if i.size else 10**9
 
-    # iteration gap: never (within rounding noise) fewer FP32 iterations than FP64 ones to reach a level
-    for lvl in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7):
-        assert first(h32, lvl) >= first(h64, lvl) - 2, (lvl, first(h32, lvl), first(h64, lvl))
+    # iteration gap: the same count at a loose level (BiCGStab's non-monotone path moves the
+    # intermediate ones either way), a systematic FP32 deficit near the 32-bit precision
+    assert abs(first(h32, 1e-3) - first(h64, 1e-3)) <= 2
+    for lvl in (1e-7, 1e-8):
+        assert first(h32, lvl) > first(h64, lvl), (lvl, first(h32, lvl), first(h64, lvl))
     # the FP32 solver's true residual (oracle) stalls above 1e-8 however long it runs ...
     op.solve(bd, x, mode=hz.HZ_MODE_MIXED_IR, max_outer=1, inner_tol=1e-15, max_inner=500, raise_on_error=False)
     _, rn = oracle.residual(A, b, host(x).reshape(b.shape))

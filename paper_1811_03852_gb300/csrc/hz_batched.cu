@@ -159,7 +159,7 @@ __device__ double restart_column_cg(const Grid& g, int64_t col, const Bands<floa
 }
 
 template <int V, int UT, int UM>
-__global__ void __launch_bounds__(kBS) k_batched(BatchArgs A) {
+__global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
   __shared__ SysCtl sc[kMaxSys];
   __shared__ double acc[kMaxSys][2];
   const int nsys = A.nsys;

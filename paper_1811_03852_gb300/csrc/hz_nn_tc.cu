@@ -34,10 +34,7 @@ constexpr unsigned kUsedBytes = kRing * kSlotBytes + kWBytes + 256;
 constexpr unsigned kSmemBytes = kUsedBytes;
 constexpr int kCtasPerSm = kUsedBytes * 2 + 2048 <= 228 * 1024 ? 2 : 1;
 static_assert(kUsedBytes <= kSmemBytes, "shared-memory layout");
-// TMEM accumulators: [buffer (level parity)][input level k-1, k, k+1][row][16 channels]
-// = 2 x 3 x 2 x 16 = 192 columns (a power of two is allocated)
-constexpr int kAccCols = 3 * kTJ * 16;
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 64;                    // two buffers x two rows x 16 columns
 constexpr long long kWaitLimitNs = 500000000LL;  // bound of a completion wait
 // instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, N = 16, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
@@ -250,20 +247,18 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
         const bool has[3] = {k > 0, true, k + 1 < g.nz};
         const unsigned sl[3] = {((k + kRing - 1) % kRing) * kSlotBytes, (k % kRing) * kSlotBytes,
                                 ((k + 1) % kRing) * kSlotBytes};
-        // six independent accumulator chains (input level x row) of nine taps, interleaved
+        uint32_t acc = 0;  // the rows' accumulator chains are interleaved tap by tap
 #pragma unroll
-        for (int j9 = 0; j9 < 9; ++j9) {
+        for (int tp = 0; tp < kTaps; ++tp) {
+          const int dk = tp / 9, dj = (tp / 3) % 3 - 1, di = tp % 3 - 1;
+          if (!has[dk]) continue;
 #pragma unroll
-          for (int dk = 0; dk < 3; ++dk) {
-            if (!has[dk]) continue;
-            const int tp = dk * 9 + j9, dj = j9 / 3 - 1, di = j9 % 3 - 1;
-#pragma unroll
-            for (int r = 0; r < kTJ; ++r) {
-              const uint32_t dcol = tmem + (uint32_t)((k & 1) * kAccCols + (dk * kTJ + r) * 16);
-              const unsigned off = sl[dk] + (unsigned)(((r + 1 + dj) * kPI + 1 + di) * 16);
-              umma(dcol, adesc0 + (off >> 4), bdesc0 + (uint64_t)(tp * 32), j9 > 0 ? 1u : 0u);
-            }
+          for (int r = 0; r < kTJ; ++r) {
+            const uint32_t dcol = tmem + (uint32_t)((k & 1) * (kTJ * 16) + r * 16);
+            const unsigned off = sl[dk] + (unsigned)(((r + 1 + dj) * kPI + 1 + di) * 16);
+            umma(dcol, adesc0 + (off >> 4), bdesc0 + (uint64_t)(tp * 32), acc);
           }
+          acc = 1;
         }
         umma_commit(mb + 8u * (k & 1));
       }
@@ -279,27 +274,20 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
       if (k >= 1) {  // epilogue of level k-1
         const int kk = k - 1;
         const int gi = t.i0 + 32 * warp + lane;
-        const bool hse[3] = {kk > 0, true, kk + 1 < g.nz};  // accumulators written for level kk
 #pragma unroll
         for (int r = 0; r < kTJ; ++r) {
-          const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((kk & 1) * kAccCols + r * 16);
+          const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((kk & 1) * (kTJ * 16) + r * 16);
           const int gj = t.j0 + r;
           const bool valid = gi < g.nx && gj < g.ny;
           const int64_t p = (int64_t)kk * plane + (int64_t)gj * g.nx + gi;
           if (MODE == 0) {
-            float a[kC];
-#pragma unroll
-            for (int c = 0; c < kC; ++c) a[c] = Bs[c];
-#pragma unroll
-            for (int dk = 0; dk < 3; ++dk) {  // bias + level k-1 + level k + level k+1
-              if (!hse[dk]) continue;
-              uint32_t v[16];
-              tmem_ld16(taddr + (uint32_t)(dk * kTJ * 16), v);
-              tmem_wait_ld();
-#pragma unroll
-              for (int c = 0; c < kC; ++c) a[c] += __uint_as_float(v[c]);
-            }
+            uint32_t v[16];
+            tmem_ld16(taddr, v);
+            tmem_wait_ld();
             if (valid) {
+              float a[kC];
+#pragma unroll
+              for (int c = 0; c < kC; ++c) a[c] = __uint_as_float(v[c]) + Bs[c];
               if (z) {
 #pragma unroll
                 for (int c = 0; c < kC; c += 4)
@@ -312,16 +300,11 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
               reinterpret_cast<uint4*>(hout + p * kC)[1] = reinterpret_cast<const uint4*>(hv)[1];
             }
           } else {
-            float y = Bs[0];
-#pragma unroll
-            for (int dk = 0; dk < 3; ++dk) {
-              if (!hse[dk]) continue;
-              uint32_t v;
-              tmem_ld1(taddr + (uint32_t)(dk * kTJ * 16), v);
-              tmem_wait_ld();
-              y += __uint_as_float(v);
-            }
+            uint32_t v;
+            tmem_ld1(taddr, v);
+            tmem_wait_ld();
             if (valid) {
+              const float y = __uint_as_float(v) + Bs[0];
               out[p] = base ? fmaf(sigma, y, base[p]) : y;
             }
           }

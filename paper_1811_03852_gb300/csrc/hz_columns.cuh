@@ -93,11 +93,13 @@ __device__ __forceinline__ GroupNbr group_nbr(const Grid& g, int64_t c0) {
 // Thomas algorithm on V columns with unit diagonal and pre-computed factors:
 // forward y_k = m_k q_k - l_k y_(k-1), back z_k = y_k - c'_k z_(k+1).  The
 // input q_k = src.make(values src.load fetched for level k) is the fused
-// axpy.  y is parked in out and re-read by the back sweep (an L2 hit).
-template <typename T, int V, int U, typename Src>
+// axpy.  y is parked in out and re-read by the back sweep (an L2 hit while the
+// column's footprint stays in L2), or with SM in shared memory ys laid out
+// [level][thread][V] (kBS * V values per level), which keeps it off L2 and HBM.
+template <typename T, int V, int U, typename Src, bool SM = false>
 __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* __restrict__ m,
                                            const T* __restrict__ l, const T* __restrict__ cp, T* __restrict__ out,
-                                           Src& src) {
+                                           Src& src, T* ys = nullptr) {
   constexpr int NIN = Src::NIN;
   const int64_t ncol = g.ncol;
   const int nz = g.nz;
@@ -126,7 +128,10 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
           y.a[c] = fma(mm[u].a[c], q.a[c], -ll[u].a[c] * yprev[c]);
           yprev[c] = y.a[c];
         }
-        stp(out + idx, y);
+        if constexpr (SM)
+          stp(ys + ((int64_t)(k0 + u) * kBS + threadIdx.x) * V, y);
+        else
+          stp(out + idx, y);
       }
     }
     src.flush();
@@ -140,7 +145,10 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
     for (int u = 0; u < U; ++u) {
       if (k0 - u >= 0) {
         const int64_t idx = (int64_t)(k0 - u) * ncol + c0;
-        yy[u] = ldp<T, V, LD_PLAIN>(out + idx);  // written by this thread above: coherent load
+        if constexpr (SM)
+          yy[u] = ldp<T, V, LD_PLAIN>(ys + ((int64_t)(k0 - u) * kBS + threadIdx.x) * V);
+        else
+          yy[u] = ldp<T, V, LD_PLAIN>(out + idx);  // written by this thread above: coherent load
         cc[u] = ldp<T, V, LD_NC>(cp + idx);
       }
     }

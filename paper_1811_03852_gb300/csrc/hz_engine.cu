@@ -647,9 +647,10 @@ void free_op(hz_op op) {
 }
 
 // ---- column-kernel variants -------------------------------------------------
-bool variant_ok(int prec, int kind, int id, int nx) {
+bool variant_ok(int prec, int kind, int id, int nx, int nz) {
   int v = 1, u = 1;
   variant_shape(prec, kind, id, &v, &u);
+  if (variant_parks_smem(prec, kind, id) && (size_t)nz * kBS * v * (prec ? 8 : 4) > 227 * 1024) return false;
   return nx % v == 0;
 }
 
@@ -659,7 +660,7 @@ int default_variant(int prec, int kind, int nx) {
   for (int i = 0; i < num_variants(prec, kind); ++i) {
     int v = 1, u = 1;
     variant_shape(prec, kind, i, &v, &u);
-    if (nx % v == 0 && v > bestv) {
+    if (nx % v == 0 && v > bestv && !variant_parks_smem(prec, kind, i)) {
       best = i;
       bestv = v;
     }
@@ -706,7 +707,7 @@ void load_tuned(hz_op op) {
         char want[400];
         tune_key(op, pr, kind, want, sizeof(want));
         if (strcmp(want, key) != 0 || var < 0) continue;
-        if (kind < 2 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx))
+        if (kind < 2 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx, op->g.nz))
           (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = var;
         else if (kind >= 2 && sor_variant_ok(pr, kind - 2, var, op->g.nx))
           op->L.vsor[pr][kind - 2] = var;
@@ -807,6 +808,7 @@ int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_
   cudaEventCreate(&op->ev1);
   // launch shapes: each kernel fills the SMs to its own occupancy (grid-stride loops)
   op->L = Launch{op->sms, (op->g.ncol + kBS - 1) / kBS, (n / 4 + 255) / 256 + 1, op->stream};
+  op->L.nz = nz;
   warm_launch_cache(op->L);
   for (int pr = 0; pr < 2; ++pr) {
     op->L.vpre[pr] = default_variant(pr, 0, nx);
@@ -1125,7 +1127,7 @@ int autotune_prec(hz_op op, int reps, double* best_ms) {
     int best = -1;
     double bms = 1e30;
     for (int id = 0; id < num_variants(pr, kind); ++id) {
-      if (!variant_ok(pr, kind, id, op->g.nx)) continue;
+      if (!variant_ok(pr, kind, id, op->g.nx, op->g.nz)) continue;
       Launch L = op->L;
       (kind == 0 ? L.vpre : L.vmv)[pr] = id;
       double ms;
@@ -1283,7 +1285,7 @@ int hz_op_set_variants(hz_op op, int pre32, int mv32, int pre64, int mv64) {
   for (int q = 0; q < 4; ++q) {
     const int pr = q / 2, kind = q % 2;
     if (v[q] < 0) continue;
-    if (v[q] >= num_variants(pr, kind) || !variant_ok(pr, kind, v[q], op->g.nx)) return HZ_ERR_INVALID;
+    if (v[q] >= num_variants(pr, kind) || !variant_ok(pr, kind, v[q], op->g.nx, op->g.nz)) return HZ_ERR_INVALID;
   }
   for (int q = 0; q < 4; ++q) {
     const int pr = q / 2, kind = q % 2;

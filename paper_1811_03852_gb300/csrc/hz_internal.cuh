@@ -141,6 +141,7 @@ struct Launch {
   int vpre[2];       // variant of the Thomas kernels, [0] FP32, [1] FP64
   int vmv[2];        // variant of the stencil kernels
   int vsor[2][3];    // tri-SOR variants: [prec][0 colour pass, 1 matvec, 2 first pass]
+  int nz;            // levels of the operator (shared-memory size of the parking variants)
 };
 
 // tri-SOR kernel variants (kind 0 colour pass, 1 matvec, 2 first pass):
@@ -156,6 +157,8 @@ bool sor_variant_ok(int prec, int kind, int id, int nx);
 // depth = levels per software-pipelined batch.
 int num_variants(int prec, int kind);
 void variant_shape(int prec, int kind, int id, int* vec, int* depth);
+// the Thomas variant parks its forward sweep in shared memory (nz * kBS * vec values per block)
+bool variant_parks_smem(int prec, int kind, int id);
 template <typename T>
 void warm_kernels(const Launch& L);
 
@@ -163,7 +166,7 @@ void warm_kernels(const Launch& L);
 // occupancy (queried once per kernel and cached), capped by the work and by
 // the slots of the reduction buffer.  warm_launch_cache() queries every
 // kernel up front so that no query happens during stream capture.
-int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks);
+int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks, size_t smem = 0);
 void warm_launch_cache(const Launch& L);
 
 template <typename T>

@@ -30,11 +30,14 @@ namespace hz {
 // ---- variants ----------------------------------------------------------------
 template <typename T>
 struct Variants;
+// Thomas variants with pre_sm = 1 park the forward sweep in shared memory
+// (nz * kBS * V values per block) instead of the output vector.
 template <>
 struct Variants<float> {
-  static constexpr int NPRE = 4, NMV = 4;
-  static constexpr int pre_v[NPRE] = {1, 4, 4, 2};
-  static constexpr int pre_u[NPRE] = {8, 2, 1, 4};
+  static constexpr int NPRE = 9, NMV = 4;
+  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4};
+  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2};
+  static constexpr int pre_sm[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1};
   static constexpr int mv_v[NMV] = {1, 4, 2, 2};
   static constexpr int mv_u[NMV] = {4, 1, 2, 1};
 };
@@ -43,11 +46,19 @@ struct Variants<double> {
   static constexpr int NPRE = 3, NMV = 3;
   static constexpr int pre_v[NPRE] = {1, 2, 2};
   static constexpr int pre_u[NPRE] = {4, 2, 1};
+  static constexpr int pre_sm[NPRE] = {0, 0, 0};
   static constexpr int mv_v[NMV] = {1, 2, 1};
   static constexpr int mv_u[NMV] = {2, 1, 1};
 };
 
 constexpr int kMinBlocks = 6;  // launch bound of the column kernels: at most 80 registers per thread
+
+// shared memory of a parking variant for nz levels (0 for the others), and its limit
+constexpr size_t kParkMax = 227 * 1024;
+template <typename T, int V, bool SM>
+constexpr size_t park_bytes(int nz) {
+  return SM ? (size_t)nz * kBS * V * sizeof(T) : 0;
+}
 
 template <typename T>
 __device__ __forceinline__ T ldro(const T* p) {
@@ -183,15 +194,19 @@ __device__ __noinline__ double restart_column(const Grid& g, int64_t col, const 
 
 // ---------------------------------------------------------------------------
 // k_pre_p: p = r + beta (p - omega v), ph = T^-1 p (the common case).
-template <typename T, int V, int U>
+// dynamic shared memory of the variants that park the forward sweep there
+extern __shared__ __align__(16) unsigned char hz_park[];
+
+template <typename T, int V, int U, bool SM>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_p(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl) {
   if (ctl->state != ST_RUNNING || ctl->fresh) return;
+  T* ys = reinterpret_cast<T*>(hz_park);
   const T beta = (T)ctl->beta, omega = (T)ctl->omega;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
     SrcP<T, V> src{rin, w.p, w.v, beta, omega};
-    thomas_vec<T, V, U>(g, q * V, a.m, a.l, a.cp, w.ph, src);
+    thomas_vec<T, V, U, SrcP<T, V>, SM>(g, q * V, a.m, a.l, a.cp, w.ph, src, ys);
   }
 }
 
@@ -247,16 +262,17 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs
 
 // ---------------------------------------------------------------------------
 // k_pre_s: s = r - alpha v, <s, s> (half-step exit test), sh = T^-1 s
-template <typename T, int V, int U>
+template <typename T, int V, int U, bool SM>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_s(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
+  T* ys = reinterpret_cast<T*>(hz_park);
   const T alpha = (T)ctl->alpha;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
   double acc = 0.0;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
     SrcS<T, V> src{rin, w.v, w.s, alpha, T(0), 0.0};
-    thomas_vec<T, V, U>(g, q * V, a.m, a.l, a.cp, w.sh, src);
+    thomas_vec<T, V, U, SrcS<T, V>, SM>(g, q * V, a.m, a.l, a.cp, w.sh, src, ys);
     acc += src.acc;
   }
   double vv[1] = {acc}, out[1];
@@ -393,13 +409,14 @@ __global__ void __launch_bounds__(kBS) k_matvec_hat(Grid g, Bands<T> a, const T*
   }
 }
 
-template <typename T, int V, int U>
+template <typename T, int V, int U, bool SM>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_tinv(Grid g, Bands<T> a, const T* __restrict__ r,
                                                           T* __restrict__ z) {
+  T* ys = reinterpret_cast<T*>(hz_park);
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
     SrcCopy<T, V> src{r, nullptr};
-    thomas_vec<T, V, U>(g, q * V, a.m, a.l, a.cp, z, src);
+    thomas_vec<T, V, U, SrcCopy<T, V>, SM>(g, q * V, a.m, a.l, a.cp, z, src, ys);
   }
 }
 
@@ -417,7 +434,8 @@ template <typename T, int I = 0, typename F>
 cudaError_t with_pre(int var, F&& f) {
   if constexpr (I < Variants<T>::NPRE) {
     if (var == I)
-      return f(std::integral_constant<int, Variants<T>::pre_v[I]>{}, std::integral_constant<int, Variants<T>::pre_u[I]>{});
+      return f(std::integral_constant<int, Variants<T>::pre_v[I]>{}, std::integral_constant<int, Variants<T>::pre_u[I]>{},
+               std::integral_constant<bool, Variants<T>::pre_sm[I] != 0>{});
     return with_pre<T, I + 1>(var, f);
   } else {
     return cudaErrorInvalidValue;
@@ -442,19 +460,24 @@ inline int64_t blocks_for(int64_t items, int block) { return (items + block - 1)
 template <typename T>
 cudaError_t launch_pre_p_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
   k_pre_start<T><<<grid_for((const void*)k_pre_start<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
-  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc) {
+  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Sc) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    const void* k = (const void*)k_pre_p<T, V, U>;
-    k_pre_p<T, V, U><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl);
+    constexpr bool SM = decltype(Sc)::value;
+    const void* k = (const void*)k_pre_p<T, V, U, SM>;
+    const size_t sm = park_bytes<T, V, SM>(g.nz);
+    k_pre_p<T, V, U, SM><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm), kBS, sm, L.stream>>>(g, a, w, ctl);
     return cudaGetLastError();
   });
 }
 template <typename T>
 cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc) {
+  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Sc) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    const void* k = (const void*)k_pre_s<T, V, U>;
-    k_pre_s<T, V, U><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl, red);
+    constexpr bool SM = decltype(Sc)::value;
+    const void* k = (const void*)k_pre_s<T, V, U, SM>;
+    const size_t sm = park_bytes<T, V, SM>(g.nz);
+    k_pre_s<T, V, U, SM><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm), kBS, sm, L.stream>>>(g, a, w, ctl,
+                                                                                                      red);
     return cudaGetLastError();
   });
 }
@@ -482,10 +505,12 @@ cudaError_t launch_matvec_hat_t(const Grid& g, const Bands<T>& a, const T* x, T*
 }
 template <typename T>
 cudaError_t launch_tinv_t(const Grid& g, const Bands<T>& a, const T* r, T* z, const Launch& L) {
-  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc) {
+  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Sc) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    const void* k = (const void*)k_tinv<T, V, U>;
-    k_tinv<T, V, U><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, r, z);
+    constexpr bool SM = decltype(Sc)::value;
+    const void* k = (const void*)k_tinv<T, V, U, SM>;
+    const size_t sm = park_bytes<T, V, SM>(g.nz);
+    k_tinv<T, V, U, SM><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm), kBS, sm, L.stream>>>(g, a, r, z);
     return cudaGetLastError();
   });
 }
@@ -508,11 +533,16 @@ void warm_t(const Launch& L) {
   grid_for((const void*)k_upd<T>, 256, L, 1);
   grid_for((const void*)k_matvec_hat<T>, kBS, L, 1);
   for (int i = 0; i < Variants<T>::NPRE; ++i)
-    with_pre<T>(i, [&](auto Vc, auto Uc) {
+    with_pre<T>(i, [&](auto Vc, auto Uc, auto Sc) {
       constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-      grid_for((const void*)k_pre_p<T, V, U>, kBS, L, 1);
-      grid_for((const void*)k_pre_s<T, V, U>, kBS, L, 1);
-      grid_for((const void*)k_tinv<T, V, U>, kBS, L, 1);
+      constexpr bool SM = decltype(Sc)::value;
+      const size_t sm = park_bytes<T, V, SM>(L.nz);
+      const void* ks[3] = {(const void*)k_pre_p<T, V, U, SM>, (const void*)k_pre_s<T, V, U, SM>,
+                           (const void*)k_tinv<T, V, U, SM>};
+      for (const void* k : ks) {
+        if (SM && sm <= kParkMax) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kParkMax);
+        if (sm <= kParkMax) grid_for(k, kBS, L, 1, sm);
+      }
       return cudaSuccess;
     });
   for (int i = 0; i < Variants<T>::NMV; ++i)

@@ -1,7 +1,8 @@
 // hz_launch.cu -- launch shapes (occupancy-derived grids), variant tables and
 // the stand-alone deterministic dot product.
+#include <map>
 #include <mutex>
-#include <unordered_map>
+#include <utility>
 
 #include "hz_krylov.cuh"
 
@@ -9,22 +10,23 @@ namespace hz {
 
 namespace {
 std::mutex g_occ_mu;
-std::unordered_map<const void*, int> g_occ;  // blocks per SM of each kernel at its block size
+std::map<std::pair<const void*, size_t>, int> g_occ;  // blocks per SM of each (kernel, dynamic smem)
 }  // namespace
 
-int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks) {
+int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks, size_t smem) {
   int per_sm = 0;
   {
     std::lock_guard<std::mutex> lk(g_occ_mu);
-    auto it = g_occ.find(kernel);
+    const auto key = std::make_pair(kernel, smem);
+    auto it = g_occ.find(key);
     if (it != g_occ.end()) {
       per_sm = it->second;
     } else {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
       }
-      g_occ[kernel] = per_sm;
+      g_occ[key] = per_sm;
     }
   }
   int64_t gsz = (int64_t)per_sm * L.sms;
@@ -64,6 +66,11 @@ void warm_launch_cache(const Launch& L) {
 int num_variants(int prec, int kind) {
   if (prec == 0) return kind == 0 ? Variants<float>::NPRE : Variants<float>::NMV;
   return kind == 0 ? Variants<double>::NPRE : Variants<double>::NMV;
+}
+
+bool variant_parks_smem(int prec, int kind, int id) {
+  if (kind != 0) return false;
+  return prec == 0 ? Variants<float>::pre_sm[id] != 0 : Variants<double>::pre_sm[id] != 0;
 }
 
 void variant_shape(int prec, int kind, int id, int* vec, int* depth) {

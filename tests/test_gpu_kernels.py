@@ -188,7 +188,7 @@ def test_every_column_variant_matches_oracle(shape, prec):
     L = hz.load()
     pi = 1 if prec == "fp64" else 0
     tried = 0
-    for var in range(8):
+    for var in range(12):
         for kind in (0, 1):
             args = [-1, -1, -1, -1]
             args[2 * pi + kind] = var
@@ -215,3 +215,28 @@ def test_autotune_picks_valid_variants_and_solves():
     info = op.solve(dev(b), x)
     _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
     assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8
+
+
+def test_every_thomas_variant_solves():
+    # the solver's own Thomas kernels (k_pre_p, k_pre_s) in every FP32 variant,
+    # including those that park the forward sweep in shared memory
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    A, b = gen.make_system(96, 72, 20, 5, 6, z_unit="m")
+    op = hz.Operator(A)
+    L = hz.load()
+    x_ref, _ = oracle.solve(A, b, mode=oracle.MODE_FP64, tol=1e-12, eta=1e-13)
+    tried = 0
+    for var in range(12):
+        if L.hz_op_set_variants(op.handle, var, -1, -1, -1) != 0:
+            continue
+        tried += 1
+        x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+        info = op.solve(dev(b), x)
+        xh = host(x).reshape(b.shape)
+        _, rn = oracle.residual(A, b, xh)
+        assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8, var
+        assert np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref) <= 1e-6, var
+    assert tried >= 8

@@ -250,6 +250,13 @@ cudaError_t launch_body(hz_op op, cudaStream_t s, unsigned long long cond, int u
 
 // Build the inner loop as a graph: one conditional WHILE node whose body is
 // one iteration; k_upd sets the condition from the device.
+void drop_graph(GraphSlot& gs) {
+  if (gs.exec) cudaGraphExecDestroy(gs.exec);
+  if (gs.graph) cudaGraphDestroy(gs.graph);
+  gs.exec = nullptr;
+  gs.graph = nullptr;
+}
+
 template <typename F>
 int build_loop_graph(hz_op op, GraphSlot& gs, F&& body) {
   if (gs.exec) return HZ_OK;
@@ -267,17 +274,13 @@ int build_loop_graph(hz_op op, GraphSlot& gs, F&& body) {
   cudaError_t e = body((unsigned long long)h);
   cudaGraph_t out = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(op->cap, &out);
-  CK(e);
-  CK(e2);
-  CK(cudaGraphInstantiate(&gs.exec, gs.graph, 0));
+  if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&gs.exec, gs.graph, 0);
+  if (e != cudaSuccess || e2 != cudaSuccess) {  // leave the slot empty for the next attempt
+    cudaGetLastError();
+    drop_graph(gs);
+    CK(e != cudaSuccess ? e : e2);
+  }
   return HZ_OK;
-}
-
-void drop_graph(GraphSlot& gs) {
-  if (gs.exec) cudaGraphExecDestroy(gs.exec);
-  if (gs.graph) cudaGraphDestroy(gs.graph);
-  gs.exec = nullptr;
-  gs.graph = nullptr;
 }
 
 // the tri-SOR loop graph of one precision, rebuilt when (sweeps, omega) change
@@ -311,9 +314,12 @@ int build_graph(hz_op op) {
   cudaError_t e = launch_body<T>(op, op->cap, (unsigned long long)h, 1);
   cudaGraph_t out = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(op->cap, &out);
-  CK(e);
-  CK(e2);
-  CK(cudaGraphInstantiate(&gs.exec, gs.graph, 0));
+  if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&gs.exec, gs.graph, 0);
+  if (e != cudaSuccess || e2 != cudaSuccess) {  // leave the slot empty for the next attempt
+    cudaGetLastError();
+    drop_graph(gs);
+    CK(e != cudaSuccess ? e : e2);
+  }
   return HZ_OK;
 }
 
@@ -650,7 +656,7 @@ void free_op(hz_op op) {
 bool variant_ok(int prec, int kind, int id, int nx, int nz) {
   int v = 1, u = 1;
   variant_shape(prec, kind, id, &v, &u);
-  if (variant_parks_smem(prec, kind, id) && (size_t)nz * kBS * v * (prec ? 8 : 4) > 227 * 1024) return false;
+  if (variant_parks_smem(prec, kind, id) && (size_t)nz * kBS * v * (prec ? 8 : 4) > 200 * 1024) return false;
   return nx % v == 0;
 }
 
@@ -1130,13 +1136,15 @@ int autotune_prec(hz_op op, int reps, double* best_ms) {
       if (!variant_ok(pr, kind, id, op->g.nx, op->g.nz)) continue;
       Launch L = op->L;
       (kind == 0 ? L.vpre : L.vmv)[pr] = id;
-      double ms;
-      if (kind == 0)
-        ms = time_it([&] { return launch_pre_p<T>(op->g, a, w, op->ctl, op->red, L); }) +
-             time_it([&] { return launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L); });
-      else
-        ms = time_it([&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }) +
-             time_it([&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); });
+      double m1, m2;
+      if (kind == 0) {
+        m1 = time_it([&] { return launch_pre_p<T>(op->g, a, w, op->ctl, op->red, L); });
+        m2 = time_it([&] { return launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L); });
+      } else {
+        m1 = time_it([&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); });
+        m2 = time_it([&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); });
+      }
+      const double ms = (m1 < 0 || m2 < 0) ? -1.0 : m1 + m2;  // a failed launch fails the tuning
       if (ms < 0) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1204,12 +1212,17 @@ int autotune_sor(hz_op op, int reps) {
       double ms;
       if (kind == 0)
         ms = time_it([&] { return launch_sor_pass<T>(op->g, a, w.p, w.ph, w.ph, w.t, 1, 1, 1.5, op->ctl, L); });
-      else if (kind == 1)
-        ms = time_it([&] { return launch_mv_rb<T>(op->g, a, w, 0, op->ctl, op->red, L); }) +
-             time_it([&] { return launch_mv_rb<T>(op->g, a, w, 1, op->ctl, op->red, L); });
-      else
-        ms = time_it([&] { return launch_sor_first<T>(op->g, a, w, w.t, 1.5, 0, op->ctl, op->red, L); }) +
-             time_it([&] { return launch_sor_first<T>(op->g, a, w, w.t, 1.5, 1, op->ctl, op->red, L); });
+      else {
+        const double m1 = kind == 1 ? time_it([&] { return launch_mv_rb<T>(op->g, a, w, 0, op->ctl, op->red, L); })
+                                    : time_it([&] {
+                                        return launch_sor_first<T>(op->g, a, w, w.t, 1.5, 0, op->ctl, op->red, L);
+                                      });
+        const double m2 = kind == 1 ? time_it([&] { return launch_mv_rb<T>(op->g, a, w, 1, op->ctl, op->red, L); })
+                                    : time_it([&] {
+                                        return launch_sor_first<T>(op->g, a, w, w.t, 1.5, 1, op->ctl, op->red, L);
+                                      });
+        ms = (m1 < 0 || m2 < 0) ? -1.0 : m1 + m2;
+      }
       if (ms < 0) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -53,8 +53,10 @@ struct Variants<double> {
 
 constexpr int kMinBlocks = 6;  // launch bound of the column kernels: at most 80 registers per thread
 
-// shared memory of a parking variant for nz levels (0 for the others), and its limit
-constexpr size_t kParkMax = 227 * 1024;
+// shared memory of a parking variant for nz levels (0 for the others), and its
+// limit (below the 227 KB opt-in maximum, which also holds the kernels' static
+// reduction buffers)
+constexpr size_t kParkMax = 200 * 1024;
 template <typename T, int V, bool SM>
 constexpr size_t park_bytes(int nz) {
   return SM ? (size_t)nz * kBS * V * sizeof(T) : 0;
@@ -540,8 +542,10 @@ void warm_t(const Launch& L) {
       const void* ks[3] = {(const void*)k_pre_p<T, V, U, SM>, (const void*)k_pre_s<T, V, U, SM>,
                            (const void*)k_tinv<T, V, U, SM>};
       for (const void* k : ks) {
-        if (SM && sm <= kParkMax) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kParkMax);
-        if (sm <= kParkMax) grid_for(k, kBS, L, 1, sm);
+        if (sm > kParkMax) continue;  // the variant is not valid for this nz
+        if (SM && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kParkMax) != cudaSuccess)
+          cudaGetLastError();  // the launch reports it; nothing stale is left behind
+        grid_for(k, kBS, L, 1, sm);
       }
       return cudaSuccess;
     });

@@ -117,6 +117,25 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_max(value, device):
+    """Largest value over the ranks of the process group (all-reduce MAX); the value itself
+    without a group or with one rank.  The replicas' slowest time is the job's time."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
+    the slowest taking `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -243,11 +262,7 @@ def run_ours(args):
             infos.append(op.solve(bd, x, params=params))
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{dev}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = replica_max(e0.elapsed_time(e1), f"cuda:{dev}")
         return ms, infos
 
     # setup (operator update: scaling + Thomas factors), timed separately
@@ -267,7 +282,7 @@ def run_ours(args):
     clocks = clk.summary()
     for i in infos:
         assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
-    value = world * args.steps / (ms * 1e-3)
+    value = job_rate(world, args.steps, ms * 1e-3)
     launches = int(sum(i["kernel_launches"] for i in infos))
 
     fp64 = None
@@ -315,12 +330,8 @@ def run_ours(args):
     for _ in range(e2e_steps):
         op.solve(bh, xh, params=pm)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+    e2e_s = replica_max(time.perf_counter() - t0, f"cuda:{dev}")
+    e2e = {"value": job_rate(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n}
 
     # per-kernel profile of one more solve (CUDA events around every launch on the op's stream)

@@ -234,7 +234,12 @@ int hz_get_history(hz_op op, double* hist, int cap);
  * Autotuner for the column kernels (not in the paper: a launch-shape search).
  * The Thomas kernels (k_pre_p, k_pre_s) and the stencil kernels (k_mv) come
  * in variants: vec columns per thread (vector loads; vec must divide nx) and
- * depth levels per software-pipelined batch.  hz_op_autotune times every
+ * depth levels per software-pipelined batch; a Thomas variant also fixes
+ * where the forward sweep waits for the back sweep (the output vector, shared
+ * memory, or the output vector stored with the L2 evict-last priority while
+ * the streamed arrays are evict-first) and may cap the resident blocks per
+ * SM.  All variants of a kernel compute the same values; dot partial sums
+ * follow the launch shape.  hz_op_autotune times every
  * valid variant on the operator's own arrays (3 launches each, CUDA events on
  * the operator's stream) and keeps the fastest; flags bit 0 also tunes the
  * FP64 kernels (allocating the FP64 work vectors); flags bit 1 also tunes the

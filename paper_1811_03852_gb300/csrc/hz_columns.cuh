@@ -8,6 +8,8 @@
 // of U consecutive levels are issued before any of them is used.
 #pragma once
 
+#include <type_traits>
+
 #include "hz_internal.cuh"
 
 namespace hz {
@@ -19,8 +21,91 @@ struct Pack {
 
 // vector load.  M = LD_PLAIN: coherent (data this thread wrote); LD_NC: read-only
 // for the whole launch (non-coherent path); LD_CG: written earlier in the same
-// launch by other blocks (L2 only, never a stale L1 line)
-enum LoadMode : int { LD_PLAIN = 0, LD_NC = 1, LD_CG = 2 };
+// launch by other blocks (L2 only, never a stale L1 line).  LD_NC_EF and
+// LD_PLAIN_EF are LD_NC and LD_PLAIN with the L2 evict-first priority: for
+// arrays that stream through once per launch, so that L2 keeps what is re-read
+// (the parked forward sweep of a Thomas variant, stored evict-last).
+enum LoadMode : int { LD_PLAIN = 0, LD_NC = 1, LD_CG = 2, LD_NC_EF = 3, LD_PLAIN_EF = 4 };
+// store priority in L2: ST_PLAIN (normal), ST_EF (evict first), ST_EL (evict last)
+enum StoreMode : int { ST_PLAIN = 0, ST_EF = 1, ST_EL = 2 };
+
+// L2 cache policies (PTX createpolicy, fraction 1.0: every access of the
+// instruction that carries the policy gets the priority)
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// loads with an L2 cache policy, by width: 4, 8 or 16 bytes (FP32 x1/x2/x4, FP64 x1/x2)
+template <typename W, bool NC>
+__device__ __forceinline__ W ld_hint(const W* p, uint64_t pol) {
+  W r;
+  if constexpr (std::is_same<W, float>::value) {
+    if constexpr (NC)
+      asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+    else
+      asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol) : "memory");
+  } else if constexpr (std::is_same<W, float2>::value) {
+    if constexpr (NC)
+      asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.x), "=f"(r.y) : "l"(p), "l"(pol));
+    else
+      asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                   : "=f"(r.x), "=f"(r.y)
+                   : "l"(p), "l"(pol)
+                   : "memory");
+  } else if constexpr (std::is_same<W, float4>::value) {
+    if constexpr (NC)
+      asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+          : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+          : "l"(p), "l"(pol));
+    else
+      asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                   : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                   : "l"(p), "l"(pol)
+                   : "memory");
+  } else if constexpr (std::is_same<W, double>::value) {
+    if constexpr (NC)
+      asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+    else
+      asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol) : "memory");
+  } else {
+    static_assert(std::is_same<W, double2>::value, "unsupported load width");
+    if constexpr (NC)
+      asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(p), "l"(pol));
+    else
+      asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                   : "=d"(r.x), "=d"(r.y)
+                   : "l"(p), "l"(pol)
+                   : "memory");
+  }
+  return r;
+}
+
+template <typename W>
+__device__ __forceinline__ void st_hint(W* p, const W& v, uint64_t pol) {
+  if constexpr (std::is_same<W, float>::value) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+  } else if constexpr (std::is_same<W, float2>::value) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+  } else if constexpr (std::is_same<W, float4>::value) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+  } else if constexpr (std::is_same<W, double>::value) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+  } else {
+    static_assert(std::is_same<W, double2>::value, "unsupported store width");
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+  }
+}
 
 template <typename W, int M>
 __device__ __forceinline__ W ldw(const W* p) {
@@ -28,8 +113,22 @@ __device__ __forceinline__ W ldw(const W* p) {
     return __ldg(p);
   else if constexpr (M == LD_CG)
     return __ldcg(p);
+  else if constexpr (M == LD_NC_EF)
+    return ld_hint<W, true>(p, l2_evict_first());
+  else if constexpr (M == LD_PLAIN_EF)
+    return ld_hint<W, false>(p, l2_evict_first());
   else
     return *p;
+}
+
+template <typename W, int S>
+__device__ __forceinline__ void stw(W* p, const W& v) {
+  if constexpr (S == ST_EF)
+    st_hint<W>(p, v, l2_evict_first());
+  else if constexpr (S == ST_EL)
+    st_hint<W>(p, v, l2_evict_last());
+  else
+    *p = v;
 }
 
 template <typename T, int V, int M>
@@ -57,16 +156,16 @@ __device__ __forceinline__ Pack<T, V> ldp(const T* p) {
   return r;
 }
 
-template <typename T, int V>
+template <typename T, int V, int S = ST_PLAIN>
 __device__ __forceinline__ void stp(T* p, const Pack<T, V>& v) {
   if constexpr (V == 1) {
-    *p = v.a[0];
+    stw<T, S>(p, v.a[0]);
   } else if constexpr (sizeof(T) == 4 && V == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
+    stw<float4, S>(reinterpret_cast<float4*>(p), make_float4(v.a[0], v.a[1], v.a[2], v.a[3]));
   } else if constexpr (sizeof(T) == 4 && V == 2) {
-    *reinterpret_cast<float2*>(p) = make_float2(v.a[0], v.a[1]);
+    stw<float2, S>(reinterpret_cast<float2*>(p), make_float2(v.a[0], v.a[1]));
   } else if constexpr (sizeof(T) == 8 && V == 2) {
-    *reinterpret_cast<double2*>(p) = make_double2(v.a[0], v.a[1]);
+    stw<double2, S>(reinterpret_cast<double2*>(p), make_double2(v.a[0], v.a[1]));
   }
 }
 
@@ -90,16 +189,27 @@ __device__ __forceinline__ GroupNbr group_nbr(const Grid& g, int64_t c0) {
   return n;
 }
 
+// Where a Thomas variant parks the forward sweep y until the back sweep reads
+// it: PARK_OUT in the output vector (an L2 hit while the columns in flight fit
+// in L2), PARK_SMEM in shared memory, PARK_OUT_L2 in the output vector stored
+// with the L2 evict-last priority while every streamed array is loaded and
+// stored evict-first, so that the parked values are the last to leave L2.
+enum ParkMode : int { PARK_OUT = 0, PARK_SMEM = 1, PARK_OUT_L2 = 2 };
+
 // Thomas algorithm on V columns with unit diagonal and pre-computed factors:
 // forward y_k = m_k q_k - l_k y_(k-1), back z_k = y_k - c'_k z_(k+1).  The
 // input q_k = src.make(values src.load fetched for level k) is the fused
-// axpy.  y is parked in out and re-read by the back sweep (an L2 hit while the
-// column's footprint stays in L2), or with SM in shared memory ys laid out
-// [level][thread][V] (kBS * V values per level), which keeps it off L2 and HBM.
-template <typename T, int V, int U, typename Src, bool SM = false>
+// axpy.  y is parked in out and re-read by the back sweep (PARK_OUT,
+// PARK_OUT_L2), or in shared memory ys laid out [level][thread][V] (kBS * V
+// values per level; PARK_SMEM), which keeps it off L2 and HBM.
+template <typename T, int V, int U, typename Src, int P = PARK_OUT>
 __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* __restrict__ m,
                                            const T* __restrict__ l, const T* __restrict__ cp, T* __restrict__ out,
                                            Src& src, T* ys = nullptr) {
+  constexpr bool SM = P == PARK_SMEM;
+  constexpr int LF = P == PARK_OUT_L2 ? LD_NC_EF : LD_NC;      // factors: streamed once
+  constexpr int SY = P == PARK_OUT_L2 ? ST_EL : ST_PLAIN;      // y: re-read by the back sweep
+  constexpr int SZ = P == PARK_OUT_L2 ? ST_EF : ST_PLAIN;      // z: written once (drops y's priority)
   constexpr int NIN = Src::NIN;
   const int64_t ncol = g.ncol;
   const int nz = g.nz;
@@ -113,8 +223,8 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
       if (k0 + u < nz) {
         const int64_t idx = (int64_t)(k0 + u) * ncol + c0;
         src.load(idx, v[u]);
-        mm[u] = ldp<T, V, LD_NC>(m + idx);
-        ll[u] = ldp<T, V, LD_NC>(l + idx);
+        mm[u] = ldp<T, V, LF>(m + idx);
+        ll[u] = ldp<T, V, LF>(l + idx);
       }
     }
 #pragma unroll
@@ -131,7 +241,7 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
         if constexpr (SM)
           stp(ys + ((int64_t)(k0 + u) * kBS + threadIdx.x) * V, y);
         else
-          stp(out + idx, y);
+          stp<T, V, SY>(out + idx, y);
       }
     }
     src.flush();
@@ -149,7 +259,7 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
           yy[u] = ldp<T, V, LD_PLAIN>(ys + ((int64_t)(k0 - u) * kBS + threadIdx.x) * V);
         else
           yy[u] = ldp<T, V, LD_PLAIN>(out + idx);  // written by this thread above: coherent load
-        cc[u] = ldp<T, V, LD_NC>(cp + idx);
+        cc[u] = ldp<T, V, LF>(cp + idx);
       }
     }
 #pragma unroll
@@ -162,51 +272,56 @@ __device__ __forceinline__ void thomas_vec(const Grid& g, int64_t c0, const T* _
           z.a[c] = fma(-cc[u].a[c], zn[c], yy[u].a[c]);
           zn[c] = z.a[c];
         }
-        stp(out + idx, z);
+        stp<T, V, SZ>(out + idx, z);
       }
     }
   }
 }
 
 // inputs of the Thomas sweeps ------------------------------------------------
-template <typename T, int V, int M = LD_NC>
+// EF: the streamed inputs and outputs carry the L2 evict-first priority (the
+// sources of a PARK_OUT_L2 variant; M is then LD_NC)
+template <typename T, int V, int M = LD_NC, bool EF = false>
 struct SrcP {  // p = r + beta (p - omega v)
   static constexpr int NIN = 3;
+  static constexpr int MI = EF ? LD_NC_EF : M, MP = EF ? LD_PLAIN_EF : LD_PLAIN, SO = EF ? ST_EF : ST_PLAIN;
   const T* __restrict__ r;
   T* __restrict__ p;
   const T* __restrict__ v;
   T beta, omega;
   __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) {
-    o[0] = ldp<T, V, M>(r + idx);
-    o[1] = ldp<T, V, LD_PLAIN>(p + idx);
-    o[2] = ldp<T, V, M>(v + idx);
+    o[0] = ldp<T, V, MI>(r + idx);
+    o[1] = ldp<T, V, MP>(p + idx);
+    o[2] = ldp<T, V, MI>(v + idx);
   }
   __device__ __forceinline__ Pack<T, V> make(const Pack<T, V> (&o)[NIN], int64_t idx) {
     Pack<T, V> q;
 #pragma unroll
     for (int c = 0; c < V; ++c) q.a[c] = fma(beta, fma(-omega, o[2].a[c], o[1].a[c]), o[0].a[c]);
-    stp(p + idx, q);
+    stp<T, V, SO>(p + idx, q);
     return q;
   }
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V, int M = LD_NC>
+template <typename T, int V, int M = LD_NC, bool EF = false>
 struct SrcCopy {  // q = r, optionally stored to dst
   static constexpr int NIN = 1;
+  static constexpr int MI = EF ? LD_NC_EF : M, SO = EF ? ST_EF : ST_PLAIN;
   const T* __restrict__ r;
   T* __restrict__ dst;
-  __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) { o[0] = ldp<T, V, M>(r + idx); }
+  __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) { o[0] = ldp<T, V, MI>(r + idx); }
   __device__ __forceinline__ Pack<T, V> make(const Pack<T, V> (&o)[NIN], int64_t idx) {
-    if (dst) stp(dst + idx, o[0]);
+    if (dst) stp<T, V, SO>(dst + idx, o[0]);
     return o[0];
   }
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V, int M = LD_NC>
+template <typename T, int V, int M = LD_NC, bool EF = false>
 struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, FP64 across batches
   static constexpr int NIN = 2;
+  static constexpr int MI = EF ? LD_NC_EF : M, SO = EF ? ST_EF : ST_PLAIN;
   const T* __restrict__ r;
   const T* __restrict__ v;
   T* __restrict__ s;
@@ -214,8 +329,8 @@ struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, F
   T part;
   double acc;
   __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) {
-    o[0] = ldp<T, V, M>(r + idx);
-    o[1] = ldp<T, V, M>(v + idx);
+    o[0] = ldp<T, V, MI>(r + idx);
+    o[1] = ldp<T, V, MI>(v + idx);
   }
   __device__ __forceinline__ Pack<T, V> make(const Pack<T, V> (&o)[NIN], int64_t idx) {
     Pack<T, V> q;
@@ -224,7 +339,7 @@ struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, F
       q.a[c] = fma(-alpha, o[1].a[c], o[0].a[c]);
       part = fma(q.a[c], q.a[c], part);
     }
-    stp(s + idx, q);
+    stp<T, V, SO>(s + idx, q);
     return q;
   }
   __device__ __forceinline__ void flush() {

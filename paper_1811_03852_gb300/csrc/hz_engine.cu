@@ -660,9 +660,19 @@ bool variant_ok(int prec, int kind, int id, int nx, int nz) {
   return nx % v == 0;
 }
 
-// widest vector the row length allows (the autotuner may pick another)
+// The launch shape used until the autotuner picks one: the Thomas variant that
+// parks its forward sweep in the output vector under L2 priorities with two
+// columns per thread where the row length allows, else the widest vector the
+// row length allows.
 int default_variant(int prec, int kind, int nx) {
   int best = 0, bestv = 0;
+  if (kind == 0) {
+    for (int i = 0; i < num_variants(prec, kind); ++i) {
+      int v = 1, u = 1;
+      variant_shape(prec, kind, i, &v, &u);
+      if (variant_park_mode(prec, i) == 2 && v == 2 && nx % 2 == 0) return i;
+    }
+  }
   for (int i = 0; i < num_variants(prec, kind); ++i) {
     int v = 1, u = 1;
     variant_shape(prec, kind, i, &v, &u);

@@ -159,14 +159,18 @@ int num_variants(int prec, int kind);
 void variant_shape(int prec, int kind, int id, int* vec, int* depth);
 // the Thomas variant parks its forward sweep in shared memory (nz * kBS * vec values per block)
 bool variant_parks_smem(int prec, int kind, int id);
+// where Thomas variant id parks its forward sweep (0 output vector, 1 shared memory, 2 output vector with L2 priorities)
+int variant_park_mode(int prec, int id);
 template <typename T>
 void warm_kernels(const Launch& L);
 
 // Blocks for a grid-stride kernel: every SM filled to that kernel's own
-// occupancy (queried once per kernel and cached), capped by the work and by
-// the slots of the reduction buffer.  warm_launch_cache() queries every
-// kernel up front so that no query happens during stream capture.
-int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks, size_t smem = 0);
+// occupancy (queried once per kernel and cached) or to per_sm_cap blocks when
+// that is smaller and positive, capped by the work and by the slots of the
+// reduction buffer.  warm_launch_cache() queries every kernel up front so that
+// no query happens during stream capture.
+int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks, size_t smem = 0,
+             int per_sm_cap = 0);
 void warm_launch_cache(const Launch& L);
 
 template <typename T>

@@ -30,23 +30,28 @@ namespace hz {
 // ---- variants ----------------------------------------------------------------
 template <typename T>
 struct Variants;
-// Thomas variants with pre_sm = 1 park the forward sweep in shared memory
-// (nz * kBS * V values per block) instead of the output vector.
+// Thomas variants: V columns per thread, U levels per batch, pre_p where the
+// forward sweep is parked (ParkMode: 0 the output vector, 1 shared memory,
+// nz * kBS * V values per block, 2 the output vector with L2 priorities) and
+// pre_b resident blocks per SM (0: as many as fit).  Fewer resident columns
+// keep the parked sweep of every column in flight inside L2.
 template <>
 struct Variants<float> {
-  static constexpr int NPRE = 9, NMV = 4;
-  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4};
-  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2};
-  static constexpr int pre_sm[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1};
+  static constexpr int NPRE = 13, NMV = 4;
+  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2};
+  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4};
+  static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};
+  static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3};
   static constexpr int mv_v[NMV] = {1, 4, 2, 2};
   static constexpr int mv_u[NMV] = {4, 1, 2, 1};
 };
 template <>
 struct Variants<double> {
-  static constexpr int NPRE = 3, NMV = 3;
-  static constexpr int pre_v[NPRE] = {1, 2, 2};
-  static constexpr int pre_u[NPRE] = {4, 2, 1};
-  static constexpr int pre_sm[NPRE] = {0, 0, 0};
+  static constexpr int NPRE = 6, NMV = 3;
+  static constexpr int pre_v[NPRE] = {1, 2, 2, 2, 2, 1};
+  static constexpr int pre_u[NPRE] = {4, 2, 1, 1, 1, 4};
+  static constexpr int pre_p[NPRE] = {0, 0, 0, 2, 2, 2};
+  static constexpr int pre_b[NPRE] = {0, 0, 0, 3, 0, 0};
   static constexpr int mv_v[NMV] = {1, 2, 1};
   static constexpr int mv_u[NMV] = {2, 1, 1};
 };
@@ -57,9 +62,9 @@ constexpr int kMinBlocks = 6;  // launch bound of the column kernels: at most 80
 // limit (below the 227 KB opt-in maximum, which also holds the kernels' static
 // reduction buffers)
 constexpr size_t kParkMax = 200 * 1024;
-template <typename T, int V, bool SM>
+template <typename T, int V, int P>
 constexpr size_t park_bytes(int nz) {
-  return SM ? (size_t)nz * kBS * V * sizeof(T) : 0;
+  return P == PARK_SMEM ? (size_t)nz * kBS * V * sizeof(T) : 0;
 }
 
 template <typename T>
@@ -199,16 +204,17 @@ __device__ __noinline__ double restart_column(const Grid& g, int64_t col, const 
 // dynamic shared memory of the variants that park the forward sweep there
 extern __shared__ __align__(16) unsigned char hz_park[];
 
-template <typename T, int V, int U, bool SM>
+template <typename T, int V, int U, int P>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_p(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl) {
   if (ctl->state != ST_RUNNING || ctl->fresh) return;
+  using S = SrcP<T, V, LD_NC, P == PARK_OUT_L2>;
   T* ys = reinterpret_cast<T*>(hz_park);
   const T beta = (T)ctl->beta, omega = (T)ctl->omega;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
-    SrcP<T, V> src{rin, w.p, w.v, beta, omega};
-    thomas_vec<T, V, U, SrcP<T, V>, SM>(g, q * V, a.m, a.l, a.cp, w.ph, src, ys);
+    S src{rin, w.p, w.v, beta, omega};
+    thomas_vec<T, V, U, S, P>(g, q * V, a.m, a.l, a.cp, w.ph, src, ys);
   }
 }
 
@@ -264,17 +270,18 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs
 
 // ---------------------------------------------------------------------------
 // k_pre_s: s = r - alpha v, <s, s> (half-step exit test), sh = T^-1 s
-template <typename T, int V, int U, bool SM>
+template <typename T, int V, int U, int P>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_s(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
+  using S = SrcS<T, V, LD_NC, P == PARK_OUT_L2>;
   T* ys = reinterpret_cast<T*>(hz_park);
   const T alpha = (T)ctl->alpha;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
   double acc = 0.0;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
-    SrcS<T, V> src{rin, w.v, w.s, alpha, T(0), 0.0};
-    thomas_vec<T, V, U, SrcS<T, V>, SM>(g, q * V, a.m, a.l, a.cp, w.sh, src, ys);
+    S src{rin, w.v, w.s, alpha, T(0), 0.0};
+    thomas_vec<T, V, U, S, P>(g, q * V, a.m, a.l, a.cp, w.sh, src, ys);
     acc += src.acc;
   }
   double vv[1] = {acc}, out[1];
@@ -411,14 +418,15 @@ __global__ void __launch_bounds__(kBS) k_matvec_hat(Grid g, Bands<T> a, const T*
   }
 }
 
-template <typename T, int V, int U, bool SM>
+template <typename T, int V, int U, int P>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_tinv(Grid g, Bands<T> a, const T* __restrict__ r,
                                                           T* __restrict__ z) {
+  using S = SrcCopy<T, V, LD_NC, P == PARK_OUT_L2>;
   T* ys = reinterpret_cast<T*>(hz_park);
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
-    SrcCopy<T, V> src{r, nullptr};
-    thomas_vec<T, V, U, SrcCopy<T, V>, SM>(g, q * V, a.m, a.l, a.cp, z, src, ys);
+    S src{r, nullptr};
+    thomas_vec<T, V, U, S, P>(g, q * V, a.m, a.l, a.cp, z, src, ys);
   }
 }
 
@@ -437,7 +445,7 @@ cudaError_t with_pre(int var, F&& f) {
   if constexpr (I < Variants<T>::NPRE) {
     if (var == I)
       return f(std::integral_constant<int, Variants<T>::pre_v[I]>{}, std::integral_constant<int, Variants<T>::pre_u[I]>{},
-               std::integral_constant<bool, Variants<T>::pre_sm[I] != 0>{});
+               std::integral_constant<int, Variants<T>::pre_p[I]>{}, Variants<T>::pre_b[I]);
     return with_pre<T, I + 1>(var, f);
   } else {
     return cudaErrorInvalidValue;
@@ -462,24 +470,23 @@ inline int64_t blocks_for(int64_t items, int block) { return (items + block - 1)
 template <typename T>
 cudaError_t launch_pre_p_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
   k_pre_start<T><<<grid_for((const void*)k_pre_start<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
-  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Sc) {
-    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    constexpr bool SM = decltype(Sc)::value;
-    const void* k = (const void*)k_pre_p<T, V, U, SM>;
-    const size_t sm = park_bytes<T, V, SM>(g.nz);
-    k_pre_p<T, V, U, SM><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm), kBS, sm, L.stream>>>(g, a, w, ctl);
+  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
+    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+    const void* k = (const void*)k_pre_p<T, V, U, P>;
+    const size_t sm = park_bytes<T, V, P>(g.nz);
+    k_pre_p<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, w,
+                                                                                                          ctl);
     return cudaGetLastError();
   });
 }
 template <typename T>
 cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Sc) {
-    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    constexpr bool SM = decltype(Sc)::value;
-    const void* k = (const void*)k_pre_s<T, V, U, SM>;
-    const size_t sm = park_bytes<T, V, SM>(g.nz);
-    k_pre_s<T, V, U, SM><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm), kBS, sm, L.stream>>>(g, a, w, ctl,
-                                                                                                      red);
+  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
+    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+    const void* k = (const void*)k_pre_s<T, V, U, P>;
+    const size_t sm = park_bytes<T, V, P>(g.nz);
+    k_pre_s<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, w,
+                                                                                                          ctl, red);
     return cudaGetLastError();
   });
 }
@@ -507,12 +514,11 @@ cudaError_t launch_matvec_hat_t(const Grid& g, const Bands<T>& a, const T* x, T*
 }
 template <typename T>
 cudaError_t launch_tinv_t(const Grid& g, const Bands<T>& a, const T* r, T* z, const Launch& L) {
-  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Sc) {
-    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    constexpr bool SM = decltype(Sc)::value;
-    const void* k = (const void*)k_tinv<T, V, U, SM>;
-    const size_t sm = park_bytes<T, V, SM>(g.nz);
-    k_tinv<T, V, U, SM><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm), kBS, sm, L.stream>>>(g, a, r, z);
+  return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
+    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+    const void* k = (const void*)k_tinv<T, V, U, P>;
+    const size_t sm = park_bytes<T, V, P>(g.nz);
+    k_tinv<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, r, z);
     return cudaGetLastError();
   });
 }
@@ -535,12 +541,12 @@ void warm_t(const Launch& L) {
   grid_for((const void*)k_upd<T>, 256, L, 1);
   grid_for((const void*)k_matvec_hat<T>, kBS, L, 1);
   for (int i = 0; i < Variants<T>::NPRE; ++i)
-    with_pre<T>(i, [&](auto Vc, auto Uc, auto Sc) {
-      constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-      constexpr bool SM = decltype(Sc)::value;
-      const size_t sm = park_bytes<T, V, SM>(L.nz);
-      const void* ks[3] = {(const void*)k_pre_p<T, V, U, SM>, (const void*)k_pre_s<T, V, U, SM>,
-                           (const void*)k_tinv<T, V, U, SM>};
+    with_pre<T>(i, [&](auto Vc, auto Uc, auto Pc, int) {
+      constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+      constexpr bool SM = P == PARK_SMEM;
+      const size_t sm = park_bytes<T, V, P>(L.nz);
+      const void* ks[3] = {(const void*)k_pre_p<T, V, U, P>, (const void*)k_pre_s<T, V, U, P>,
+                           (const void*)k_tinv<T, V, U, P>};
       for (const void* k : ks) {
         if (sm > kParkMax) continue;  // the variant is not valid for this nz
         if (SM && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kParkMax) != cudaSuccess)

@@ -13,7 +13,7 @@ std::mutex g_occ_mu;
 std::map<std::pair<const void*, size_t>, int> g_occ;  // blocks per SM of each (kernel, dynamic smem)
 }  // namespace
 
-int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks, size_t smem) {
+int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks, size_t smem, int per_sm_cap) {
   int per_sm = 0;
   {
     std::lock_guard<std::mutex> lk(g_occ_mu);
@@ -29,6 +29,7 @@ int grid_for(const void* kernel, int block, const Launch& L, int64_t work_blocks
       g_occ[key] = per_sm;
     }
   }
+  if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
   int64_t gsz = (int64_t)per_sm * L.sms;
   if (gsz > work_blocks) gsz = work_blocks;
   if (gsz > kMaxGrid) gsz = kMaxGrid;
@@ -70,7 +71,11 @@ int num_variants(int prec, int kind) {
 
 bool variant_parks_smem(int prec, int kind, int id) {
   if (kind != 0) return false;
-  return prec == 0 ? Variants<float>::pre_sm[id] != 0 : Variants<double>::pre_sm[id] != 0;
+  return (prec == 0 ? Variants<float>::pre_p[id] : Variants<double>::pre_p[id]) == PARK_SMEM;
+}
+
+int variant_park_mode(int prec, int id) {
+  return prec == 0 ? Variants<float>::pre_p[id] : Variants<double>::pre_p[id];
 }
 
 void variant_shape(int prec, int kind, int id, int* vec, int* depth) {

@@ -188,7 +188,7 @@ def test_every_column_variant_matches_oracle(shape, prec):
     L = hz.load()
     pi = 1 if prec == "fp64" else 0
     tried = 0
-    for var in range(12):
+    for var in range(16):
         for kind in (0, 1):
             args = [-1, -1, -1, -1]
             args[2 * pi + kind] = var
@@ -202,6 +202,50 @@ def test_every_column_variant_matches_oracle(shape, prec):
             ev = np.max(np.abs(host(v).reshape(nz, ny, nx) - ref_v) / scale)
             assert eph <= tol and ev <= tol, (var, kind, eph, ev)
     assert tried >= 2
+
+
+# Thomas variants that park the forward sweep in the output vector under L2
+# priorities (some with a cap on resident blocks), each paired with the plain
+# variant of the same shape (columns per thread, levels per batch)
+L2_PAIRS = {"fp32": [(3, 9), (3, 10), (3, 12), (1, 11)], "fp64": [(2, 3), (2, 4), (0, 5)]}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("shape", [(96, 72, 20), (640, 48, 70), (38, 6, 9)])
+def test_l2_priority_variants_match_plain_bitwise(shape, prec):
+    # cache priorities and grid caps change where data lives, not the
+    # arithmetic: T^-1 p and Ahat T^-1 p agree bit for bit with the plain variant
+    import torch
+
+    nx, ny, nz = shape
+    hz, A, op = _op(nx, ny, nz, z_unit="m")
+    n = nx * ny * nz
+    P = hz.HZ_PREC_FP64 if prec == "fp64" else hz.HZ_PREC_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    pi = 1 if prec == "fp64" else 0
+    p = dev(gen.normals(41, 0, n), dt)
+    L = hz.load()
+
+    def run(var):
+        args = [-1, -1, -1, -1]
+        args[2 * pi] = var
+        if L.hz_op_set_variants(op.handle, *args) != 0:
+            return None  # the shape's vector width does not divide nx
+        ph = torch.empty(n, dtype=dt, device="cuda")
+        v = torch.empty(n, dtype=dt, device="cuda")
+        op.precond_matvec(p, ph, v, P)
+        return host(ph), host(v)
+
+    tried = 0
+    for plain, hinted in L2_PAIRS[prec]:
+        a = run(plain)
+        b = run(hinted)
+        assert (a is None) == (b is None), (plain, hinted)
+        if a is None:
+            continue
+        tried += 1
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (plain, hinted)
+    assert tried >= 1
 
 
 def test_autotune_picks_valid_variants_and_solves():
@@ -229,7 +273,7 @@ def test_every_thomas_variant_solves():
     L = hz.load()
     x_ref, _ = oracle.solve(A, b, mode=oracle.MODE_FP64, tol=1e-12, eta=1e-13)
     tried = 0
-    for var in range(12):
+    for var in range(16):
         if L.hz_op_set_variants(op.handle, var, -1, -1, -1) != 0:
             continue
         tried += 1

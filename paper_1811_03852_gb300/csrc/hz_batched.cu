@@ -243,9 +243,9 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
       const int64_t q = (item - d.item0) * kBS + threadIdx.x;
       double v[1] = {0.0};
       if (q < d.g.ncol / V) {
-        SrcS<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, 0.0};
+        SrcS<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, {}};
         thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.sh, src);
-        v[0] = src.acc;
+        v[0] = src.acc.value();
       }
       block_add<1>(v, &acc[s][0]);
     }
@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
       if (q < d.g.ncol / V) {
         const bool half = c.state == ST_HALF;
         const float* r0 = c.r0sel ? d.w.r0 : d.w.rhs;
+        DotAcc<float> u0{}, u1{};
         for (int k = 0; k < d.g.nz; ++k) {
           const int64_t idx = (int64_t)k * d.g.ncol + q * V;
           Pack<float, V> xv, pv = ldp<float, V, LD_CG>(d.w.ph + idx);
@@ -318,11 +319,13 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
               a1 = fmaf(rv.a[u], rv.a[u], a1);
             }
             stp(d.w.r + idx, rv);
-            v[0] += (double)a0;
-            v[1] += (double)a1;
+            u0.add(a0);
+            u1.add(a1);
           }
           stp(d.w.x + idx, xv);
         }
+        v[0] = u0.value();
+        v[1] = u1.value();
       }
       block_add<2>(v, &acc[s][0]);
     }

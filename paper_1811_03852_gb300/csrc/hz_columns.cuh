@@ -42,18 +42,21 @@ __device__ __forceinline__ uint64_t l2_evict_last() {
   return p;
 }
 
-// loads with an L2 cache policy, by width: 4, 8 or 16 bytes (FP32 x1/x2/x4, FP64 x1/x2)
+// loads with an L2 cache policy, by width: 4, 8 or 16 bytes (FP32 x1/x2/x4,
+// FP64 x1/x2).  volatile keeps them in program order: the column kernels issue
+// a whole batch of loads before the first use, and a compiler free to sink an
+// asm load next to its use would serialise the batch.
 template <typename W, bool NC>
 __device__ __forceinline__ W ld_hint(const W* p, uint64_t pol) {
   W r;
   if constexpr (std::is_same<W, float>::value) {
     if constexpr (NC)
-      asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+      asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
     else
       asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol) : "memory");
   } else if constexpr (std::is_same<W, float2>::value) {
     if constexpr (NC)
-      asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.x), "=f"(r.y) : "l"(p), "l"(pol));
+      asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.x), "=f"(r.y) : "l"(p), "l"(pol));
     else
       asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
                    : "=f"(r.x), "=f"(r.y)
@@ -61,7 +64,7 @@ __device__ __forceinline__ W ld_hint(const W* p, uint64_t pol) {
                    : "memory");
   } else if constexpr (std::is_same<W, float4>::value) {
     if constexpr (NC)
-      asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
           : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
           : "l"(p), "l"(pol));
     else
@@ -71,13 +74,13 @@ __device__ __forceinline__ W ld_hint(const W* p, uint64_t pol) {
                    : "memory");
   } else if constexpr (std::is_same<W, double>::value) {
     if constexpr (NC)
-      asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+      asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
     else
       asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol) : "memory");
   } else {
     static_assert(std::is_same<W, double2>::value, "unsupported load width");
     if constexpr (NC)
-      asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(p), "l"(pol));
+      asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(p), "l"(pol));
     else
       asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
                    : "=d"(r.x), "=d"(r.y)
@@ -318,8 +321,11 @@ struct SrcCopy {  // q = r, optionally stored to dst
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V, int M = LD_NC, bool EF = false>
-struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, FP64 across batches
+// DOT: also accumulate <s, s> (FP32 (or FP64) over one batch, DotAcc across
+// batches); the single-system solver leaves it to the stencil kernel, which
+// reads s anyway, and keeps the Thomas sweep free of it
+template <typename T, int V, int M = LD_NC, bool EF = false, bool DOT = true>
+struct SrcS {  // s = r - alpha v
   static constexpr int NIN = 2;
   static constexpr int MI = EF ? LD_NC_EF : M, SO = EF ? ST_EF : ST_PLAIN;
   const T* __restrict__ r;
@@ -327,7 +333,7 @@ struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, F
   T* __restrict__ s;
   T alpha;
   T part;
-  double acc;
+  DotAcc<T> acc;
   __device__ __forceinline__ void load(int64_t idx, Pack<T, V> (&o)[NIN]) {
     o[0] = ldp<T, V, MI>(r + idx);
     o[1] = ldp<T, V, MI>(v + idx);
@@ -337,27 +343,40 @@ struct SrcS {  // s = r - alpha v, with <s, s>: FP32 (or FP64) over one batch, F
 #pragma unroll
     for (int c = 0; c < V; ++c) {
       q.a[c] = fma(-alpha, o[1].a[c], o[0].a[c]);
-      part = fma(q.a[c], q.a[c], part);
+      if constexpr (DOT) part = fma(q.a[c], q.a[c], part);
     }
     stp<T, V, SO>(s + idx, q);
     return q;
   }
   __device__ __forceinline__ void flush() {
-    acc += (double)part;
-    part = T(0);
+    if constexpr (DOT) {
+      acc.add(part);
+      part = T(0);
+    }
   }
 };
 
 // y = c + H x on V columns, U levels per batch (H = E, W, N, S bands of Ahat).
 // MODE 0: d0 += <r0, y>.  MODE 1: d0 += <y, c>, d1 += <y, y>.  MODE 2: no dots.
-// Each batch's dot partial is FP32 (FP64 solver: FP64) and is added to the
-// FP64 accumulators once per batch.
-template <typename T, int V, int U, int MODE, int M = LD_NC>
+// MODE 3: as MODE 1 and *d2 += <c, c>.
+// Each batch's dot partial is FP32 (FP64 solver: FP64); the batches of the
+// group are summed in a DotAcc and the group's total is added to the FP64
+// accumulators.  EF (with M = LD_NC): every array read
+// once (c, the bands, r0) and y carry the L2 evict-first priority, so that
+// the rows of x, read again as the north and south neighbours of the next
+// rows, stay in L2.
+template <typename T, int V, int U, int MODE, int M = LD_NC, bool EF = false>
 __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T>& a, const T* __restrict__ cen,
                                         const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ r0,
-                                        double& d0, double& d1) {
+                                        double& d0, double& d1, double* d2 = nullptr) {
+  static_assert(!EF || M == LD_NC, "L2 priorities with read-only loads only");
+  constexpr bool TWO = MODE == 1 || MODE == 3;  // <y, c> and <y, y>
+  constexpr int MS = EF ? LD_NC_EF : M;         // streamed vectors
+  constexpr int MB = EF ? LD_NC_EF : LD_NC;     // bands
+  constexpr int SY = EF ? ST_EF : ST_PLAIN;
   const GroupNbr nb = group_nbr<V>(g, c0);
   const int64_t ncol = g.ncol, nx = g.nx;
+  DotAcc<T> s0{}, s1{}, s2{};
   for (int k0 = 0; k0 < g.nz; k0 += U) {
     Pack<T, V> cc[U], e[U], w[U], nn[U], ss[U], xc[U], xn[U], xs[U], q[U];
     T xw1[U], xe1[U];
@@ -365,30 +384,30 @@ __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T
     for (int u = 0; u < U; ++u) {
       if (k0 + u < g.nz) {
         const int64_t idx = (int64_t)(k0 + u) * ncol + c0;
-        cc[u] = ldp<T, V, M>(cen + idx);
-        e[u] = ldp<T, V, LD_NC>(a.E + idx);
-        w[u] = ldp<T, V, LD_NC>(a.W + idx);
+        cc[u] = ldp<T, V, MS>(cen + idx);
+        e[u] = ldp<T, V, MB>(a.E + idx);
+        w[u] = ldp<T, V, MB>(a.W + idx);
         if constexpr (V > 1) xc[u] = ldp<T, V, M>(x + idx);
         xw1[u] = ldw<T, M>(x + idx + nb.w_off);
         xe1[u] = ldw<T, M>(x + idx + nb.e_off);
         if (nb.hn) {
-          nn[u] = ldp<T, V, LD_NC>(a.N + idx);
+          nn[u] = ldp<T, V, MB>(a.N + idx);
           xn[u] = ldp<T, V, M>(x + idx + nx);
         } else {
 #pragma unroll
           for (int c = 0; c < V; ++c) nn[u].a[c] = xn[u].a[c] = T(0);
         }
         if (nb.hs) {
-          ss[u] = ldp<T, V, LD_NC>(a.S + idx);
+          ss[u] = ldp<T, V, MB>(a.S + idx);
           xs[u] = ldp<T, V, M>(x + idx - nx);
         } else {
 #pragma unroll
           for (int c = 0; c < V; ++c) ss[u].a[c] = xs[u].a[c] = T(0);
         }
-        if constexpr (MODE == 0) q[u] = ldp<T, V, M>(r0 + idx);
+        if constexpr (MODE == 0) q[u] = ldp<T, V, MS>(r0 + idx);
       }
     }
-    T p0 = T(0), p1 = T(0);
+    T p0 = T(0), p1 = T(0), p2 = T(0);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (k0 + u < g.nz) {
@@ -405,17 +424,22 @@ __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T
           yy.a[c] = t;
           if constexpr (MODE == 0) {
             p0 = fma(q[u].a[c], t, p0);
-          } else if constexpr (MODE == 1) {
+          } else if constexpr (TWO) {
             p0 = fma(t, cc[u].a[c], p0);
             p1 = fma(t, t, p1);
+            if constexpr (MODE == 3) p2 = fma(cc[u].a[c], cc[u].a[c], p2);
           }
         }
-        stp(y + idx, yy);
+        stp<T, V, SY>(y + idx, yy);
       }
     }
-    d0 += (double)p0;
-    d1 += (double)p1;
+    if constexpr (MODE != 2) s0.add(p0);
+    if constexpr (TWO) s1.add(p1);
+    if constexpr (MODE == 3) s2.add(p2);
   }
+  if constexpr (MODE != 2) d0 += s0.value();
+  if constexpr (TWO) d1 += s1.value();
+  if constexpr (MODE == 3) *d2 += s2.value();
 }
 
 }  // namespace hz

@@ -367,14 +367,15 @@ int profiled_iteration(hz_op op) {
   if (c->state != ST_RUNNING) return HZ_OK;
   CKS(prof_launch(op, 3, 8 * B * n, [&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }));
   CKS(prof_launch(op, 4, 7 * B * n, [&] { return launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L); }));
-  op->launches += 2;
+  // k_mv<1> also takes the half-step test on ||s||: the state after it says
+  // which update k_upd makes
+  CKS(prof_launch(op, 5, 7 * B * n, [&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); }));
+  op->launches += 3;
   CKS(state(c));
   const bool half = c->state == ST_HALF;
-  if (!half)
-    CKS(prof_launch(op, 5, 7 * B * n, [&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); }));
   const double bu = half ? (xz ? 2 : 3) * B : (xz ? 7 : 8) * B;
   CKS(prof_launch(op, 6, bu * n, [&] { return launch_upd<T>(op->g, w, op->ctl, op->red, 0ull, 0, L); }));
-  op->launches += half ? 1 : 2;
+  op->launches += 1;
   return HZ_OK;
 }
 

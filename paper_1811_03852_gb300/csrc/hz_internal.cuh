@@ -71,6 +71,34 @@ struct Vecs {  // inner Krylov vectors
   T *rhs, *r, *r0, *p, *ph, *v, *s, *sh, *t, *x;
 };
 
+// Running sum of a dot product's per-batch partials within one thread.  FP32:
+// an unevaluated pair hi + lo updated by Knuth's TwoSum (error-free in
+// round-to-nearest, Knuth, TAOCP vol. 2, Sec. 4.2.2), which carries about 48
+// significant bits with FP32 additions only, so the loop issues no FP64
+// instruction (FP64 issue is scarce on this GPU and a per-batch FP64 add
+// stalls every warp at the batch boundary).  The thread's total is read once,
+// in FP64, by the grid reduction.  FP64: a plain double.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+  float hi, lo;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bv = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(x, bv));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct DotAcc<double> {
+  double s;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
 // Deterministic block + grid reduction of ND doubles.  Every block stores its
 // partial in a fixed slot; the last block to arrive (ticket) sums the slots in
 // slot order, so the result depends only on the launch shape.  Returns true in

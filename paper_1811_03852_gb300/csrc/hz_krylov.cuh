@@ -9,8 +9,8 @@
 //   k_pre_start : first iteration after a start (p = r) or a restart (Sec. 4)
 //   k_pre_p     : p = r + beta (p - omega v)         then ph = T^-1 p    (Thomas along k)
 //   k_mv<0>     : v = p + H ph,  <r0, v>  -> alpha   (T ph = p, so Ahat ph = p + H ph)
-//   k_pre_s     : s = r - alpha v, <s, s>            then sh = T^-1 s
-//   k_mv<1>     : t = s + H sh,  <t, s>, <t, t> -> omega
+//   k_pre_s     : s = r - alpha v                    then sh = T^-1 s
+//   k_mv<1>     : t = s + H sh,  <t, s>, <t, t>, <s, s> -> half-step exit test, omega
 //   k_upd       : x += alpha ph + omega sh, r = s - omega t, <r0, r>, <r, r> -> beta, stop/restart
 //
 // H = the four horizontal bands (E, W, N, S) of Ahat.  Column kernels come in
@@ -34,26 +34,30 @@ struct Variants;
 // forward sweep is parked (ParkMode: 0 the output vector, 1 shared memory,
 // nz * kBS * V values per block, 2 the output vector with L2 priorities) and
 // pre_b resident blocks per SM (0: as many as fit).  Fewer resident columns
-// keep the parked sweep of every column in flight inside L2.
+// keep the parked sweep of every column in flight inside L2.  Stencil
+// variants: mv_v columns per thread, mv_u levels per batch, mv_h L2 priorities
+// (the arrays read once evict-first, so that rows of x stay in L2).
 template <>
 struct Variants<float> {
-  static constexpr int NPRE = 13, NMV = 4;
+  static constexpr int NPRE = 13, NMV = 7;
   static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2};
   static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4};
   static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};
   static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3};
-  static constexpr int mv_v[NMV] = {1, 4, 2, 2};
-  static constexpr int mv_u[NMV] = {4, 1, 2, 1};
+  static constexpr int mv_v[NMV] = {1, 4, 2, 2, 4, 2, 2};
+  static constexpr int mv_u[NMV] = {4, 1, 2, 1, 1, 2, 1};
+  static constexpr int mv_h[NMV] = {0, 0, 0, 0, 1, 1, 1};
 };
 template <>
 struct Variants<double> {
-  static constexpr int NPRE = 6, NMV = 3;
+  static constexpr int NPRE = 6, NMV = 5;
   static constexpr int pre_v[NPRE] = {1, 2, 2, 2, 2, 1};
   static constexpr int pre_u[NPRE] = {4, 2, 1, 1, 1, 4};
   static constexpr int pre_p[NPRE] = {0, 0, 0, 2, 2, 2};
   static constexpr int pre_b[NPRE] = {0, 0, 0, 3, 0, 0};
-  static constexpr int mv_v[NMV] = {1, 2, 1};
-  static constexpr int mv_u[NMV] = {2, 1, 1};
+  static constexpr int mv_v[NMV] = {1, 2, 1, 2, 1};
+  static constexpr int mv_u[NMV] = {2, 1, 1, 1, 2};
+  static constexpr int mv_h[NMV] = {0, 0, 0, 1, 1};
 };
 
 constexpr int kMinBlocks = 6;  // launch bound of the column kernels: at most 80 registers per thread
@@ -247,45 +251,47 @@ __global__ void __launch_bounds__(kBS, 4) k_pre_start(Grid g, Bands<T> a, Vecs<T
 
 // ---------------------------------------------------------------------------
 // k_mv<0>: v = p + H ph and <r0, v>  ->  alpha = rho / <r0, v>
-// k_mv<1>: t = s + H sh, <t, s> and <t, t>  ->  omega = <t,s>/<t,t>
-template <typename T, int MODE, int V, int U>
+// k_mv<1>: t = s + H sh, <t, s>, <t, t> and <s, s>  ->  the half-step exit
+// test on ||s|| (it reads every s anyway, so the test costs no traffic here;
+// in the Thomas sweep of k_pre_s the running sum slowed the sweep by a sixth),
+// then omega = <t,s>/<t,t>
+template <typename T, int MODE, int V, int U, bool H>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
   const T* __restrict__ cen = MODE == 0 ? w.p : w.s;
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
   const T* __restrict__ r0 = ctl->r0sel ? w.r0 : w.rhs;
-  double acc0 = 0.0, acc1 = 0.0;
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS)
-    hmv_vec<T, V, U, MODE>(g, q * V, a, cen, x, y, r0, acc0, acc1);
+    hmv_vec<T, V, U, MODE == 0 ? 0 : 3, LD_NC, H>(g, q * V, a, cen, x, y, r0, acc0, acc1, &acc2);
   if (MODE == 0) {
     double vv[1] = {acc0}, out[1];
     if (grid_reduce<1>(vv, red, out)) fin_alpha(ctl, out[0]);
   } else {
-    double vv[2] = {acc0, acc1}, out[2];
-    if (grid_reduce<2>(vv, red, out)) fin_omega(ctl, out[0], out[1]);
+    double vv[3] = {acc0, acc1, acc2}, out[3];
+    if (grid_reduce<3>(vv, red, out)) {
+      fin_snorm(ctl, out[2]);
+      if (ctl->state == ST_RUNNING) fin_omega(ctl, out[0], out[1]);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_pre_s: s = r - alpha v, <s, s> (half-step exit test), sh = T^-1 s
+// k_pre_s: s = r - alpha v, sh = T^-1 s (the half-step test on ||s|| follows in k_mv<1>)
 template <typename T, int V, int U, int P>
-__global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_s(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
+__global__ void __launch_bounds__(kBS, kMinBlocks) k_pre_s(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl) {
   if (ctl->state != ST_RUNNING) return;
-  using S = SrcS<T, V, LD_NC, P == PARK_OUT_L2>;
+  using S = SrcS<T, V, LD_NC, P == PARK_OUT_L2, false>;
   T* ys = reinterpret_cast<T*>(hz_park);
   const T alpha = (T)ctl->alpha;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
-  double acc = 0.0;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS) {
-    S src{rin, w.v, w.s, alpha, T(0), 0.0};
+    S src{rin, w.v, w.s, alpha, T(0), {}};
     thomas_vec<T, V, U, S, P>(g, q * V, a.m, a.l, a.cp, w.sh, src, ys);
-    acc += src.acc;
   }
-  double vv[1] = {acc}, out[1];
-  if (grid_reduce<1>(vv, red, out)) fin_snorm(ctl, out[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
   const T* __restrict__ t = w.t;
   using V = typename Vec4<T>::type;
   constexpr int VW = Vec4<T>::W;
-  double acc0 = 0.0, acc1 = 0.0;
+  DotAcc<T> acc0{}, acc1{};
   const int64_t n = g.n;
   const int64_t nv = (n % VW == 0) ? n / VW : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -379,8 +385,8 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
       }
       vstore<V>(x + e, xv);
       vstore<V>(r + e, rv);
-      acc0 += (double)a0;
-      acc1 += (double)a1;
+      acc0.add(a0);
+      acc1.add(a1);
     }
   }
   if (nv == 0) {  // scalar path for sizes that are not a multiple of the vector width
@@ -391,13 +397,13 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
         xv = fma(omega, sh[e], xv);
         const T rv = fma(-omega, t[e], s[e]);
         r[e] = rv;
-        acc0 += (double)(r0[e] * rv);
-        acc1 += (double)(rv * rv);
+        acc0.add(r0[e] * rv);
+        acc1.add(rv * rv);
       }
       x[e] = xv;
     }
   }
-  double vv[2] = {acc0, acc1}, out[2];
+  double vv[2] = {acc0.value(), acc1.value()}, out[2];
   if (grid_reduce<2>(vv, red, out)) {
     const int st = fin_iteration(ctl, half, out[0], out[1]);
     if (use_cond) cudaGraphSetConditional(cond, (st == ST_RUNNING || st == ST_RESTART) ? 1u : 0u);
@@ -430,13 +436,13 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_tinv(Grid g, Bands<T> a, co
   }
 }
 
-template <typename T, int V, int U>
+template <typename T, int V, int U, bool H>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_hmv(Grid g, Bands<T> a, const T* __restrict__ cen,
                                                          const T* __restrict__ x, T* __restrict__ y) {
   const int64_t ng = g.ncol / V;
   double d0 = 0.0, d1 = 0.0;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS)
-    hmv_vec<T, V, U, 2>(g, q * V, a, cen, x, y, nullptr, d0, d1);
+    hmv_vec<T, V, U, 2, LD_NC, H>(g, q * V, a, cen, x, y, nullptr, d0, d1);
 }
 
 // ---- variant dispatch ----------------------------------------------------------
@@ -455,7 +461,8 @@ template <typename T, int I = 0, typename F>
 cudaError_t with_mv(int var, F&& f) {
   if constexpr (I < Variants<T>::NMV) {
     if (var == I)
-      return f(std::integral_constant<int, Variants<T>::mv_v[I]>{}, std::integral_constant<int, Variants<T>::mv_u[I]>{});
+      return f(std::integral_constant<int, Variants<T>::mv_v[I]>{}, std::integral_constant<int, Variants<T>::mv_u[I]>{},
+               std::integral_constant<bool, Variants<T>::mv_h[I] != 0>{});
     return with_mv<T, I + 1>(var, f);
   } else {
     return cudaErrorInvalidValue;
@@ -486,16 +493,17 @@ cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, C
     const void* k = (const void*)k_pre_s<T, V, U, P>;
     const size_t sm = park_bytes<T, V, P>(g.nz);
     k_pre_s<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, w,
-                                                                                                          ctl, red);
+                                                                                                          ctl);
     return cudaGetLastError();
   });
 }
 template <typename T, int MODE>
 cudaError_t launch_mv_t_(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc) {
+  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    const void* k = (const void*)k_mv<T, MODE, V, U>;
-    k_mv<T, MODE, V, U><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl, red);
+    constexpr bool H = decltype(Hc)::value;
+    const void* k = (const void*)k_mv<T, MODE, V, U, H>;
+    k_mv<T, MODE, V, U, H><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl, red);
     return cudaGetLastError();
   });
 }
@@ -526,10 +534,11 @@ template <typename T>
 cudaError_t launch_precond_matvec_t(const Grid& g, const Bands<T>& a, const T* p, T* ph, T* v, const Launch& L) {
   cudaError_t e = launch_tinv_t<T>(g, a, p, ph, L);
   if (e != cudaSuccess) return e;
-  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc) {
+  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    const void* k = (const void*)k_hmv<T, V, U>;
-    k_hmv<T, V, U><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, p, ph, v);
+    constexpr bool H = decltype(Hc)::value;
+    const void* k = (const void*)k_hmv<T, V, U, H>;
+    k_hmv<T, V, U, H><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, p, ph, v);
     return cudaGetLastError();
   });
 }
@@ -556,11 +565,12 @@ void warm_t(const Launch& L) {
       return cudaSuccess;
     });
   for (int i = 0; i < Variants<T>::NMV; ++i)
-    with_mv<T>(i, [&](auto Vc, auto Uc) {
+    with_mv<T>(i, [&](auto Vc, auto Uc, auto Hc) {
       constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-      grid_for((const void*)k_mv<T, 0, V, U>, kBS, L, 1);
-      grid_for((const void*)k_mv<T, 1, V, U>, kBS, L, 1);
-      grid_for((const void*)k_hmv<T, V, U>, kBS, L, 1);
+      constexpr bool H = decltype(Hc)::value;
+      grid_for((const void*)k_mv<T, 0, V, U, H>, kBS, L, 1);
+      grid_for((const void*)k_mv<T, 1, V, U, H>, kBS, L, 1);
+      grid_for((const void*)k_hmv<T, V, U, H>, kBS, L, 1);
       return cudaSuccess;
     });
 }

@@ -255,7 +255,7 @@ struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP
   T* __restrict__ s;
   T alpha;
   T part;
-  double acc;
+  DotAcc<T> acc;
   __device__ __forceinline__ void load(int64_t idx, In& o) {
     o.r = ldp<T, V, LD_NC>(r + idx);
     o.v = ldp<T, V, LD_NC>(v + idx);
@@ -271,7 +271,7 @@ struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP
     return q;
   }
   __device__ __forceinline__ void flush() {
-    acc += (double)part;
+    acc.add(part);
     part = T(0);
   }
 };
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
         update_group<T, V, U>(rb, q0, src);
     }
   } else {
-    SrcSu<T, V> src{rin, w.v, w.s, (T)ctl->alpha, T(0), 0.0};
+    SrcSu<T, V> src{rin, w.v, w.s, (T)ctl->alpha, T(0), {}};
     for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
       const int64_t q0 = rb_group<V>(rb, hg, it);
       if (q0 < 0) continue;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
       else
         update_group<T, V, U>(rb, q0, src);
     }
-    double vv[1] = {src.acc}, o[1];
+    double vv[1] = {src.acc.value()}, o[1];
     if (grid_reduce<1>(vv, red, o)) fin_snorm(ctl, o[0]);
   }
 }
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
   const int64_t ncol = rb.ncol;
   const int nz = rb.nz;
   const int64_t hg = rb.H / V;
-  double acc0 = 0.0, acc1 = 0.0;
+  DotAcc<T> acc0{}, acc1{};
   const int64_t items = rb_items(hg);
   for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
     const int64_t q0 = rb_group<V>(rb, hg, it);
@@ -568,15 +568,15 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
           x0 = xp[u];
         }
       }
-      acc0 += (double)a0;
-      acc1 += (double)a1;
+      acc0.add(a0);
+      if (MODE == 1) acc1.add(a1);
     }
   }
   if (MODE == 0) {
-    double vv[1] = {acc0}, o[1];
+    double vv[1] = {acc0.value()}, o[1];
     if (grid_reduce<1>(vv, red, o)) fin_alpha(ctl, o[0]);
   } else {
-    double vv[2] = {acc0, acc1}, o[2];
+    double vv[2] = {acc0.value(), acc1.value()}, o[2];
     if (grid_reduce<2>(vv, red, o)) fin_omega(ctl, o[0], o[1]);
   }
 }

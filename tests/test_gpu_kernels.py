@@ -204,10 +204,12 @@ def test_every_column_variant_matches_oracle(shape, prec):
     assert tried >= 2
 
 
-# Thomas variants that park the forward sweep in the output vector under L2
-# priorities (some with a cap on resident blocks), each paired with the plain
-# variant of the same shape (columns per thread, levels per batch)
-L2_PAIRS = {"fp32": [(3, 9), (3, 10), (3, 12), (1, 11)], "fp64": [(2, 3), (2, 4), (0, 5)]}
+# Thomas variants (kind 0) that park the forward sweep in the output vector
+# under L2 priorities (some with a cap on resident blocks) and stencil variants
+# (kind 1) that stream under L2 priorities, each paired with the plain variant
+# of the same shape (columns per thread, levels per batch)
+L2_PAIRS = {"fp32": [(0, 3, 9), (0, 3, 10), (0, 3, 12), (0, 1, 11), (1, 1, 4), (1, 2, 5), (1, 3, 6)],
+            "fp64": [(0, 2, 3), (0, 2, 4), (0, 0, 5), (1, 1, 3), (1, 0, 4)]}
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -226,9 +228,9 @@ def test_l2_priority_variants_match_plain_bitwise(shape, prec):
     p = dev(gen.normals(41, 0, n), dt)
     L = hz.load()
 
-    def run(var):
+    def run(kind, var):
         args = [-1, -1, -1, -1]
-        args[2 * pi] = var
+        args[2 * pi + kind] = var
         if L.hz_op_set_variants(op.handle, *args) != 0:
             return None  # the shape's vector width does not divide nx
         ph = torch.empty(n, dtype=dt, device="cuda")
@@ -237,15 +239,15 @@ def test_l2_priority_variants_match_plain_bitwise(shape, prec):
         return host(ph), host(v)
 
     tried = 0
-    for plain, hinted in L2_PAIRS[prec]:
-        a = run(plain)
-        b = run(hinted)
-        assert (a is None) == (b is None), (plain, hinted)
+    for kind, plain, hinted in L2_PAIRS[prec]:
+        a = run(kind, plain)
+        b = run(kind, hinted)
+        assert (a is None) == (b is None), (kind, plain, hinted)
         if a is None:
             continue
         tried += 1
-        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (plain, hinted)
-    assert tried >= 1
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (kind, plain, hinted)
+    assert tried >= 2
 
 
 def test_autotune_picks_valid_variants_and_solves():
@@ -284,3 +286,28 @@ def test_every_thomas_variant_solves():
         assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8, var
         assert np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref) <= 1e-6, var
     assert tried >= 8
+
+
+def test_every_stencil_variant_solves():
+    # the solver's own stencil kernels (k_mv, with their dot products) in every
+    # FP32 and FP64 variant, in the mixed and the FP64 solver
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    A, b = gen.make_system(96, 72, 20, 7, 8, z_unit="m")
+    op = hz.Operator(A)
+    L = hz.load()
+    tried = 0
+    for pi, mode in ((0, hz.HZ_MODE_MIXED_IR), (1, hz.HZ_MODE_FP64)):
+        for var in range(16):
+            args = [-1, -1, -1, -1]
+            args[2 * pi + 1] = var
+            if L.hz_op_set_variants(op.handle, *args) != 0:
+                continue
+            tried += 1
+            x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+            info = op.solve(dev(b), x, mode=mode)
+            _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+            assert info["status"] == 0 and rn / np.linalg.norm(b) <= 1e-8, (pi, var)
+    assert tried >= 10

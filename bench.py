@@ -56,6 +56,9 @@ def parse():
                     help="override the workload's grid (same recipe and seeds; for profiling smaller cases)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven inner loop (same kernels); ncu cannot profile kernels inside conditional graphs")
+    ap.add_argument("--variants", type=int, nargs=2, metavar=("PRE32", "MV32"),
+                    help="fix the FP32 Thomas and stencil variants instead of autotuning them (profiling a known launch "
+                         "shape); FP64 and tri-SOR kernels are still tuned unless --no-fp64 / --no-trisor")
     return ap.parse_args()
 
 
@@ -194,7 +197,7 @@ def cpu_baseline(A, b, dims, outer, inner, mode_mixed=True, reps=1):
 # workloads (same algorithm and seeds; python bench.py on a GB300): the work the
 # oracle's per-piece timings are composed with where a full oracle solve would
 # take hours.
-GPU_COUNTS = {("n1280", "radius"): (3, 532)}
+GPU_COUNTS = {("n1280", "radius"): (3, 473)}
 
 
 def run_reference(args):
@@ -265,7 +268,13 @@ def run_ours(args):
     x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
     use_sor = (args.precond == "trisor" or not args.no_trisor) and nx % 2 == 0
     # launch-shape search, outside the timed region
-    variants = op.autotune(fp64=not args.no_fp64, trisor=use_sor)
+    if args.variants:
+        if not args.no_fp64 or use_sor:
+            op.autotune(fp64=not args.no_fp64, trisor=use_sor)
+        op.set_variants(pre32=args.variants[0], mv32=args.variants[1])
+        variants = op.variants()
+    else:
+        variants = op.autotune(fp64=not args.no_fp64, trisor=use_sor)
     if use_sor:
         variants["trisor"] = {f"{'fp64' if p == hz.HZ_PREC_FP64 else 'fp32'}/{('pass', 'matvec', 'first')[k]}": v
                               for (p, k), v in op.sor_variants().items()}
@@ -380,10 +389,13 @@ def run_ours(args):
         try:
             from paper_1811_03852_gb300 import _build
 
+            # DRAM bytes per launch from an ncu capture of the same workload, valid only
+            # while the kernel's source files and the autotuned variant are unchanged
             tj = json.load(open(tp))
             ent = tj.get(dom)
-            if ent and ent.get("src") == _build._deps_hash() and ent.get("workload") == args.workload:
-                traffic = ent["bytes_per_launch"]
+            kind = "mv32" if dom.startswith("k_mv") else "pre32"
+            if (ent and ent.get("workload") == args.workload and ent.get("src") == _build.src_hash(ent["files"])):
+                traffic = ent["bytes_per_launch"].get(str(variants.get(kind)))
         except Exception:
             traffic = None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

@@ -43,6 +43,18 @@ def _deps_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def src_hash(files) -> str:
+    """Hash of the named source files (relative to the package's csrc/ or include/):
+    identifies the code a profile of one kernel was taken on."""
+    h = hashlib.sha256()
+    for f in sorted(files):
+        d = INCLUDE if f.endswith(".h") else CSRC
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    h.update(" ".join(ARCH).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")

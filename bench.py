@@ -421,7 +421,10 @@ def run_ours(args):
                                f"{make_seed(args)} mixed IR tol 1e-8 eta {args.eta:g} precond {args.precond}",
                    "l2": "inputs larger than L2 (vectors 1.4-2.8 GB)", "parallelism": f"replicas x{world}"},
         "solve": {"outer": infos[0]["outer_iters"], "inner": infos[0]["inner_iters"],
-                  "true_rel_residual": infos[0]["true_rel_residual"]},
+                  "true_rel_residual": infos[0]["true_rel_residual"],
+                  "ms_per_inner": round(ms / args.steps / max(1, infos[0]["inner_iters"]), 3)},
+        "device": {"name": torch.cuda.get_device_name(dev),
+                   "sms": torch.cuda.get_device_properties(dev).multi_processor_count},
         "fp64": fp64,
         "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
         "trisor": trisor,

@@ -253,8 +253,9 @@ int hz_get_history(hz_op op, double* hist, int cap);
  */
 int hz_op_autotune(hz_op op, int flags);
 /* tri-SOR kernel variants: kind 0 = colour pass, 1 = matvec, 2 = first pass
-   (vector update fused with the first red pass); each is a (levels per
-   batch, blocks per SM) shape.  Count per prec (HZ_PREC_*) and kind (0 for an
+   (vector update fused with the first red pass); each is a (columns per
+   thread, levels per batch, blocks per SM) shape, some with L2 priorities
+   (once-read arrays evict-first, the parked forward sweep evict-last).  Count per prec (HZ_PREC_*) and kind (0 for an
    invalid pair); get/set the operator's choice (set: HZ_ERR_INVALID for an id
    out of range).  Every variant computes the same columns the same way; the
    matvec's dot partial sums follow the shape. */

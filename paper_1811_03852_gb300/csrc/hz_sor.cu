@@ -98,10 +98,15 @@ __device__ __forceinline__ Pack<T, V> zero_pack() {
 // factors: forward y_k = m_k q_k - l_k y_(k-1) with q_k = src.make(...), y
 // parked in z; back x_k = y_k - c'_k x_(k+1) and
 // z_k = (1 - omega) zold_k + omega x_k (zold == nullptr: zero).
-template <typename T, int V, int U, typename Src>
+// H: L2 priorities (the arrays read once evict-first, the parked forward
+// sweep evict-last so that it is still in L2 for the back sweep).
+template <typename T, int V, int U, typename Src, bool H = false>
 __device__ __forceinline__ void sor_group(const Rb& rb, int64_t q0, const T* __restrict__ m, const T* __restrict__ l,
                                           const T* __restrict__ cp, const T* __restrict__ zold, T* __restrict__ z,
                                           T omega, T keep, Src& src) {
+  constexpr int LF = H ? LD_NC_EF : LD_NC;
+  constexpr int SY = H ? ST_EL : ST_PLAIN;
+  constexpr int SZ = H ? ST_EF : ST_PLAIN;
   const int64_t ncol = rb.ncol;
   const int nz = rb.nz;
   T yprev[V];
@@ -115,8 +120,8 @@ __device__ __forceinline__ void sor_group(const Rb& rb, int64_t q0, const T* __r
       if (k0 + u < nz) {
         const int64_t idx = (int64_t)(k0 + u) * ncol + q0;
         src.load(idx, v[u]);
-        mm[u] = ldp<T, V, LD_NC>(m + idx);
-        ll[u] = ldp<T, V, LD_NC>(l + idx);
+        mm[u] = ldp<T, V, LF>(m + idx);
+        ll[u] = ldp<T, V, LF>(l + idx);
       }
     }
 #pragma unroll
@@ -130,7 +135,7 @@ __device__ __forceinline__ void sor_group(const Rb& rb, int64_t q0, const T* __r
           y.a[c] = fma(mm[u].a[c], q.a[c], -ll[u].a[c] * yprev[c]);
           yprev[c] = y.a[c];
         }
-        stp(z + idx, y);
+        stp<T, V, SY>(z + idx, y);
       }
     }
     src.flush();
@@ -146,8 +151,8 @@ __device__ __forceinline__ void sor_group(const Rb& rb, int64_t q0, const T* __r
       if (k0 - u >= 0) {
         const int64_t idx = (int64_t)(k0 - u) * ncol + q0;
         yy[u] = ldp<T, V, LD_PLAIN>(z + idx);  // written by this thread above: coherent load
-        cc[u] = ldp<T, V, LD_NC>(cp + idx);
-        zo[u] = zold ? ldp<T, V, LD_NC>(zold + idx) : zero_pack<T, V>();
+        cc[u] = ldp<T, V, LF>(cp + idx);
+        zo[u] = zold ? ldp<T, V, LF>(zold + idx) : zero_pack<T, V>();
       }
     }
 #pragma unroll
@@ -160,15 +165,18 @@ __device__ __forceinline__ void sor_group(const Rb& rb, int64_t q0, const T* __r
           xn[c] = fma(-cc[u].a[c], xn[c], yy[u].a[c]);
           o.a[c] = fma(keep, zo[u].a[c], omega * xn[c]);
         }
-        stp(z + idx, o);
+        stp<T, V, SZ>(z + idx, o);
       }
     }
   }
 }
 
 // inputs of the relaxed solves ------------------------------------------------
-template <typename T, int V>
+// EF: the sources' once-read arrays carry the L2 evict-first priority (the
+// other colour's z, read again by the neighbouring rows, does not)
+template <typename T, int V, bool EF = false>
 struct SrcHz {  // q = rc - (E zE + W zW + N zN + S zS); nbr == false: q = rc
+  static constexpr int MI = EF ? LD_NC_EF : LD_NC;
   struct In {
     Pack<T, V> rc, e, w, n, s, zm, zn, zs;
     T zx;
@@ -182,20 +190,20 @@ struct SrcHz {  // q = rc - (E zE + W zW + N zN + S zS); nbr == false: q = rc
   RbGrp gr;
   bool nbr;
   __device__ __forceinline__ void load(int64_t idx, In& o) {
-    o.rc = ldp<T, V, LD_NC>(rc + idx);
+    o.rc = ldp<T, V, MI>(rc + idx);
     if (nbr) {
-      o.e = ldp<T, V, LD_NC>(E + idx);
-      o.w = ldp<T, V, LD_NC>(W + idx);
+      o.e = ldp<T, V, MI>(E + idx);
+      o.w = ldp<T, V, MI>(W + idx);
       o.zm = ldp<T, V, LD_NC>(z + idx + gr.mir);
       o.zx = ldw<T, LD_NC>(z + idx + gr.xo);
       if (gr.hn) {
-        o.n = ldp<T, V, LD_NC>(N + idx);
+        o.n = ldp<T, V, MI>(N + idx);
         o.zn = ldp<T, V, LD_NC>(z + idx + gr.mir + gr.hx);
       } else {
         o.n = o.zn = zero_pack<T, V>();
       }
       if (gr.hs) {
-        o.s = ldp<T, V, LD_NC>(S + idx);
+        o.s = ldp<T, V, MI>(S + idx);
         o.zs = ldp<T, V, LD_NC>(z + idx + gr.mir - gr.hx);
       } else {
         o.s = o.zs = zero_pack<T, V>();
@@ -218,8 +226,9 @@ struct SrcHz {  // q = rc - (E zE + W zW + N zN + S zS); nbr == false: q = rc
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V>
+template <typename T, int V, bool EF = false>
 struct SrcPu {  // p = r + beta (p - omega v) (fresh: p = r), stored
+  static constexpr int MI = EF ? LD_NC_EF : LD_NC, MP = EF ? LD_PLAIN_EF : LD_PLAIN, SO = EF ? ST_EF : ST_PLAIN;
   struct In {
     Pack<T, V> r, p, v;
   };
@@ -229,24 +238,27 @@ struct SrcPu {  // p = r + beta (p - omega v) (fresh: p = r), stored
   T beta, omega;
   bool fresh;
   __device__ __forceinline__ void load(int64_t idx, In& o) {
-    o.r = ldp<T, V, LD_NC>(r + idx);
+    o.r = ldp<T, V, MI>(r + idx);
     if (!fresh) {
-      o.p = ldp<T, V, LD_PLAIN>(p + idx);
-      o.v = ldp<T, V, LD_NC>(v + idx);
+      o.p = ldp<T, V, MP>(p + idx);
+      o.v = ldp<T, V, MI>(v + idx);
     }
   }
   __device__ __forceinline__ Pack<T, V> make(const In& o, int64_t idx) {
     Pack<T, V> q;
 #pragma unroll
     for (int c = 0; c < V; ++c) q.a[c] = fresh ? o.r.a[c] : fma(beta, fma(-omega, o.v.a[c], o.p.a[c]), o.r.a[c]);
-    stp(p + idx, q);
+    stp<T, V, SO>(p + idx, q);
     return q;
   }
   __device__ __forceinline__ void flush() {}
 };
 
-template <typename T, int V>
-struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP64 across)
+// DOT: also accumulate <s, s>; the solver's half-step test takes it from
+// k_mv_rb<1> instead, which reads s anyway
+template <typename T, int V, bool EF = false, bool DOT = true>
+struct SrcSu {  // s = r - alpha v, stored, optionally with <s, s> (FP32 within a batch, DotAcc across)
+  static constexpr int MI = EF ? LD_NC_EF : LD_NC, SO = EF ? ST_EF : ST_PLAIN;
   struct In {
     Pack<T, V> r, v;
   };
@@ -257,22 +269,24 @@ struct SrcSu {  // s = r - alpha v, stored, with <s, s> (FP32 within a batch, FP
   T part;
   DotAcc<T> acc;
   __device__ __forceinline__ void load(int64_t idx, In& o) {
-    o.r = ldp<T, V, LD_NC>(r + idx);
-    o.v = ldp<T, V, LD_NC>(v + idx);
+    o.r = ldp<T, V, MI>(r + idx);
+    o.v = ldp<T, V, MI>(v + idx);
   }
   __device__ __forceinline__ Pack<T, V> make(const In& o, int64_t idx) {
     Pack<T, V> q;
 #pragma unroll
     for (int c = 0; c < V; ++c) {
       q.a[c] = fma(-alpha, o.v.a[c], o.r.a[c]);
-      part = fma(q.a[c], q.a[c], part);
+      if constexpr (DOT) part = fma(q.a[c], q.a[c], part);
     }
-    stp(s + idx, q);
+    stp<T, V, SO>(s + idx, q);
     return q;
   }
   __device__ __forceinline__ void flush() {
-    acc.add(part);
-    part = T(0);
+    if constexpr (DOT) {
+      acc.add(part);
+      part = T(0);
+    }
   }
 };
 
@@ -377,24 +391,27 @@ __global__ void __launch_bounds__(kBS) k_rb_copy(Grid g, const T* __restrict__ s
 
 // ---------------------------------------------------------------------------
 // Variants (the autotuner picks one per kernel, precision and grid): V columns
-// per thread (V divides nx/2), U levels per batch and MINB blocks per SM (the
-// register budget).  Variant 0 of every table has V = 1 (any even nx).  The
-// tables list only shapes that compile without spills.
+// per thread (V divides nx/2), U levels per batch, MINB blocks per SM (the
+// register budget) and h: L2 priorities (once-read arrays evict-first, the
+// parked forward sweep evict-last).  Variant 0 of every table has V = 1 (any
+// even nx).  The tables list only shapes that compile without spills.
 template <typename T>
 struct SorVar;
 template <>
 struct SorVar<float> {
-  static constexpr int NK[3] = {6, 5, 4};
-  static constexpr int v[3][6] = {{1, 1, 2, 4, 4, 2}, {1, 1, 2, 4, 4, 0}, {1, 2, 4, 2, 0, 0}};
-  static constexpr int u[3][6] = {{2, 3, 1, 1, 1, 2}, {4, 2, 2, 1, 2, 0}, {4, 2, 1, 2, 0, 0}};
-  static constexpr int b[3][6] = {{6, 5, 6, 6, 5, 4}, {6, 8, 6, 6, 4, 0}, {6, 6, 4, 4, 0, 0}};
+  static constexpr int NK[3] = {9, 8, 6};
+  static constexpr int v[3][9] = {{1, 1, 2, 4, 4, 2, 4, 2, 4}, {1, 1, 2, 4, 4, 2, 4, 2}, {1, 2, 4, 2, 4, 2}};
+  static constexpr int u[3][9] = {{2, 3, 1, 1, 1, 2, 1, 2, 1}, {4, 2, 2, 1, 2, 2, 1, 1}, {4, 2, 1, 2, 1, 2}};
+  static constexpr int b[3][9] = {{6, 5, 6, 6, 5, 4, 5, 4, 6}, {6, 8, 6, 6, 4, 6, 6, 6}, {6, 6, 4, 4, 4, 4}};
+  static constexpr int h[3][9] = {{0, 0, 0, 0, 0, 0, 1, 1, 1}, {0, 0, 0, 0, 0, 1, 1, 1}, {0, 0, 0, 0, 1, 1}};
 };
 template <>
 struct SorVar<double> {
-  static constexpr int NK[3] = {4, 4, 3};
-  static constexpr int v[3][6] = {{1, 1, 2, 2, 0, 0}, {1, 1, 2, 2, 0, 0}, {1, 2, 2, 0, 0, 0}};
-  static constexpr int u[3][6] = {{1, 2, 1, 1, 0, 0}, {1, 2, 1, 1, 0, 0}, {1, 1, 1, 0, 0, 0}};
-  static constexpr int b[3][6] = {{6, 4, 4, 5, 0, 0}, {6, 4, 6, 4, 0, 0}, {6, 4, 5, 0, 0, 0}};
+  static constexpr int NK[3] = {6, 5, 4};
+  static constexpr int v[3][9] = {{1, 1, 2, 2, 2, 2}, {1, 1, 2, 2, 2}, {1, 2, 2, 2}};
+  static constexpr int u[3][9] = {{1, 2, 1, 1, 1, 1}, {1, 2, 1, 1, 1}, {1, 1, 1, 1}};
+  static constexpr int b[3][9] = {{6, 4, 4, 5, 4, 5}, {6, 4, 6, 4, 6}, {6, 4, 5, 4}};
+  static constexpr int h[3][9] = {{0, 0, 0, 0, 1, 1}, {0, 0, 0, 0, 1}, {0, 0, 0, 1}};
 };
 
 template <typename T, int KIND, int I = 0, typename F>
@@ -402,7 +419,8 @@ cudaError_t with_sor(int id, F&& f) {
   if constexpr (I < SorVar<T>::NK[KIND]) {
     if (id == I)
       return f(std::integral_constant<int, SorVar<T>::v[KIND][I]>{}, std::integral_constant<int, SorVar<T>::u[KIND][I]>{},
-               std::integral_constant<int, SorVar<T>::b[KIND][I]>{});
+               std::integral_constant<int, SorVar<T>::b[KIND][I]>{},
+               std::integral_constant<bool, SorVar<T>::h[KIND][I] != 0>{});
     return with_sor<T, KIND, I + 1>(id, f);
   } else {
     return cudaErrorInvalidValue;
@@ -413,11 +431,11 @@ cudaError_t with_sor(int id, F&& f) {
 // k_sor_first<0>: p = r + beta (p - omega v) (p = r after a start; on a
 //   restart, Sec. 4: r = rhs - Ahat x, r0 = r, p = r and ||r||^2), then the red
 //   pass of the first sweep on the new p: z1 = omega T^-1 p on red columns.
-// k_sor_first<1>: s = r - alpha v, ||s||^2 (half-step exit test), then the
-//   same first red pass on s.
+// k_sor_first<1>: s = r - alpha v, then the same first red pass on s (the
+//   half-step test on ||s|| follows in k_mv_rb<1>).
 // All columns are updated; only the red half (compact columns < H) continues
 // into the tridiagonal solve.
-template <typename T, int MODE, int V, int U, int MINB>
+template <typename T, int MODE, int V, int U, int MINB, bool H>
 __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vecs<T> w, T* __restrict__ z1,
                                                          double omega_d, Ctl* ctl, Red red) {
   const Rb rb = make_rb(g);
@@ -444,27 +462,27 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
   const int64_t hg = rb.H / V;
   const int64_t items = rb_items(hg);
   if (MODE == 0) {
-    SrcPu<T, V> src{rin, w.p, w.v, (T)ctl->beta, (T)ctl->omega, ctl->fresh != 0};
+    using S = SrcPu<T, V, H>;
+    S src{rin, w.p, w.v, (T)ctl->beta, (T)ctl->omega, ctl->fresh != 0};
     for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
       const int64_t q0 = rb_group<V>(rb, hg, it);
       if (q0 < 0) continue;
       if (q0 < rb.H)
-        sor_group<T, V, U>(rb, q0, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
+        sor_group<T, V, U, S, H>(rb, q0, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
       else
         update_group<T, V, U>(rb, q0, src);
     }
   } else {
-    SrcSu<T, V> src{rin, w.v, w.s, (T)ctl->alpha, T(0), {}};
+    using S = SrcSu<T, V, H, false>;
+    S src{rin, w.v, w.s, (T)ctl->alpha, T(0), {}};
     for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
       const int64_t q0 = rb_group<V>(rb, hg, it);
       if (q0 < 0) continue;
       if (q0 < rb.H)
-        sor_group<T, V, U>(rb, q0, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
+        sor_group<T, V, U, S, H>(rb, q0, a.m, a.l, a.cp, nullptr, z1, omega, T(0), src);
       else
         update_group<T, V, U>(rb, q0, src);
     }
-    double vv[1] = {src.acc.value()}, o[1];
-    if (grid_reduce<1>(vv, red, o)) fin_snorm(ctl, o[0]);
   }
 }
 
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
 // may be the same buffer: the pass reads only the other colour's half of it
 // and writes only its own.  ctl (may be null): nothing to do unless the inner
 // solve is running.
-template <typename T, int V, int U, int MINB>
+template <typename T, int V, int U, int MINB, bool H>
 __global__ void __launch_bounds__(kBS, MINB) k_sor_pass(Grid g, Bands<T> a, const T* __restrict__ rc,
                                                         const T* __restrict__ znbr, const T* __restrict__ zold,
                                                         T* __restrict__ zout, int colour, int nbr, double omega_d,
@@ -487,19 +505,25 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_pass(Grid g, Bands<T> a, cons
   const int64_t hg = rb.H / V;
   for (int64_t h = (int64_t)blockIdx.x * kBS + threadIdx.x; h < hg; h += (int64_t)gridDim.x * kBS) {
     const int64_t q0 = (int64_t)colour * rb.H + h * V;
-    SrcHz<T, V> src{rc, a.E, a.W, a.N, a.S, znbr, rb_grp<V>(rb, q0), nbr != 0};
-    sor_group<T, V, U>(rb, q0, a.m, a.l, a.cp, zold, zout, omega, keep, src);
+    using S = SrcHz<T, V, H>;
+    S src{rc, a.E, a.W, a.N, a.S, znbr, rb_grp<V>(rb, q0), nbr != 0};
+    sor_group<T, V, U, S, H>(rb, q0, a.m, a.l, a.cp, zold, zout, omega, keep, src);
   }
 }
 
 // y = Ahat x in compact order with the iteration's dots:
-// MODE 0 (x = ph, y = v): <r0, v> -> alpha;  MODE 1 (x = sh, y = t): <t, s>, <t, t> -> omega.
+// MODE 0 (x = ph, y = v): <r0, v> -> alpha;  MODE 1 (x = sh, y = t): <t, s>,
+// <t, t> and <s, s> -> the half-step exit test on ||s||, then omega.  H: the
+// bands and the dot partner (read once) evict-first in L2; x, whose mirror
+// groups are read again by the neighbouring rows, keeps the normal priority.
 // The group's own values ride down in registers (x_(k-1), x_k); each level
 // loads x_(k+1), the mirror groups of rows j-1, j, j+1 and one scalar, six
 // bands and the dot partner.
-template <typename T, int MODE, int V, int U, int MINB>
+template <typename T, int MODE, int V, int U, int MINB, bool H>
 __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
+  constexpr int MB = H ? LD_NC_EF : LD_NC;
+  constexpr int SY = H ? ST_EF : ST_PLAIN;
   const Rb rb = make_rb(g);
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
@@ -507,7 +531,7 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
   const int64_t ncol = rb.ncol;
   const int nz = rb.nz;
   const int64_t hg = rb.H / V;
-  DotAcc<T> acc0{}, acc1{};
+  DotAcc<T> acc0{}, acc1{}, acc2{};
   const int64_t items = rb_items(hg);
   for (int64_t it = (int64_t)blockIdx.x * kBS + threadIdx.x; it < items; it += (int64_t)gridDim.x * kBS) {
     const int64_t q0 = rb_group<V>(rb, hg, it);
@@ -525,26 +549,26 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
           xp[u] = k + 1 < nz ? ldp<T, V, LD_NC>(x + idx + ncol) : zero_pack<T, V>();
           hm[u] = ldp<T, V, LD_NC>(x + idx + gr.mir);
           hx1[u] = ldw<T, LD_NC>(x + idx + gr.xo);
-          be[u] = ldp<T, V, LD_NC>(a.E + idx);
-          bw[u] = ldp<T, V, LD_NC>(a.W + idx);
+          be[u] = ldp<T, V, MB>(a.E + idx);
+          bw[u] = ldp<T, V, MB>(a.W + idx);
           if (gr.hn) {
             hn[u] = ldp<T, V, LD_NC>(x + idx + gr.mir + gr.hx);
-            bn[u] = ldp<T, V, LD_NC>(a.N + idx);
+            bn[u] = ldp<T, V, MB>(a.N + idx);
           } else {
             hn[u] = bn[u] = zero_pack<T, V>();
           }
           if (gr.hs) {
             hs[u] = ldp<T, V, LD_NC>(x + idx + gr.mir - gr.hx);
-            bs[u] = ldp<T, V, LD_NC>(a.S + idx);
+            bs[u] = ldp<T, V, MB>(a.S + idx);
           } else {
             hs[u] = bs[u] = zero_pack<T, V>();
           }
-          bu[u] = ldp<T, V, LD_NC>(a.U + idx);
-          bd[u] = ldp<T, V, LD_NC>(a.D + idx);
-          cc[u] = ldp<T, V, LD_NC>(c + idx);
+          bu[u] = ldp<T, V, MB>(a.U + idx);
+          bd[u] = ldp<T, V, MB>(a.D + idx);
+          cc[u] = ldp<T, V, MB>(c + idx);
         }
       }
-      T a0 = T(0), a1 = T(0);
+      T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int k = k0 + u;
@@ -561,23 +585,32 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
             t = fma(bd[u].a[cl], xm.a[cl], t);
             yy.a[cl] = t;
             a0 = fma(cc[u].a[cl], t, a0);
-            if (MODE == 1) a1 = fma(t, t, a1);
+            if (MODE == 1) {
+              a1 = fma(t, t, a1);
+              a2 = fma(cc[u].a[cl], cc[u].a[cl], a2);
+            }
           }
-          stp(y + (int64_t)k * ncol + q0, yy);
+          stp<T, V, SY>(y + (int64_t)k * ncol + q0, yy);
           xm = x0;
           x0 = xp[u];
         }
       }
       acc0.add(a0);
-      if (MODE == 1) acc1.add(a1);
+      if (MODE == 1) {
+        acc1.add(a1);
+        acc2.add(a2);
+      }
     }
   }
   if (MODE == 0) {
     double vv[1] = {acc0.value()}, o[1];
     if (grid_reduce<1>(vv, red, o)) fin_alpha(ctl, o[0]);
   } else {
-    double vv[2] = {acc0.value(), acc1.value()}, o[2];
-    if (grid_reduce<2>(vv, red, o)) fin_omega(ctl, o[0], o[1]);
+    double vv[3] = {acc0.value(), acc1.value(), acc2.value()}, o[3];
+    if (grid_reduce<3>(vv, red, o)) {
+      fin_snorm(ctl, o[2]);
+      if (ctl->state == ST_RUNNING) fin_omega(ctl, o[0], o[1]);
+    }
   }
 }
 
@@ -602,16 +635,17 @@ inline int64_t rb_blocks(const Grid& g, int V) { return 2 * ((g.ncol / 2 / V + k
 template <typename T>
 cudaError_t launch_sor_first(const Grid& g, const Bands<T>& a, const Vecs<T>& w, T* z1, double omega, int mode,
                              Ctl* ctl, Red red, const Launch& L) {
-  return with_sor<T, 2>(L.vsor[sor_prec<T>()][2], [&](auto vc, auto uc, auto bc) {
+  return with_sor<T, 2>(L.vsor[sor_prec<T>()][2], [&](auto vc, auto uc, auto bc, auto hc) {
     constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+    constexpr bool H = decltype(hc)::value;
     if ((g.nx / 2) % V) return cudaErrorInvalidValue;
     const int64_t wb = rb_blocks(g, V);
     if (mode == 0)
-      k_sor_first<T, 0, V, U, B><<<grid_for((const void*)k_sor_first<T, 0, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
-          g, a, w, z1, omega, ctl, red);
+      k_sor_first<T, 0, V, U, B, H><<<grid_for((const void*)k_sor_first<T, 0, V, U, B, H>, kBS, L, wb), kBS, 0,
+                                      L.stream>>>(g, a, w, z1, omega, ctl, red);
     else
-      k_sor_first<T, 1, V, U, B><<<grid_for((const void*)k_sor_first<T, 1, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
-          g, a, w, z1, omega, ctl, red);
+      k_sor_first<T, 1, V, U, B, H><<<grid_for((const void*)k_sor_first<T, 1, V, U, B, H>, kBS, L, wb), kBS, 0,
+                                      L.stream>>>(g, a, w, z1, omega, ctl, red);
     return cudaGetLastError();
   });
 }
@@ -619,11 +653,12 @@ cudaError_t launch_sor_first(const Grid& g, const Bands<T>& a, const Vecs<T>& w,
 template <typename T>
 cudaError_t launch_sor_pass(const Grid& g, const Bands<T>& a, const T* rc, const T* znbr, const T* zold, T* zout,
                             int colour, int nbr, double omega, const Ctl* ctl, const Launch& L) {
-  return with_sor<T, 0>(L.vsor[sor_prec<T>()][0], [&](auto vc, auto uc, auto bc) {
+  return with_sor<T, 0>(L.vsor[sor_prec<T>()][0], [&](auto vc, auto uc, auto bc, auto hc) {
     constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+    constexpr bool H = decltype(hc)::value;
     if ((g.nx / 2) % V) return cudaErrorInvalidValue;
     const int64_t wb = (g.ncol / 2 / V + kBS - 1) / kBS;
-    k_sor_pass<T, V, U, B><<<grid_for((const void*)k_sor_pass<T, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+    k_sor_pass<T, V, U, B, H><<<grid_for((const void*)k_sor_pass<T, V, U, B, H>, kBS, L, wb), kBS, 0, L.stream>>>(
         g, a, rc, znbr, zold, zout, colour, nbr, omega, ctl);
     return cudaGetLastError();
   });
@@ -632,15 +667,16 @@ cudaError_t launch_sor_pass(const Grid& g, const Bands<T>& a, const T* rc, const
 template <typename T>
 cudaError_t launch_mv_rb(const Grid& g, const Bands<T>& a, const Vecs<T>& w, int mode, Ctl* ctl, Red red,
                          const Launch& L) {
-  return with_sor<T, 1>(L.vsor[sor_prec<T>()][1], [&](auto vc, auto uc, auto bc) {
+  return with_sor<T, 1>(L.vsor[sor_prec<T>()][1], [&](auto vc, auto uc, auto bc, auto hc) {
     constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
+    constexpr bool H = decltype(hc)::value;
     if ((g.nx / 2) % V) return cudaErrorInvalidValue;
     const int64_t wb = rb_blocks(g, V);
     if (mode == 0)
-      k_mv_rb<T, 0, V, U, B><<<grid_for((const void*)k_mv_rb<T, 0, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+      k_mv_rb<T, 0, V, U, B, H><<<grid_for((const void*)k_mv_rb<T, 0, V, U, B, H>, kBS, L, wb), kBS, 0, L.stream>>>(
           g, a, w, ctl, red);
     else
-      k_mv_rb<T, 1, V, U, B><<<grid_for((const void*)k_mv_rb<T, 1, V, U, B>, kBS, L, wb), kBS, 0, L.stream>>>(
+      k_mv_rb<T, 1, V, U, B, H><<<grid_for((const void*)k_mv_rb<T, 1, V, U, B, H>, kBS, L, wb), kBS, 0, L.stream>>>(
           g, a, w, ctl, red);
     return cudaGetLastError();
   });
@@ -651,22 +687,26 @@ void warm_sor(const Launch& L) {
   grid_for((const void*)k_rb_copy<T, true>, kBS, L, 1);
   grid_for((const void*)k_rb_copy<T, false>, kBS, L, 1);
   for (int id = 0; id < SorVar<T>::NK[0]; ++id)
-    with_sor<T, 0>(id, [&](auto vc, auto uc, auto bc) {
-      grid_for((const void*)k_sor_pass<T, decltype(vc)::value, decltype(uc)::value, decltype(bc)::value>, kBS, L, 1);
+    with_sor<T, 0>(id, [&](auto vc, auto uc, auto bc, auto hc) {
+      grid_for((const void*)k_sor_pass<T, decltype(vc)::value, decltype(uc)::value, decltype(bc)::value,
+                                       decltype(hc)::value>,
+               kBS, L, 1);
       return cudaSuccess;
     });
   for (int id = 0; id < SorVar<T>::NK[1]; ++id)
-    with_sor<T, 1>(id, [&](auto vc, auto uc, auto bc) {
+    with_sor<T, 1>(id, [&](auto vc, auto uc, auto bc, auto hc) {
       constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
-      grid_for((const void*)k_mv_rb<T, 0, V, U, B>, kBS, L, 1);
-      grid_for((const void*)k_mv_rb<T, 1, V, U, B>, kBS, L, 1);
+      constexpr bool H = decltype(hc)::value;
+      grid_for((const void*)k_mv_rb<T, 0, V, U, B, H>, kBS, L, 1);
+      grid_for((const void*)k_mv_rb<T, 1, V, U, B, H>, kBS, L, 1);
       return cudaSuccess;
     });
   for (int id = 0; id < SorVar<T>::NK[2]; ++id)
-    with_sor<T, 2>(id, [&](auto vc, auto uc, auto bc) {
+    with_sor<T, 2>(id, [&](auto vc, auto uc, auto bc, auto hc) {
       constexpr int V = decltype(vc)::value, U = decltype(uc)::value, B = decltype(bc)::value;
-      grid_for((const void*)k_sor_first<T, 0, V, U, B>, kBS, L, 1);
-      grid_for((const void*)k_sor_first<T, 1, V, U, B>, kBS, L, 1);
+      constexpr bool H = decltype(hc)::value;
+      grid_for((const void*)k_sor_first<T, 0, V, U, B, H>, kBS, L, 1);
+      grid_for((const void*)k_sor_first<T, 1, V, U, B, H>, kBS, L, 1);
       return cudaSuccess;
     });
 }

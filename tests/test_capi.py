@@ -44,8 +44,8 @@ def test_version_and_defaults_without_gpu():
     # the binding's struct matches the header's layout (two doubles, nine ints, one int, one double)
     assert ctypes.sizeof(hz.hz_solve_params) == 64
     # tri-SOR variant tables: FP32 pass/matvec/first, FP64 the same; invalid pairs count 0
-    assert [hz.sor_variant_count(hz.HZ_PREC_FP32, k) for k in range(4)] == [6, 5, 4, 0]
-    assert [hz.sor_variant_count(hz.HZ_PREC_FP64, k) for k in range(4)] == [4, 4, 3, 0]
+    assert [hz.sor_variant_count(hz.HZ_PREC_FP32, k) for k in range(4)] == [9, 8, 6, 0]
+    assert [hz.sor_variant_count(hz.HZ_PREC_FP64, k) for k in range(4)] == [6, 5, 4, 0]
     assert hz.sor_variant_count(7, 0) == 0 and hz.sor_variant_count(hz.HZ_PREC_FP32, -1) == 0
     names = [hz.load().hz_kernel_name(k).decode() for k in range(hz.NUM_KERNELS)]
     assert names[7:] == ["k_sor_first", "k_sor_pass", "k_mv_rb", "k_rb_copy"] and hz.load().hz_kernel_name(

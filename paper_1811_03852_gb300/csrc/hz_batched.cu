@@ -161,10 +161,10 @@ __device__ double restart_column_cg(const Grid& g, int64_t col, const Bands<floa
 template <int V, int UT, int UM>
 __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
   __shared__ SysCtl sc[kMaxSys];
-  __shared__ double acc[kMaxSys][2];
+  __shared__ double acc[kMaxSys][3];
   const int nsys = A.nsys;
   auto zero_acc = [&]() {
-    for (int s = threadIdx.x; s < nsys; s += blockDim.x) acc[s][0] = acc[s][1] = 0.0;
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) acc[s][0] = acc[s][1] = acc[s][2] = 0.0;
     __syncthreads();
   };
   auto store_acc = [&](int d0, int nd) {
@@ -233,33 +233,21 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
     if (!grid_sync(A)) return;
     load_ctl(A, sc);
 
-    // ---- phase C: s = r - alpha v, <s, s>, sh = T^-1 s ----
-    zero_acc();
+    // ---- phase C: s = r - alpha v, sh = T^-1 s (the test on ||s|| is phase D's) ----
     for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
       const int s = sys_of(A, item);
       const SysCtl c = sc[s];
       if (c.state != ST_RUNNING) continue;
       const SysDesc& d = A.sys[s];
       const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[1] = {0.0};
       if (q < d.g.ncol / V) {
-        SrcS<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, {}};
+        SrcS<float, V, LD_CG, false, false> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, {}};
         thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.sh, src);
-        v[0] = src.acc.value();
       }
-      block_add<1>(v, &acc[s][0]);
-    }
-    store_acc(2, 1);
-    if (!grid_sync(A)) return;
-    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
-      const int s = blockIdx.x;
-      if (sc[s].state == ST_RUNNING) fin_snorm(A.sys[s].ctl, slots_sum(A, s, 2));
-      __threadfence();
     }
     if (!grid_sync(A)) return;
-    load_ctl(A, sc);
 
-    // ---- phase D: t = s + H sh, <t, s>, <t, t> ----
+    // ---- phase D: t = s + H sh, <t, s>, <t, t>, <s, s> -> half-step test, omega ----
     zero_acc();
     for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
       const int s = sys_of(A, item);
@@ -267,15 +255,20 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
       if (c.state != ST_RUNNING) continue;
       const SysDesc& d = A.sys[s];
       const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[2] = {0.0, 0.0};
-      if (q < d.g.ncol / V) hmv_vec<float, V, UM, 1, LD_CG>(d.g, q * V, d.a, d.w.s, d.w.sh, d.w.t, nullptr, v[0], v[1]);
-      block_add<2>(v, &acc[s][0]);
+      double v[3] = {0.0, 0.0, 0.0};
+      if (q < d.g.ncol / V)
+        hmv_vec<float, V, UM, 3, LD_CG>(d.g, q * V, d.a, d.w.s, d.w.sh, d.w.t, nullptr, v[0], v[1], &v[2]);
+      block_add<3>(v, &acc[s][0]);
     }
-    store_acc(0, 2);
+    store_acc(0, 3);
     if (!grid_sync(A)) return;
     if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
       const int s = blockIdx.x;
-      if (sc[s].state == ST_RUNNING) fin_omega(A.sys[s].ctl, slots_sum(A, s, 0), slots_sum(A, s, 1));
+      if (sc[s].state == ST_RUNNING) {
+        Ctl* ctl = A.sys[s].ctl;
+        fin_snorm(ctl, slots_sum(A, s, 2));
+        if (ctl->state == ST_RUNNING) fin_omega(ctl, slots_sum(A, s, 0), slots_sum(A, s, 1));
+      }
       __threadfence();
     }
     if (!grid_sync(A)) return;

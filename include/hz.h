@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define HZ_ABI_VERSION 2
+#define HZ_ABI_VERSION 3
 
 typedef struct hz_op_s* hz_op;
 
@@ -154,16 +154,30 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
 /*
  * Solve nsys independent systems (each with its own operator, which may have
  * its own grid).  b[s], x0[s] (may be NULL) and x[s] follow hz_solve's rules
- * (device pointers only).  The inner FP32 Krylov iterations of all systems
- * run in one persistent cooperative launch per refinement step, with
- * per-system scalars and convergence masks, phases separated by a grid
- * barrier whose waits are bounded (HZ_ERR_TIMEOUT instead of a hang).
- * 1 <= nsys <= 64 distinct operators sharing one stream; mixed mode only
- * (params->mode = HZ_MODE_MIXED_IR, else HZ_ERR_UNSUPPORTED).
- * infos: host array of nsys reports, may be NULL.  Returns the worst status.
+ * (device pointers only).  1 <= nsys <= 64 distinct operators sharing one
+ * stream; mixed mode only (params->mode = HZ_MODE_MIXED_IR, else
+ * HZ_ERR_UNSUPPORTED).  infos: host array of nsys reports, may be NULL.
+ * Returns the worst status.
+ *
+ * Strategies (hz_solve_batched_ex; hz_solve_batched = HZ_BATCH_AUTO):
+ *   HZ_BATCH_PERSISTENT: the inner FP32 Krylov iterations of all systems run
+ *     in one persistent cooperative launch per refinement step, with
+ *     per-system scalars and convergence masks, phases separated by a grid
+ *     barrier whose waits are bounded (HZ_ERR_TIMEOUT instead of a hang).
+ *   HZ_BATCH_SEQUENTIAL: hz_solve on each system in turn (graph-captured
+ *     inner loops, each kernel at its own occupancy); same arithmetic per
+ *     system as a single solve.
+ *   HZ_BATCH_AUTO: SEQUENTIAL when every system has at least 2^20 points (one
+ *     system then fills the GPU), else PERSISTENT.
+ * Any other strategy value: HZ_ERR_INVALID.
  */
+#define HZ_BATCH_AUTO 0
+#define HZ_BATCH_PERSISTENT 1
+#define HZ_BATCH_SEQUENTIAL 2
 int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
                      const hz_solve_params* params, hz_solve_info* infos);
+int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, const double* const* x0,
+                        double* const* x, const hz_solve_params* params, hz_solve_info* infos, int strategy);
 
 /* Test hook of hz_solve_batched (process-wide, affects later batched calls):
    timeout_ns bounds every grid-barrier wait of the persistent kernel (<= 0:

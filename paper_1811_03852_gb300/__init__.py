@@ -34,6 +34,7 @@ HZ_ERR_NONFINITE = 6
 HZ_ERR_TIMEOUT = 7
 HZ_ERR_UNSUPPORTED = 8
 
+HZ_BATCH_AUTO, HZ_BATCH_PERSISTENT, HZ_BATCH_SEQUENTIAL = 0, 1, 2
 HZ_MODE_FP64 = 0
 HZ_MODE_MIXED_IR = 1
 HZ_PREC_FP64 = 0
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True):
         "hz_op_dims": (i32, [pv, P(i32), P(i32), P(i32)]),
         "hz_solve": (i32, [pv, pv, pv, pv, P(hz_solve_params), P(hz_solve_info)]),
         "hz_solve_batched": (i32, [i32, P(pv), P(pv), P(pv), P(pv), P(hz_solve_params), P(hz_solve_info)]),
+        "hz_solve_batched_ex": (i32, [i32, P(pv), P(pv), P(pv), P(pv), P(hz_solve_params), P(hz_solve_info), i32]),
         "hz_get_history": (i32, [pv, pv, i32]),
         "hz_matvec": (i32, [pv, i32, pv, pv]),
         "hz_precond_apply": (i32, [pv, i32, pv, pv]),
@@ -300,8 +302,9 @@ class Operator:
         _check(load().hz_op_export(self._h, what, prec, _ptr(dst)), "hz_op_export")
 
 
-def solve_batched(ops, bs, xs, x0s=None, params=None, raise_on_error=True, **kw):
-    """Solve several systems (each its own Operator) in one batched call; returns a list of info dicts."""
+def solve_batched(ops, bs, xs, x0s=None, params=None, raise_on_error=True, strategy=0, **kw):
+    """Solve several systems (each its own Operator) in one batched call; returns a list of info dicts.
+    strategy: HZ_BATCH_AUTO (0), HZ_BATCH_PERSISTENT (1) or HZ_BATCH_SEQUENTIAL (2)."""
     L = load()
     k = len(ops)
     p = params if params is not None else default_params(**kw)
@@ -311,7 +314,7 @@ def solve_batched(ops, bs, xs, x0s=None, params=None, raise_on_error=True, **kw)
     xp = arr(*[_ptr(x) for x in xs])
     x0p = arr(*[_ptr(x) for x in x0s]) if x0s is not None else None
     infos = (hz_solve_info * k)()
-    st = L.hz_solve_batched(k, hs, bp, x0p, xp, ctypes.byref(p), infos)
+    st = L.hz_solve_batched_ex(k, hs, bp, x0p, xp, ctypes.byref(p), infos, int(strategy))
     out = [i.as_dict() for i in infos]
     if st != HZ_OK and raise_on_error:
         raise HzError(st, f"hz_solve_batched {out}")

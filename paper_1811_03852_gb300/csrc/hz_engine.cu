@@ -1503,7 +1503,14 @@ int hz_batched_debug(long long timeout_ns, int leave_block) {
 
 int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
                      const hz_solve_params* pp, hz_solve_info* infos) {
+  return hz_solve_batched_ex(nsys, ops, b, x0, x, pp, infos, HZ_BATCH_AUTO);
+}
+
+int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, const double* const* x0,
+                        double* const* x, const hz_solve_params* pp, hz_solve_info* infos, int strategy) {
   if (nsys < 1 || nsys > kMaxSys || !ops || !b || !x) return HZ_ERR_INVALID;
+  if (strategy != HZ_BATCH_AUTO && strategy != HZ_BATCH_PERSISTENT && strategy != HZ_BATCH_SEQUENTIAL)
+    return HZ_ERR_INVALID;
   hz_solve_params p;
   if (pp)
     p = *pp;
@@ -1523,6 +1530,26 @@ int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const d
     for (int r = 0; r < q; ++r)
       if (ops[r] == ops[q]) return HZ_ERR_INVALID;  // each system needs its own work vectors
     if (ops[q]->g.nx % 4) vec = 1;
+  }
+  // Systems that each fill the GPU on their own run one after another through
+  // the single-system path (its graph-captured inner loop and per-kernel
+  // variants at full occupancy); smaller ones share the persistent launch,
+  // whose one-launch-per-refinement-step pays off when a system alone cannot
+  // keep the SMs busy.
+  if (strategy == HZ_BATCH_AUTO) {
+    int64_t smallest = ops[0]->g.n;
+    for (int q = 1; q < nsys; ++q) smallest = std::min(smallest, ops[q]->g.n);
+    strategy = smallest >= kBatchSeqMinPoints ? HZ_BATCH_SEQUENTIAL : HZ_BATCH_PERSISTENT;
+  }
+  if (strategy == HZ_BATCH_SEQUENTIAL) {
+    int worst = HZ_OK;
+    for (int q = 0; q < nsys; ++q) {
+      hz_solve_info tmp;
+      const int st = hz_solve(ops[q], b[q], x0 ? x0[q] : nullptr, x[q], &p, infos ? &infos[q] : &tmp);
+      if (st != HZ_OK && (worst == HZ_OK || st == HZ_ERR_CUDA)) worst = st;
+      if (st == HZ_ERR_CUDA) return st;
+    }
+    return worst;
   }
   std::vector<SysDesc> sys(nsys);
   int64_t item0 = 0;

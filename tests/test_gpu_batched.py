@@ -1,4 +1,5 @@
-"""Batched persistent solve (many uneven systems, one cooperative launch per refinement step).
+"""Batched solves: the persistent strategy (many uneven systems, one cooperative
+launch per refinement step) and the sequential one (hz_solve per system).
 
 Each system of a batch must reach the true FP64 residual 1e-8 (recomputed by
 the oracle) and agree with its own single-system solve to 1e-6 (relative 2-norm).
@@ -86,7 +87,7 @@ def test_batched_barrier_timeout_is_reported_not_hung():
     xs = [torch.empty(b.size, dtype=torch.float64, device="cuda") for _, b in systems]
     try:
         hz.batched_debug(timeout_ns=200_000_000, leave_block=1)
-        st, infos = hz.solve_batched(ops, bs, xs, raise_on_error=False)
+        st, infos = hz.solve_batched(ops, bs, xs, raise_on_error=False, strategy=hz.HZ_BATCH_PERSISTENT)
     finally:
         hz.batched_debug(0, -1)
     assert st == hz.HZ_ERR_TIMEOUT and all(i["status"] == hz.HZ_ERR_TIMEOUT for i in infos)
@@ -108,15 +109,41 @@ def test_batched_rejects_bad_arguments():
     assert st == hz.HZ_ERR_INVALID  # the same operator twice
     st, _ = hz.solve_batched([op], [bd], [x], mode=hz.HZ_MODE_FP64, raise_on_error=False)
     assert st == hz.HZ_ERR_UNSUPPORTED
+    st, _ = hz.solve_batched([op], [bd], [x], raise_on_error=False, strategy=3)
+    assert st == hz.HZ_ERR_INVALID
 
 
-def test_batched_32_uneven_systems_full_size():
+@pytest.mark.parametrize("strategy", [1, 2])
+def test_batched_strategies_match_single_solves(strategy):
+    # persistent (1): same algorithm, its own launch shape (agrees to 1e-6);
+    # sequential (2): each system through hz_solve (bit-identical to it)
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    specs = [(96, 72, 20, 31, 32), (64, 48, 20, 33, 34), (130, 65, 11, 35, 36)]
+    systems = _systems(specs, z_unit="m")
+    xs, infos, ops = _batched(systems, strategy=strategy)
+    for (A, b), x, info, op in zip(systems, xs, infos, ops):
+        assert info["status"] == 0, info
+        xd = torch.empty(b.size, dtype=torch.float64, device="cuda")
+        single = op.solve(dev(b), xd)
+        xsgl = host(xd).reshape(b.shape)
+        if strategy == hz.HZ_BATCH_SEQUENTIAL:
+            assert np.array_equal(x, xsgl) and info["inner_iters"] == single["inner_iters"]
+        else:
+            assert np.linalg.norm(x - xsgl) / np.linalg.norm(xsgl) <= 1e-6
+
+
+@pytest.mark.parametrize("strategy", [0, 1])
+def test_batched_32_uneven_systems_full_size(strategy):
     # the 32-system batch (grids 192x144, 320x240, 640x480, 70 levels): every
-    # system's true residual recomputed by the oracle over all points
+    # system's true residual recomputed by the oracle over all points, with the
+    # automatic strategy (sequential at these sizes) and the persistent launch
     specs = [gen.batched_spec(i) for i in range(32)]
     specs = [(s["nx"], s["ny"], s["nz"], s["seed_coef"], s["seed_rhs"]) for s in specs]
     systems = _systems(specs, z_unit="radius")
-    xs, infos, _ = _batched(systems)
+    xs, infos, _ = _batched(systems, strategy=strategy)
     for (A, b), x, info in zip(systems, xs, infos):
         assert info["status"] == 0, info
         _, rn = oracle.residual(A, b, x)

@@ -1501,6 +1501,10 @@ int hz_batched_debug(long long timeout_ns, int leave_block) {
   return HZ_OK;
 }
 
+// batched solves: systems of at least this many points each fill the GPU alone
+// (the automatic strategy then solves them one after another)
+constexpr int64_t kBatchSeqMinPoints = int64_t(1) << 20;
+
 int hz_solve_batched(int nsys, const hz_op* ops, const double* const* b, const double* const* x0, double* const* x,
                      const hz_solve_params* pp, hz_solve_info* infos) {
   return hz_solve_batched_ex(nsys, ops, b, x0, x, pp, infos, HZ_BATCH_AUTO);

@@ -306,9 +306,6 @@ cudaError_t nn_pair_launch(int64_t n, const double* A7, const double* b, const d
 
 // ---- batched persistent solve (hz_batched.cu) ----
 constexpr int kMaxSys = 64;
-// batched solves: systems of at least this many points each fill the GPU alone
-// (the automatic strategy then solves them one after another)
-constexpr int64_t kBatchSeqMinPoints = int64_t(1) << 20;
 struct SysDesc {
   Grid g;
   Bands<float> a;

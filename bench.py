@@ -422,7 +422,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (vectors 1.4-2.8 GB)", "parallelism": f"replicas x{world}"},
         "solve": {"outer": infos[0]["outer_iters"], "inner": infos[0]["inner_iters"],
                   "true_rel_residual": infos[0]["true_rel_residual"],
-                  "ms_per_inner": round(ms / args.steps / max(1, infos[0]["inner_iters"]), 3)},
+                  "ms_per_inner": round(ms / args.steps / max(1, infos[0]["inner_iters"]), 3),
+                  "inner_all_timed": sorted({i["inner_iters"] for i in infos})},
         "device": {"name": torch.cuda.get_device_name(dev),
                    "sms": torch.cuda.get_device_properties(dev).multi_processor_count},
         "fp64": fp64,

@@ -255,7 +255,9 @@ int hz_get_history(hz_op op, double* hist, int cap);
  * SM.  All variants of a kernel compute the same values; dot partial sums
  * follow the launch shape.  hz_op_autotune times every
  * valid variant on the operator's own arrays (3 launches each, CUDA events on
- * the operator's stream) and keeps the fastest; flags bit 0 also tunes the
+ * the operator's stream) and keeps the fastest, or the lowest-numbered variant
+ * within 2% of it (a stable choice: the dot products' rounding, hence the
+ * iteration count, follows the variant); flags bit 0 also tunes the
  * FP64 kernels (allocating the FP64 work vectors); flags bit 1 also tunes the
  * tri-SOR kernels (for nx even; allocating their colour-compact copies of the
  * bands), in FP32 and, with bit 0, FP64.  If the environment

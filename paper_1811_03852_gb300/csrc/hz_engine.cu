@@ -109,6 +109,11 @@ struct hz_op_s {
   hz_nn nn = nullptr;      // learned stage (not owned)
 };
 
+namespace hz {
+// l2: the variant uses L2 priorities; cap: its blocks per SM (0: as many as fit)  (hz_launch.cu)
+void variant_flags(int prec, int kind, int id, int* l2, int* cap);
+}  // namespace hz
+
 namespace {
 
 template <typename T>
@@ -661,18 +666,27 @@ bool variant_ok(int prec, int kind, int id, int nx, int nz) {
   return nx % v == 0;
 }
 
-// The launch shape used until the autotuner picks one: the Thomas variant that
-// parks its forward sweep in the output vector under L2 priorities with two
-// columns per thread where the row length allows, else the widest vector the
-// row length allows.
+// The launch shape used until the autotuner picks one (and kept by it unless
+// another is clearly faster), the best measured on GB300 inside the N1280
+// iteration: for the Thomas kernels, the variant that parks its forward sweep
+// under L2 priorities with two columns per thread and no block cap; for the
+// stencil kernels, the L2-priority variant with two columns per thread and the
+// deepest batch.  Rows whose length two does not divide: the widest vector
+// the row length allows.
 int default_variant(int prec, int kind, int nx) {
   int best = 0, bestv = 0;
-  if (kind == 0) {
+  if (nx % 2 == 0) {
+    int pick = -1, pu = 0;
     for (int i = 0; i < num_variants(prec, kind); ++i) {
-      int v = 1, u = 1;
+      int v = 1, u = 1, l2 = 0, cap = 0;
       variant_shape(prec, kind, i, &v, &u);
-      if (variant_park_mode(prec, i) == 2 && v == 2 && nx % 2 == 0) return i;
+      variant_flags(prec, kind, i, &l2, &cap);
+      if (v == 2 && l2 && cap == 0 && u > pu) {
+        pick = i;
+        pu = u;
+      }
     }
+    if (pick >= 0) return pick;
   }
   for (int i = 0; i < num_variants(prec, kind); ++i) {
     int v = 1, u = 1;
@@ -1107,6 +1121,23 @@ namespace {
 // Time one precision's column kernels in every valid variant on the operator's
 // own arrays (work vectors zeroed; a control block set to "running" before
 // each launch) and keep the fastest Thomas and stencil variants.
+// The variant the autotuner keeps: the fastest in its trials, unless the
+// default variant (dflt >= 0) is within 2% of it.  Variants that close differ
+// by less than the run-to-run noise of the trials, the isolated trials do not
+// see how the kernels of one iteration share L2, and the dot products'
+// rounding order (hence the Krylov iteration count) follows the launch shape:
+// keeping the default then keeps the choice, and the solve, the same from run
+// to run.
+constexpr double kTuneTie = 0.02;
+int pick_variant(const std::vector<double>& ms, int dflt) {
+  int best = -1;
+  for (size_t id = 0; id < ms.size(); ++id)
+    if (ms[id] >= 0.0 && (best < 0 || ms[id] < ms[best])) best = (int)id;
+  if (best >= 0 && dflt >= 0 && dflt < (int)ms.size() && ms[dflt] >= 0.0 && ms[dflt] <= ms[best] * (1.0 + kTuneTie))
+    return dflt;
+  return best;
+}
+
 template <typename T>
 int autotune_prec(hz_op op, int reps, double* best_ms) {
   const int pr = sizeof(T) == 8 ? 1 : 0;
@@ -1141,8 +1172,7 @@ int autotune_prec(hz_op op, int reps, double* best_ms) {
     return tot / reps;
   };
   for (int kind = 0; kind < 2; ++kind) {
-    int best = -1;
-    double bms = 1e30;
+    std::vector<double> times(num_variants(pr, kind), -1.0);  // -1: not valid for this grid
     for (int id = 0; id < num_variants(pr, kind); ++id) {
       if (!variant_ok(pr, kind, id, op->g.nx, op->g.nz)) continue;
       Launch L = op->L;
@@ -1162,13 +1192,11 @@ int autotune_prec(hz_op op, int reps, double* best_ms) {
         set_err(cudaGetLastError(), "autotune launch", __LINE__);
         return HZ_ERR_CUDA;
       }
-      if (ms < bms) {
-        bms = ms;
-        best = id;
-      }
+      times[id] = ms;
     }
+    const int best = pick_variant(times, default_variant(pr, kind, op->g.nx));
     if (best >= 0) (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = best;
-    if (best_ms) best_ms[kind] = bms;
+    if (best_ms) best_ms[kind] = best >= 0 ? times[best] : 1e30;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1214,8 +1242,7 @@ int autotune_sor(hz_op op, int reps) {
     return tot / reps;
   };
   for (int kind = 0; kind < 3; ++kind) {
-    int best = -1;
-    double bms = 1e30;
+    std::vector<double> times(sor_num_variants(pr, kind), -1.0);
     for (int id = 0; id < sor_num_variants(pr, kind); ++id) {
       if (!sor_variant_ok(pr, kind, id, op->g.nx)) continue;
       Launch L = op->L;
@@ -1240,11 +1267,9 @@ int autotune_sor(hz_op op, int reps) {
         set_err(cudaGetLastError(), "autotune launch", __LINE__);
         return HZ_ERR_CUDA;
       }
-      if (ms < bms) {
-        bms = ms;
-        best = id;
-      }
+      times[id] = ms;
     }
+    const int best = pick_variant(times, -1);
     if (best >= 0) op->L.vsor[pr][kind] = best;
   }
   cudaEventDestroy(e0);

@@ -198,7 +198,9 @@ __device__ __noinline__ double restart_column(const Grid& g, int64_t col, const 
     w.r0[idx] = rk;
     cacc = fma(rk, rk, cacc);
   }
-  SrcCopy<T, 1> src{w.r, w.p};
+  // r was written just above, in this launch: coherent loads (the read-only
+  // path may serve a line cached before the write)
+  SrcCopy<T, 1, LD_PLAIN> src{w.r, w.p};
   thomas_vec<T, 1, 4>(g, col, a.m, a.l, a.cp, w.ph, src);
   return (double)cacc;
 }

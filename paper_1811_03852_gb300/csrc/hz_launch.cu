@@ -74,6 +74,16 @@ bool variant_parks_smem(int prec, int kind, int id) {
   return (prec == 0 ? Variants<float>::pre_p[id] : Variants<double>::pre_p[id]) == PARK_SMEM;
 }
 
+void variant_flags(int prec, int kind, int id, int* l2, int* cap) {
+  if (kind == 0) {
+    *l2 = (prec == 0 ? Variants<float>::pre_p[id] : Variants<double>::pre_p[id]) == PARK_OUT_L2;
+    *cap = prec == 0 ? Variants<float>::pre_b[id] : Variants<double>::pre_b[id];
+  } else {
+    *l2 = prec == 0 ? Variants<float>::mv_h[id] : Variants<double>::mv_h[id];
+    *cap = 0;
+  }
+}
+
 int variant_park_mode(int prec, int id) {
   return prec == 0 ? Variants<float>::pre_p[id] : Variants<double>::pre_p[id];
 }

@@ -22,11 +22,15 @@ def test_fp32_vs_fp64_bicgstab_behaviour():
     op = hz.Operator(A)
     bd = dev(b)
     x = torch.empty(b.size, dtype=torch.float64, device="cuda")
-    hist = {}
+    hist, R = {}, {}
     for name, mode in (("fp32", hz.HZ_MODE_MIXED_IR), ("fp64", hz.HZ_MODE_FP64)):
-        op.solve(bd, x, mode=mode, max_outer=1, inner_tol=1e-15, max_inner=500, record_history=1,
+        # one BiCGStab solve of 1000 iterations (no refinement), recursive residual history of
+        # the scaled system, then the paper's R = ||b - A x|| / ||b|| of the result (oracle)
+        op.solve(bd, x, mode=mode, max_outer=1, inner_tol=1e-15, max_inner=1000, record_history=1,
                  raise_on_error=False)
         hist[name] = np.array(op.history())
+        _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
+        R[name] = rn / np.linalg.norm(b)
     h32, h64 = hist["fp32"], hist["fp64"]
     # indistinguishable at first (the paper's Fig. 1: the curves coincide for the first iterations)
     assert np.all(np.abs(h32[:5] - h64[:5]) <= 1e-3 * h64[:5])
@@ -40,22 +44,13 @@ def test_fp32_vs_fp64_bicgstab_behaviour():
     # iteration gap: the same count at a loose level (BiCGStab's non-monotone path moves the
     # intermediate ones either way) ...
     assert abs(first(h32, 1e-3) - first(h64, 1e-3)) <= 2
-    # ... and at R = 1e-7 (Sec. 4 measures R = ||b - A x_i|| / ||b||, the true residual): after
-    # as many iterations as the FP64 solver needs to get there, the FP32 iterate is not there.
-    # (The FP32 recursive residual drifts away from the true one, in a direction set by the
-    # rounding order, so it says nothing about this.)
-    n64 = first(h64, 1e-7)
-    assert n64 < 500
-    R = {}
-    for name, mode in (("fp32", hz.HZ_MODE_MIXED_IR), ("fp64", hz.HZ_MODE_FP64)):
-        op.solve(bd, x, mode=mode, max_outer=1, inner_tol=1e-15, max_inner=n64, raise_on_error=False)
-        _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
-        R[name] = rn / np.linalg.norm(b)
-    assert R["fp64"] <= 1e-6 and R["fp32"] > 1e-7, (n64, R)
-    # the FP32 solver's true residual (oracle) stalls above 1e-8 however long it runs ...
-    op.solve(bd, x, mode=hz.HZ_MODE_MIXED_IR, max_outer=1, inner_tol=1e-15, max_inner=500, raise_on_error=False)
-    _, rn = oracle.residual(A, b, host(x).reshape(b.shape))
-    assert rn / np.linalg.norm(b) > 1e-8
+    # ... and at R = 1e-7 (Sec. 4 measures R = ||b - A x_i|| / ||b||, the true residual of the
+    # unscaled system): within 1000 iterations the FP64 solver gets there and the FP32 solver,
+    # whose true residual stalls above the 32-bit limit however long it runs, does not.  (The
+    # recursive history above is that of the diagonally scaled system and, in FP32, drifts
+    # away from the true residual in a direction set by the rounding order: it says nothing
+    # about this.)
+    assert R["fp64"] <= 1e-7 and R["fp32"] > 1e-7, R
     # ... while refinement around FP32 inner solves reaches it
     info = op.solve(bd, x, tol=1e-8)
     _, rn = oracle.residual(A, b, host(x).reshape(b.shape))

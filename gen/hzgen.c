@@ -176,17 +176,32 @@ int hzgen_rhs(int nx, int ny, int nz, uint64_t seed, double noise_frac, double* 
     }
     for (int k = 0; k < nz; ++k) Z[q * nz + k] = amp[q] * cos(M_PI * nq[q] * (k + 0.5) / nz + ch[q]);
   }
-  double ss = 0.0;
-#pragma omp parallel for schedule(static) reduction(+ : ss)
-  for (int64_t p = 0; p < n; ++p) {
-    const int i = (int)(p % nx);
-    const int j = (int)((p / nx) % ny);
-    const int k = (int)(p / ((int64_t)nx * ny));
-    double f = 0.0;
-    for (int q = 0; q < NMODES; ++q) f += X[q * nx + i] * Y[q * ny + j] * Z[q * nz + k];
-    b[p] = f;
-    ss += f * f;
+  /* sum of squares in fixed chunks, each summed in index order, the chunk sums
+     then added in chunk order: the same bits whatever the thread count (an
+     OpenMP reduction would combine per-thread partials in an order that
+     follows the number of threads, and so would the right-hand side) */
+  const int64_t CH = (int64_t)1 << 16;
+  const int64_t nch = (n + CH - 1) / CH;
+  double* part = (double*)malloc(sizeof(double) * (size_t)nch);
+  if (!part) { free(X); free(Y); free(Z); return -2; }
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nch; ++c) {
+    const int64_t p1 = (c + 1) * CH < n ? (c + 1) * CH : n;
+    double sc = 0.0;
+    for (int64_t p = c * CH; p < p1; ++p) {
+      const int i = (int)(p % nx);
+      const int j = (int)((p / nx) % ny);
+      const int k = (int)(p / ((int64_t)nx * ny));
+      double f = 0.0;
+      for (int q = 0; q < NMODES; ++q) f += X[q * nx + i] * Y[q * ny + j] * Z[q * nz + k];
+      b[p] = f;
+      sc += f * f;
+    }
+    part[c] = sc;
   }
+  double ss = 0.0;
+  for (int64_t c = 0; c < nch; ++c) ss += part[c];
+  free(part);
   double rms = sqrt(ss / (double)n);
   double inv = rms > 0.0 ? 1.0 / rms : 1.0;
 #pragma omp parallel for schedule(static)

@@ -197,7 +197,7 @@ def cpu_baseline(A, b, dims, outer, inner, mode_mixed=True, reps=1):
 # workloads (same algorithm and seeds; python bench.py on a GB300): the work the
 # oracle's per-piece timings are composed with where a full oracle solve would
 # take hours.
-GPU_COUNTS = {("n1280", "radius"): (3, 473)}
+GPU_COUNTS = {("n1280", "radius"): (3, 569)}
 
 
 def run_reference(args):

@@ -102,9 +102,10 @@ __global__ void k_psum(const double* __restrict__ part, int pstride, int nblocks
   }
 }
 
-// y = a * x (elementwise); a = 1/sqrt(*nrm2) when inv_sqrt, else *a
-__global__ void __launch_bounds__(256) k_scale(int64_t n, const float* __restrict__ x, float* __restrict__ y,
-                                               const double* __restrict__ s, int inv_sqrt) {
+// y = a * x (elementwise); a = 1/sqrt(*nrm2) when inv_sqrt, else *a.  x may be
+// y (in-place normalisation), so neither is restrict-qualified.
+__global__ void __launch_bounds__(256) k_scale(int64_t n, const float* x, float* y, const double* __restrict__ s,
+                                               int inv_sqrt) {
   const double sv = *s;
   const float a = (float)(inv_sqrt ? (sv > 0.0 ? 1.0 / sqrt(sv) : 0.0) : sv);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)

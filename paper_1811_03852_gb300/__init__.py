@@ -258,7 +258,9 @@ class Operator:
         return rn.value, bn.value
 
     def autotune(self, fp64=True, trisor=False):
-        """Pick the fastest column-kernel variants for this grid (timed on the GPU)."""
+        """Pick the column-kernel variants for this grid from timed trials on the GPU: the fastest,
+        unless the measured default is within 2% of it (a stable choice; the dot products'
+        rounding, hence the iteration count, follows the variant)."""
         _check(load().hz_op_autotune(self._h, (1 if fp64 else 0) | (2 if trisor else 0)), "hz_op_autotune")
         return self.variants()
 

@@ -13,7 +13,7 @@ same run (fp64_* keys).
 
 Under torchrun every rank solves its own copy (replicas: the path has no
 data-parallel exchange) and rank 0 prints one JSON line.  --impl reference
-times the CPU oracle (serial C) on the host cores instead.
+times the CPU oracle (C, its OpenMP build on all host cores) instead.
 """
 from __future__ import annotations
 
@@ -156,54 +156,95 @@ def make_inputs(args):
     return (nx, ny, nz), A, b
 
 
-def cpu_baseline(A, b, dims, outer, inner, mode_mixed=True, reps=1):
-    """Oracle (serial C, as it stands) timed on the host: one call each of the
-    true residual, T^-1 and Ahat x over the full system, composed with the GPU
-    solve's outer/inner counts (one inner iteration = 2 T^-1 + 2 Ahat x)."""
+def _oracle_pieces(A, b, Ah32, bh32, threads, iters):
+    """Wall time of one FP64 true residual and of `iters` (ascending) FP32 BiCGStab runs of
+    the oracle on the full system with the given OpenMP threads."""
+    import oracle
+
+    used = oracle.use_openmp(True, threads)
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    oracle.residual(A, b, x)
+    t_res = time.perf_counter() - t0
+    t_k = {}
+    for k in iters:
+        t0 = time.perf_counter()
+        oracle.bicgstab(Ah32, bh32, eta=1e-30, maxit=k, fp32=True)
+        t_k[k] = time.perf_counter() - t0
+    return used, t_res, t_k
+
+
+def cpu_baseline(A, b, dims, outer, inner, full_solve=True):
+    """The oracle as it stands (plain C; its OpenMP build shares out the point and column loops
+    and gives the same bits as the serial build) timed on this host's cores on a bounded sample
+    of the same solve: one FP64 true residual, and the oracle's own FP32 BiCGStab (T^-1, every
+    vector update and dot product included) run for 1 and 3 iterations, which separates the
+    cost of an inner iteration from that of an inner solve's start.  The solve is composed from
+    them with the GPU solve's refinement steps and inner iterations.  The same sample with one
+    thread is reported too; and, where it takes seconds, a full oracle mixed solve of the
+    640x480x70 system (seeds 11/12), not extrapolated."""
     import oracle
 
     nx, ny, nz = dims
+    cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    Ah = oracle.scale(A)
-    t_scale = time.perf_counter() - t0
-    x = np.zeros_like(b)
-    ts = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.residual(A, b, x)
-        t_res = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        z = oracle.apply_Tinv(Ah, b)
-        t_tinv = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        oracle.matvec_hat(Ah, z)
-        t_mv = time.perf_counter() - t0
-        t_solve = (outer + 1) * t_res + inner * 2 * (t_tinv + t_mv)
-        ts.append(t_solve)
-    t_solve = min(ts)
-    return {
+    oracle.use_openmp(True, cores)
+    Ah32 = oracle.scale(A).astype(np.float32)
+    bh32 = (b / A[0]).astype(np.float32)
+    t_prep = time.perf_counter() - t0
+    used, t_res, t_k = _oracle_pieces(A, b, Ah32, bh32, cores, (1, 3))
+    t_it = max((t_k[3] - t_k[1]) / 2.0, 1e-9)
+    t_start = max(t_k[1] - t_it, 0.0)
+    t_solve = (outer + 1) * t_res + outer * t_start + inner * t_it
+    used1, t_res1, t_k1 = _oracle_pieces(A, b, Ah32, bh32, 1, (1,))
+    t_solve1 = (outer + 1) * t_res1 + inner * t_k1[1]
+    out = {
         "value": 1.0 / t_solve,
         "unit": "solves/s",
-        "cores": 1,
+        "cores": used,
         "kind": "oracle",
-        "sample": (f"oracle (serial C, FP64) timed once per piece on the full {nx}x{ny}x{nz} system: true residual "
-                   f"{t_res:.2f} s, T^-1 {t_tinv:.2f} s, Ahat x {t_mv:.2f} s (scaling {t_scale:.2f} s, not counted); "
-                   f"composed as {outer + 1} residuals + {inner} iterations x (2 T^-1 + 2 Ahat x), the counts of the "
-                   f"GPU mixed solve of this system"),
+        "sample": (f"oracle (C, OpenMP build, {used} threads on {cores} host cores, FP32 inner / FP64 outer) timed on "
+                   f"the full {nx}x{ny}x{nz} system: true residual {t_res:.2f} s, its FP32 BiCGStab for 1 and 3 "
+                   f"iterations {t_k[1]:.2f} / {t_k[3]:.2f} s (an iteration {t_it:.2f} s, a start {t_start:.2f} s; "
+                   f"scaling and FP32 casts {t_prep:.1f} s, not counted); composed as {outer + 1} residuals + "
+                   f"{outer} starts + {inner} iterations, the counts of the GPU mixed solve of this system"),
+        "single_thread": {"value": 1.0 / t_solve1, "unit": "solves/s", "cores": used1,
+                          "sample": f"the same pieces with one thread: true residual {t_res1:.2f} s, one FP32 "
+                                    f"iteration with its start {t_k1[1]:.2f} s; composed as {outer + 1} residuals + "
+                                    f"{inner} iterations (each charged a start)"},
     }
+    del Ah32, bh32
+    if full_solve:
+        import gen
+
+        w = gen.WORKLOADS["mixed640"]
+        A6 = gen.make_operator(w["nx"], w["ny"], w["nz"], w["seed_coef"], z_unit="radius")
+        b6 = gen.make_rhs(w["nx"], w["ny"], w["nz"], w["seed_rhs"])
+        oracle.use_openmp(True, cores)
+        t0 = time.perf_counter()
+        _, info = oracle.solve(A6, b6, mode=oracle.MODE_MIXED, tol=1e-8, max_outer=20, max_inner=4000)
+        sec = time.perf_counter() - t0
+        out["full_solve_640x480x70"] = {
+            "value": 1.0 / sec, "unit": "solves/s", "cores": used, "seconds": round(sec, 2),
+            "outer": info["outer"], "inner": info["inner"], "true_rel_residual": info["R"],
+            "sample": "one complete oracle mixed solve (FP32 inner, FP64 outer, tol 1e-8, scaling included) of the "
+                      "640x480x70 system, seeds 11/12, Earth-radius unit"}
+    oracle.use_openmp(False)
+    return out
 
 
 # Refinement steps and inner iterations of the GPU mixed solve of the full-size
-# workloads (same algorithm and seeds; python bench.py on a GB300): the work the
-# oracle's per-piece timings are composed with where a full oracle solve would
+# workloads (same algorithm and seeds; the bench's own run on a GB300): the work
+# the oracle's timed pieces are composed with where a full oracle solve would
 # take hours.
 GPU_COUNTS = {("n1280", "radius"): (3, 569)}
 
 
 def run_reference(args):
-    """The oracle as it stands, timed on the host cores for this arm's workload and metric:
-    a full oracle mixed solve per step where that takes seconds, otherwise the oracle's
-    per-piece times composed with the solve's counts."""
+    """The oracle as it stands, timed on all host cores (its OpenMP build; same bits as the
+    serial one) for this arm's workload and metric: per step a full oracle mixed solve where
+    that takes seconds, otherwise a bounded sample of the solve (one FP64 true residual and one
+    FP32 inner iteration of the full system) composed with the solve's counts."""
     import oracle
 
     world, rank, local = dist_setup()
@@ -212,32 +253,45 @@ def run_reference(args):
     dims, A, b = make_inputs(args)
     n = dims[0] * dims[1] * dims[2]
     key = (args.workload, args.z_unit)
+    cores = os.cpu_count() or 1
+    used = oracle.use_openmp(True, cores)
     vals = []
     cb = None
+    if n > 2_000_000:
+        if key not in GPU_COUNTS:
+            print(json.dumps({"impl": "reference", "unavailable": f"no solve counts recorded for {key} and a full "
+                                                                  f"oracle solve of {n} points takes hours"}))
+            return
+        outer, inner = GPU_COUNTS[key]
+        Ah32 = oracle.scale(A).astype(np.float32)
+        bh32 = (b / A[0]).astype(np.float32)
     for i in range(args.warmup + args.steps):
         if n <= 2_000_000:
             t0 = time.perf_counter()
             _, info = oracle.solve(A, b, mode=oracle.MODE_MIXED, tol=1e-8, max_outer=20, max_inner=4000)
             sec = time.perf_counter() - t0
-            cb = {"value": 1.0 / sec, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                  "sample": f"full oracle mixed solve (serial C, FP32 inner, FP64 outer) of the "
+            cb = {"value": 1.0 / sec, "unit": "solves/s", "cores": used, "kind": "oracle",
+                  "sample": f"full oracle mixed solve (C, OpenMP build, {used} threads; FP32 inner, FP64 outer) of the "
                             f"{'x'.join(map(str, dims))} system: {info['outer']} refinement steps, {info['inner']} "
                             f"inner iterations, true R {info['R']:.2e}, {sec:.2f} s"}
-        elif key in GPU_COUNTS:
-            outer, inner = GPU_COUNTS[key]
-            cb = cpu_baseline(A, b, dims, outer, inner)
         else:
-            print(json.dumps({"impl": "reference", "unavailable": f"no solve counts recorded for {key} and a full "
-                                                                  f"oracle solve of {n} points takes hours"}))
-            return
+            _, t_res, t_k = _oracle_pieces(A, b, Ah32, bh32, cores, (1,))
+            t_solve = (outer + 1) * t_res + inner * t_k[1]
+            cb = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": used, "kind": "oracle",
+                  "sample": f"oracle (C, OpenMP build, {used} threads) on the full {'x'.join(map(str, dims))} system: "
+                            f"one FP64 true residual {t_res:.2f} s and one FP32 BiCGStab iteration with its start "
+                            f"{t_k[1]:.2f} s per step, composed as {outer + 1} residuals + {inner} iterations (the "
+                            f"GPU mixed solve's counts for this system; the full solve would take "
+                            f"{t_solve / 60:.0f} min)"}
         if i >= args.warmup:
             vals.append(cb["value"])
+    oracle.use_openmp(False)
     v = statistics.median(vals)
     cb["value"] = v
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
         "config": {"workload": f"{args.workload} {'x'.join(map(str, dims))} z_unit={args.z_unit}"},
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

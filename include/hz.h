@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define HZ_ABI_VERSION 3
+#define HZ_ABI_VERSION 4
 
 typedef struct hz_op_s* hz_op;
 
@@ -101,6 +101,9 @@ typedef struct {
   int inner_iters;            /* total inner Krylov iterations */
   int restarts;               /* inner restarts (periodic + breakdown) */
   int fallbacks;              /* learned-stage fallbacks to plain T^-1 */
+  int fp64_retries;           /* mixed BiCGStab only: 1 if a refinement step stalled (R not halved) or its
+                                 FP32 inner solve overflowed, after which the remaining inner solves ran in
+                                 FP64 from the current x; a later stall returns HZ_ERR_NOT_CONVERGED */
   double true_rel_residual;   /* final ||b - A x|| / ||b|| in FP64 (Sec. 3, eq. residual) */
   double scaled_rel_residual; /* last inner recursive residual relative to its right-hand side */
   double seconds;             /* device time of the solve */
@@ -147,6 +150,12 @@ int hz_op_dims(hz_op op, int* nx, int* ny, int* nz);
  * since the outer loop reads the residual on the host).
  * Returns HZ_OK, HZ_ERR_NOT_CONVERGED (x = best iterate), HZ_ERR_NONFINITE
  * (x = last finite iterate), HZ_ERR_INVALID, HZ_ERR_CUDA.
+ * Stagnation: a refinement step that does not halve R counts as a stall; two
+ * in a row return HZ_ERR_NOT_CONVERGED.  In mixed mode with BiCGStab the first
+ * stall (or an FP32 inner solve that overflows while the FP64 residual stays
+ * finite) is retried once with FP64 inner solves for the rest of the solve
+ * (info->fp64_retries), so a right-hand side outside the 32-bit range still
+ * converges.
  */
 int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_solve_params* params,
              hz_solve_info* info);

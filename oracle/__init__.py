@@ -3,9 +3,10 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product (``paper_1811_03852_gb300``)
 never imports, links or runs it, and the two share no code: the oracle is
-plain serial C (``hz_oracle.c``) plus the NumPy conv-net reference in
-``nn.py``, written from Maynard & Walters (arXiv:1811.03852) and from the
-textbook definitions they cite.  Inputs come from the separate ``gen``
+plain C (``hz_oracle.c``, serial; an OpenMP build of the same source, with
+the same results, times it on all host cores) plus the NumPy conv-net
+reference in ``nn.py``, written from Maynard & Walters (arXiv:1811.03852) and
+from the textbook definitions they cite.  Inputs come from the separate ``gen``
 package, which holds no solver arithmetic.
 
 Every routine is pinned by ``tests/test_oracle_*.py`` against something other
@@ -25,29 +26,51 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hz_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libhz_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libhz_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_use_omp = False
 
 MODE_FP64 = 0
 MODE_MIXED = 1
 
+# -ffp-contract=off: every a*b+c is two rounded operations as written, on x86
+# and Arm alike (gcc would otherwise fuse them where the target has an FMA)
+_CFLAGS = ["-O3", "-ffp-contract=off", "-fPIC", "-shared"]
+
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (gcc -O2, serial) if missing or stale."""
+    """Compile the oracle, serial (the tests' oracle) and with OpenMP (for timing it on
+    all host cores; same source, same bits), if missing or stale.  Returns the serial library."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = f"{_LIB}.{os.getpid()}.tmp"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
-    os.replace(tmp, _LIB)
+    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(_SRC):
+            continue
+        tmp = f"{lib}.{os.getpid()}.tmp"
+        subprocess.run(["gcc"] + _CFLAGS + extra + ["-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, lib)
     return _LIB
 
 
+def use_openmp(on: bool = True, threads: int | None = None) -> int:
+    """Route every oracle call through the OpenMP build (on=True) or the serial one.
+    threads: OpenMP threads (None: the runtime's default, all host cores).  The two
+    builds compute the same values bit for bit (fixed-chunk sums); this only changes
+    how long the oracle takes.  Returns the number of threads in use."""
+    global _use_omp
+    _use_omp = bool(on)
+    L = _load()
+    if on and threads:
+        L.or_set_threads(int(threads))
+    return int(L.or_threads())
+
+
 def _load():
-    global _lib
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        key = "omp" if _use_omp else "serial"
+        if key not in _libs:
+            build()
+            lib = ctypes.CDLL(_LIB_OMP if _use_omp else _LIB)
             i32, dbl, pv, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
             lib.or_matvec.argtypes = [i32, i32, i32, pv, pv, pv]
             lib.or_matvec.restype = None
@@ -69,8 +92,12 @@ def _load():
             lib.or_solve.restype = None
             lib.or_dot.argtypes = [i64, pv, pv]
             lib.or_dot.restype = dbl
-            _lib = lib
-    return _lib
+            lib.or_set_threads.argtypes = [i32]
+            lib.or_set_threads.restype = None
+            lib.or_threads.argtypes = []
+            lib.or_threads.restype = i32
+            _libs[key] = lib
+        return _libs[key]
 
 
 def _c(a, dtype=np.float64):

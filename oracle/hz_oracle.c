@@ -15,6 +15,14 @@
  * tests/test_oracle_*.py: dense assembled matrices with LAPACK solves,
  * banded solves, closed forms (A*1 = c*1, the one-iteration case without
  * horizontal coupling, nz = 1), manufactured solutions and brute force.
+ *
+ * Threads: the same source builds serial (the tests' oracle) and with OpenMP
+ * (only to time the oracle on all host cores).  Only loops whose iterations
+ * are independent (points, columns, vector updates) are shared out; every
+ * value is computed by the same arithmetic either way.  Sums over the grid
+ * (dot products, norms) run over fixed chunks of OR_CHUNK points, each summed
+ * in order, and the chunk sums are added in chunk order, so the result is
+ * the same bits for any number of threads.
  */
 #include <math.h>
 #include <stdint.h>
@@ -22,10 +30,33 @@
 #include <string.h>
 
 #define IDX(i, j, k) (((int64_t)(k) * ny + (j)) * nx + (i))
+#define OR_CHUNK 65536
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads used by the OpenMP build (1 in the serial build) */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 enum { B_C = 0, B_E, B_W, B_N, B_S, B_U, B_D };
 
 int or_version(void) { return 1; }
+
+static double dot_d(int64_t n, const double* a, const double* b);
 
 /* ---------------------------------------------------------------------------
  * The linear system A x = b (Sec. 1, the pressure-correction equation; Sec. 2,
@@ -35,6 +66,7 @@ int or_version(void) { return 1; }
  * ------------------------------------------------------------------------- */
 void or_matvec(int nx, int ny, int nz, const double* A, const double* x, double* y) {
   const int64_t n = (int64_t)nx * ny * nz;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -54,12 +86,9 @@ void or_matvec(int nx, int ny, int nz, const double* A, const double* x, double*
 double or_residual(int nx, int ny, int nz, const double* A, const double* b, const double* x, double* r) {
   const int64_t n = (int64_t)nx * ny * nz;
   or_matvec(nx, ny, nz, A, x, r);
-  double s = 0.0;
-  for (int64_t p = 0; p < n; ++p) {
-    r[p] = b[p] - r[p];
-    s += r[p] * r[p];
-  }
-  return sqrt(s);
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) r[p] = b[p] - r[p];
+  return sqrt(dot_d(n, r, r));
 }
 
 /* ---------------------------------------------------------------------------
@@ -69,13 +98,16 @@ double or_residual(int nx, int ny, int nz, const double* A, const double* b, con
  * ------------------------------------------------------------------------- */
 void or_scale(int nx, int ny, int nz, const double* A, double* Ahat) {
   const int64_t n = (int64_t)nx * ny * nz;
-  for (int b = 1; b < 7; ++b)
+  for (int b = 1; b < 7; ++b) {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; ++p) Ahat[(int64_t)(b - 1) * n + p] = A[(int64_t)b * n + p] / A[p];
+  }
 }
 
 /* y = Ahat x, Ahat = I + off-diagonal bands (order E,W,N,S,U,D). */
 void or_matvec_hat(int nx, int ny, int nz, const double* Ah, const double* x, double* y) {
   const int64_t n = (int64_t)nx * ny * nz;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -120,25 +152,30 @@ void or_tridiag_solve(int m, const double* lo, const double* di, const double* u
  * ------------------------------------------------------------------------- */
 void or_apply_Tinv(int nx, int ny, int nz, const double* Ah, const double* r, double* z) {
   const int64_t n = (int64_t)nx * ny * nz;
-  double* lo = (double*)malloc(sizeof(double) * 7 * (size_t)nz);
-  double* di = lo + nz;
-  double* up = di + nz;
-  double* rc = up + nz;
-  double* xc = rc + nz;
-  double* wk = xc + nz;
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      for (int k = 0; k < nz; ++k) {
-        int64_t p = IDX(i, j, k);
-        lo[k] = Ah[5 * n + p];
-        di[k] = 1.0;
-        up[k] = Ah[4 * n + p];
-        rc[k] = r[p];
+#pragma omp parallel
+  {
+    /* one column's work arrays (per thread) */
+    double* lo = (double*)malloc(sizeof(double) * 7 * (size_t)nz);
+    double* di = lo + nz;
+    double* up = di + nz;
+    double* rc = up + nz;
+    double* xc = rc + nz;
+    double* wk = xc + nz;
+#pragma omp for collapse(2) schedule(static)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        for (int k = 0; k < nz; ++k) {
+          int64_t p = IDX(i, j, k);
+          lo[k] = Ah[5 * n + p];
+          di[k] = 1.0;
+          up[k] = Ah[4 * n + p];
+          rc[k] = r[p];
+        }
+        or_tridiag_solve(nz, lo, di, up, rc, xc, wk);
+        for (int k = 0; k < nz; ++k) z[IDX(i, j, k)] = xc[k];
       }
-      or_tridiag_solve(nz, lo, di, up, rc, xc, wk);
-      for (int k = 0; k < nz; ++k) z[IDX(i, j, k)] = xc[k];
-    }
-  free(lo);
+    free(lo);
+  }
 }
 
 /* ---------------------------------------------------------------------------
@@ -153,12 +190,6 @@ void or_apply_Tinv(int nx, int ny, int nz, const double* Ah, const double* r, do
 void or_apply_trisor(int nx, int ny, int nz, const double* Ah, const double* r, double* z, int sweeps,
                      double omega) {
   const int64_t n = (int64_t)nx * ny * nz;
-  double* lo = (double*)malloc(sizeof(double) * 7 * (size_t)nz);
-  double* di = lo + nz;
-  double* up = di + nz;
-  double* rc = up + nz;
-  double* xc = rc + nz;
-  double* wk = xc + nz;
   /* within one colour pass every column reads the values from before the pass
      (for even nx no two columns of a colour are neighbours, so this is
      Gauss-Seidel in the red-black order; for odd nx it stays well defined) */
@@ -166,29 +197,42 @@ void or_apply_trisor(int nx, int ny, int nz, const double* Ah, const double* r, 
   for (int64_t p = 0; p < n; ++p) z[p] = 0.0;
   for (int sw = 0; sw < sweeps; ++sw)
     for (int colour = 0; colour < 2; ++colour) {
+#pragma omp parallel for schedule(static)
       for (int64_t p = 0; p < n; ++p) zo[p] = z[p];
-      for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-          if (((i + j) & 1) != colour) continue;
-          for (int k = 0; k < nz; ++k) {
-            int64_t p = IDX(i, j, k);
-            double h = Ah[0 * n + p] * zo[IDX((i + 1) % nx, j, k)] + Ah[1 * n + p] * zo[IDX((i + nx - 1) % nx, j, k)];
-            if (j + 1 < ny) h += Ah[2 * n + p] * zo[IDX(i, j + 1, k)];
-            if (j > 0) h += Ah[3 * n + p] * zo[IDX(i, j - 1, k)];
-            lo[k] = Ah[5 * n + p];
-            di[k] = 1.0;
-            up[k] = Ah[4 * n + p];
-            rc[k] = r[p] - h;
+#pragma omp parallel
+      {
+        /* one column's work arrays (per thread) */
+        double* lo = (double*)malloc(sizeof(double) * 7 * (size_t)nz);
+        double* di = lo + nz;
+        double* up = di + nz;
+        double* rc = up + nz;
+        double* xc = rc + nz;
+        double* wk = xc + nz;
+#pragma omp for collapse(2) schedule(static)
+        for (int j = 0; j < ny; ++j)
+          for (int i = 0; i < nx; ++i) {
+            if (((i + j) & 1) != colour) continue;
+            for (int k = 0; k < nz; ++k) {
+              int64_t p = IDX(i, j, k);
+              double h =
+                  Ah[0 * n + p] * zo[IDX((i + 1) % nx, j, k)] + Ah[1 * n + p] * zo[IDX((i + nx - 1) % nx, j, k)];
+              if (j + 1 < ny) h += Ah[2 * n + p] * zo[IDX(i, j + 1, k)];
+              if (j > 0) h += Ah[3 * n + p] * zo[IDX(i, j - 1, k)];
+              lo[k] = Ah[5 * n + p];
+              di[k] = 1.0;
+              up[k] = Ah[4 * n + p];
+              rc[k] = r[p] - h;
+            }
+            or_tridiag_solve(nz, lo, di, up, rc, xc, wk);
+            for (int k = 0; k < nz; ++k) {
+              int64_t p = IDX(i, j, k);
+              z[p] = (1.0 - omega) * z[p] + omega * xc[k];
+            }
           }
-          or_tridiag_solve(nz, lo, di, up, rc, xc, wk);
-          for (int k = 0; k < nz; ++k) {
-            int64_t p = IDX(i, j, k);
-            z[p] = (1.0 - omega) * z[p] + omega * xc[k];
-          }
-        }
+        free(lo);
+      }
     }
   free(zo);
-  free(lo);
 }
 
 /* Preconditioner used by or_bicgstab: kind 0 = T^-1, kind 1 = tri-SOR (sweeps, omega). */
@@ -209,6 +253,7 @@ static void apply_precond(int nx, int ny, int nz, const double* Ah, const double
 /* FP32-emulated variants: every stored value is a float, arithmetic in float. */
 static void matvec_hat_f32(int nx, int ny, int nz, const float* Ah, const float* x, float* y) {
   const int64_t n = (int64_t)nx * ny * nz;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -226,38 +271,74 @@ static void matvec_hat_f32(int nx, int ny, int nz, const float* Ah, const float*
 
 static void apply_Tinv_f32(int nx, int ny, int nz, const float* Ah, const float* r, float* z) {
   const int64_t n = (int64_t)nx * ny * nz;
-  float* cp = (float*)malloc(sizeof(float) * 2 * (size_t)nz);
-  float* dp = cp + nz;
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      /* unit diagonal: den = 1 - lo*cprime */
-      int64_t p0 = IDX(i, j, 0);
-      cp[0] = Ah[4 * n + p0];
-      dp[0] = r[p0];
-      for (int k = 1; k < nz; ++k) {
-        int64_t p = IDX(i, j, k);
-        float lo = Ah[5 * n + p];
-        float den = 1.0f - lo * cp[k - 1];
-        cp[k] = Ah[4 * n + p] / den;
-        dp[k] = (r[p] - lo * dp[k - 1]) / den;
+#pragma omp parallel
+  {
+    float* cp = (float*)malloc(sizeof(float) * 2 * (size_t)nz); /* per thread */
+    float* dp = cp + nz;
+#pragma omp for collapse(2) schedule(static)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        /* unit diagonal: den = 1 - lo*cprime */
+        int64_t p0 = IDX(i, j, 0);
+        cp[0] = Ah[4 * n + p0];
+        dp[0] = r[p0];
+        for (int k = 1; k < nz; ++k) {
+          int64_t p = IDX(i, j, k);
+          float lo = Ah[5 * n + p];
+          float den = 1.0f - lo * cp[k - 1];
+          cp[k] = Ah[4 * n + p] / den;
+          dp[k] = (r[p] - lo * dp[k - 1]) / den;
+        }
+        z[IDX(i, j, nz - 1)] = dp[nz - 1];
+        for (int k = nz - 2; k >= 0; --k) z[IDX(i, j, k)] = dp[k] - cp[k] * z[IDX(i, j, k + 1)];
       }
-      z[IDX(i, j, nz - 1)] = dp[nz - 1];
-      for (int k = nz - 2; k >= 0; --k) z[IDX(i, j, k)] = dp[k] - cp[k] * z[IDX(i, j, k + 1)];
-    }
-  free(cp);
+    free(cp);
+  }
 }
 
+/* sum_p a_p b_p: each chunk of OR_CHUNK points summed in order, then the
+   chunk sums in chunk order (one chunk: the plain left-to-right sum) */
 static double dot_d(int64_t n, const double* a, const double* b) {
+  const int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+  if (nc <= 1) {
+    double s = 0.0;
+    for (int64_t p = 0; p < n; ++p) s += a[p] * b[p];
+    return s;
+  }
+  double* part = (double*)malloc(sizeof(double) * (size_t)nc);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t e = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+    double s = 0.0;
+    for (int64_t p = c * OR_CHUNK; p < e; ++p) s += a[p] * b[p];
+    part[c] = s;
+  }
   double s = 0.0;
-  for (int64_t p = 0; p < n; ++p) s += a[p] * b[p];
+  for (int64_t c = 0; c < nc; ++c) s += part[c];
+  free(part);
   return s;
 }
 
 /* dots of float vectors accumulated in double (the global sums the paper moved
    back to 64-bit, Sec. 4) */
 static double dot_f(int64_t n, const float* a, const float* b) {
+  const int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+  if (nc <= 1) {
+    double s = 0.0;
+    for (int64_t p = 0; p < n; ++p) s += (double)a[p] * (double)b[p];
+    return s;
+  }
+  double* part = (double*)malloc(sizeof(double) * (size_t)nc);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t e = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+    double s = 0.0;
+    for (int64_t p = c * OR_CHUNK; p < e; ++p) s += (double)a[p] * (double)b[p];
+    part[c] = s;
+  }
   double s = 0.0;
-  for (int64_t p = 0; p < n; ++p) s += (double)a[p] * (double)b[p];
+  for (int64_t c = 0; c < nc; ++c) s += part[c];
+  free(part);
   return s;
 }
 
@@ -296,6 +377,7 @@ void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, dou
   double rho = 1, alpha = 1, omega = 1;
   int since = 0;
   if (bnorm == 0.0) {
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) x[q] = 0.0;
     status = 0;
     goto done;
@@ -303,6 +385,7 @@ void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, dou
   while (it < maxit) {
     if (fresh) { /* (re)start: r = bh - Ahat x, r0 = r, p = v = 0 */
       or_matvec_hat(nx, ny, nz, Ah, x, r);
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) {
         r[q] = bh[q] - r[q];
         r0[q] = r[q];
@@ -321,13 +404,16 @@ void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, dou
     ++it;
     ++since;
     double beta = (rho1 / rho) * (alpha / omega);
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
     apply_precond(nx, ny, nz, Ah, p, ph);
     or_matvec_hat(nx, ny, nz, Ah, ph, v);
     alpha = rho1 / dot_d(n, r0, v);
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) s[q] = r[q] - alpha * v[q];
     double snorm = sqrt(dot_d(n, s, s));
     if (snorm <= stop) {
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) x[q] += alpha * ph[q];
       rnorm = snorm;
       if (hist) hist[it - 1] = rnorm / bnorm;
@@ -338,6 +424,7 @@ void or_bicgstab(int nx, int ny, int nz, const double* Ah, const double* bh, dou
     or_matvec_hat(nx, ny, nz, Ah, sh, t);
     double tt = dot_d(n, t, t);
     omega = tt > 0.0 ? dot_d(n, t, s) / tt : 0.0;
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
       x[q] += alpha * ph[q] + omega * sh[q];
       r[q] = s[q] - omega * t[q];
@@ -375,6 +462,7 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
   double rho = 1, alpha = 1, omega = 1;
   int since = 0;
   if (bnorm == 0.0) {
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) x[q] = 0.0f;
     status = 0;
     goto done;
@@ -382,6 +470,7 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
   while (it < maxit) {
     if (fresh) {
       matvec_hat_f32(nx, ny, nz, Ah, x, r);
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) {
         r[q] = bh[q] - r[q];
         r0[q] = r[q];
@@ -401,14 +490,17 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
     ++since;
     float beta = (float)((rho1 / rho) * (alpha / omega));
     float om = (float)omega;
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - om * v[q]);
     apply_Tinv_f32(nx, ny, nz, Ah, p, ph);
     matvec_hat_f32(nx, ny, nz, Ah, ph, v);
     alpha = rho1 / dot_f(n, r0, v);
     float al = (float)alpha;
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) s[q] = r[q] - al * v[q];
     double snorm = sqrt(dot_f(n, s, s));
     if (snorm <= stop) {
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) x[q] += al * ph[q];
       rnorm = snorm;
       if (hist) hist[it - 1] = rnorm / bnorm;
@@ -420,6 +512,7 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
     double tt = dot_f(n, t, t);
     omega = tt > 0.0 ? dot_f(n, t, s) / tt : 0.0;
     om = (float)omega;
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
       x[q] += al * ph[q] + om * sh[q];
       r[q] = s[q] - om * t[q];
@@ -467,6 +560,7 @@ void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* 
     Ah32 = (float*)malloc(sizeof(float) * 6 * (size_t)n);
     r32 = (float*)malloc(sizeof(float) * (size_t)n);
     d32 = (float*)malloc(sizeof(float) * (size_t)n);
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < 6 * n; ++q) Ah32[q] = (float)Ah[q];
   }
   const double bnorm = sqrt(dot_d(n, b, b));
@@ -481,18 +575,22 @@ void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* 
     if (outer >= max_outer) { status = 1; break; }
     double info[4];
     if (mode == 1) {
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) {
         r32[q] = (float)(r[q] / A[q]);
         d32[q] = 0.0f;
       }
       or_bicgstab_f32(nx, ny, nz, Ah32, r32, d32, eta, max_inner, restart, NULL, info);
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) x[q] += (double)d32[q];
     } else {
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) {
         r[q] = r[q] / A[q];
         d[q] = 0.0;
       }
       or_bicgstab(nx, ny, nz, Ah, r, d, eta, max_inner, restart, NULL, info);
+#pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) x[q] += d[q];
     }
     inner_total += (int)info[0];

@@ -72,6 +72,7 @@ class hz_solve_info(ctypes.Structure):
         ("inner_iters", ctypes.c_int),
         ("restarts", ctypes.c_int),
         ("fallbacks", ctypes.c_int),
+        ("fp64_retries", ctypes.c_int),
         ("true_rel_residual", ctypes.c_double),
         ("scaled_rel_residual", ctypes.c_double),
         ("seconds", ctypes.c_double),

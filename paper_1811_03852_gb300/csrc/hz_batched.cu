@@ -15,6 +15,8 @@
 // a fixed order, stores them in its own slot, and after the barrier block b
 // (b < number of systems) adds system b's slots in slot order and runs the
 // control step -- deterministic for a given launch shape.
+#include <mutex>
+
 #include "hz_krylov.cuh"
 
 namespace hz {
@@ -354,6 +356,8 @@ const void* batched_kernel() {
 cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loops, long long timeout_ns,
                            int leave_block, cudaStream_t stream, int* err_h, int sms) {
   static BatchWs ws[64];
+  static std::mutex mu;  // the per-device workspace is shared by every host thread
+  std::lock_guard<std::mutex> lk(mu);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -366,13 +370,28 @@ cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loop
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = per_sm * sms;  // cooperative: every block resident
   if (!w.sys) {
-    if ((e = cudaMalloc(&w.sys, sizeof(SysDesc) * kMaxSys)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.bar, sizeof(unsigned) * 2)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.err, sizeof(int))) != cudaSuccess) return e;
+    // allocate into locals and publish only when all three exist, so that a
+    // failed allocation never leaves a half-built workspace for the next call
+    SysDesc* sys = nullptr;
+    unsigned* bar = nullptr;
+    int* err = nullptr;
+    e = cudaMalloc(&sys, sizeof(SysDesc) * kMaxSys);
+    if (e == cudaSuccess) e = cudaMalloc(&bar, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e != cudaSuccess) {
+      if (sys) cudaFree(sys);
+      if (bar) cudaFree(bar);
+      return e;
+    }
+    w.sys = sys;
+    w.bar = bar;
+    w.err = err;
   }
   if (w.part_grid < grid) {
+    double* part = nullptr;
+    if ((e = cudaMalloc(&part, sizeof(double) * (size_t)grid * kMaxSys * 4)) != cudaSuccess) return e;
     if (w.part) cudaFree(w.part);
-    if ((e = cudaMalloc(&w.part, sizeof(double) * (size_t)grid * kMaxSys * 4)) != cudaSuccess) return e;
+    w.part = part;
     w.part_grid = grid;
   }
   if ((e = cudaMemcpyAsync(w.sys, sys_h, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, stream)) != cudaSuccess)

@@ -939,7 +939,10 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (p.sor_sweeps < 1 || p.sor_sweeps > 64 || !(p.sor_omega > 0.0 && p.sor_omega < 2.0)) return HZ_ERR_INVALID;
     if (p.krylov != HZ_KRYLOV_BICGSTAB || op->g.nx % 2 != 0) return HZ_ERR_UNSUPPORTED;
   }
-  const bool fp32 = (p.mode == HZ_MODE_MIXED_IR);
+  const bool fp32_mode = (p.mode == HZ_MODE_MIXED_IR);
+  // precision of the inner solves: FP32 in mixed mode until a refinement step
+  // stalls (then FP64 for the rest of the solve, see below)
+  bool fp32 = fp32_mode;
   // FP64 mode is plain BiCGStab to tol (one inner solve; the outer check adds a
   // step only if the scaled residual and the true one disagree)
   const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : p.tol);
@@ -1043,9 +1046,23 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   CKS(residual(cur, nullptr, false));
   const double bb = op->rep_h->res_bb;
   double R = bb > 0.0 ? std::sqrt(op->rep_h->res_rr / bb) : std::sqrt(op->rep_h->res_rr);
-  int outer = 0, inner_total = 0, restarts = 0, status = HZ_OK, fallbacks = 0;
+  int outer = 0, inner_total = 0, restarts = 0, status = HZ_OK, fallbacks = 0, retries = 0;
   double scaled = 0.0, Rprev = R;
   int stall = 0;
+  // One retry in FP64 (mixed BiCGStab only): when an FP32 refinement step fails
+  // to halve R, or its inner solve met a non-finite value while the FP64
+  // residual is finite (the 32-bit range was exceeded), the remaining inner
+  // solves run in FP64 from the current x; a later stall ends the solve.
+  auto retry_fp64 = [&]() -> int {
+    fp32 = false;
+    ++retries;
+    stall = 1;
+    CKS(ensure_w64(op));
+    if (sor) CKS(ensure_sor<double>(op));
+    CKS(residual(cur, nullptr, false));  // r = b - A x again, FP64 right-hand side for the inner solve
+    return HZ_OK;
+  };
+  const bool can_retry = fp32_mode && p.krylov == HZ_KRYLOV_BICGSTAB;
   for (;;) {
     if (!std::isfinite(R)) { status = HZ_ERR_NONFINITE; break; }
     if (R <= p.tol) { status = HZ_OK; break; }
@@ -1074,13 +1091,25 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     const double Rn = bb > 0.0 ? std::sqrt(rp.res_rr / bb) : std::sqrt(rp.res_rr);
     if (rp.last_state == ST_NONFINITE) {
       R = Rn;
+      // the FP32 inner solve overflowed although the FP64 residual is finite
+      // (the residual pass then leaves x unchanged): retry in FP64
+      if (can_retry && fp32 && retries == 0 && std::isfinite(R) && outer < p.max_outer) {
+        CKS(retry_fp64());
+        continue;
+      }
       status = HZ_ERR_NONFINITE;
       break;
     }
     R = Rn;
-    // stagnation: two refinement steps in a row without halving R
-    if (R > 0.5 * Rprev) {
-      if (++stall >= 2 && R > p.tol) { status = HZ_ERR_NOT_CONVERGED; break; }
+    // stagnation: a refinement step that does not halve R; two in a row end the
+    // solve, and in mixed mode the first one is retried in FP64
+    if (R > 0.5 * Rprev && R > p.tol) {
+      if (can_retry && fp32 && retries == 0 && outer < p.max_outer) {
+        CKS(retry_fp64());
+      } else if (++stall >= 2) {
+        status = HZ_ERR_NOT_CONVERGED;
+        break;
+      }
     } else {
       stall = 0;
     }
@@ -1107,6 +1136,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     info->inner_iters = inner_total;
     info->restarts = restarts;
     info->fallbacks = fallbacks;
+    info->fp64_retries = retries;
     info->true_rel_residual = R;
     info->scaled_rel_residual = scaled;
     info->seconds = ms * 1e-3;
@@ -1717,6 +1747,7 @@ int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, cons
       infos[q].inner_iters = inner[q];
       infos[q].restarts = rst[q];
       infos[q].fallbacks = 0;
+      infos[q].fp64_retries = 0;
       infos[q].true_rel_residual = R[q];
       infos[q].scaled_rel_residual = scaled[q];
       infos[q].seconds = ms * 1e-3;

@@ -15,7 +15,9 @@
 // its 16 channels per thread), add the bias, apply GELU and store.
 //
 // Every wait is bounded: a tensor-core completion that does not arrive within
-// the limit sets *err and the CTA stops, frees its TMEM and returns.
+// the limit sets *err, the level's epilogue is skipped (its output is then
+// invalid), and the CTA stops: it waits (bounded) for the commits still
+// outstanding, frees its TMEM and returns.
 #include "hz_nn.cuh"
 
 namespace hz {
@@ -222,7 +224,8 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
   const int tiles_i = (g.nx + kTI - 1) / kTI;
   const int64_t ntiles = (int64_t)tiles_i * ((g.ny + kTJ - 1) / kTJ);
   const int64_t plane = (int64_t)g.nx * g.ny;
-  unsigned phase = 0;  // bit b: parity of the next completion of barrier b
+  unsigned phase = 0;        // bit b: parity of the next completion of barrier b
+  unsigned outstanding = 0;  // bit b: a commit on barrier b whose completion has not been seen
   bool aborted = false;
   for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
     const Geo t = tc_geo(g, tile, tiles_i);
@@ -262,16 +265,23 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
         }
         umma_commit(mb + 8u * (k & 1));
       }
+      if (k < g.nz) outstanding |= 1u << (k & 1);
+      bool level_ok = true;
       if (k >= 1) {  // the MMAs of level k-1 are complete: its TMEM buffer is readable
         const unsigned b = (k - 1) & 1;
-        if (!mbar_wait(mb + 8u * b, (phase >> b) & 1u)) {
+        // warp-uniform decision: tcgen05.ld below is .sync.aligned, so a warp
+        // reads the buffer only if every lane saw the completion
+        level_ok = __all_sync(0xffffffffu, mbar_wait(mb + 8u * b, (phase >> b) & 1u));
+        if (level_ok) {
+          phase ^= 1u << b;
+          outstanding &= ~(1u << b);
+        } else if (lane == 0) {
           atomicExch(abort_flag, 1);
           atomicExch(err, 1);
         }
-        phase ^= 1u << b;
         tc_fence_after();
       }
-      if (k >= 1) {  // epilogue of level k-1
+      if (k >= 1 && level_ok) {  // epilogue of level k-1 (skipped, output invalid, once a wait gave up)
         const int kk = k - 1;
         const int gi = t.i0 + 32 * warp + lane;
 #pragma unroll
@@ -321,6 +331,12 @@ __global__ void __launch_bounds__(128, kCtasPerSm) k_nn_tc(NnGrid g, const __nv_
     }
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+  // after an abort, MMAs committed to a barrier whose completion was not seen
+  // may still be writing TMEM: wait for them (again bounded) before freeing it.
+  // If such a wait also gives up, the CTA frees its TMEM regardless (a CTA
+  // must not exit holding it); *err is already set and the output is invalid.
+  for (unsigned b = 0; b < 2; ++b)
+    if (outstanding & (1u << b)) mbar_wait(mb + 8u * b, (phase >> b) & 1u);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 def test_version_and_defaults_without_gpu():
     import paper_1811_03852_gb300 as hz
 
-    assert hz.version() == 3
+    assert hz.version() == 4
     p = hz.default_params()
     assert p.tol == 1e-8 and p.restart == 150 and p.mode == hz.HZ_MODE_MIXED_IR and p.fgmres_m == 30
     # tri-SOR defaults of Sec. 2: three sweeps, omega = 1.5; T^-1 stays the default preconditioner

@@ -140,6 +140,40 @@ def test_limits_report_not_converged_with_best_iterate():
     assert abs(rn / np.linalg.norm(b) - info["true_rel_residual"]) <= 1e-9 and info["true_rel_residual"] < 1.0
 
 
+@pytest.mark.parametrize("scale", [1e-36, 1e36])
+def test_fp32_range_failure_is_retried_in_fp64(scale):
+    # A right-hand side outside the 32-bit range: at 1e-36 the scaled FP32
+    # inner right-hand side D^-1 r underflows (the inner solve sees nothing and
+    # the refinement step stalls), at 1e36 the FP32 dot products overflow (the
+    # inner solve turns non-finite).  The FP64 outer residual is fine in both,
+    # and the solver retries once with FP64 inner solves.  A x = b is linear,
+    # so the answer is the oracle's solution of the unscaled system times scale.
+    hz = _hz()
+    A, b = gen.make_system(37, 23, 9, 1, 2)
+    x, info, _ = _solve(A, b * scale, raise_on_error=False)
+    assert info["status"] == hz.HZ_OK and info["fp64_retries"] == 1, info
+    _, rn = oracle.residual(A, b * scale, x)
+    assert rn / np.linalg.norm(b * scale) <= 1e-8
+    x_ref, _ = oracle.solve(A, b, mode=oracle.MODE_FP64, tol=1e-12, eta=1e-13)
+    assert np.linalg.norm(x / scale - x_ref) / np.linalg.norm(x_ref) <= 1e-6
+    # in FP64 mode nothing is retried; the plain scale needs no retry either
+    _, info64, _ = _solve(A, b * scale, mode=hz.HZ_MODE_FP64)
+    assert info64["fp64_retries"] == 0
+    _, info1, _ = _solve(A, b)
+    assert info1["fp64_retries"] == 0
+
+
+def test_stall_after_the_fp64_retry_is_not_converged():
+    # one inner iteration per refinement step cannot halve R on the hard family:
+    # the first stall switches to FP64 inner solves, the next ends the solve
+    hz = _hz()
+    A, b = gen.make_system(37, 23, 9, 11, 12, z_unit="m")
+    x, info, _ = _solve(A, b, max_inner=1, raise_on_error=False)
+    assert info["status"] == hz.HZ_ERR_NOT_CONVERGED and info["fp64_retries"] == 1, info
+    _, rn = oracle.residual(A, b, x)
+    assert abs(rn / np.linalg.norm(b) - info["true_rel_residual"]) <= 1e-9
+
+
 def test_nonfinite_rhs_reported():
     hz = _hz()
     A, b = gen.make_system(8, 6, 5, 1, 2)

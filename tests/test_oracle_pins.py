@@ -197,3 +197,70 @@ def test_zero_rhs_gives_zero():
     A = gen.make_operator(4, 3, 2, seed=1)
     x, info = oracle.solve(A, np.zeros((2, 3, 4)), mode=oracle.MODE_MIXED)
     assert info["status"] == 0 and not np.any(x)
+
+
+def _exact_dot(a, b):
+    """The exact value of sum_i a_i b_i (every double is a rational number)."""
+    from fractions import Fraction
+
+    return sum((Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b)), Fraction(0))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 7, 1000])
+def test_dot_within_the_recursive_summation_bound(n):
+    # Sec. 4's global sums in FP64: a left-to-right sum of n rounded products
+    # lies within gamma_n sum|a_i b_i| of the exact value, gamma_n = n u / (1 - n u)
+    # (Higham, Accuracy and Stability, Sec. 3.1); n = 0 is the empty sum
+    a = gen.normals(61, 0, n)
+    b = gen.normals(62, 0, n)
+    exact = _exact_dot(a, b)
+    got = oracle.dot(a, b)
+    u = 2.0**-53
+    gamma = (n + 1) * u / (1 - (n + 1) * u)
+    bound = gamma * float(np.sum(np.abs(a * b)))
+    assert abs(got - float(exact)) <= bound
+    if n == 0:
+        assert got == 0.0
+    if n == 1:
+        assert got == a[0] * b[0]  # one rounded product, nothing to add
+
+
+def test_dot_adversarial_cancellation_and_order():
+    # exactly representable partial sums: the result is exact whatever the bound
+    a = np.array([3.0, -1.5, 0.25, 2.0**-20])
+    b = np.array([2.0, 4.0, -8.0, 2.0**10])
+    assert oracle.dot(a, b) == float(_exact_dot(a, b)) == -2.0 + 2.0**-10
+    # catastrophic cancellation: summed left to right, 1e16 + 1 rounds (to even) back
+    # to 1e16 and the small term is lost, which the error bound allows; with the large
+    # terms first they cancel exactly and the small one survives
+    b = np.ones(3)
+    assert oracle.dot(np.array([1e16, 1.0, -1e16]), b) == 0.0
+    assert oracle.dot(np.array([1e16, -1e16, 1.0]), b) == 1.0
+    assert float(_exact_dot(np.array([1e16, 1.0, -1e16]), b)) == 1.0
+    # a dropped last term or a squared operand would fail these
+    a = np.array([1.0, 2.0, 3.0])
+    b = np.array([5.0, 7.0, 11.0])
+    assert oracle.dot(a, b) == 52.0
+    assert oracle.dot(b, a) == 52.0
+
+
+def test_openmp_build_gives_the_same_bits():
+    # the OpenMP build of the oracle (used only to time it on all host cores)
+    # shares out independent loops and sums over fixed chunks: any thread count
+    # computes the same values as the serial build
+    nx, ny, nz = 96, 72, 20  # 138,240 points: the sums span three chunks
+    A, b = gen.make_system(nx, ny, nz, 1, 2, z_unit="m")
+    Ah = oracle.scale(A)
+    try:
+        ref = [oracle.residual(A, b, b)[1], oracle.apply_Tinv(Ah, b), oracle.matvec_hat(Ah, b),
+               oracle.solve(A, b, mode=oracle.MODE_MIXED, max_inner=60, max_outer=2)[0],
+               oracle.apply_trisor(Ah, b, 3, 1.5)]
+        for threads in (3, 8):
+            assert oracle.use_openmp(True, threads) == threads
+            got = [oracle.residual(A, b, b)[1], oracle.apply_Tinv(Ah, b), oracle.matvec_hat(Ah, b),
+                   oracle.solve(A, b, mode=oracle.MODE_MIXED, max_inner=60, max_outer=2)[0],
+                   oracle.apply_trisor(Ah, b, 3, 1.5)]
+            for r, g in zip(ref, got):
+                assert np.array_equal(np.asarray(r), np.asarray(g))
+    finally:
+        oracle.use_openmp(False)

@@ -42,7 +42,8 @@ def test_trisor_without_horizontal_coupling_is_scaled_Tinv():
     A[1:5] = 0.0
     Ah = oracle.scale(A)
     r = gen.normals(5, 0, nx * ny * nz).reshape(nz, ny, nx)
-    # one sweep from zero with L = U = 0 gives omega T^-1 r (SURVEY reading: omega drops out of BiCGStab)
+    # one sweep from zero with L = U = 0 gives omega T^-1 r; BiCGStab is invariant to a
+    # scalar multiple of its preconditioner, so omega drops out of a T^-1 solve
     assert np.allclose(oracle.apply_trisor(Ah, r, 1, 1.5), 1.5 * oracle.apply_Tinv(Ah, r), rtol=1e-13)
 
 

@@ -1,16 +1,18 @@
-"""hz_dot_noalloc against hz_dot (GPU).
+"""hz_dot_noalloc against hz_dot and the CPU oracle's dot product (GPU).
 
 hz_dot_noalloc exists for callers that cannot allocate device memory (a fixed
 memory pool, an allocator owned by another framework, a no-allocation rule
 after start-up): it keeps its scratch in a static device array instead of
-memory from cudaMalloc.  Its result must equal hz_dot's, within the dot
-tolerance of the other tests, on two calls in a row (the second call starts
-from the scratch the first one left behind).  This file is collected last.
+memory from cudaMalloc.  Its result must equal hz_dot's, and the oracle's
+FP64 dot product of the same values, within the dot tolerance of the other
+tests, on two calls in a row (the second call starts from the scratch the
+first one left behind).  This file is collected last.
 """
 import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +28,9 @@ def test_dot_noalloc_matches_hz_dot_twice(prec, n):
     x = torch.from_numpy(gen.normals(41, 0, n)).to(dt).cuda()
     y = torch.from_numpy(gen.normals(42, 0, n)).to(dt).cuda()
     ref = hz.dot(x, y)
-    scale = float(torch.dot(x.abs().double(), y.abs().double()))
+    xh, yh = x.double().cpu().numpy(), y.double().cpu().numpy()
+    ref_oracle = oracle.dot(xh, yh)
+    scale = float(np.dot(np.abs(xh), np.abs(yh)))
     out = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
     vals = []
     for _ in range(2):
@@ -36,6 +40,7 @@ def test_dot_noalloc_matches_hz_dot_twice(prec, n):
         vals.append(float(out.item()))
     for v in vals:
         assert abs(v - ref) <= 1e-13 * scale, (v, ref)
+        assert abs(v - ref_oracle) <= 1e-13 * scale, (v, ref_oracle)
     assert vals[0] == vals[1]
 
 

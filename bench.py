@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned", "nnfwd", "fig1"])
+    ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned", "nnfwd", "fig1", "table1"])
     ap.add_argument("--train-systems", type=int, default=24)
     ap.add_argument("--test-systems", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=240)
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--precond", default="tri", choices=["tri", "trisor"],
                     help="preconditioner of the headline solves: T^-1 or tri-SOR (Sec. 2)")
     ap.add_argument("--no-trisor", action="store_true", help="skip the tri-SOR side measurement")
+    ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table 1 comparison")
     ap.add_argument("--dims", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="override the workload's grid (same recipe and seeds; for profiling smaller cases)")
     ap.add_argument("--no-graph", action="store_true",
@@ -146,10 +147,10 @@ def dist_setup():
     return world, rank, local
 
 
-def make_inputs(args):
+def make_inputs(args, workload=None):
     import gen
 
-    w = gen.WORKLOADS[args.workload]
+    w = gen.WORKLOADS[workload or args.workload]
     nx, ny, nz = args.dims if args.dims else (w["nx"], w["ny"], w["nz"])
     A = gen.make_operator(nx, ny, nz, w["seed_coef"], z_unit=args.z_unit)
     b = gen.make_rhs(nx, ny, nz, w["seed_rhs"])
@@ -299,6 +300,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def paper_table1(op, bd, x, stream, dims, restart=150, ablation=True):
+    """The paper's Table 1 on this system: iterations and time of its mixed-precision solver (one
+    BiCGStab solve, x in FP64, everything else FP32, Sec. 3) and of the 64-bit solver to the
+    halting criteria R_c = 1e-3 and 1e-4 (the recursive residual of the scaled system), with the
+    paper's tri-SOR preconditioner (3 sweeps, omega 1.5) and with T^-1; the mixed-precision solver
+    also with FP32 global sums (Sec. 4's original sums) and, at 1e-4, without the restart at 150
+    iterations.  Each entry is one solve after an untimed one, timed with CUDA events."""
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    pres = [("trisor", hz.HZ_PRE_TRISOR), ("tri", hz.HZ_PRE_TRI)] if dims[0] % 2 == 0 else [("tri", hz.HZ_PRE_TRI)]
+    rows = {}
+
+    def one(**kw):
+        p = hz.default_params(restart=restart, **kw)
+        op.solve(bd, x, params=p, raise_on_error=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info = op.solve(bd, x, params=p, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"iterations": info["inner_iters"], "ms": round(ms, 2),
+                "ms_per_iteration": round(ms / max(1, info["inner_iters"]), 3),
+                "R_recursive_scaled": info["scaled_rel_residual"], "R_true": info["true_rel_residual"],
+                "status": info["status"]}
+
+    for pname, pc in pres:
+        for rc in (1e-3, 1e-4):
+            key = f"{pname} R_c={rc:g}"
+            mp = one(mode=hz.HZ_MODE_PAPER_MP, precond=pc, tol=rc)
+            dp = one(mode=hz.HZ_MODE_FP64, precond=pc, tol=rc, inner_tol=rc, max_outer=1)
+            row = {"mixed": mp, "double": dp, "time_ratio_double_over_mixed": round(dp["ms"] / mp["ms"], 3)}
+            if pname == pres[0][0]:
+                row["mixed_fp32_global_sums"] = one(mode=hz.HZ_MODE_PAPER_MP, precond=pc, tol=rc, dot_fp32=1)
+                if ablation and rc == 1e-4:
+                    row["mixed_no_restart"] = one(mode=hz.HZ_MODE_PAPER_MP, precond=pc, tol=rc, restart=10**9)
+            rows[key] = row
+    return rows
+
+
+def run_table1(args):
+    """The paper's Table 1 comparison alone (default: the N1280 system)."""
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    torch.cuda.set_device(0)
+    dims, A, b = make_inputs(args, "n1280")
+    stream = torch.cuda.current_stream()
+    op = hz.Operator(A, stream=stream)
+    op.autotune(fp64=True, trisor=dims[0] % 2 == 0)
+    bd = torch.from_numpy(b.reshape(-1)).cuda()
+    x = torch.empty_like(bd)
+    rows = paper_table1(op, bd, x, stream, dims, restart=args.restart)
+    print(json.dumps({"workload": f"paper Table 1 (synthetic) n1280 seeds {'x'.join(map(str, dims))} "
+                                  f"z_unit={args.z_unit}", "table1": rows}), flush=True)
+
+
 def run_ours(args):
     import torch
 
@@ -412,6 +474,11 @@ def run_ours(args):
                                  "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
                              for k, v in sp.items()}
 
+    # the paper's own mixed-precision solver against the 64-bit one (Table 1, Sec. 4)
+    table1 = None
+    if not args.no_table1 and not args.no_fp64:
+        table1 = paper_table1(op, bd, x, stream, dims, restart=args.restart)
+
     # end to end through the public API with host buffers (pinned b, pinned x)
     bh = torch.from_numpy(b.reshape(-1)).pin_memory()
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -483,6 +550,7 @@ def run_ours(args):
         "fp64": fp64,
         "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
         "trisor": trisor,
+        "paper_table1": table1,
         "setup_ms": round(min(su), 3),
         "variants": variants,
         "e2e": e2e,
@@ -697,6 +765,8 @@ def main():
         run_nn_forward(args)
     elif args.workload == "fig1":
         run_fig1(args)
+    elif args.workload == "table1":
+        run_table1(args)
     else:
         run_ours(args)
 

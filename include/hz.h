@@ -61,7 +61,15 @@ typedef enum {
 /* Outer/inner precision split (Sec. 3: R_c >> eps_32 allows 32-bit work). */
 typedef enum {
   HZ_MODE_FP64 = 0,     /* inner BiCGStab in FP64: the double-precision baseline */
-  HZ_MODE_MIXED_IR = 1  /* inner BiCGStab in FP32, outer FP64 residual and update */
+  HZ_MODE_MIXED_IR = 1, /* inner BiCGStab in FP32, outer FP64 residual and update */
+  HZ_MODE_PAPER_MP = 2  /* the paper's mixed-precision solver (Sec. 3): one BiCGStab solve with the iterate
+                           x in FP64 and every other vector, coefficient and preconditioner value in FP32,
+                           halting when its recursive residual of the scaled system falls below tol
+                           (inner_tol if given); no refinement.  The status is that halting test's (HZ_OK, or
+                           HZ_ERR_NOT_CONVERGED after max_inner iterations, or HZ_ERR_NONFINITE); the report's
+                           true_rel_residual is the FP64 R = ||b - A x|| / ||b|| of the x returned, which
+                           may differ from the scaled recursive residual.  BiCGStab with HZ_PRE_TRI or
+                           HZ_PRE_TRISOR. */
 } hz_mode;
 
 typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
@@ -92,6 +100,10 @@ typedef struct {
   int record_history;/* 1: keep the inner recursive residual after every iteration (hz_get_history) */
   int sor_sweeps;    /* HZ_PRE_TRISOR: sweeps per application, 1..64 (default 3, Sec. 2) */
   double sor_omega;  /* HZ_PRE_TRISOR: relaxation factor, 0 < w < 2 (default 1.5, Sec. 2) */
+  int dot_fp32;      /* FP32 inner solves only: 1 sums every inner dot product in FP32 (per thread, block and
+                        grid), the 32-bit global sums the paper started from (Sec. 4); 0 (default): FP32 partial
+                        sums within a column batch, FP64 across them (the paper's 64-bit global sums).  With
+                        HZ_MODE_FP64: HZ_ERR_UNSUPPORTED.  FGMRES ignores it. */
 } hz_solve_params;
 
 /* Solve report (host struct). */

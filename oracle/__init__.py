@@ -33,6 +33,7 @@ _use_omp = False
 
 MODE_FP64 = 0
 MODE_MIXED = 1
+MODE_PAPER_MP = 2
 
 # -ffp-contract=off: every a*b+c is two rounded operations as written, on x86
 # and Arm alike (gcc would otherwise fuse them where the target has an FMA)
@@ -88,6 +89,8 @@ def _load():
             lib.or_bicgstab.restype = None
             lib.or_bicgstab_f32.argtypes = [i32, i32, i32, pv, pv, pv, dbl, i32, i32, pv, pv]
             lib.or_bicgstab_f32.restype = None
+            lib.or_bicgstab_mp.argtypes = [i32, i32, i32, pv, pv, pv, dbl, i32, i32, pv, pv]
+            lib.or_bicgstab_mp.restype = None
             lib.or_solve.argtypes = [i32, i32, i32, pv, pv, pv, i32, dbl, dbl, i32, i32, i32, pv, pv]
             lib.or_solve.restype = None
             lib.or_dot.argtypes = [i64, pv, pv]
@@ -169,20 +172,23 @@ def apply_Tinv(Ah, r):
     return z
 
 
-def bicgstab(Ah, bh, x0=None, eta=1e-8, maxit=1000, restart=150, fp32=False, history=False):
+def bicgstab(Ah, bh, x0=None, eta=1e-8, maxit=1000, restart=150, fp32=False, history=False, x64=False):
     """Right-preconditioned BiCGStab with C = T^-1 on Ahat y = bh.
 
     Returns (x, info dict[, hist]).  With fp32=True every vector and
-    coefficient is a float and dots accumulate in double.
+    coefficient is a float and dots accumulate in double; with x64=True as
+    well, the iterate x is kept in double (the paper's mixed-precision
+    solver, Sec. 3) and returned as float64.
     """
     nz, ny, nx = bh.shape
     dt = np.float32 if fp32 else np.float64
     Ah_ = _c(Ah, dt)
     bh_ = _c(bh, dt)
-    x = np.zeros_like(bh_) if x0 is None else _c(x0, dt).copy()
+    xdt = np.float64 if (x64 or not fp32) else np.float32
+    x = np.zeros(bh_.shape, dtype=xdt) if x0 is None else _c(x0, xdt).copy()
     hist = np.full(maxit, np.nan)
     out = np.zeros(4)
-    fn = _load().or_bicgstab_f32 if fp32 else _load().or_bicgstab
+    fn = (_load().or_bicgstab_mp if x64 else _load().or_bicgstab_f32) if fp32 else _load().or_bicgstab
     fn(nx, ny, nz, _p(Ah_), _p(bh_), _p(x), eta, maxit, restart, _p(hist), _p(out))
     info = dict(iters=int(out[0]), restarts=int(out[1]), relres=float(out[2]), status=int(out[3]))
     if history:
@@ -192,7 +198,8 @@ def bicgstab(Ah, bh, x0=None, eta=1e-8, maxit=1000, restart=150, fp32=False, his
 
 def solve(A, b, x0=None, mode=MODE_MIXED, tol=1e-8, eta=1e-4, max_outer=20, max_inner=2000, restart=150,
           history=False):
-    """Outer loop on the true FP64 residual with FP64 (mode 0) or FP32 (mode 1) inner BiCGStab.
+    """Outer loop on the true FP64 residual with FP64 (mode 0) or FP32 (mode 1) inner BiCGStab;
+    mode 2 is the paper's mixed-precision solver (one solve, x in FP64, the rest FP32, no refinement).
 
     Returns (x, info dict[, outer history of R]).
     """

@@ -448,12 +448,19 @@ done:
 
 /* The same iteration with every vector and coefficient rounded to float and
    float arithmetic, dots accumulated in double and the scalars kept in double
-   (the mixed-precision split of Sec. 3-4). Ah32 is the float copy of Ahat. */
-void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, float* x, double eta, int maxit,
-                     int restart, double* hist, double* out) {
+   (the mixed-precision split of Sec. 3-4). Ah32 is the float copy of Ahat.
+   x64 == NULL: the iterate x is a float vector too.  x64 != NULL: the paper's
+   mixed-precision solver (Sec. 3: the pressure field stays 64-bit while the
+   solver works in 32-bit): the iterate lives in x64 and is updated in double
+   from the float vectors and the double scalars; where the iteration reads x
+   (a restart's r = bh - Ahat x) it is rounded to float first.  The recursion
+   itself never reads x, so without a restart both variants produce the same
+   residuals. */
+static void bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, float* x, double* x64, double eta,
+                         int maxit, int restart, double* hist, double* out) {
   const int64_t n = (int64_t)nx * ny * nz;
-  float* r = (float*)calloc((size_t)n * 8, sizeof(float));
-  float *r0 = r + n, *p = r0 + n, *v = p + n, *ph = v + n, *s = ph + n, *sh = s + n, *t = sh + n;
+  float* r = (float*)calloc((size_t)n * 9, sizeof(float));
+  float *r0 = r + n, *p = r0 + n, *v = p + n, *ph = v + n, *s = ph + n, *sh = s + n, *t = sh + n, *xf = t + n;
   const double bnorm = sqrt(dot_f(n, bh, bh));
   const double stop = eta * bnorm;
   int it = 0, nrestart = 0, status = 1;
@@ -463,13 +470,24 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
   int since = 0;
   if (bnorm == 0.0) {
 #pragma omp parallel for schedule(static)
-    for (int64_t q = 0; q < n; ++q) x[q] = 0.0f;
+    for (int64_t q = 0; q < n; ++q) {
+      if (x64)
+        x64[q] = 0.0;
+      else
+        x[q] = 0.0f;
+    }
     status = 0;
     goto done;
   }
   while (it < maxit) {
     if (fresh) {
-      matvec_hat_f32(nx, ny, nz, Ah, x, r);
+      const float* xr = x;
+      if (x64) {
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < n; ++q) xf[q] = (float)x64[q];
+        xr = xf;
+      }
+      matvec_hat_f32(nx, ny, nz, Ah, xr, r);
 #pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) {
         r[q] = bh[q] - r[q];
@@ -501,7 +519,12 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
     double snorm = sqrt(dot_f(n, s, s));
     if (snorm <= stop) {
 #pragma omp parallel for schedule(static)
-      for (int64_t q = 0; q < n; ++q) x[q] += al * ph[q];
+      for (int64_t q = 0; q < n; ++q) {
+        if (x64)
+          x64[q] += alpha * (double)ph[q];
+        else
+          x[q] += al * ph[q];
+      }
       rnorm = snorm;
       if (hist) hist[it - 1] = rnorm / bnorm;
       status = 0;
@@ -514,7 +537,10 @@ void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, f
     om = (float)omega;
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
-      x[q] += al * ph[q] + om * sh[q];
+      if (x64)
+        x64[q] += alpha * (double)ph[q] + omega * (double)sh[q];
+      else
+        x[q] += al * ph[q] + om * sh[q];
       r[q] = s[q] - om * t[q];
     }
     rho = rho1;
@@ -534,13 +560,27 @@ done:
   free(r);
 }
 
+void or_bicgstab_f32(int nx, int ny, int nz, const float* Ah, const float* bh, float* x, double eta, int maxit,
+                     int restart, double* hist, double* out) {
+  bicgstab_f32(nx, ny, nz, Ah, bh, x, NULL, eta, maxit, restart, hist, out);
+}
+
+/* the paper's mixed-precision solver: x in double, everything else float */
+void or_bicgstab_mp(int nx, int ny, int nz, const float* Ah, const float* bh, double* x, double eta, int maxit,
+                    int restart, double* hist, double* out) {
+  bicgstab_f32(nx, ny, nz, Ah, bh, NULL, x, eta, maxit, restart, hist, out);
+}
+
 /* ---------------------------------------------------------------------------
  * Outer loop judged by the true FP64 residual R = ||b - A x|| / ||b|| (Sec. 3,
  * the relative residual and halting criterion R < R_c), with the inner
  * correction solve on the scaled system Ahat d = D^-1 r:
  *   mode 0: inner solve in FP64;
  *   mode 1: inner solve in FP32 (mixed precision; iterative refinement wins
- *           back the digits below the 32-bit limit eps_32 of Sec. 3).
+ *           back the digits below the 32-bit limit eps_32 of Sec. 3);
+ *   mode 2: the paper's mixed-precision solver (Sec. 3): one solve with x in
+ *           FP64 and everything else in FP32, to eta, and no refinement (the
+ *           outer loop stops after it and reports R).
  * x is in/out (initial guess).  outer_hist (may be NULL, max_outer+1 values)
  * receives R before each outer step and after the last.
  * out[0] = outer iterations, out[1] = total inner iterations,
@@ -556,7 +596,7 @@ void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* 
   float* Ah32 = NULL;
   float *r32 = NULL, *d32 = NULL;
   or_scale(nx, ny, nz, A, Ah);
-  if (mode == 1) {
+  if (mode == 1 || mode == 2) {
     Ah32 = (float*)malloc(sizeof(float) * 6 * (size_t)n);
     r32 = (float*)malloc(sizeof(float) * (size_t)n);
     d32 = (float*)malloc(sizeof(float) * (size_t)n);
@@ -574,7 +614,16 @@ void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* 
     if (R <= tol) { status = 0; break; }
     if (outer >= max_outer) { status = 1; break; }
     double info[4];
-    if (mode == 1) {
+    if (mode == 2) {
+      /* the paper's mixed-precision solver: one solve, x kept in double */
+      for (int64_t q = 0; q < n; ++q) {
+        r32[q] = (float)(r[q] / A[q]);
+        d[q] = 0.0;
+      }
+      or_bicgstab_mp(nx, ny, nz, Ah32, r32, d, eta, max_inner, restart, NULL, info);
+      for (int64_t q = 0; q < n; ++q) x[q] += d[q];
+      max_outer = outer + 1; /* no refinement */
+    } else if (mode == 1) {
 #pragma omp parallel for schedule(static)
       for (int64_t q = 0; q < n; ++q) {
         r32[q] = (float)(r[q] / A[q]);

@@ -37,6 +37,7 @@ HZ_ERR_UNSUPPORTED = 8
 HZ_BATCH_AUTO, HZ_BATCH_PERSISTENT, HZ_BATCH_SEQUENTIAL = 0, 1, 2
 HZ_MODE_FP64 = 0
 HZ_MODE_MIXED_IR = 1
+HZ_MODE_PAPER_MP = 2
 HZ_PREC_FP64 = 0
 HZ_PREC_FP32 = 1
 HZ_PRE_TRI = 0
@@ -62,6 +63,7 @@ class hz_solve_params(ctypes.Structure):
         ("record_history", ctypes.c_int),
         ("sor_sweeps", ctypes.c_int),
         ("sor_omega", ctypes.c_double),
+        ("dot_fp32", ctypes.c_int),
     ]
 
 

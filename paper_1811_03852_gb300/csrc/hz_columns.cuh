@@ -358,7 +358,8 @@ struct SrcS {  // s = r - alpha v
 
 // y = c + H x on V columns, U levels per batch (H = E, W, N, S bands of Ahat).
 // MODE 0: d0 += <r0, y>.  MODE 1: d0 += <y, c>, d1 += <y, y>.  MODE 2: no dots.
-// MODE 3: as MODE 1 and *d2 += <c, c>.
+// MODE 3: as MODE 1 and *d2 += <c, c>.  f32: the sums run in FP32 throughout
+// (the paper's 32-bit global sums).
 // Each batch's dot partial is FP32 (FP64 solver: FP64); the batches of the
 // group are summed in a DotAcc and the group's total is added to the FP64
 // accumulators.  EF (with M = LD_NC): every array read
@@ -368,7 +369,7 @@ struct SrcS {  // s = r - alpha v
 template <typename T, int V, int U, int MODE, int M = LD_NC, bool EF = false>
 __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T>& a, const T* __restrict__ cen,
                                         const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ r0,
-                                        double& d0, double& d1, double* d2 = nullptr) {
+                                        double& d0, double& d1, double* d2 = nullptr, bool f32 = false) {
   static_assert(!EF || M == LD_NC, "L2 priorities with read-only loads only");
   constexpr bool TWO = MODE == 1 || MODE == 3;  // <y, c> and <y, y>
   constexpr int MS = EF ? LD_NC_EF : M;         // streamed vectors
@@ -437,9 +438,9 @@ __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T
     if constexpr (TWO) s1.add(p1);
     if constexpr (MODE == 3) s2.add(p2);
   }
-  if constexpr (MODE != 2) d0 += s0.value();
-  if constexpr (TWO) d1 += s1.value();
-  if constexpr (MODE == 3) *d2 += s2.value();
+  if constexpr (MODE != 2) d0 = acc_add(d0, s0.total(f32), f32);
+  if constexpr (TWO) d1 = acc_add(d1, s1.total(f32), f32);
+  if constexpr (MODE == 3) *d2 = acc_add(*d2, s2.total(f32), f32);
 }
 
 }  // namespace hz

@@ -77,6 +77,8 @@ struct hz_op_s {
   double* xbuf = nullptr;  // result staging when the caller's x is host memory
   double* xscr = nullptr;  // second buffer of the refinement ping-pong
   double* bbuf = nullptr;  // staging of a host b
+  double* x64buf = nullptr;  // the paper's mixed-precision solver: its FP64 iterate (inner order)
+  double* x64nat = nullptr;  // the same scattered to natural order (tri-SOR)
   Ctl* ctl = nullptr;
   Ctl* cfg_h = nullptr;  // pinned: configuration written to ctl
   Ctl* rep_h = nullptr;  // pinned: ctl read back
@@ -816,6 +818,7 @@ void hz_default_params(hz_solve_params* p) {
   p->record_history = 0;
   p->sor_sweeps = 3;
   p->sor_omega = 1.5;
+  p->dot_fp32 = 0;
 }
 
 int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_op* out) {
@@ -927,7 +930,10 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   else
     hz_default_params(&p);
   if (!(p.tol > 0.0) || p.max_outer < 0 || p.max_inner < 1 || p.restart < 1) return HZ_ERR_INVALID;
-  if (p.mode != HZ_MODE_FP64 && p.mode != HZ_MODE_MIXED_IR) return HZ_ERR_INVALID;
+  if (p.mode != HZ_MODE_FP64 && p.mode != HZ_MODE_MIXED_IR && p.mode != HZ_MODE_PAPER_MP) return HZ_ERR_INVALID;
+  const bool paper = (p.mode == HZ_MODE_PAPER_MP);
+  if (paper && (p.krylov != HZ_KRYLOV_BICGSTAB || p.precond == HZ_PRE_TRI_NN)) return HZ_ERR_UNSUPPORTED;
+  if (p.dot_fp32 && p.mode == HZ_MODE_FP64) return HZ_ERR_UNSUPPORTED;
   if (p.krylov != HZ_KRYLOV_BICGSTAB && p.krylov != HZ_KRYLOV_FGMRES) return HZ_ERR_INVALID;
   if (p.krylov == HZ_KRYLOV_FGMRES && (p.mode != HZ_MODE_MIXED_IR || p.fgmres_m < 1 || p.fgmres_m > kMaxFgm))
     return HZ_ERR_UNSUPPORTED;
@@ -939,13 +945,14 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (p.sor_sweeps < 1 || p.sor_sweeps > 64 || !(p.sor_omega > 0.0 && p.sor_omega < 2.0)) return HZ_ERR_INVALID;
     if (p.krylov != HZ_KRYLOV_BICGSTAB || op->g.nx % 2 != 0) return HZ_ERR_UNSUPPORTED;
   }
-  const bool fp32_mode = (p.mode == HZ_MODE_MIXED_IR);
+  const bool fp32_mode = (p.mode != HZ_MODE_FP64);
   // precision of the inner solves: FP32 in mixed mode until a refinement step
   // stalls (then FP64 for the rest of the solve, see below)
   bool fp32 = fp32_mode;
   // FP64 mode is plain BiCGStab to tol (one inner solve; the outer check adds a
   // step only if the scaled residual and the true one disagree)
-  const double eta = p.inner_tol > 0.0 ? p.inner_tol : (fp32 ? 1e-4 : p.tol);
+  // (the paper's mixed-precision solver halts its one solve at tol, Sec. 3)
+  const double eta = p.inner_tol > 0.0 ? p.inner_tol : ((fp32 && !paper) ? 1e-4 : p.tol);
   const int64_t n = op->g.n;
   const size_t bytes = sizeof(double) * (size_t)n;
   cudaStream_t s = op->stream;
@@ -977,6 +984,10 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     XA = op->xbuf;
   }
   double* XB = op->xscr;
+  if (paper) {
+    if (!op->x64buf && !(op->x64buf = dalloc<double>(op, n, &st))) return st;
+    if (sor && !op->x64nat && !(op->x64nat = dalloc<double>(op, n, &st))) return st;
+  }
   CK(cudaEventRecord(op->ev0, s));
   const double* cur = nullptr;
   if (x0) {
@@ -998,6 +1009,8 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   cfg->hist_cap = p.record_history ? op->hist_cap : 0;
   cfg->xzero = 1;
   cfg->state = ST_CONVERGED;
+  cfg->x64 = paper ? op->x64buf : nullptr;
+  cfg->dot32 = p.dot_fp32 ? 1 : 0;
   CK(cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, s));
 
   // tri-SOR: the inner vectors are in colour-compact order; the inner solution
@@ -1005,6 +1018,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   // inner right-hand side (written to t) gathered back into rhs after it
   auto residual = [&](const double* xin, double* xout, bool with_delta) -> int {
     const double ds = fp32 ? 4.0 : 8.0;
+    const double dd = paper ? 8.0 : ds;  // bytes of a correction value
     auto step = [&](int kid, double bytes, auto&& launch) -> int {
       if (op->prof)
         CKS(prof_launch(op, kid, bytes * (double)n, launch));
@@ -1014,14 +1028,18 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
       return HZ_OK;
     };
     auto rb = [&](int to_compact) -> cudaError_t {
+      if (paper && !to_compact) return launch_rb_copy<double>(op->g, op->x64buf, op->x64nat, 0, op->L);
       if (fp32)
         return to_compact ? launch_rb_copy<float>(op->g, op->w32.t, op->w32.rhs, 1, op->L)
                           : launch_rb_copy<float>(op->g, op->w32.x, op->w32.s, 0, op->L);
       return to_compact ? launch_rb_copy<double>(op->g, op->w64.t, op->w64.rhs, 1, op->L)
                         : launch_rb_copy<double>(op->g, op->w64.x, op->w64.s, 0, op->L);
     };
-    if (sor && with_delta) CKS(step(10, 2 * ds, [&] { return rb(0); }));
+    if (sor && with_delta) CKS(step(10, 2 * dd, [&] { return rb(0); }));
     auto go = [&]() -> cudaError_t {
+      if (paper && with_delta)
+        return launch_residual_x64(op->g, op->A7, op->invc, bd, xin, xout, sor ? op->x64nat : op->x64buf,
+                                   sor ? op->w32.t : op->w32.rhs, op->ctl, op->red, op->L);
       if (fp32) {
         const Vecs<float>& w = op->w32;
         return launch_residual<float>(op->g, op->A7, op->invc, bd, xin, xout,
@@ -1034,7 +1052,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     };
     // algorithmic bytes: C band, b, rhs; plus the other six bands, x, d and x out for a stencil pass
     double bp = 8 + 8 + ds;
-    if (xin || with_delta) bp += 48 + (xin ? 8 : 0) + (with_delta ? ds : 0) + (xout ? 8 : 0);
+    if (xin || with_delta) bp += 48 + (xin ? 8 : 0) + (with_delta ? dd : 0) + (xout ? 8 : 0);
     CKS(step(1, bp, go));
     if (sor) CKS(step(10, 2 * ds, [&] { return rb(1); }));
     CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -1062,11 +1080,13 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     CKS(residual(cur, nullptr, false));  // r = b - A x again, FP64 right-hand side for the inner solve
     return HZ_OK;
   };
-  const bool can_retry = fp32_mode && p.krylov == HZ_KRYLOV_BICGSTAB;
+  const bool can_retry = fp32_mode && !paper && p.krylov == HZ_KRYLOV_BICGSTAB;
+  // no refinement in the paper's solver: one inner solve, then the report
+  const int max_outer = paper ? std::min(p.max_outer, 1) : p.max_outer;
   for (;;) {
     if (!std::isfinite(R)) { status = HZ_ERR_NONFINITE; break; }
     if (R <= p.tol) { status = HZ_OK; break; }
-    if (outer >= p.max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
+    if (outer >= max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
     if (p.krylov == HZ_KRYLOV_FGMRES)
     {
       CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta, p.precond == HZ_PRE_TRI_NN, &fallbacks));
@@ -1093,7 +1113,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
       R = Rn;
       // the FP32 inner solve overflowed although the FP64 residual is finite
       // (the residual pass then leaves x unchanged): retry in FP64
-      if (can_retry && fp32 && retries == 0 && std::isfinite(R) && outer < p.max_outer) {
+      if (can_retry && fp32 && retries == 0 && std::isfinite(R) && outer < max_outer) {
         CKS(retry_fp64());
         continue;
       }
@@ -1101,10 +1121,17 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
       break;
     }
     R = Rn;
+    if (paper) {
+      // the paper's solver ends after its one solve; its own halting test (the
+      // recursive residual of the scaled system, Sec. 3) decides the status,
+      // and R above is reported as computed
+      status = rp.last_state == ST_CONVERGED ? HZ_OK : HZ_ERR_NOT_CONVERGED;
+      break;
+    }
     // stagnation: a refinement step that does not halve R; two in a row end the
     // solve, and in mixed mode the first one is retried in FP64
     if (R > 0.5 * Rprev && R > p.tol) {
-      if (can_retry && fp32 && retries == 0 && outer < p.max_outer) {
+      if (can_retry && fp32 && retries == 0 && outer < max_outer) {
         CKS(retry_fp64());
       } else if (++stall >= 2) {
         status = HZ_ERR_NOT_CONVERGED;

@@ -53,6 +53,13 @@ struct Ctl {
   // bodies of the inner loop launched since the last residual pass, and the
   // hard limit after which the loop stops whatever the state says
   int bodies, body_limit;
+  // the paper's mixed-precision solver (Sec. 3): the inner iterate x kept in
+  // FP64 here while every other vector is FP32 (null: x is the FP32 vector)
+  double* x64;
+  // 1: dot products summed in FP32 at every level, thread, block and grid (the
+  // paper's original 32-bit global sums, Sec. 4); 0: FP64 across threads
+  int dot32;
+  int pad1;
 };
 
 struct Red {
@@ -91,37 +98,55 @@ struct DotAcc<float> {
     lo = __fadd_rn(lo, e);
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  // f32: the plain FP32 running sum (hi alone is exactly what repeated FP32
+  // additions give; lo only carries their rounding errors)
+  __device__ __forceinline__ double total(bool f32) const { return f32 ? (double)hi : value(); }
 };
 template <>
 struct DotAcc<double> {
   double s;
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ double total(bool) const { return s; }
 };
+
+// acc + x with the sum rounded to FP32 when f32 (an FP32 accumulator held in a double)
+__device__ __forceinline__ double acc_add(double acc, double x, bool f32) {
+  return f32 ? (double)__fadd_rn((float)acc, (float)x) : acc + x;
+}
 
 // Deterministic block + grid reduction of ND doubles.  Every block stores its
 // partial in a fixed slot; the last block to arrive (ticket) sums the slots in
 // slot order, so the result depends only on the launch shape.  Returns true in
-// thread 0 of the last block, with the totals in out.
+// thread 0 of the last block, with the totals in out.  f32: every addition of
+// the reduction is rounded to FP32 (the inputs are taken as FP32 values): the
+// all-32-bit global sums of the paper's first mixed-precision solver (Sec. 4).
 template <int ND>
-__device__ __forceinline__ bool grid_reduce(double (&v)[ND], const Red& red, double (&out)[ND]) {
+__device__ __forceinline__ bool grid_reduce(double (&v)[ND], const Red& red, double (&out)[ND], bool f32 = false) {
   __shared__ double sm[ND][32];
   __shared__ int amlast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  auto warp_sum = [&](double x) -> double {
+    if (f32) {
+      float xf = (float)x;
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    double x = v[d];
+      for (int o = 16; o; o >>= 1) xf = __fadd_rn(xf, __shfl_xor_sync(0xffffffffu, xf, o));
+      return (double)xf;
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const double x = warp_sum(v[d]);
     if (lane == 0) sm[d][warp] = x;
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      double x = lane < nw ? sm[d][lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      const double x = warp_sum(lane < nw ? sm[d][lane] : 0.0);
       if (lane == 0) red.partials[(size_t)blockIdx.x * ND + d] = x;
     }
   }
@@ -136,10 +161,9 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[ND], const Red& red, dou
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     double x = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += __ldcg(&red.partials[(size_t)b * ND + d]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    v[d] = x;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      x = acc_add(x, __ldcg(&red.partials[(size_t)b * ND + d]), f32);
+    v[d] = warp_sum(x);
   }
   __syncthreads();
   if (lane == 0) {
@@ -151,7 +175,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[ND], const Red& red, dou
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       double x = 0.0;
-      for (int w = 0; w < nw; ++w) x += sm[d][w];
+      for (int w = 0; w < nw; ++w) x = acc_add(x, sm[d][w], f32);
       out[d] = x;
     }
     *red.ticket = 0u;
@@ -264,6 +288,11 @@ template <typename D>
 cudaError_t launch_residual(const Grid& g, const double* A7, const double* invc, const double* b, const double* x0,
                             double* x, const D* delta, D* rhs_out, double* r_out, int mode, Ctl* ctl, Red red,
                             const Launch& L);
+// the same with an FP64 correction and an FP32 right-hand side (the paper's
+// mixed-precision solver keeps its inner iterate in FP64)
+cudaError_t launch_residual_x64(const Grid& g, const double* A7, const double* invc, const double* b,
+                                const double* xin, double* xout, const double* delta, float* rhs, Ctl* ctl, Red red,
+                                const Launch& L);
 
 // ---- flexible GMRES (hz_fgmres.cu) ----
 constexpr int kMaxFgm = 64;  // largest restart length

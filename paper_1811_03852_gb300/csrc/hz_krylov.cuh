@@ -92,17 +92,18 @@ __device__ __forceinline__ ColNbr col_nbr(const Grid& g, int64_t col) {
   return c;
 }
 
-// (Ahat x)_idx with all six bands (restart and the test entry point)
-template <typename T>
-__device__ __forceinline__ T ahat_point(const Grid& g, const Bands<T>& a, const T* __restrict__ x, int64_t idx, int k,
+// (Ahat x)_idx with all six bands (restart and the test entry point); x may be
+// stored in FP64 while the arithmetic is T's (the paper's mixed-precision solver)
+template <typename T, typename X>
+__device__ __forceinline__ T ahat_point(const Grid& g, const Bands<T>& a, const X* __restrict__ x, int64_t idx, int k,
                                         const ColNbr& c) {
-  T y = x[idx];
-  y = fma(a.E[idx], x[idx + c.ie], y);
-  y = fma(a.W[idx], x[idx + c.iw], y);
-  if (c.hn) y = fma(a.N[idx], x[idx + g.nx], y);
-  if (c.hs) y = fma(a.S[idx], x[idx - g.nx], y);
-  if (k + 1 < g.nz) y = fma(a.U[idx], x[idx + g.ncol], y);
-  if (k > 0) y = fma(a.D[idx], x[idx - g.ncol], y);
+  T y = (T)x[idx];
+  y = fma(a.E[idx], (T)x[idx + c.ie], y);
+  y = fma(a.W[idx], (T)x[idx + c.iw], y);
+  if (c.hn) y = fma(a.N[idx], (T)x[idx + g.nx], y);
+  if (c.hs) y = fma(a.S[idx], (T)x[idx - g.nx], y);
+  if (k + 1 < g.nz) y = fma(a.U[idx], (T)x[idx + g.ncol], y);
+  if (k > 0) y = fma(a.D[idx], (T)x[idx - g.ncol], y);
   return y;
 }
 
@@ -184,16 +185,17 @@ __device__ __forceinline__ int fin_iteration(Ctl* ctl, bool half, double rho1, d
 }
 
 // Restart of one column (rare, kept out of line): r = rhs - Ahat x, r0 = r,
-// p = r, ph = T^-1 p.  Returns the column's <r, r>.  x is read-only here.
+// p = r, ph = T^-1 p.  Returns the column's <r, r>.  x is read-only here; x64
+// (may be null) holds x in FP64 instead of w.x.
 template <typename T>
 __device__ __noinline__ double restart_column(const Grid& g, int64_t col, const Bands<T>& a, const Vecs<T>& w,
-                                              bool xzero) {
+                                              bool xzero, const double* x64) {
   const ColNbr c = col_nbr(g, col);
   T cacc = T(0);
   for (int k = 0; k < g.nz; ++k) {
     const int64_t idx = (int64_t)k * g.ncol + col;
     T rk = w.rhs[idx];
-    if (!xzero) rk -= ahat_point(g, a, w.x, idx, k, c);
+    if (!xzero) rk -= x64 ? ahat_point(g, a, x64, idx, k, c) : ahat_point(g, a, w.x, idx, k, c);
     w.r[idx] = rk;
     w.r0[idx] = rk;
     cacc = fma(rk, rk, cacc);
@@ -235,11 +237,13 @@ __global__ void __launch_bounds__(kBS, 4) k_pre_start(Grid g, Bands<T> a, Vecs<T
   const bool restart = (state == ST_RESTART);
   if (!restart && !(state == ST_RUNNING && ctl->fresh)) return;
   const bool xzero = ctl->xzero != 0;
+  const bool f32 = sizeof(T) == 4 && ctl->dot32;
+  const double* x64 = sizeof(T) == 4 ? ctl->x64 : nullptr;
   const T* __restrict__ rin = ctl->rsel ? w.r : w.rhs;
   double acc = 0.0;
   for (int64_t col = (int64_t)blockIdx.x * kBS + threadIdx.x; col < g.ncol; col += (int64_t)gridDim.x * kBS) {
     if (restart) {
-      acc += restart_column<T>(g, col, a, w, xzero);
+      acc = acc_add(acc, restart_column<T>(g, col, a, w, xzero, x64), f32);
     } else {
       SrcCopy<T, 1> src{rin, w.p};
       thomas_vec<T, 1, 8>(g, col, a.m, a.l, a.cp, w.ph, src);
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(kBS, 4) k_pre_start(Grid g, Bands<T> a, Vecs<T
   }
   if (restart) {
     double vv[1] = {acc}, out[1];
-    if (grid_reduce<1>(vv, red, out)) fin_restart(ctl, out[0]);
+    if (grid_reduce<1>(vv, red, out, f32)) fin_restart(ctl, out[0]);
   }
 }
 
@@ -264,16 +268,17 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs
   const T* __restrict__ x = MODE == 0 ? w.ph : w.sh;
   T* __restrict__ y = MODE == 0 ? w.v : w.t;
   const T* __restrict__ r0 = ctl->r0sel ? w.r0 : w.rhs;
+  const bool f32 = sizeof(T) == 4 && ctl->dot32;
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS)
-    hmv_vec<T, V, U, MODE == 0 ? 0 : 3, LD_NC, H>(g, q * V, a, cen, x, y, r0, acc0, acc1, &acc2);
+    hmv_vec<T, V, U, MODE == 0 ? 0 : 3, LD_NC, H>(g, q * V, a, cen, x, y, r0, acc0, acc1, &acc2, f32);
   if (MODE == 0) {
     double vv[1] = {acc0}, out[1];
-    if (grid_reduce<1>(vv, red, out)) fin_alpha(ctl, out[0]);
+    if (grid_reduce<1>(vv, red, out, f32)) fin_alpha(ctl, out[0]);
   } else {
     double vv[3] = {acc0, acc1, acc2}, out[3];
-    if (grid_reduce<3>(vv, red, out)) {
+    if (grid_reduce<3>(vv, red, out, f32)) {
       fin_snorm(ctl, out[2]);
       if (ctl->state == ST_RUNNING) fin_omega(ctl, out[0], out[1]);
     }
@@ -343,7 +348,12 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
   }
   const bool half = (state == ST_HALF);
   const bool xzero = ctl->xzero != 0;
-  const T alpha = (T)ctl->alpha, omega = (T)ctl->omega;
+  const bool f32 = sizeof(T) == 4 && ctl->dot32;
+  // the paper's mixed-precision solver keeps x in FP64 (updated in FP64 from
+  // the FP32 vectors and the FP64 scalars); otherwise x is a T vector
+  double* __restrict__ x64 = sizeof(T) == 4 ? ctl->x64 : nullptr;
+  const double alpha_d = ctl->alpha, omega_d = ctl->omega;
+  const T alpha = (T)alpha_d, omega = (T)omega_d;
   const T* __restrict__ r0 = ctl->r0sel ? w.r0 : w.rhs;
   T* __restrict__ x = w.x;
   T* __restrict__ r = w.r;
@@ -359,20 +369,18 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += stride) {
     const int64_t e = q * VW;
-    T xv[VW], pv[VW];
-    if (xzero) {
+    T xv[VW], pv[VW], shv[VW];
+    if (!x64) {  // loads in the order of the streams: x, ph, then sh, s, t, r0
+      if (xzero) {
 #pragma unroll
-      for (int u = 0; u < VW; ++u) xv[u] = T(0);
-    } else {
-      vload<V>(x + e, xv);
+        for (int u = 0; u < VW; ++u) xv[u] = T(0);
+      } else {
+        vload<V>(x + e, xv);
+      }
     }
     vload<V>(ph + e, pv);
-    if (half) {
-#pragma unroll
-      for (int u = 0; u < VW; ++u) xv[u] = fma(alpha, pv[u], xv[u]);
-      vstore<V>(x + e, xv);
-    } else {
-      T shv[VW], sv[VW], tv[VW], r0v[VW], rv[VW];
+    if (!half) {
+      T sv[VW], tv[VW], r0v[VW], rv[VW];
       vload<V>(sh + e, shv);
       vload<V>(s + e, sv);
       vload<V>(t + e, tv);
@@ -380,33 +388,56 @@ __global__ void __launch_bounds__(256) k_upd(Grid g, Vecs<T> w, Ctl* ctl, Red re
       T a0 = T(0), a1 = T(0);
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
-        xv[u] = fma(omega, shv[u], fma(alpha, pv[u], xv[u]));
         rv[u] = fma(-omega, tv[u], sv[u]);
         a0 = fma(r0v[u], rv[u], a0);
         a1 = fma(rv[u], rv[u], a1);
       }
-      vstore<V>(x + e, xv);
       vstore<V>(r + e, rv);
       acc0.add(a0);
       acc1.add(a1);
     }
+    if (x64) {
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        double xd = xzero ? 0.0 : x64[e + u];
+        xd = fma(alpha_d, (double)pv[u], xd);
+        if (!half) xd = fma(omega_d, (double)shv[u], xd);
+        x64[e + u] = xd;
+      }
+      continue;
+    }
+    if (half) {
+#pragma unroll
+      for (int u = 0; u < VW; ++u) xv[u] = fma(alpha, pv[u], xv[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < VW; ++u) xv[u] = fma(omega, shv[u], fma(alpha, pv[u], xv[u]));
+    }
+    vstore<V>(x + e, xv);
   }
   if (nv == 0) {  // scalar path for sizes that are not a multiple of the vector width
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-      T xv = xzero ? T(0) : x[e];
-      xv = fma(alpha, ph[e], xv);
+      if (x64) {
+        double xd = xzero ? 0.0 : x64[e];
+        xd = fma(alpha_d, (double)ph[e], xd);
+        if (!half) xd = fma(omega_d, (double)sh[e], xd);
+        x64[e] = xd;
+      } else {
+        T xv = xzero ? T(0) : x[e];
+        xv = fma(alpha, ph[e], xv);
+        if (!half) xv = fma(omega, sh[e], xv);
+        x[e] = xv;
+      }
       if (!half) {
-        xv = fma(omega, sh[e], xv);
         const T rv = fma(-omega, t[e], s[e]);
         r[e] = rv;
         acc0.add(r0[e] * rv);
         acc1.add(rv * rv);
       }
-      x[e] = xv;
     }
   }
-  double vv[2] = {acc0.value(), acc1.value()}, out[2];
-  if (grid_reduce<2>(vv, red, out)) {
+  double vv[2] = {acc0.total(f32), acc1.total(f32)}, out[2];
+  if (grid_reduce<2>(vv, red, out, f32)) {
     const int st = fin_iteration(ctl, half, out[0], out[1]);
     if (use_cond) cudaGraphSetConditional(cond, (st == ST_RUNNING || st == ST_RESTART) ? 1u : 0u);
   }

@@ -78,12 +78,14 @@ cudaError_t launch_setup(const Grid& g, const double* A7, SetupOut o, const Laun
 // Writes xout = x (if given; never the buffer it reads), rhs = D^-1 r in D's
 // precision, r_out (optional), and reduces ||r||^2, ||b||^2, ||rhs||^2.  The
 // last block stores them in the control block and resets it for the next
-// inner solve (tolerance eta relative to ||rhs||).
-template <typename D, bool HAS_X, bool HAS_D>
+// inner solve (tolerance eta relative to ||rhs||).  The correction delta is in
+// DD: the inner precision D, or FP64 when the inner iterate was kept in FP64
+// (the paper's mixed-precision solver).
+template <typename D, typename DD, bool HAS_X, bool HAS_D>
 __global__ void __launch_bounds__(kBS) k_residual(Grid g, const double* __restrict__ A7,
                                                   const double* __restrict__ invc, const double* __restrict__ b,
                                                   const double* __restrict__ xin, double* __restrict__ xout,
-                                                  const D* __restrict__ delta, D* __restrict__ rhs,
+                                                  const DD* __restrict__ delta, D* __restrict__ rhs,
                                                   double* __restrict__ r_out, Ctl* ctl, Red red) {
   const int64_t n = g.n, ncol = g.ncol;
   // the inner correction is used only if the inner solve wrote it and it is finite
@@ -183,32 +185,50 @@ __global__ void __launch_bounds__(kBS) k_residual(Grid g, const double* __restri
   }
 }
 
+template <typename D, typename DD>
+cudaError_t launch_residual_t(const Grid& g, const double* A7, const double* invc, const double* b,
+                              const double* xin, double* xout, const DD* delta, D* rhs, double* r_out, Ctl* ctl,
+                              Red red, const Launch& L) {
+  const bool hx = xin != nullptr, hd = delta != nullptr;
+  if (hx && hd)
+    k_residual<D, DD, true, true><<<grid_for((const void*)k_residual<D, DD, true, true>, kBS, L, L.wcol), kBS, 0,
+                                    L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+  else if (hx)
+    k_residual<D, DD, true, false><<<grid_for((const void*)k_residual<D, DD, true, false>, kBS, L, L.wcol), kBS, 0,
+                                     L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+  else if (hd)
+    k_residual<D, DD, false, true><<<grid_for((const void*)k_residual<D, DD, false, true>, kBS, L, L.wcol), kBS, 0,
+                                     L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+  else
+    k_residual<D, DD, false, false><<<grid_for((const void*)k_residual<D, DD, false, false>, kBS, L, L.wcol), kBS,
+                                      0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
+  return cudaGetLastError();
+}
+
 template <typename D>
 cudaError_t launch_residual(const Grid& g, const double* A7, const double* invc, const double* b, const double* xin,
                             double* xout, const D* delta, D* rhs, double* r_out, int mode, Ctl* ctl, Red red,
                             const Launch& L) {
   (void)mode;
-  const bool hx = xin != nullptr, hd = delta != nullptr;
-  if (hx && hd)
-    k_residual<D, true, true><<<grid_for((const void*)k_residual<D, true, true>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
-  else if (hx)
-    k_residual<D, true, false><<<grid_for((const void*)k_residual<D, true, false>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
-  else if (hd)
-    k_residual<D, false, true><<<grid_for((const void*)k_residual<D, false, true>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
-  else
-    k_residual<D, false, false><<<grid_for((const void*)k_residual<D, false, false>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red);
-  return cudaGetLastError();
+  return launch_residual_t<D, D>(g, A7, invc, b, xin, xout, delta, rhs, r_out, ctl, red, L);
+}
+
+cudaError_t launch_residual_x64(const Grid& g, const double* A7, const double* invc, const double* b,
+                                const double* xin, double* xout, const double* delta, float* rhs, Ctl* ctl, Red red,
+                                const Launch& L) {
+  return launch_residual_t<float, double>(g, A7, invc, b, xin, xout, delta, rhs, nullptr, ctl, red, L);
 }
 
 void warm_launch_kernels(const Launch& L) {
   grid_for((const void*)k_setup, kBS, L, 1);
-#define HZ_WARM_RES(D)                                               \
-  grid_for((const void*)k_residual<D, true, true>, kBS, L, 1);       \
-  grid_for((const void*)k_residual<D, true, false>, kBS, L, 1);      \
-  grid_for((const void*)k_residual<D, false, true>, kBS, L, 1);      \
-  grid_for((const void*)k_residual<D, false, false>, kBS, L, 1);
-  HZ_WARM_RES(float)
-  HZ_WARM_RES(double)
+#define HZ_WARM_RES(D, DD)                                               \
+  grid_for((const void*)k_residual<D, DD, true, true>, kBS, L, 1);       \
+  grid_for((const void*)k_residual<D, DD, true, false>, kBS, L, 1);      \
+  grid_for((const void*)k_residual<D, DD, false, true>, kBS, L, 1);      \
+  grid_for((const void*)k_residual<D, DD, false, false>, kBS, L, 1);
+  HZ_WARM_RES(float, float)
+  HZ_WARM_RES(double, double)
+  HZ_WARM_RES(float, double)
 #undef HZ_WARM_RES
 }
 

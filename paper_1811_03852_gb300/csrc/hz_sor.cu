@@ -325,21 +325,23 @@ __device__ __forceinline__ int64_t rb_group(const Rb& rb, int64_t hg, int64_t w)
 // r0 = r, p = r, and for a red column z1 = omega T^-1 p.  Returns <r, r>.
 template <typename T>
 __device__ __noinline__ double restart_rb(const Rb& rb, const Bands<T>& a, const Vecs<T>& w, int64_t q, bool xzero,
-                                          T* z1, T omega) {
+                                          T* z1, T omega, const double* x64) {
   const RbGrp gr = rb_grp<1>(rb, q);
+  // x in T, or held in FP64 by the paper's mixed-precision solver (arithmetic in T)
+  auto X = [&](int64_t i) -> T { return x64 ? (T)x64[i] : w.x[i]; };
   T acc = T(0);
   for (int k = 0; k < rb.nz; ++k) {
     const int64_t idx = (int64_t)k * rb.ncol + q;
     T v = w.rhs[idx];
     if (!xzero) {
-      const T xm = w.x[idx + gr.mir], xx = w.x[idx + gr.xo];
-      T y = w.x[idx];
+      const T xm = X(idx + gr.mir), xx = X(idx + gr.xo);
+      T y = X(idx);
       y = fma(a.E[idx], gr.p ? xx : xm, y);
       y = fma(a.W[idx], gr.p ? xm : xx, y);
-      if (gr.hn) y = fma(a.N[idx], w.x[idx + gr.mir + gr.hx], y);
-      if (gr.hs) y = fma(a.S[idx], w.x[idx + gr.mir - gr.hx], y);
-      if (k + 1 < rb.nz) y = fma(a.U[idx], w.x[idx + rb.ncol], y);
-      if (k > 0) y = fma(a.D[idx], w.x[idx - rb.ncol], y);
+      if (gr.hn) y = fma(a.N[idx], X(idx + gr.mir + gr.hx), y);
+      if (gr.hs) y = fma(a.S[idx], X(idx + gr.mir - gr.hx), y);
+      if (k + 1 < rb.nz) y = fma(a.U[idx], X(idx + rb.ncol), y);
+      if (k > 0) y = fma(a.D[idx], X(idx - rb.ncol), y);
       v -= y;
     }
     w.r[idx] = v;
@@ -453,10 +455,12 @@ __global__ void __launch_bounds__(kBS, MINB) k_sor_first(Grid g, Bands<T> a, Vec
   double acc = 0.0;
   if (MODE == 0 && restart) {
     const bool xzero = ctl->xzero != 0;
+    const bool f32 = sizeof(T) == 4 && ctl->dot32;
+    const double* x64 = sizeof(T) == 4 ? ctl->x64 : nullptr;
     for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < rb.ncol; q += (int64_t)gridDim.x * kBS)
-      acc += restart_rb<T>(rb, a, w, q, xzero, z1, omega);
+      acc = acc_add(acc, restart_rb<T>(rb, a, w, q, xzero, z1, omega, x64), f32);
     double vv[1] = {acc}, o[1];
-    if (grid_reduce<1>(vv, red, o)) fin_restart(ctl, o[0]);
+    if (grid_reduce<1>(vv, red, o, f32)) fin_restart(ctl, o[0]);
     return;
   }
   const int64_t hg = rb.H / V;
@@ -602,12 +606,13 @@ __global__ void __launch_bounds__(kBS, MINB) k_mv_rb(Grid g, Bands<T> a, Vecs<T>
       }
     }
   }
+  const bool f32 = sizeof(T) == 4 && ctl->dot32;
   if (MODE == 0) {
-    double vv[1] = {acc0.value()}, o[1];
-    if (grid_reduce<1>(vv, red, o)) fin_alpha(ctl, o[0]);
+    double vv[1] = {acc0.total(f32)}, o[1];
+    if (grid_reduce<1>(vv, red, o, f32)) fin_alpha(ctl, o[0]);
   } else {
-    double vv[3] = {acc0.value(), acc1.value(), acc2.value()}, o[3];
-    if (grid_reduce<3>(vv, red, o)) {
+    double vv[3] = {acc0.total(f32), acc1.total(f32), acc2.total(f32)}, o[3];
+    if (grid_reduce<3>(vv, red, o, f32)) {
       fin_snorm(ctl, o[2]);
       if (ctl->state == ST_RUNNING) fin_omega(ctl, o[0], o[1]);
     }

@@ -41,8 +41,6 @@ def test_version_and_defaults_without_gpu():
     assert p.tol == 1e-8 and p.restart == 150 and p.mode == hz.HZ_MODE_MIXED_IR and p.fgmres_m == 30
     # tri-SOR defaults of Sec. 2: three sweeps, omega = 1.5; T^-1 stays the default preconditioner
     assert p.precond == hz.HZ_PRE_TRI and p.sor_sweeps == 3 and p.sor_omega == 1.5
-    # the binding's struct matches the header's layout (two doubles, nine ints, one int, one double)
-    assert ctypes.sizeof(hz.hz_solve_params) == 64
     # tri-SOR variant tables: FP32 pass/matvec/first, FP64 the same; invalid pairs count 0
     assert [hz.sor_variant_count(hz.HZ_PREC_FP32, k) for k in range(4)] == [9, 8, 6, 0]
     assert [hz.sor_variant_count(hz.HZ_PREC_FP64, k) for k in range(4)] == [6, 5, 4, 0]
@@ -79,3 +77,34 @@ def test_product_does_not_reference_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "hz_oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # compile a probe against include/hz.h and compare every field offset and
+    # the sizes of the two host structs with the ctypes binding
+    import subprocess
+
+    import paper_1811_03852_gb300 as hz
+
+    structs = {"hz_solve_params": hz.hz_solve_params, "hz_solve_info": hz.hz_solve_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hz.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-I", inc, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            a, b, c = ln.split()
+            got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

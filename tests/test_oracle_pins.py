@@ -264,3 +264,58 @@ def test_openmp_build_gives_the_same_bits():
                 assert np.array_equal(np.asarray(r), np.asarray(g))
     finally:
         oracle.use_openmp(False)
+
+
+@pytest.mark.parametrize("z_unit", ["radius", "m"])
+def test_paper_mp_bicgstab_shares_the_fp32_recursion(z_unit):
+    # Sec. 3's mixed-precision solver keeps x in FP64 and everything else in
+    # FP32.  BiCGStab never reads x between restarts, so without a restart its
+    # recursive residuals are the FP32 solver's, bit for bit, and the two
+    # iterates differ only by the rounding of x's own updates
+    nx, ny, nz = 16, 12, 6
+    A, b = gen.make_system(nx, ny, nz, 3, 4, z_unit=z_unit)
+    Ah = oracle.scale(A)
+    bh = b / A[0]
+    x32, i32, h32 = oracle.bicgstab(Ah, bh, eta=1e-5, maxit=200, restart=10**6, fp32=True, history=True)
+    x64, i64, h64 = oracle.bicgstab(Ah, bh, eta=1e-5, maxit=200, restart=10**6, fp32=True, x64=True, history=True)
+    assert x64.dtype == np.float64 and x32.dtype == np.float32
+    assert i32["restarts"] == i64["restarts"] == 0
+    assert i32["iters"] == i64["iters"] and np.array_equal(h32, h64)
+    assert np.linalg.norm(x64 - x32) <= 1e-5 * np.linalg.norm(x64)
+
+
+@pytest.mark.parametrize("case", [((4, 4, 3), "radius"), ((6, 5, 4), "radius"), ((4, 4, 3), "m")])
+def test_paper_mp_solve_vs_dense_lu(case):
+    # one FP32 solve to R_c = 1e-5 with x in FP64 and no refinement (mode 2):
+    # on systems whose recursion stays smooth, the residual of the scaled system
+    # (Sec. 2 scales by D^-1 outside the solver) recomputed densely in FP64 meets
+    # the tolerance up to FP32 rounding, and x is the dense LU solution within
+    # the conditioning of that residual
+    shape, z_unit = case
+    nx, ny, nz = shape
+    A, b = gen.make_system(nx, ny, nz, 5, 6, z_unit=z_unit)
+    M = dense_operator(A)
+    xs = np.linalg.solve(M, b.ravel())
+    x, info, hist = oracle.solve(A, b, mode=oracle.MODE_PAPER_MP, tol=1e-5, eta=1e-5, history=True)
+    assert info["outer"] == 1 and len(hist) == 2  # one solve, no refinement
+    r = b.ravel() - M @ x.ravel()
+    assert info["R"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(b), rel=1e-9)
+    d = A[0].ravel()
+    Ms = M / d[:, None]
+    rs = np.linalg.norm(r / d) / np.linalg.norm(b.ravel() / d)
+    assert rs <= 2e-5
+    assert np.linalg.norm(x.ravel() - xs) <= np.linalg.cond(Ms) * 2e-5 * np.linalg.norm(xs)
+
+
+def test_paper_mp_first_iterations_match_fp64():
+    # Sec. 4: after one iteration the mixed-precision and 64-bit solvers agree to
+    # about seven significant figures (the precision of a 32-bit number), and
+    # they stay close for the first few
+    nx, ny, nz = 16, 12, 6
+    A, b = gen.make_system(nx, ny, nz, 3, 4, z_unit="m")
+    Ah = oracle.scale(A)
+    bh = b / A[0]
+    _, _, hmp = oracle.bicgstab(Ah, bh, eta=1e-12, maxit=5, fp32=True, x64=True, history=True)
+    _, _, h64 = oracle.bicgstab(Ah, bh, eta=1e-12, maxit=5, history=True)
+    rel = np.abs(hmp - h64) / h64
+    assert rel[0] <= 1e-6 and np.all(rel <= 1e-4), rel

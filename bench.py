@@ -53,6 +53,7 @@ def parse():
                     help="preconditioner of the headline solves: T^-1 or tri-SOR (Sec. 2)")
     ap.add_argument("--no-trisor", action="store_true", help="skip the tri-SOR side measurement")
     ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table 1 comparison")
+    ap.add_argument("--no-bands16", action="store_true", help="skip the 16-bit horizontal-band solves")
     ap.add_argument("--dims", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="override the workload's grid (same recipe and seeds; for profiling smaller cases)")
     ap.add_argument("--no-graph", action="store_true",
@@ -315,7 +316,8 @@ def paper_table1(op, bd, x, stream, dims, restart=150, ablation=True):
     rows = {}
 
     def one(**kw):
-        p = hz.default_params(restart=restart, **kw)
+        kw.setdefault("restart", restart)
+        p = hz.default_params(**kw)
         op.solve(bd, x, params=p, raise_on_error=False)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -333,7 +335,7 @@ def paper_table1(op, bd, x, stream, dims, restart=150, ablation=True):
         for rc in (1e-3, 1e-4):
             key = f"{pname} R_c={rc:g}"
             mp = one(mode=hz.HZ_MODE_PAPER_MP, precond=pc, tol=rc)
-            dp = one(mode=hz.HZ_MODE_FP64, precond=pc, tol=rc, inner_tol=rc, max_outer=1)
+            dp = one(mode=hz.HZ_MODE_PAPER_DP, precond=pc, tol=rc)
             row = {"mixed": mp, "double": dp, "time_ratio_double_over_mixed": round(dp["ms"] / mp["ms"], 3)}
             if pname == pres[0][0]:
                 row["mixed_fp32_global_sums"] = one(mode=hz.HZ_MODE_PAPER_MP, precond=pc, tol=rc, dot_fp32=1)
@@ -341,6 +343,27 @@ def paper_table1(op, bd, x, stream, dims, restart=150, ablation=True):
                     row["mixed_no_restart"] = one(mode=hz.HZ_MODE_PAPER_MP, precond=pc, tol=rc, restart=10**9)
             rows[key] = row
     return rows
+
+
+def table1_hard(restart=150):
+    """paper_table1 on the 640x480x70 system of the metres family (seeds 11/12)."""
+    import torch
+
+    import gen
+    import paper_1811_03852_gb300 as hz
+
+    w = gen.WORKLOADS["mixed640"]
+    dims = (w["nx"], w["ny"], w["nz"])
+    A = gen.make_operator(*dims, w["seed_coef"], z_unit="m")
+    b = gen.make_rhs(*dims, w["seed_rhs"])
+    stream = torch.cuda.current_stream()
+    op = hz.Operator(A, stream=stream)
+    op.autotune(fp64=True, trisor=True)
+    bd = torch.from_numpy(b.reshape(-1)).cuda()
+    x = torch.empty_like(bd)
+    rows = paper_table1(op, bd, x, stream, dims, restart=restart)
+    op.close()
+    return {f"mixed640 {'x'.join(map(str, dims))} z_unit=m": rows}
 
 
 def run_table1(args):
@@ -356,9 +379,11 @@ def run_table1(args):
     op.autotune(fp64=True, trisor=dims[0] % 2 == 0)
     bd = torch.from_numpy(b.reshape(-1)).cuda()
     x = torch.empty_like(bd)
-    rows = paper_table1(op, bd, x, stream, dims, restart=args.restart)
-    print(json.dumps({"workload": f"paper Table 1 (synthetic) n1280 seeds {'x'.join(map(str, dims))} "
-                                  f"z_unit={args.z_unit}", "table1": rows}), flush=True)
+    rows = {f"n1280 {'x'.join(map(str, dims))} z_unit={args.z_unit}":
+            paper_table1(op, bd, x, stream, dims, restart=args.restart)}
+    op.close()
+    rows.update(table1_hard(args.restart))
+    print(json.dumps({"workload": "paper Table 1 (synthetic)", "table1": rows}), flush=True)
 
 
 def run_ours(args):
@@ -474,10 +499,35 @@ def run_ours(args):
                                  "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
                              for k, v in sp.items()}
 
-    # the paper's own mixed-precision solver against the 64-bit one (Table 1, Sec. 4)
+    # 16-bit storage of the horizontal bands (BF16 and FP16) in the same mixed solve
+    bands16 = None
+    if not args.no_bands16:
+        bands16 = {}
+        for name, fmt in (("bf16", hz.HZ_BANDS_BF16), ("fp16", hz.HZ_BANDS_FP16)):
+            op.set_band_format(fmt)
+            ms16, inf16 = timed(pm, max(1, min(2, args.steps)), 1)
+            op.profile(True)
+            op.solve(bd, x, params=pm)
+            pr16 = {k: v for k, v in op.profile_read().items() if v[0] > 0 and k != "k_setup"}
+            op.profile(False)
+            bands16[name] = {
+                "value": round(world * len(inf16) / (ms16 * 1e-3), 4), "ms_per_solve": round(ms16 / len(inf16), 3),
+                "outer": inf16[0]["outer_iters"], "inner": inf16[0]["inner_iters"],
+                "true_rel_residual": max(i["true_rel_residual"] for i in inf16),
+                "status": [i["status"] for i in inf16],
+                "ms_per_inner": round(ms16 / len(inf16) / max(1, inf16[0]["inner_iters"]), 3),
+                "kernels_GBps": {k: round(v[2] / (v[1] * 1e-3) / 1e9, 1) for k, v in pr16.items() if v[1] > 0},
+                "kernels_ms_per_launch": {k: round(v[1] / v[0], 4) for k, v in pr16.items()}}
+        op.set_band_format(hz.HZ_BANDS_FP32)
+
+    # the paper's own mixed-precision solver against the 64-bit one (Table 1, Sec. 4): on this
+    # system, and on the hard (metres) family at 640x480x70, where the solve from x0 = 0 takes
+    # tens of iterations as the paper's did
     table1 = None
     if not args.no_table1 and not args.no_fp64:
-        table1 = paper_table1(op, bd, x, stream, dims, restart=args.restart)
+        table1 = {f"{args.workload} {nx}x{ny}x{nz} z_unit={args.z_unit}":
+                  paper_table1(op, bd, x, stream, dims, restart=args.restart, ablation=False)}
+        table1.update(table1_hard(args.restart))
 
     # end to end through the public API with host buffers (pinned b, pinned x)
     bh = torch.from_numpy(b.reshape(-1)).pin_memory()
@@ -550,6 +600,7 @@ def run_ours(args):
         "fp64": fp64,
         "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
         "trisor": trisor,
+        "bands16": bands16,
         "paper_table1": table1,
         "setup_ms": round(min(su), 3),
         "variants": variants,

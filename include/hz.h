@@ -62,7 +62,7 @@ typedef enum {
 typedef enum {
   HZ_MODE_FP64 = 0,     /* inner BiCGStab in FP64: the double-precision baseline */
   HZ_MODE_MIXED_IR = 1, /* inner BiCGStab in FP32, outer FP64 residual and update */
-  HZ_MODE_PAPER_MP = 2  /* the paper's mixed-precision solver (Sec. 3): one BiCGStab solve with the iterate
+  HZ_MODE_PAPER_MP = 2, /* the paper's mixed-precision solver (Sec. 3): one BiCGStab solve with the iterate
                            x in FP64 and every other vector, coefficient and preconditioner value in FP32,
                            halting when its recursive residual of the scaled system falls below tol
                            (inner_tol if given); no refinement.  The status is that halting test's (HZ_OK, or
@@ -70,6 +70,8 @@ typedef enum {
                            true_rel_residual is the FP64 R = ||b - A x|| / ||b|| of the x returned, which
                            may differ from the scaled recursive residual.  BiCGStab with HZ_PRE_TRI or
                            HZ_PRE_TRISOR. */
+  HZ_MODE_PAPER_DP = 3  /* its 64-bit counterpart in the paper's comparison (Sec. 4, Table 1): the same single
+                           solve, halting test and report, everything in FP64 */
 } hz_mode;
 
 typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
@@ -103,7 +105,7 @@ typedef struct {
   int dot_fp32;      /* FP32 inner solves only: 1 sums every inner dot product in FP32 (per thread, block and
                         grid), the 32-bit global sums the paper started from (Sec. 4); 0 (default): FP32 partial
                         sums within a column batch, FP64 across them (the paper's 64-bit global sums).  With
-                        HZ_MODE_FP64: HZ_ERR_UNSUPPORTED.  FGMRES ignores it. */
+                        HZ_MODE_FP64 or HZ_MODE_PAPER_DP: HZ_ERR_UNSUPPORTED.  FGMRES ignores it. */
 } hz_solve_params;
 
 /* Solve report (host struct). */
@@ -253,6 +255,29 @@ int hz_nn_crops(int nx, int ny, int nz, const float* fa, const float* fb, int nc
 /* checkpoint: FP32 master weights, Adam moments and step (host file) */
 int hz_nn_save(hz_nn nn, const char* path);
 int hz_nn_load(hz_nn nn, const char* path);
+/* ---- storage of the horizontal bands ---------------------------------------
+ * The paper's argument for 32-bit numbers (Secs. 1 and 3) is that smaller
+ * data moves less.  Carried one step further: the four horizontal bands
+ * E, W, N, S of D^-1 A, read by the stencil kernels twice per inner BiCGStab
+ * iteration, can be stored in 16 bits (BF16: 8 significant bits, the FP32
+ * range; FP16: 11 significant bits, values below 6.1e-5 subnormal), widened
+ * to FP32 for the arithmetic.  The vertical part T (the U and D bands and the
+ * Thomas factors) stays FP32: its rows sum to nearly zero, and 16-bit
+ * rounding would change the near-singular columns.  The FP64 outer residual
+ * keeps the exact FP64 A, so the refinement loop corrects what the rounding
+ * changes (at the cost of the inner solves' convergence).  The format applies
+ * to the FP32 BiCGStab solver with T^-1 (mixed mode and HZ_MODE_PAPER_MP) and
+ * to hz_matvec and hz_precond_matvec in HZ_PREC_FP32; FGMRES, tri-SOR, the
+ * batched solver and hz_nn_make_pair read the FP32 bands.  The 16-bit copies
+ * (8 bytes per point) are made on the first call and redone by
+ * hz_op_update.  Rounding: to nearest even, BF16 from the FP32 value, FP16
+ * from the FP64 value. */
+#define HZ_BANDS_FP32 0
+#define HZ_BANDS_BF16 1
+#define HZ_BANDS_FP16 2
+int hz_op_set_band_format(hz_op op, int fmt);
+int hz_op_get_band_format(hz_op op, int* fmt);
+
 /* attach a network to an operator for params->precond = HZ_PRE_TRI_NN (NULL detaches) */
 int hz_op_set_nn(hz_op op, hz_nn nn);
 /* Training pair of an iterate x_k with exact solution x_star (all FP64, n):
@@ -260,6 +285,42 @@ int hz_op_set_nn(hz_op op, hz_nn nn);
    in = e1 / sigma, target = (e - z1) / sigma, sigma = rms(e1) (host out). */
 int hz_nn_make_pair(hz_op op, const double* b, const double* xk, const double* x_star, float* in, float* target,
                     double* sigma);
+
+/* Training of the learned stage on one system (not in the paper: the stage is
+ * an extra preconditioner of the flexible solver).  For the operator op and
+ * right-hand side b (device, n doubles):
+ *   1. x* = the FP64 solution to xstar_tol (hz_solve, HZ_MODE_FP64);
+ *   2. for each k in iterates: x_k = the mixed solver's iterate after one
+ *      refinement step of k inner iterations from x = 0, and its training pair
+ *      (stage input, target) from hz_nn_make_pair;
+ *   3. steps Adam steps (hz_nn_train_step, with clip), each on batch crops of
+ *      one pair: (crop + 8) x (crop + 8) columns and all levels (a halo of 4
+ *      columns, the receptive field of the four 3x3x3 layers, is excluded from
+ *      the loss), stacked along j.  The pair and the crop corners (i0 uniform
+ *      over the row, j0 uniform over [0, ny - crop)) are drawn from a
+ *      counter-based generator: SplitMix64 (Steele, Lea and Flood 2014) keyed
+ *      by (seed, stream, draw number), so a call is reproducible.
+ * The network's Adam state carries over from call to call: train on many
+ * systems by calling once per system (each operator can be created just
+ * before and destroyed after its call), with its own stream value.
+ * Requires crop + 8 <= nx and crop < ny.  losses: host array of steps values
+ * (the loss of each step, before its update), may be NULL.  Device memory for
+ * x*, the iterates and the pairs is allocated for the call and freed after it.
+ * Errors: HZ_ERR_INVALID (arguments), the errors of the calls above. */
+typedef struct {
+  int steps;          /* Adam steps on this system's pairs (default 40) */
+  int batch;          /* crops per step (default 16) */
+  int crop;           /* interior width of a crop in columns (default 64) */
+  int n_iterates;     /* 1..16 entries of iterates used (default 6) */
+  int iterates[16];   /* inner iterations k of the iterates x_k (default 1, 2, 4, 8, 16, 32) */
+  double xstar_tol;   /* tolerance of the FP64 solve for x* (default 1e-11) */
+  double lr;          /* Adam learning rate (default 3e-4) */
+  double clip;        /* global gradient 2-norm clip (default 1; <= 0: none) */
+  unsigned long long seed;    /* random draws: (seed, stream) select the counter stream */
+  unsigned long long stream;
+} hz_nn_train_params;
+void hz_nn_train_defaults(hz_nn_train_params* p);
+int hz_nn_train(hz_nn nn, hz_op op, const double* b, const hz_nn_train_params* p, double* losses);
 
 /* Inner recursive residual history of the last solve with record_history=1:
    copies up to cap values into hist (host) and returns how many. */
@@ -381,7 +442,9 @@ int hz_dot_noalloc(int prec, int64_t n, const void* x, const void* y, void* stre
 /* Copy the operator's derived data to device memory dst:
    what = 0: scaled bands [6][n] (E,W,N,S,U,D) in prec;
    what = 1: Thomas factors [3][n] (m, l, c') in prec, where the forward sweep
-             is y_k = m_k p_k - l_k y_(k-1) and the back sweep z_k = y_k - c'_k z_(k+1). */
+             is y_k = m_k p_k - l_k y_(k-1) and the back sweep z_k = y_k - c'_k z_(k+1);
+   what = 2: the 16-bit horizontal bands [4][n] (E,W,N,S; the bit patterns) of an
+             operator whose band format is BF16 or FP16 (prec ignored; else HZ_ERR_INVALID). */
 int hz_op_export(hz_op op, int what, int prec, void* dst);
 
 #ifdef __cplusplus

@@ -91,7 +91,7 @@ def _load():
             lib.or_bicgstab_f32.restype = None
             lib.or_bicgstab_mp.argtypes = [i32, i32, i32, pv, pv, pv, dbl, i32, i32, pv, pv]
             lib.or_bicgstab_mp.restype = None
-            lib.or_solve.argtypes = [i32, i32, i32, pv, pv, pv, i32, dbl, dbl, i32, i32, i32, pv, pv]
+            lib.or_solve.argtypes = [i32, i32, i32, pv, pv, pv, i32, dbl, dbl, i32, i32, i32, pv, pv, pv]
             lib.or_solve.restype = None
             lib.or_dot.argtypes = [i64, pv, pv]
             lib.or_dot.restype = dbl
@@ -197,9 +197,11 @@ def bicgstab(Ah, bh, x0=None, eta=1e-8, maxit=1000, restart=150, fp32=False, his
 
 
 def solve(A, b, x0=None, mode=MODE_MIXED, tol=1e-8, eta=1e-4, max_outer=20, max_inner=2000, restart=150,
-          history=False):
+          history=False, inner_bands=None):
     """Outer loop on the true FP64 residual with FP64 (mode 0) or FP32 (mode 1) inner BiCGStab;
     mode 2 is the paper's mixed-precision solver (one solve, x in FP64, the rest FP32, no refinement).
+    inner_bands: the FP32 inner operator (6, nz, ny, nx) of modes 1 and 2 instead of float(Ahat),
+    e.g. round_hbands(scale(A), fmt).
 
     Returns (x, info dict[, outer history of R]).
     """
@@ -208,8 +210,9 @@ def solve(A, b, x0=None, mode=MODE_MIXED, tol=1e-8, eta=1e-4, max_outer=20, max_
     x = np.zeros_like(b) if x0 is None else _c(x0).copy()
     hist = np.full(max_outer + 1, np.nan)
     out = np.zeros(5)
+    ib = None if inner_bands is None else _c(inner_bands, np.float32)
     _load().or_solve(nx, ny, nz, _p(A), _p(b), _p(x), mode, tol, eta, max_outer, max_inner, restart, _p(hist),
-                     _p(out))
+                     _p(out), None if ib is None else _p(ib))
     info = dict(outer=int(out[0]), inner=int(out[1]), R=float(out[2]), status=int(out[3]), restarts=int(out[4]))
     if history:
         return x, info, hist[: info["outer"] + 1]
@@ -244,3 +247,37 @@ def set_precond(kind, sweeps=3, omega=1.5):
     L.or_set_precond.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
     L.or_set_precond.restype = None
     L.or_set_precond(kind, sweeps, omega)
+
+
+# ---- 16-bit storage of the horizontal bands ---------------------------------------
+def round_bf16(x):
+    """x rounded to bfloat16 (1 sign, 8 exponent, 7 fraction bits; the FP32 exponent range), to
+    nearest with ties to even, from the FP32 rounding of x; returned as float64 values.
+    Written from the format: keep the top 16 bits of the FP32 pattern, adding half of the last
+    kept place (less one) plus the kept place's lowest bit before truncating."""
+    f = np.ascontiguousarray(x, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def round_fp16(x):
+    """x rounded to IEEE binary16 (to nearest, ties to even, subnormals below 2^-14), as float64."""
+    return np.ascontiguousarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+def bits16(x, fmt):
+    """The 16-bit patterns of values already rounded to the format (1 = BF16, 2 = FP16)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if fmt == 1:
+        return (x.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    return x.astype(np.float16).view(np.uint16)
+
+
+def round_hbands(Ah, fmt):
+    """Ahat with its horizontal bands E, W, N, S (rows 0..3) rounded to BF16 (fmt 1) or FP16
+    (fmt 2) and the vertical bands U, D unchanged."""
+    out = np.array(Ah, dtype=np.float64, copy=True)
+    out[:4] = round_bf16(out[:4]) if fmt == 1 else round_fp16(out[:4])
+    return out
+

@@ -582,13 +582,16 @@ void or_bicgstab_mp(int nx, int ny, int nz, const float* Ah, const float* bh, do
  *           FP64 and everything else in FP32, to eta, and no refinement (the
  *           outer loop stops after it and reports R).
  * x is in/out (initial guess).  outer_hist (may be NULL, max_outer+1 values)
- * receives R before each outer step and after the last.
+ * receives R before each outer step and after the last.  Ah32_in (may be
+ * NULL): the FP32 operator of the inner solves of modes 1 and 2 ([6][n],
+ * E,W,N,S,U,D), instead of the float rounding of Ahat.
  * out[0] = outer iterations, out[1] = total inner iterations,
  * out[2] = final true R, out[3] = status (0 ok, 1 not converged, 2 non-finite),
  * out[4] = total restarts.
  * ------------------------------------------------------------------------- */
 void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* x, int mode, double tol,
-              double eta, int max_outer, int max_inner, int restart, double* outer_hist, double* out) {
+              double eta, int max_outer, int max_inner, int restart, double* outer_hist, double* out,
+              const float* Ah32_in) {
   const int64_t n = (int64_t)nx * ny * nz;
   double* Ah = (double*)malloc(sizeof(double) * 6 * (size_t)n);
   double* r = (double*)malloc(sizeof(double) * (size_t)n);
@@ -600,8 +603,10 @@ void or_solve(int nx, int ny, int nz, const double* A, const double* b, double* 
     Ah32 = (float*)malloc(sizeof(float) * 6 * (size_t)n);
     r32 = (float*)malloc(sizeof(float) * (size_t)n);
     d32 = (float*)malloc(sizeof(float) * (size_t)n);
+    /* the FP32 inner operator: the float rounding of Ahat, or the caller's
+       (e.g. with the horizontal bands stored in 16 bits) */
 #pragma omp parallel for schedule(static)
-    for (int64_t q = 0; q < 6 * n; ++q) Ah32[q] = (float)Ah[q];
+    for (int64_t q = 0; q < 6 * n; ++q) Ah32[q] = Ah32_in ? Ah32_in[q] : (float)Ah[q];
   }
   const double bnorm = sqrt(dot_d(n, b, b));
   int outer = 0, inner_total = 0, status = 1, restarts = 0;

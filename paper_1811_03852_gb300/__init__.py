@@ -38,11 +38,13 @@ HZ_BATCH_AUTO, HZ_BATCH_PERSISTENT, HZ_BATCH_SEQUENTIAL = 0, 1, 2
 HZ_MODE_FP64 = 0
 HZ_MODE_MIXED_IR = 1
 HZ_MODE_PAPER_MP = 2
+HZ_MODE_PAPER_DP = 3
 HZ_PREC_FP64 = 0
 HZ_PREC_FP32 = 1
 HZ_PRE_TRI = 0
 HZ_PRE_TRI_NN = 1
 HZ_PRE_TRISOR = 2
+HZ_BANDS_FP32, HZ_BANDS_BF16, HZ_BANDS_FP16 = 0, 1, 2
 HZ_KRYLOV_BICGSTAB = 0
 HZ_KRYLOV_FGMRES = 1
 NUM_KERNELS = 11
@@ -134,6 +136,8 @@ def load(build_if_missing: bool = True):
         "hz_profile_enable": (i32, [pv, i32]),
         "hz_profile_read": (i32, [pv, i32, P(ctypes.c_longlong), P(dbl), P(dbl)]),
         "hz_kernel_name": (ctypes.c_char_p, [i32]),
+        "hz_op_set_band_format": (i32, [pv, i32]),
+        "hz_op_get_band_format": (i32, [pv, P(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -303,6 +307,15 @@ class Operator:
             out[L.hz_kernel_name(k).decode()] = (la.value, ms.value, by.value)
         return out
 
+    def set_band_format(self, fmt):
+        """Storage of the horizontal bands for the FP32 BiCGStab kernels: HZ_BANDS_FP32, _BF16 or _FP16."""
+        _check(load().hz_op_set_band_format(self._h, int(fmt)), "hz_op_set_band_format")
+
+    def band_format(self):
+        v = ctypes.c_int()
+        _check(load().hz_op_get_band_format(self._h, ctypes.byref(v)), "hz_op_get_band_format")
+        return v.value
+
     def export(self, what, prec, dst):
         _check(load().hz_op_export(self._h, what, prec, _ptr(dst)), "hz_op_export")
 
@@ -364,6 +377,21 @@ def version() -> int:
 
 
 # ---- learned preconditioner stage ---------------------------------------------------
+class hz_nn_train_params(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int),
+        ("batch", ctypes.c_int),
+        ("crop", ctypes.c_int),
+        ("n_iterates", ctypes.c_int),
+        ("iterates", ctypes.c_int * 16),
+        ("xstar_tol", ctypes.c_double),
+        ("lr", ctypes.c_double),
+        ("clip", ctypes.c_double),
+        ("seed", ctypes.c_ulonglong),
+        ("stream", ctypes.c_ulonglong),
+    ]
+
+
 def _nn_sigs(L):
     i32, dbl, pv = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
     P = ctypes.POINTER
@@ -382,6 +410,8 @@ def _nn_sigs(L):
         "hz_nn_load": (i32, [pv, ctypes.c_char_p]),
         "hz_op_set_nn": (i32, [pv, pv]),
         "hz_nn_make_pair": (i32, [pv, pv, pv, pv, pv, pv, P(dbl)]),
+        "hz_nn_train_defaults": (None, [P(hz_nn_train_params)]),
+        "hz_nn_train": (i32, [pv, pv, pv, P(hz_nn_train_params), pv]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -461,6 +491,26 @@ class Net:
         _nn_check(_nnlib().hz_nn_train_step(self._h, nx, ny, nz, seg_ny or ny, int(periodic), border, _ptr(x), _ptr(t),
                                             lr, clip, ctypes.byref(loss)), "hz_nn_train_step")
         return loss.value
+
+    def train(self, op, b, iterates=None, **kw):
+        """hz_nn_train: pairs from the system (op, b) and kw["steps"] Adam steps on crops of them.
+        kw: fields of hz_nn_train_params (steps, batch, crop, xstar_tol, lr, clip, seed, stream).
+        Returns the losses of the steps."""
+        L = _nnlib()
+        p = hz_nn_train_params()
+        L.hz_nn_train_defaults(ctypes.byref(p))
+        if iterates is not None:
+            its = list(iterates)
+            p.n_iterates = len(its)
+            for q, k in enumerate(its):
+                p.iterates[q] = int(k)
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        out = np.zeros(max(1, p.steps))
+        _nn_check(L.hz_nn_train(self._h, op.handle, _ptr(b), ctypes.byref(p), out.ctypes.data), "hz_nn_train")
+        return out[: p.steps].tolist()
 
     def save(self, path):
         _nn_check(_nnlib().hz_nn_save(self._h, str(path).encode()), "hz_nn_save")

@@ -10,6 +10,8 @@
 
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "hz_internal.cuh"
 
 namespace hz {
@@ -110,6 +112,13 @@ __device__ __forceinline__ void st_hint(W* p, const W& v, uint64_t pol) {
   }
 }
 
+// 16-bit loads with an L2 cache policy (one value)
+__device__ __forceinline__ uint16_t ld_hint_u16(const uint16_t* p, uint64_t pol) {
+  uint16_t r;
+  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
 template <typename W, int M>
 __device__ __forceinline__ W ldw(const W* p) {
   if constexpr (M == LD_NC)
@@ -169,6 +178,54 @@ __device__ __forceinline__ void stp(T* p, const Pack<T, V>& v) {
     stw<float2, S>(reinterpret_cast<float2*>(p), make_float2(v.a[0], v.a[1]));
   } else if constexpr (sizeof(T) == 8 && V == 2) {
     stw<double2, S>(reinterpret_cast<double2*>(p), make_double2(v.a[0], v.a[1]));
+  }
+}
+
+// V consecutive 16-bit band values (BF16 or FP16 by HB) widened to FP32; the
+// V values are one 2V-byte load (the band arrays are 8-byte aligned at every
+// group start)
+__device__ __forceinline__ float widen16(uint32_t h, int hb) {
+  return hb == HB_BF16 ? __uint_as_float(h << 16) : __half2float(__ushort_as_half((unsigned short)h));
+}
+template <int HB, int V, int M>
+__device__ __forceinline__ Pack<float, V> ld16(const uint16_t* p) {
+  static_assert(HB == HB_BF16 || HB == HB_FP16, "16-bit band format");
+  constexpr bool EF = (M == LD_NC_EF);
+  Pack<float, V> r;
+  if constexpr (V == 1) {
+    const uint16_t h = EF ? ld_hint_u16(p, l2_evict_first()) : __ldg(reinterpret_cast<const unsigned short*>(p));
+    r.a[0] = widen16(h, HB);
+  } else if constexpr (V == 2) {
+    const uint32_t h = EF ? __float_as_uint(ld_hint<float, true>(reinterpret_cast<const float*>(p), l2_evict_first()))
+                          : __ldg(reinterpret_cast<const unsigned int*>(p));
+    r.a[0] = widen16(h & 0xFFFFu, HB);
+    r.a[1] = widen16(h >> 16, HB);
+  } else {
+    static_assert(V == 4, "unsupported vector width");
+    uint2 h;
+    if constexpr (EF) {
+      const float2 f = ld_hint<float2, true>(reinterpret_cast<const float2*>(p), l2_evict_first());
+      h = make_uint2(__float_as_uint(f.x), __float_as_uint(f.y));
+    } else {
+      h = __ldg(reinterpret_cast<const uint2*>(p));
+    }
+    r.a[0] = widen16(h.x & 0xFFFFu, HB);
+    r.a[1] = widen16(h.x >> 16, HB);
+    r.a[2] = widen16(h.y & 0xFFFFu, HB);
+    r.a[3] = widen16(h.y >> 16, HB);
+  }
+  return r;
+}
+
+// horizontal band b (0 E, 1 W, 2 N, 3 S) of V columns at idx: FP32/FP64 or 16-bit by HB
+template <typename T, int V, int M, int HB>
+__device__ __forceinline__ Pack<T, V> ldband(const Bands<T>& a, int b, int64_t idx) {
+  if constexpr (HB == HB_F32) {
+    const T* base = b == 0 ? a.E : b == 1 ? a.W : b == 2 ? a.N : a.S;
+    return ldp<T, V, M>(base + idx);
+  } else {
+    static_assert(sizeof(T) == 4, "16-bit bands feed the FP32 kernels");
+    return ld16<HB, V, M>(a.h16 + (int64_t)b * a.h16s + idx);
   }
 }
 
@@ -356,7 +413,8 @@ struct SrcS {  // s = r - alpha v
   }
 };
 
-// y = c + H x on V columns, U levels per batch (H = E, W, N, S bands of Ahat).
+// y = c + H x on V columns, U levels per batch (H = E, W, N, S bands of Ahat,
+// read in FP32/FP64 or, for HB = HB_BF16 / HB_FP16, from their 16-bit copies).
 // MODE 0: d0 += <r0, y>.  MODE 1: d0 += <y, c>, d1 += <y, y>.  MODE 2: no dots.
 // MODE 3: as MODE 1 and *d2 += <c, c>.  f32: the sums run in FP32 throughout
 // (the paper's 32-bit global sums).
@@ -366,7 +424,7 @@ struct SrcS {  // s = r - alpha v
 // once (c, the bands, r0) and y carry the L2 evict-first priority, so that
 // the rows of x, read again as the north and south neighbours of the next
 // rows, stay in L2.
-template <typename T, int V, int U, int MODE, int M = LD_NC, bool EF = false>
+template <typename T, int V, int U, int MODE, int M = LD_NC, bool EF = false, int HB = HB_F32>
 __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T>& a, const T* __restrict__ cen,
                                         const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ r0,
                                         double& d0, double& d1, double* d2 = nullptr, bool f32 = false) {
@@ -386,20 +444,20 @@ __device__ __forceinline__ void hmv_vec(const Grid& g, int64_t c0, const Bands<T
       if (k0 + u < g.nz) {
         const int64_t idx = (int64_t)(k0 + u) * ncol + c0;
         cc[u] = ldp<T, V, MS>(cen + idx);
-        e[u] = ldp<T, V, MB>(a.E + idx);
-        w[u] = ldp<T, V, MB>(a.W + idx);
+        e[u] = ldband<T, V, MB, HB>(a, 0, idx);
+        w[u] = ldband<T, V, MB, HB>(a, 1, idx);
         if constexpr (V > 1) xc[u] = ldp<T, V, M>(x + idx);
         xw1[u] = ldw<T, M>(x + idx + nb.w_off);
         xe1[u] = ldw<T, M>(x + idx + nb.e_off);
         if (nb.hn) {
-          nn[u] = ldp<T, V, MB>(a.N + idx);
+          nn[u] = ldband<T, V, MB, HB>(a, 2, idx);
           xn[u] = ldp<T, V, M>(x + idx + nx);
         } else {
 #pragma unroll
           for (int c = 0; c < V; ++c) nn[u].a[c] = xn[u].a[c] = T(0);
         }
         if (nb.hs) {
-          ss[u] = ldp<T, V, MB>(a.S + idx);
+          ss[u] = ldband<T, V, MB, HB>(a, 3, idx);
           xs[u] = ldp<T, V, M>(x + idx - nx);
         } else {
 #pragma unroll

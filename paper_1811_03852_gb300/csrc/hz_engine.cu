@@ -77,6 +77,8 @@ struct hz_op_s {
   double* xbuf = nullptr;  // result staging when the caller's x is host memory
   double* xscr = nullptr;  // second buffer of the refinement ping-pong
   double* bbuf = nullptr;  // staging of a host b
+  int hb = HB_F32;            // storage of the horizontal bands read by the FP32 BiCGStab kernels
+  uint16_t* h16 = nullptr;    // their 16-bit copies [4][pad64(n)] (allocated on first use)
   double* x64buf = nullptr;  // the paper's mixed-precision solver: its FP64 iterate (inner order)
   double* x64nat = nullptr;  // the same scattered to natural order (tri-SOR)
   Ctl* ctl = nullptr;
@@ -131,17 +133,26 @@ T* dalloc(hz_op op, int64_t count, int* st) {
   return (T*)p;
 }
 
+// h16: the FP32 operator of the BiCGStab T^-1 path, whose stencil kernels read
+// the horizontal bands in the operator's band format; the other FP32 paths
+// (FGMRES, tri-SOR, batched, training pairs) read the FP32 bands
 template <typename T>
-Bands<T> bands_of(hz_op op);
+Bands<T> bands_of(hz_op op, bool h16 = true);
 template <>
-Bands<float> bands_of<float>(hz_op op) {
+Bands<float> bands_of<float>(hz_op op, bool h16) {
   const int64_t n = op->g.n;
   const float* a = op->ah32;
   const float* t = op->th32;
-  return Bands<float>{a, a + n, a + 2 * n, a + 3 * n, a + 4 * n, a + 5 * n, t, t + n, t + 2 * n};
+  Bands<float> b{a, a + n, a + 2 * n, a + 3 * n, a + 4 * n, a + 5 * n, t, t + n, t + 2 * n};
+  if (h16 && op->hb != HB_F32) {
+    b.h16 = op->h16;
+    b.h16s = pad64(n);
+    b.h16fmt = op->hb;
+  }
+  return b;
 }
 template <>
-Bands<double> bands_of<double>(hz_op op) {
+Bands<double> bands_of<double>(hz_op op, bool) {
   const int64_t n = op->g.n;
   const double* a = op->ah64;
   const double* t = op->th64;
@@ -197,7 +208,7 @@ int ensure_sor(hz_op op) {
     int st = HZ_OK;
     if (!(base = dalloc<T>(op, 9 * s, &st))) return st;
   }
-  const Bands<T> a = bands_of<T>(op);
+  const Bands<T> a = bands_of<T>(op, false);
   const T* src[9] = {a.E, a.W, a.N, a.S, a.U, a.D, a.m, a.l, a.cp};
   for (int q = 0; q < 9; ++q) CK(launch_rb_copy<T>(op->g, src[q], base + q * s, 1, op->L));
   op->sor_ok[pr] = true;
@@ -372,11 +383,13 @@ int profiled_iteration(hz_op op) {
   op->launches += 2;  // k_pre_start + k_pre_p
   CKS(state(c));
   if (c->state != ST_RUNNING) return HZ_OK;
-  CKS(prof_launch(op, 3, 8 * B * n, [&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }));
+  // the stencil kernels read four bands: 2 bytes fewer per band and point when they are 16-bit
+  const double hsave = (sizeof(T) == 4 && a.h16fmt != HB_F32) ? 8.0 : 0.0;
+  CKS(prof_launch(op, 3, (8 * B - hsave) * n, [&] { return launch_mv_v<T>(op->g, a, w, op->ctl, op->red, L); }));
   CKS(prof_launch(op, 4, 7 * B * n, [&] { return launch_pre_s<T>(op->g, a, w, op->ctl, op->red, L); }));
   // k_mv<1> also takes the half-step test on ||s||: the state after it says
   // which update k_upd makes
-  CKS(prof_launch(op, 5, 7 * B * n, [&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); }));
+  CKS(prof_launch(op, 5, (7 * B - hsave) * n, [&] { return launch_mv_t<T>(op->g, a, w, op->ctl, op->red, L); }));
   op->launches += 3;
   CKS(state(c));
   const bool half = c->state == ST_HALF;
@@ -529,7 +542,7 @@ int run_fgmres(hz_op op, int m, int max_inner, double eta, bool use_nn, int* fal
   const int64_t n = op->g.n;
   const Launch& L = op->L;
   cudaStream_t s = op->stream;
-  const Bands<float> a = bands_of<float>(op);
+  const Bands<float> a = bands_of<float>(op, false);
   const Vecs<float>& w32 = op->w32;
   float* const* V = W.vptr;
   float* const* Z = W.vptr + (W.m + 1);
@@ -629,6 +642,7 @@ int do_setup(hz_op op, const double* coeffs) {
     CKS(prof_launch(op, 0, 164.0 * (double)n, [&] { return launch_setup(op->g, op->A7, o, op->L); }));
   else
     CK(launch_setup(op->g, op->A7, o, op->L));
+  if (op->hb != HB_F32) CK(launch_h16(op->g, op->ah64, op->h16, pad64(n), op->hb, op->L));
   CK(cudaMemcpyAsync(op->err_h, op->err_d, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
   CK(cudaStreamSynchronize(op->stream));
   if (*op->err_h) {
@@ -885,6 +899,27 @@ int hz_op_destroy(hz_op op) {
   return HZ_OK;
 }
 
+int hz_op_set_band_format(hz_op op, int fmt) {
+  if (!op || (fmt != HZ_BANDS_FP32 && fmt != HZ_BANDS_BF16 && fmt != HZ_BANDS_FP16)) return HZ_ERR_INVALID;
+  const int hb = fmt == HZ_BANDS_BF16 ? HB_BF16 : fmt == HZ_BANDS_FP16 ? HB_FP16 : HB_F32;
+  if (hb == op->hb) return HZ_OK;
+  if (hb != HB_F32) {
+    int st = HZ_OK;
+    if (!op->h16 && !(op->h16 = dalloc<uint16_t>(op, 4 * pad64(op->g.n), &st))) return st;
+    CK(launch_h16(op->g, op->ah64, op->h16, pad64(op->g.n), hb, op->L));
+    CK(cudaStreamSynchronize(op->stream));
+  }
+  op->hb = hb;
+  drop_graph(op->gs[0]);  // the captured FP32 loop launches the previous format's kernels
+  return HZ_OK;
+}
+
+int hz_op_get_band_format(hz_op op, int* fmt) {
+  if (!op || !fmt) return HZ_ERR_INVALID;
+  *fmt = op->hb == HB_BF16 ? HZ_BANDS_BF16 : op->hb == HB_FP16 ? HZ_BANDS_FP16 : HZ_BANDS_FP32;
+  return HZ_OK;
+}
+
 int hz_op_set_nn(hz_op op, hz_nn nn) {
   if (!op) return HZ_ERR_INVALID;
   op->nn = nn;
@@ -903,8 +938,8 @@ int hz_nn_make_pair(hz_op op, const double* b, const double* xk, const double* x
   CK(launch_residual<float>(op->g, op->A7, op->invc, b, xk, nullptr, nullptr, w.rhs, op->xscr, 0, op->ctl, op->red,
                             op->L));
   CK(nn_pair_launch(n, op->A7, b, xk, x_star, op->xscr, w.r, w.s, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s));
-  CK(launch_tinv<float>(op->g, bands_of<float>(op), w.r, w.p, op->L));                          // z1 = T^-1 r
-  CK(fgm_residual(W, op->g, bands_of<float>(op), w.r, w.p, w.v, &W.st->r2, op->L));            // e1 = r - Ahat z1
+  CK(launch_tinv<float>(op->g, bands_of<float>(op, false), w.r, w.p, op->L));                   // z1 = T^-1 r
+  CK(fgm_residual(W, op->g, bands_of<float>(op, false), w.r, w.p, w.v, &W.st->r2, op->L));     // e1 = r - Ahat z1
   CK(nn_pair_launch(n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, w.s, w.v, w.p, &W.st->r2, in, target, 1,
                     s));
   CK(cudaMemcpyAsync(&op->rep_h->snorm2, &W.st->r2, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -930,10 +965,15 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   else
     hz_default_params(&p);
   if (!(p.tol > 0.0) || p.max_outer < 0 || p.max_inner < 1 || p.restart < 1) return HZ_ERR_INVALID;
-  if (p.mode != HZ_MODE_FP64 && p.mode != HZ_MODE_MIXED_IR && p.mode != HZ_MODE_PAPER_MP) return HZ_ERR_INVALID;
-  const bool paper = (p.mode == HZ_MODE_PAPER_MP);
+  if (p.mode != HZ_MODE_FP64 && p.mode != HZ_MODE_MIXED_IR && p.mode != HZ_MODE_PAPER_MP &&
+      p.mode != HZ_MODE_PAPER_DP)
+    return HZ_ERR_INVALID;
+  // the two solvers of the paper's Sec. 4 comparison: one BiCGStab solve each,
+  // halting on its own test, no refinement; the mixed one keeps x in FP64
+  const bool paper = (p.mode == HZ_MODE_PAPER_MP || p.mode == HZ_MODE_PAPER_DP);
+  const bool mp64 = (p.mode == HZ_MODE_PAPER_MP);
   if (paper && (p.krylov != HZ_KRYLOV_BICGSTAB || p.precond == HZ_PRE_TRI_NN)) return HZ_ERR_UNSUPPORTED;
-  if (p.dot_fp32 && p.mode == HZ_MODE_FP64) return HZ_ERR_UNSUPPORTED;
+  if (p.dot_fp32 && (p.mode == HZ_MODE_FP64 || p.mode == HZ_MODE_PAPER_DP)) return HZ_ERR_UNSUPPORTED;
   if (p.krylov != HZ_KRYLOV_BICGSTAB && p.krylov != HZ_KRYLOV_FGMRES) return HZ_ERR_INVALID;
   if (p.krylov == HZ_KRYLOV_FGMRES && (p.mode != HZ_MODE_MIXED_IR || p.fgmres_m < 1 || p.fgmres_m > kMaxFgm))
     return HZ_ERR_UNSUPPORTED;
@@ -945,7 +985,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (p.sor_sweeps < 1 || p.sor_sweeps > 64 || !(p.sor_omega > 0.0 && p.sor_omega < 2.0)) return HZ_ERR_INVALID;
     if (p.krylov != HZ_KRYLOV_BICGSTAB || op->g.nx % 2 != 0) return HZ_ERR_UNSUPPORTED;
   }
-  const bool fp32_mode = (p.mode != HZ_MODE_FP64);
+  const bool fp32_mode = (p.mode == HZ_MODE_MIXED_IR || p.mode == HZ_MODE_PAPER_MP);
   // precision of the inner solves: FP32 in mixed mode until a refinement step
   // stalls (then FP64 for the rest of the solve, see below)
   bool fp32 = fp32_mode;
@@ -984,7 +1024,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     XA = op->xbuf;
   }
   double* XB = op->xscr;
-  if (paper) {
+  if (mp64) {
     if (!op->x64buf && !(op->x64buf = dalloc<double>(op, n, &st))) return st;
     if (sor && !op->x64nat && !(op->x64nat = dalloc<double>(op, n, &st))) return st;
   }
@@ -1009,7 +1049,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   cfg->hist_cap = p.record_history ? op->hist_cap : 0;
   cfg->xzero = 1;
   cfg->state = ST_CONVERGED;
-  cfg->x64 = paper ? op->x64buf : nullptr;
+  cfg->x64 = mp64 ? op->x64buf : nullptr;
   cfg->dot32 = p.dot_fp32 ? 1 : 0;
   CK(cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, s));
 
@@ -1018,7 +1058,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   // inner right-hand side (written to t) gathered back into rhs after it
   auto residual = [&](const double* xin, double* xout, bool with_delta) -> int {
     const double ds = fp32 ? 4.0 : 8.0;
-    const double dd = paper ? 8.0 : ds;  // bytes of a correction value
+    const double dd = mp64 ? 8.0 : ds;  // bytes of a correction value
     auto step = [&](int kid, double bytes, auto&& launch) -> int {
       if (op->prof)
         CKS(prof_launch(op, kid, bytes * (double)n, launch));
@@ -1028,7 +1068,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
       return HZ_OK;
     };
     auto rb = [&](int to_compact) -> cudaError_t {
-      if (paper && !to_compact) return launch_rb_copy<double>(op->g, op->x64buf, op->x64nat, 0, op->L);
+      if (mp64 && !to_compact) return launch_rb_copy<double>(op->g, op->x64buf, op->x64nat, 0, op->L);
       if (fp32)
         return to_compact ? launch_rb_copy<float>(op->g, op->w32.t, op->w32.rhs, 1, op->L)
                           : launch_rb_copy<float>(op->g, op->w32.x, op->w32.s, 0, op->L);
@@ -1037,7 +1077,7 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     };
     if (sor && with_delta) CKS(step(10, 2 * dd, [&] { return rb(0); }));
     auto go = [&]() -> cudaError_t {
-      if (paper && with_delta)
+      if (mp64 && with_delta)
         return launch_residual_x64(op->g, op->A7, op->invc, bd, xin, xout, sor ? op->x64nat : op->x64buf,
                                    sor ? op->w32.t : op->w32.rhs, op->ctl, op->red, op->L);
       if (fp32) {
@@ -1570,6 +1610,13 @@ int hz_op_export(hz_op op, int what, int prec, void* dst) {
   else if (what == 0 && prec == HZ_PREC_FP64) { src = op->ah64; bytes = 6 * n * sizeof(double); }
   else if (what == 1 && prec == HZ_PREC_FP32) { src = op->th32; bytes = 3 * n * sizeof(float); }
   else if (what == 1 && prec == HZ_PREC_FP64) { src = op->th64; bytes = 3 * n * sizeof(double); }
+  else if (what == 2 && op->hb != HB_F32) {
+    for (int b = 0; b < 4; ++b)
+      CK(cudaMemcpyAsync((uint16_t*)dst + b * n, op->h16 + b * pad64(n), n * sizeof(uint16_t),
+                         cudaMemcpyDeviceToDevice, op->stream));
+    CK(cudaStreamSynchronize(op->stream));
+    return HZ_OK;
+  }
   else return HZ_ERR_INVALID;
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, op->stream));
   CK(cudaStreamSynchronize(op->stream));
@@ -1642,7 +1689,7 @@ int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, cons
   for (int q = 0; q < nsys; ++q) {
     hz_op op = ops[q];
     const int64_t ni = (op->g.ncol / vec + kBS - 1) / kBS;
-    sys[q] = SysDesc{op->g, bands_of<float>(op), op->w32, op->ctl, item0, ni};
+    sys[q] = SysDesc{op->g, bands_of<float>(op, false), op->w32, op->ctl, item0, ni};
     item0 += ni;
   }
   hz_op o0 = ops[0];

@@ -71,7 +71,15 @@ template <typename T>
 struct Bands {  // scaled operator in one precision, Ahat = I + bands
   const T *E, *W, *N, *S, *U, *D;
   const T *m, *l, *cp;  // Thomas factors of T (unit diagonal)
+  // 16-bit copies of the horizontal bands (E, W, N, S at h16 + b * h16s), read
+  // instead of E..S by the FP32 stencil kernels when h16fmt is HB_BF16 or HB_FP16
+  const uint16_t* h16;
+  int64_t h16s;
+  int h16fmt;
 };
+
+// storage of the horizontal bands read by the FP32 stencil kernels
+enum HBand : int { HB_F32 = 0, HB_BF16 = 1, HB_FP16 = 2 };
 
 template <typename T>
 struct Vecs {  // inner Krylov vectors
@@ -278,6 +286,10 @@ struct SetupOut {
   int* err;       // device error word
 };
 cudaError_t launch_setup(const Grid& g, const double* A7, SetupOut o, const Launch& L);
+// 16-bit copies (fmt HB_BF16 or HB_FP16) of the horizontal bands E, W, N, S of
+// the FP64 scaled operator ah64 ([6][n]): out[b * stride + p], rounded to
+// nearest even (BF16: from the FP32 rounding of the value, FP16: directly)
+cudaError_t launch_h16(const Grid& g, const double* ah64, uint16_t* out, int64_t stride, int fmt, const Launch& L);
 
 // residual modes
 enum ResMode : int { RES_ZERO = 0, RES_X0 = 1, RES_UPDATE = 2, RES_FROM_DELTA = 3 };

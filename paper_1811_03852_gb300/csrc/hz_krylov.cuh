@@ -94,14 +94,22 @@ __device__ __forceinline__ ColNbr col_nbr(const Grid& g, int64_t col) {
 
 // (Ahat x)_idx with all six bands (restart and the test entry point); x may be
 // stored in FP64 while the arithmetic is T's (the paper's mixed-precision solver)
+// horizontal band b at idx as the stencil kernels read it (16-bit copy if any)
+template <typename T>
+__device__ __forceinline__ T hband(const Bands<T>& a, int b, int64_t idx) {
+  if (sizeof(T) == 4 && a.h16fmt != HB_F32) return (T)widen16(a.h16[(int64_t)b * a.h16s + idx], a.h16fmt);
+  const T* base = b == 0 ? a.E : b == 1 ? a.W : b == 2 ? a.N : a.S;
+  return base[idx];
+}
+
 template <typename T, typename X>
 __device__ __forceinline__ T ahat_point(const Grid& g, const Bands<T>& a, const X* __restrict__ x, int64_t idx, int k,
                                         const ColNbr& c) {
   T y = (T)x[idx];
-  y = fma(a.E[idx], (T)x[idx + c.ie], y);
-  y = fma(a.W[idx], (T)x[idx + c.iw], y);
-  if (c.hn) y = fma(a.N[idx], (T)x[idx + g.nx], y);
-  if (c.hs) y = fma(a.S[idx], (T)x[idx - g.nx], y);
+  y = fma(hband(a, 0, idx), (T)x[idx + c.ie], y);
+  y = fma(hband(a, 1, idx), (T)x[idx + c.iw], y);
+  if (c.hn) y = fma(hband(a, 2, idx), (T)x[idx + g.nx], y);
+  if (c.hs) y = fma(hband(a, 3, idx), (T)x[idx - g.nx], y);
   if (k + 1 < g.nz) y = fma(a.U[idx], (T)x[idx + g.ncol], y);
   if (k > 0) y = fma(a.D[idx], (T)x[idx - g.ncol], y);
   return y;
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(kBS, 4) k_pre_start(Grid g, Bands<T> a, Vecs<T
 // test on ||s|| (it reads every s anyway, so the test costs no traffic here;
 // in the Thomas sweep of k_pre_s the running sum slowed the sweep by a sixth),
 // then omega = <t,s>/<t,t>
-template <typename T, int MODE, int V, int U, bool H>
+template <typename T, int MODE, int V, int U, bool H, int HB = HB_F32>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs<T> w, Ctl* ctl, Red red) {
   if (ctl->state != ST_RUNNING) return;
   const T* __restrict__ cen = MODE == 0 ? w.p : w.s;
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_mv(Grid g, Bands<T> a, Vecs
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   const int64_t ng = g.ncol / V;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS)
-    hmv_vec<T, V, U, MODE == 0 ? 0 : 3, LD_NC, H>(g, q * V, a, cen, x, y, r0, acc0, acc1, &acc2, f32);
+    hmv_vec<T, V, U, MODE == 0 ? 0 : 3, LD_NC, H, HB>(g, q * V, a, cen, x, y, r0, acc0, acc1, &acc2, f32);
   if (MODE == 0) {
     double vv[1] = {acc0}, out[1];
     if (grid_reduce<1>(vv, red, out, f32)) fin_alpha(ctl, out[0]);
@@ -469,13 +477,13 @@ __global__ void __launch_bounds__(kBS, kMinBlocks) k_tinv(Grid g, Bands<T> a, co
   }
 }
 
-template <typename T, int V, int U, bool H>
+template <typename T, int V, int U, bool H, int HB = HB_F32>
 __global__ void __launch_bounds__(kBS, kMinBlocks) k_hmv(Grid g, Bands<T> a, const T* __restrict__ cen,
                                                          const T* __restrict__ x, T* __restrict__ y) {
   const int64_t ng = g.ncol / V;
   double d0 = 0.0, d1 = 0.0;
   for (int64_t q = (int64_t)blockIdx.x * kBS + threadIdx.x; q < ng; q += (int64_t)gridDim.x * kBS)
-    hmv_vec<T, V, U, 2, LD_NC, H>(g, q * V, a, cen, x, y, nullptr, d0, d1);
+    hmv_vec<T, V, U, 2, LD_NC, H, HB>(g, q * V, a, cen, x, y, nullptr, d0, d1);
 }
 
 // ---- variant dispatch ----------------------------------------------------------
@@ -505,6 +513,15 @@ template <typename T>
 constexpr int prec_index() {
   return sizeof(T) == 8 ? 1 : 0;
 }
+// the band format of a launch as a compile-time value (FP64 kernels: FP64 bands)
+template <typename T, typename F>
+cudaError_t with_hb(int hb, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    if (hb == HB_BF16) return f(std::integral_constant<int, HB_BF16>{});
+    if (hb == HB_FP16) return f(std::integral_constant<int, HB_FP16>{});
+  }
+  return f(std::integral_constant<int, HB_F32>{});
+}
 inline int64_t blocks_for(int64_t items, int block) { return (items + block - 1) / block; }
 
 template <typename T>
@@ -533,11 +550,14 @@ cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, C
 template <typename T, int MODE>
 cudaError_t launch_mv_t_(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
   return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc) {
-    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    constexpr bool H = decltype(Hc)::value;
-    const void* k = (const void*)k_mv<T, MODE, V, U, H>;
-    k_mv<T, MODE, V, U, H><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl, red);
-    return cudaGetLastError();
+    return with_hb<T>(a.h16fmt, [&](auto Bc) {
+      constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, HB = decltype(Bc)::value;
+      constexpr bool H = decltype(Hc)::value;
+      const void* k = (const void*)k_mv<T, MODE, V, U, H, HB>;
+      k_mv<T, MODE, V, U, H, HB><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl,
+                                                                                                          red);
+      return cudaGetLastError();
+    });
   });
 }
 template <typename T>
@@ -568,11 +588,13 @@ cudaError_t launch_precond_matvec_t(const Grid& g, const Bands<T>& a, const T* p
   cudaError_t e = launch_tinv_t<T>(g, a, p, ph, L);
   if (e != cudaSuccess) return e;
   return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc) {
-    constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-    constexpr bool H = decltype(Hc)::value;
-    const void* k = (const void*)k_hmv<T, V, U, H>;
-    k_hmv<T, V, U, H><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, p, ph, v);
-    return cudaGetLastError();
+    return with_hb<T>(a.h16fmt, [&](auto Bc) {
+      constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, HB = decltype(Bc)::value;
+      constexpr bool H = decltype(Hc)::value;
+      const void* k = (const void*)k_hmv<T, V, U, H, HB>;
+      k_hmv<T, V, U, H, HB><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, p, ph, v);
+      return cudaGetLastError();
+    });
   });
 }
 
@@ -598,14 +620,17 @@ void warm_t(const Launch& L) {
       return cudaSuccess;
     });
   for (int i = 0; i < Variants<T>::NMV; ++i)
-    with_mv<T>(i, [&](auto Vc, auto Uc, auto Hc) {
-      constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value;
-      constexpr bool H = decltype(Hc)::value;
-      grid_for((const void*)k_mv<T, 0, V, U, H>, kBS, L, 1);
-      grid_for((const void*)k_mv<T, 1, V, U, H>, kBS, L, 1);
-      grid_for((const void*)k_hmv<T, V, U, H>, kBS, L, 1);
-      return cudaSuccess;
-    });
+    for (int hb = HB_F32; hb <= (sizeof(T) == 4 ? HB_FP16 : HB_F32); ++hb)
+      with_mv<T>(i, [&](auto Vc, auto Uc, auto Hc) {
+        return with_hb<T>(hb, [&](auto Bc) {
+          constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, HB = decltype(Bc)::value;
+          constexpr bool H = decltype(Hc)::value;
+          grid_for((const void*)k_mv<T, 0, V, U, H, HB>, kBS, L, 1);
+          grid_for((const void*)k_mv<T, 1, V, U, H, HB>, kBS, L, 1);
+          grid_for((const void*)k_hmv<T, V, U, H, HB>, kBS, L, 1);
+          return cudaSuccess;
+        });
+      });
 }
 
 }  // namespace hz

@@ -1287,3 +1287,138 @@ int hz_nn_load(hz_nn nn, const char* path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Training on one system (pairs, crops and Adam steps; see include/hz.h).
+namespace {
+
+// SplitMix64 finaliser (Steele, Lea and Flood 2014): a counter-based stream
+// keyed by (seed, stream, counter); uniform in [0, 1) from the top 53 bits
+uint64_t sm64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double draw(uint64_t seed, uint64_t stream, uint64_t counter) {
+  const uint64_t h = sm64(sm64(sm64(seed) ^ stream) ^ counter);
+  return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+
+constexpr int kHalo = 4;  // receptive field of four 3x3x3 layers
+
+struct TrainBufs {
+  std::vector<void*> ptrs;
+  ~TrainBufs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  T* get(int64_t count) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * (size_t)count) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void hz_nn_train_defaults(hz_nn_train_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->steps = 40;
+  p->batch = 16;
+  p->crop = 64;
+  p->n_iterates = 6;
+  for (int q = 0; q < 6; ++q) p->iterates[q] = 1 << q;
+  p->xstar_tol = 1e-11;
+  p->lr = 3e-4;
+  p->clip = 1.0;
+  p->seed = 7;
+  p->stream = 0;
+}
+
+int hz_nn_train(hz_nn nn, hz_op op, const double* b, const hz_nn_train_params* pp, double* losses) {
+  if (!nn || !op || !b || !pp) return HZ_ERR_INVALID;
+  const hz_nn_train_params p = *pp;
+  if (p.steps < 0 || p.batch < 1 || p.crop < 1 || p.n_iterates < 1 || p.n_iterates > 16 || !(p.lr > 0.0) ||
+      !(p.xstar_tol > 0.0))
+    return HZ_ERR_INVALID;
+  for (int q = 0; q < p.n_iterates; ++q)
+    if (p.iterates[q] < 1) return HZ_ERR_INVALID;
+  int nx = 0, ny = 0, nz = 0;
+  int st = hz_op_dims(op, &nx, &ny, &nz);
+  if (st != HZ_OK) return st;
+  const int cx = p.crop + 2 * kHalo, cy = cx;
+  if (cx > nx || p.crop >= ny) return HZ_ERR_INVALID;
+  const int64_t n = (int64_t)nx * ny * nz;
+  TrainBufs bufs;
+  double* xs = bufs.get<double>(n);
+  double* xk = bufs.get<double>(n);
+  float* pin = bufs.get<float>(n * p.n_iterates);
+  float* ptg = bufs.get<float>(n * p.n_iterates);
+  const int64_t cn = (int64_t)p.batch * cx * cy * nz;
+  float* bin = bufs.get<float>(cn);
+  float* btg = bufs.get<float>(cn);
+  if (!xs || !xk || !pin || !ptg || !bin || !btg) {
+    snprintf(g_nn_err, sizeof(g_nn_err), "hz_nn_train: device allocation failed");
+    return HZ_ERR_OOM;
+  }
+  // 1. the exact solution
+  hz_solve_params sp;
+  hz_default_params(&sp);
+  sp.mode = HZ_MODE_FP64;
+  sp.tol = p.xstar_tol;
+  hz_solve_info info;
+  st = hz_solve(op, b, nullptr, xs, &sp, &info);
+  if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) return st;
+  // 2. iterates of the plain mixed solver and their pairs
+  int npairs = 0;
+  for (int q = 0; q < p.n_iterates; ++q) {
+    hz_default_params(&sp);
+    sp.max_outer = 1;
+    sp.max_inner = p.iterates[q];
+    sp.inner_tol = 1e-12;
+    st = hz_solve(op, b, nullptr, xk, &sp, &info);
+    if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) return st;
+    if (info.inner_iters < 1) continue;
+    double sigma = 0.0;
+    st = hz_nn_make_pair(op, b, xk, xs, pin + npairs * n, ptg + npairs * n, &sigma);
+    if (st != HZ_OK) return st;
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) continue;
+    ++npairs;
+  }
+  if (npairs == 0) {
+    snprintf(g_nn_err, sizeof(g_nn_err), "hz_nn_train: no usable training pair (the system converged at once)");
+    return HZ_ERR_INVALID;
+  }
+  // 3. Adam steps on random crops of random pairs
+  std::vector<int> corners(2 * p.batch);
+  uint64_t ctr = 0;
+  const int jspan = ny - p.crop > 1 ? ny - p.crop : 1;
+  for (int it = 0; it < p.steps; ++it) {
+    int pi = (int)(draw(p.seed, 2 * p.stream, ctr++) * npairs);
+    if (pi >= npairs) pi = npairs - 1;
+    for (int q = 0; q < p.batch; ++q) {
+      int i0 = (int)(draw(p.seed, 2 * p.stream + 1, ctr++) * nx);
+      int j0 = (int)(draw(p.seed, 2 * p.stream + 1, ctr++) * jspan);
+      if (i0 >= nx) i0 = nx - 1;
+      if (j0 >= jspan) j0 = jspan - 1;
+      corners[2 * q] = i0 - kHalo;
+      corners[2 * q + 1] = j0 - kHalo;
+    }
+    st = hz_nn_crops(nx, ny, nz, pin + pi * n, ptg + pi * n, p.batch, cx, cy, corners.data(), bin, btg, nn->stream);
+    if (st != HZ_OK) return st;
+    double loss = 0.0;
+    st = hz_nn_train_step(nn, cx, p.batch * cy, nz, cy, 0, kHalo, bin, btg, p.lr, p.clip, &loss);
+    if (st != HZ_OK) return st;
+    if (losses) losses[it] = loss;
+  }
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  return HZ_OK;
+}
+
+}  // extern "C"
+

@@ -13,6 +13,9 @@
 // True residual (Sec. 3, r_i = b - A x_i and R = ||r_i||/||b||): FP64 with the
 // unscaled bands, fused with the refinement update x <- x + d and with the
 // scaling/cast of the next inner right-hand side D^-1 r.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "hz_internal.cuh"
 
 namespace hz {
@@ -70,6 +73,29 @@ __global__ void __launch_bounds__(kBS) k_setup(Grid g, const double* __restrict_
 
 cudaError_t launch_setup(const Grid& g, const double* A7, SetupOut o, const Launch& L) {
   k_setup<<<grid_for((const void*)k_setup, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, A7, o);
+  return cudaGetLastError();
+}
+
+// 16-bit copies of the horizontal bands E, W, N, S of Ahat (rows 0..3 of ah64),
+// rounded to nearest even: BF16 from the FP32 rounding of the FP64 value (the
+// FP32 operator's value, rounded once more), FP16 directly from the FP64 value
+__global__ void __launch_bounds__(256) k_h16(int64_t n, const double* __restrict__ ah64, uint16_t* __restrict__ out,
+                                             int64_t stride, int fmt) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 4 * n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = q / n, p = q - b * n;
+    const double v = ah64[q];
+    uint16_t h;
+    if (fmt == HB_BF16)
+      h = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+    else
+      h = __half_as_ushort(__double2half(v));
+    out[b * stride + p] = h;
+  }
+}
+
+cudaError_t launch_h16(const Grid& g, const double* ah64, uint16_t* out, int64_t stride, int fmt, const Launch& L) {
+  k_h16<<<grid_for((const void*)k_h16, 256, L, (4 * g.n + 255) / 256), 256, 0, L.stream>>>(g.n, ah64, out, stride,
+                                                                                          fmt);
   return cudaGetLastError();
 }
 
@@ -221,6 +247,7 @@ cudaError_t launch_residual_x64(const Grid& g, const double* A7, const double* i
 
 void warm_launch_kernels(const Launch& L) {
   grid_for((const void*)k_setup, kBS, L, 1);
+  grid_for((const void*)k_h16, 256, L, 1);
 #define HZ_WARM_RES(D, DD)                                               \
   grid_for((const void*)k_residual<D, DD, true, true>, kBS, L, 1);       \
   grid_for((const void*)k_residual<D, DD, true, false>, kBS, L, 1);      \

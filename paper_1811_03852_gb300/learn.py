@@ -1,9 +1,10 @@
 """Training and evaluation of the learned preconditioner stage (orchestration only).
 
-Every numerical step runs in the CUDA library: the systems are solved by
-hz_solve, the (residual, error) pairs are formed by hz_nn_make_pair, crops
-are cut by hz_nn_crops, and the network is trained by hz_nn_train_step.
-This module only decides which seeds, iterates and crop corners to use.
+Every numerical step runs in the CUDA library: hz_nn_train solves each
+system (hz_solve), forms its (residual, error) pairs (hz_nn_make_pair), cuts
+random crops (hz_nn_crops, corners from its own counter-based generator)
+and takes the Adam steps (hz_nn_train_step).  This module only chooses the
+seeds of the training and test systems and evaluates.
 
 Data (one reading of the recipe): for each training system, the exact
 solution x* comes from an FP64 solve to 1e-11; the plain mixed solver is run
@@ -12,16 +13,11 @@ pair (stage input e1/sigma, target (x* - x_k - T^-1 r)/sigma).  Random
 crops of crop x crop columns (all levels) plus a halo of 4 (the receptive
 field of four 3x3x3 layers) are cut from every pair; the loss covers the
 interior only, so each crop sees exactly the neighbourhood it would see in
-the full field.  Crop corners are drawn from the counter-based generator in
-``gen`` (they are inputs, not library arithmetic).
+the full field.
 """
 from __future__ import annotations
 
-import time
-
 import numpy as np
-
-HALO = 4
 
 
 def _torch():
@@ -67,40 +63,26 @@ def system_pairs(op, b_dev, iters=(1, 2, 4, 8, 16, 32), eta_star=1e-11):
 
 def train(net, systems, dims, steps=200, batch=16, crop=64, lr=3e-4, seed=0, z_unit="radius", iters=None,
           log=None, clip=1.0):
-    """Train on the given (seed_coef, seed_rhs) systems.  Returns the list of losses."""
+    """Train on the given (seed_coef, seed_rhs) systems, one hz_nn_train call per system (the
+    library forms the pairs, draws the crops and takes the Adam steps; the operator exists only
+    for its call).  Returns the list of losses."""
     torch = _torch()
     import gen
     import paper_1811_03852_gb300 as hz
 
     nx, ny, nz = dims
-    cx = cy = crop + 2 * HALO
-    bin_ = torch.empty(batch * cx * cy * nz, dtype=torch.float32, device="cuda")
-    btg = torch.empty_like(bin_)
     losses = []
     steps_per_sys = max(1, steps // max(1, len(systems)))
-    ctr = 0
     for si, (sc, sr) in enumerate(systems):
         A = gen.make_operator(nx, ny, nz, sc, z_unit=z_unit)
         b = torch.from_numpy(gen.make_rhs(nx, ny, nz, sr).reshape(-1)).cuda()
         op = hz.Operator(A)
-        pairs = system_pairs(op, b, **({"iters": iters} if iters else {}))
-        del op
-        for _ in range(steps_per_sys):
-            # one pair per step, `batch` crops of it, stacked along j by the crop kernel
-            pi = min(int(gen.uniform(seed, 11, ctr) * len(pairs)), len(pairs) - 1)
-            ctr += 1
-            corners = []
-            for q in range(batch):
-                i0 = int(gen.uniform(seed, 12, ctr) * nx)
-                j0 = int(gen.uniform(seed, 13, ctr) * max(1, ny - crop))
-                ctr += 1
-                corners.append((i0 - HALO, j0 - HALO))
-            hz.nn_crops(pairs[pi][0], pairs[pi][1], dims, corners, cx, cy, bin_, btg)
-            loss = net.train_step(bin_, btg, (cx, batch * cy, nz), lr=lr, seg_ny=cy, periodic=False, border=HALO,
-                                  clip=clip)
-            losses.append(loss)
-            if log and len(losses) % 20 == 0:
-                log(f"step {len(losses)} system {si} loss {loss:.4f}")
+        kw = {"iterates": iters} if iters else {}
+        losses += net.train(op, b, steps=steps_per_sys, batch=batch, crop=crop, lr=lr, clip=clip, seed=seed,
+                            stream=si, **kw)
+        op.close()
+        if log:
+            log(f"system {si} ({sc}/{sr}): {len(losses)} steps, last loss {losses[-1]:.4f}")
     return losses
 
 

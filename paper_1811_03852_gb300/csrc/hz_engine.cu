@@ -87,6 +87,7 @@ struct hz_op_s {
   Red red{};
   int* err_d = nullptr;
   int* err_h = nullptr;
+  int* kerr_d = nullptr;  // bounded-wait error word of kernels launched without a control block
   double* hist_d = nullptr;
   int hist_cap = 0;
   GraphSlot gs[2];  // [0] FP32 inner loop, [1] FP64 inner loop
@@ -675,11 +676,12 @@ void free_op(hz_op op) {
 }
 
 // ---- column-kernel variants -------------------------------------------------
-bool variant_ok(int prec, int kind, int id, int nx, int nz) {
+bool variant_ok(int prec, int kind, int id, const Grid& g) {
   int v = 1, u = 1;
   variant_shape(prec, kind, id, &v, &u);
-  if (variant_parks_smem(prec, kind, id) && (size_t)nz * kBS * v * (prec ? 8 : 4) > 200 * 1024) return false;
-  return nx % v == 0;
+  if (kind == 0 && variant_park_mode(prec, id) == kParkBulk) return prec == 0 && thomas_bulk_ok(g);
+  if (variant_parks_smem(prec, kind, id) && (size_t)g.nz * kBS * v * (prec ? 8 : 4) > 200 * 1024) return false;
+  return g.nx % v == 0;
 }
 
 // The launch shape used until the autotuner picks one (and kept by it unless
@@ -707,7 +709,8 @@ int default_variant(int prec, int kind, int nx) {
   for (int i = 0; i < num_variants(prec, kind); ++i) {
     int v = 1, u = 1;
     variant_shape(prec, kind, i, &v, &u);
-    if (nx % v == 0 && v > bestv && !variant_parks_smem(prec, kind, i)) {
+    if (nx % v == 0 && v > bestv && !variant_parks_smem(prec, kind, i) &&
+        !(kind == 0 && variant_park_mode(prec, i) == kParkBulk)) {
       best = i;
       bestv = v;
     }
@@ -754,7 +757,7 @@ void load_tuned(hz_op op) {
         char want[400];
         tune_key(op, pr, kind, want, sizeof(want));
         if (strcmp(want, key) != 0 || var < 0) continue;
-        if (kind < 2 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g.nx, op->g.nz))
+        if (kind < 2 && var < num_variants(pr, kind) && variant_ok(pr, kind, var, op->g))
           (kind == 0 ? op->L.vpre : op->L.vmv)[pr] = var;
         else if (kind >= 2 && sor_variant_ok(pr, kind - 2, var, op->g.nx))
           op->L.vsor[pr][kind - 2] = var;
@@ -876,6 +879,9 @@ int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_
   if (!(op->red.partials = dalloc<double>(op, (int64_t)kMaxGrid * kMaxND, &st))) return fail(st);
   if (!(op->red.ticket = dalloc<unsigned>(op, 1, &st))) return fail(st);
   if (!(op->err_d = dalloc<int>(op, 1, &st))) return fail(st);
+  if (!(op->kerr_d = dalloc<int>(op, 1, &st))) return fail(st);
+  if (cudaMemsetAsync(op->kerr_d, 0, sizeof(int), op->stream) != cudaSuccess) return fail(HZ_ERR_CUDA);
+  op->L.err = op->kerr_d;
   if (cudaMallocHost(&op->cfg_h, sizeof(Ctl)) != cudaSuccess) return fail(HZ_ERR_OOM);
   if (cudaMallocHost(&op->rep_h, sizeof(Ctl)) != cudaSuccess) return fail(HZ_ERR_OOM);
   if (cudaMallocHost(&op->err_h, sizeof(int)) != cudaSuccess) return fail(HZ_ERR_OOM);
@@ -1139,6 +1145,11 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     double* next = (cur == XA) ? XB : XA;
     CKS(residual(cur, next, true));
     const Ctl& rp = *op->rep_h;
+    if (rp.kerr) {
+      snprintf(g_err, sizeof(g_err), "inner solve: a bounded wait of a bulk-copy kernel ran out");
+      status = HZ_ERR_TIMEOUT;
+      break;
+    }
     // launches per inner iteration: 6 with T^-1; with tri-SOR 2 first-pass
     // kernels, 2 (2 sweeps - 1) colour passes, 2 matvecs and k_upd
     const long long per_it = sor ? 4LL * p.sor_sweeps + 3 : 6LL;
@@ -1271,7 +1282,7 @@ int autotune_prec(hz_op op, int reps, double* best_ms) {
   for (int kind = 0; kind < 2; ++kind) {
     std::vector<double> times(num_variants(pr, kind), -1.0);  // -1: not valid for this grid
     for (int id = 0; id < num_variants(pr, kind); ++id) {
-      if (!variant_ok(pr, kind, id, op->g.nx, op->g.nz)) continue;
+      if (!variant_ok(pr, kind, id, op->g)) continue;
       Launch L = op->L;
       (kind == 0 ? L.vpre : L.vmv)[pr] = id;
       double m1, m2;
@@ -1431,7 +1442,7 @@ int hz_op_set_variants(hz_op op, int pre32, int mv32, int pre64, int mv64) {
   for (int q = 0; q < 4; ++q) {
     const int pr = q / 2, kind = q % 2;
     if (v[q] < 0) continue;
-    if (v[q] >= num_variants(pr, kind) || !variant_ok(pr, kind, v[q], op->g.nx, op->g.nz)) return HZ_ERR_INVALID;
+    if (v[q] >= num_variants(pr, kind) || !variant_ok(pr, kind, v[q], op->g)) return HZ_ERR_INVALID;
   }
   for (int q = 0; q < 4; ++q) {
     const int pr = q / 2, kind = q % 2;
@@ -1494,8 +1505,25 @@ int hz_matvec(hz_op op, int prec, const void* x, void* y) {
   return HZ_OK;
 }
 
+// the bounded-wait error word of the kernels launched without a control block
+// (read and cleared; HZ_ERR_TIMEOUT if a wait ran out)
+int check_kerr(hz_op op) {
+  CK(cudaMemcpyAsync(op->err_h, op->kerr_d, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
+  CK(cudaStreamSynchronize(op->stream));
+  if (*op->err_h) {
+    CK(cudaMemsetAsync(op->kerr_d, 0, sizeof(int), op->stream));
+    snprintf(g_err, sizeof(g_err), "a bounded wait of a bulk-copy kernel ran out");
+    return HZ_ERR_TIMEOUT;
+  }
+  return HZ_OK;
+}
+
 int hz_precond_apply(hz_op op, int prec, const void* r, void* z) {
   if (!op || !r || !z || r == z) return HZ_ERR_INVALID;
+  if (prec == HZ_PREC_FP32 && variant_park_mode(0, op->L.vpre[0]) == kParkBulk) {
+    CK(launch_tinv<float>(op->g, bands_of<float>(op), (const float*)r, (float*)z, op->L));
+    return check_kerr(op);
+  }
   if (prec == HZ_PREC_FP32)
     CK(launch_tinv<float>(op->g, bands_of<float>(op), (const float*)r, (float*)z, op->L));
   else if (prec == HZ_PREC_FP64)
@@ -1546,6 +1574,10 @@ int hz_trisor_apply(hz_op op, int prec, int sweeps, double omega, const void* r,
 
 int hz_precond_matvec(hz_op op, int prec, const void* p, void* ph, void* v) {
   if (!op || !p || !ph || !v) return HZ_ERR_INVALID;
+  if (prec == HZ_PREC_FP32 && variant_park_mode(0, op->L.vpre[0]) == kParkBulk) {
+    CK(launch_precond_matvec<float>(op->g, bands_of<float>(op), (const float*)p, (float*)ph, (float*)v, op->L));
+    return check_kerr(op);
+  }
   if (prec == HZ_PREC_FP32)
     CK(launch_precond_matvec<float>(op->g, bands_of<float>(op), (const float*)p, (float*)ph, (float*)v, op->L));
   else if (prec == HZ_PREC_FP64)

@@ -59,7 +59,9 @@ struct Ctl {
   // 1: dot products summed in FP32 at every level, thread, block and grid (the
   // paper's original 32-bit global sums, Sec. 4); 0: FP64 across threads
   int dot32;
-  int pad1;
+  // device error word of the inner solve (bit 0: a bounded wait of a
+  // bulk-copy kernel ran out); the host reports HZ_ERR_TIMEOUT
+  int kerr;
 };
 
 struct Red {
@@ -202,6 +204,7 @@ struct Launch {
   int vmv[2];        // variant of the stencil kernels
   int vsor[2][3];    // tri-SOR variants: [prec][0 colour pass, 1 matvec, 2 first pass]
   int nz;            // levels of the operator (shared-memory size of the parking variants)
+  int* err;          // device error word of launches without a control block (bounded waits)
 };
 
 // tri-SOR kernel variants (kind 0 colour pass, 1 matvec, 2 first pass):
@@ -223,6 +226,15 @@ bool variant_parks_smem(int prec, int kind, int id);
 int variant_park_mode(int prec, int id);
 template <typename T>
 void warm_kernels(const Launch& L);
+
+// ---- the bulk-copy Thomas kernels (hz_thomas_bulk.cu), FP32 ----
+constexpr int kParkBulk = 3;  // their park mode in the Thomas variant tables (PARK_BULK)
+// mode 0: k_pre_p's work (p update + T^-1), 1: k_pre_s's (s = r - alpha v + T^-1),
+// 2: z = T^-1 r alone.  Valid when ncol % 4 == 0 and the tile's parked sweep fits.
+bool thomas_bulk_ok(const Grid& g);
+cudaError_t launch_thomas_bulk(int mode, const Grid& g, const Bands<float>& a, const Vecs<float>& w, const float* r,
+                               float* z, Ctl* ctl, int* err, const Launch& L);
+void warm_thomas_bulk(const Launch& L, int nz);
 
 // Blocks for a grid-stride kernel: every SM filled to that kernel's own
 // occupancy (queried once per kernel and cached) or to per_sm_cap blocks when

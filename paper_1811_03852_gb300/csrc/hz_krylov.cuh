@@ -32,18 +32,19 @@ template <typename T>
 struct Variants;
 // Thomas variants: V columns per thread, U levels per batch, pre_p where the
 // forward sweep is parked (ParkMode: 0 the output vector, 1 shared memory,
-// nz * kBS * V values per block, 2 the output vector with L2 priorities) and
+// nz * kBS * V values per block, 2 the output vector with L2 priorities, 3 the
+// bulk-copy kernel of hz_thomas_bulk.cu, which ignores V and U) and
 // pre_b resident blocks per SM (0: as many as fit).  Fewer resident columns
 // keep the parked sweep of every column in flight inside L2.  Stencil
 // variants: mv_v columns per thread, mv_u levels per batch, mv_h L2 priorities
 // (the arrays read once evict-first, so that rows of x stay in L2).
 template <>
 struct Variants<float> {
-  static constexpr int NPRE = 13, NMV = 7;
-  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2};
-  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4};
-  static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};
-  static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3};
+  static constexpr int NPRE = 14, NMV = 7;
+  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2, 1};
+  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4, 1};
+  static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3};
+  static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3, 0};
   static constexpr int mv_v[NMV] = {1, 4, 2, 2, 4, 2, 2};
   static constexpr int mv_u[NMV] = {4, 1, 2, 1, 1, 2, 1};
   static constexpr int mv_h[NMV] = {0, 0, 0, 0, 1, 1, 1};
@@ -529,22 +530,32 @@ cudaError_t launch_pre_p_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, C
   k_pre_start<T><<<grid_for((const void*)k_pre_start<T>, kBS, L, L.wcol), kBS, 0, L.stream>>>(g, a, w, ctl, red);
   return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+    if constexpr (P == PARK_BULK) {
+      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(0, g, a, w, nullptr, nullptr, ctl, &ctl->kerr, L);
+      return cudaErrorInvalidValue;
+    } else {
     const void* k = (const void*)k_pre_p<T, V, U, P>;
     const size_t sm = park_bytes<T, V, P>(g.nz);
     k_pre_p<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, w,
                                                                                                           ctl);
     return cudaGetLastError();
+    }
   });
 }
 template <typename T>
 cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
   return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+    if constexpr (P == PARK_BULK) {
+      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(1, g, a, w, nullptr, nullptr, ctl, &ctl->kerr, L);
+      return cudaErrorInvalidValue;
+    } else {
     const void* k = (const void*)k_pre_s<T, V, U, P>;
     const size_t sm = park_bytes<T, V, P>(g.nz);
     k_pre_s<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, w,
                                                                                                           ctl);
     return cudaGetLastError();
+    }
   });
 }
 template <typename T, int MODE>
@@ -577,10 +588,15 @@ template <typename T>
 cudaError_t launch_tinv_t(const Grid& g, const Bands<T>& a, const T* r, T* z, const Launch& L) {
   return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
+    if constexpr (P == PARK_BULK) {
+      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(2, g, a, Vecs<T>{}, r, z, nullptr, L.err, L);
+      return cudaErrorInvalidValue;
+    } else {
     const void* k = (const void*)k_tinv<T, V, U, P>;
     const size_t sm = park_bytes<T, V, P>(g.nz);
     k_tinv<T, V, U, P><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), sm, cap), kBS, sm, L.stream>>>(g, a, r, z);
     return cudaGetLastError();
+    }
   });
 }
 template <typename T>
@@ -607,17 +623,23 @@ void warm_t(const Launch& L) {
   for (int i = 0; i < Variants<T>::NPRE; ++i)
     with_pre<T>(i, [&](auto Vc, auto Uc, auto Pc, int) {
       constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
-      constexpr bool SM = P == PARK_SMEM;
-      const size_t sm = park_bytes<T, V, P>(L.nz);
-      const void* ks[3] = {(const void*)k_pre_p<T, V, U, P>, (const void*)k_pre_s<T, V, U, P>,
-                           (const void*)k_tinv<T, V, U, P>};
-      for (const void* k : ks) {
-        if (sm > kParkMax) continue;  // the variant is not valid for this nz
-        if (SM && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kParkMax) != cudaSuccess)
-          cudaGetLastError();  // the launch reports it; nothing stale is left behind
-        grid_for(k, kBS, L, 1, sm);
+      if constexpr (P == PARK_BULK) {
+        if (sizeof(T) == 4) warm_thomas_bulk(L, L.nz);
+        return cudaSuccess;
+      } else {
+        constexpr bool SM = P == PARK_SMEM;
+        const size_t sm = park_bytes<T, V, P>(L.nz);
+        const void* ks[3] = {(const void*)k_pre_p<T, V, U, P>, (const void*)k_pre_s<T, V, U, P>,
+                             (const void*)k_tinv<T, V, U, P>};
+        for (const void* k : ks) {
+          if (sm > kParkMax) continue;  // the variant is not valid for this nz
+          if (SM &&
+              cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kParkMax) != cudaSuccess)
+            cudaGetLastError();  // the launch reports it; nothing stale is left behind
+          grid_for(k, kBS, L, 1, sm);
+        }
+        return cudaSuccess;
       }
-      return cudaSuccess;
     });
   for (int i = 0; i < Variants<T>::NMV; ++i)
     for (int hb = HB_F32; hb <= (sizeof(T) == 4 ? HB_FP16 : HB_F32); ++hb)

@@ -242,6 +242,13 @@ int hz_nn_forward(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, co
    every crop excluded in i and j); grad: host or device doubles, loss: host */
 int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
                    const float* t, double* grad, double* loss);
+/* the gradient of the operator-weighted loss (see hz_nn_train_params.loss) on
+   stacked crops (no wrap in i): bands = the crops' six scaled bands
+   E,W,N,S,U,D of D^-1 A ([6][nx*ny*nz], host or device floats); border (>= 1)
+   excludes the points near each crop's edges in i and j from the residual;
+   neighbours outside a crop are absent.  grad: host or device doubles. */
+int hz_nn_gradient_op(hz_nn nn, int nx, int ny, int nz, int seg_ny, int border, const float* x, const float* t,
+                      const float* bands, double* grad, double* loss);
 /* one Adam step on that loss; the gradient is first scaled down to global
    2-norm clip when it is larger (clip <= 0: no clipping).  loss: host, may be NULL */
 int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
@@ -318,6 +325,10 @@ typedef struct {
   double clip;        /* global gradient 2-norm clip (default 1; <= 0: none) */
   unsigned long long seed;    /* random draws: (seed, stream) select the counter stream */
   unsigned long long stream;
+  int loss;           /* 1 (default): operator-weighted, ||D^-1 A (y - t)||^2 / ||D^-1 A t||^2 over the crop
+                         interior less one more column (with t the pair's target, D^-1 A t is the stage
+                         input: the squared relative residual left after the stage); 0: the relative MSE
+                         ||y - t||^2 / ||t||^2 of hz_nn_train_step */
 } hz_nn_train_params;
 void hz_nn_train_defaults(hz_nn_train_params* p);
 int hz_nn_train(hz_nn nn, hz_op op, const double* b, const hz_nn_train_params* p, double* losses);

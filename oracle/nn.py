@@ -152,3 +152,49 @@ def unflatten(flat):
 
 def num_params():
     return sum(CHANNELS[i + 1] * CHANNELS[i] * 27 + CHANNELS[i + 1] for i in range(4))
+
+
+# ---- operator-weighted loss: the residual left after the learned stage ------------------
+_NBR = {0: (0, 0, 1), 1: (0, 0, -1), 2: (0, 1, 0), 3: (0, -1, 0), 4: (1, 0, 0), 5: (-1, 0, 0)}  # (dk, dj, di) of E,W,N,S,U,D
+
+
+def _shift(f, dk, dj, di, seg):
+    """g[p] = f[p + (dk, dj, di)] on (nz, ny, nx) with zero outside the field and outside p's own
+    segment of seg rows in j (stacked crops); no wrap."""
+    nz, ny, nx = f.shape
+    g = np.zeros_like(f)
+    ks, ke = max(0, -dk), nz - max(0, dk)
+    is_, ie = max(0, -di), nx - max(0, di)
+    for s0 in range(0, ny, seg):
+        js, je = s0 + max(0, -dj), s0 + seg - max(0, dj)
+        g[ks:ke, js:je, is_:ie] = f[ks + dk:ke + dk, js + dj:je + dj, is_ + di:ie + di]
+    return g
+
+
+def ahat_crop(bands, d, seg=None):
+    """(Ahat d)[p] = d[p] + sum_b band_b[p] d[p + offset_b] on a training crop (nz, ny, nx) whose
+    neighbours outside the crop (or its segment of seg rows) are absent; bands (6, nz, ny, nx)."""
+    seg = seg or d.shape[1]
+    out = d.copy()
+    for b, (dk, dj, di) in _NBR.items():
+        out += bands[b] * _shift(d, dk, dj, di, seg)
+    return out
+
+
+def ahat_crop_transpose(bands, w, seg=None):
+    """The adjoint of ahat_crop: (Ahat^T w)[q] = w[q] + sum_b band_b[q - offset_b] w[q - offset_b]."""
+    seg = seg or w.shape[1]
+    out = w.copy()
+    for b, (dk, dj, di) in _NBR.items():
+        out += _shift(bands[b] * w, -dk, -dj, -di, seg)
+    return out
+
+
+def op_loss(y, t, bands, mask, seg=None):
+    """Loss ||mask Ahat (y - t)||^2 / ||mask Ahat t||^2 and its gradient dL/dy
+    = 2 Ahat^T (mask Ahat (y - t)) / ||mask Ahat t||^2.  With t = Ahat^-1 e1 (the stage's target),
+    Ahat t = e1 and the loss is the squared relative residual left after the stage."""
+    u = np.where(mask, ahat_crop(bands, y - t, seg), 0.0)
+    at = np.where(mask, ahat_crop(bands, t, seg), 0.0)
+    den = float(np.sum(at * at))
+    return float(np.sum(u * u)) / den, 2.0 * ahat_crop_transpose(bands, u, seg) / den

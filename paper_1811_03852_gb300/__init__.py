@@ -389,6 +389,7 @@ class hz_nn_train_params(ctypes.Structure):
         ("clip", ctypes.c_double),
         ("seed", ctypes.c_ulonglong),
         ("stream", ctypes.c_ulonglong),
+        ("loss", ctypes.c_int),
     ]
 
 
@@ -412,6 +413,7 @@ def _nn_sigs(L):
         "hz_nn_make_pair": (i32, [pv, pv, pv, pv, pv, pv, P(dbl)]),
         "hz_nn_train_defaults": (None, [P(hz_nn_train_params)]),
         "hz_nn_train": (i32, [pv, pv, pv, P(hz_nn_train_params), pv]),
+        "hz_nn_gradient_op": (i32, [pv, i32, i32, i32, i32, i32, pv, pv, pv, pv, P(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -492,9 +494,18 @@ class Net:
                                             lr, clip, ctypes.byref(loss)), "hz_nn_train_step")
         return loss.value
 
+    def gradient_op(self, x, t, bands, dims, seg_ny=None, border=5):
+        """Gradient and value of the operator-weighted loss on stacked crops (hz_nn_gradient_op)."""
+        nx, ny, nz = dims
+        g = np.empty(self.num_params(), dtype=np.float64)
+        loss = ctypes.c_double()
+        _nn_check(_nnlib().hz_nn_gradient_op(self._h, nx, ny, nz, seg_ny or ny, border, _ptr(x), _ptr(t), _ptr(bands),
+                                             g.ctypes.data, ctypes.byref(loss)), "hz_nn_gradient_op")
+        return g, loss.value
+
     def train(self, op, b, iterates=None, **kw):
         """hz_nn_train: pairs from the system (op, b) and kw["steps"] Adam steps on crops of them.
-        kw: fields of hz_nn_train_params (steps, batch, crop, xstar_tol, lr, clip, seed, stream).
+        kw: fields of hz_nn_train_params (steps, batch, crop, xstar_tol, lr, clip, seed, stream, loss).
         Returns the losses of the steps."""
         L = _nnlib()
         p = hz_nn_train_params()

@@ -734,6 +734,76 @@ __global__ void __launch_bounds__(256) k_nn_dy(NnGrid g, const float* __restrict
     dy[p] = in_mask(g, p, border) ? sc * (y[p] - t[p]) : 0.f;
 }
 
+// Operator-weighted loss on stacked training crops: u = mask (Ahat (y - t)),
+// loss = ||u||^2 / ||mask Ahat t||^2 (with t = Ahat^-1 e1 the target of the
+// stage, Ahat t = e1: the squared relative residual left after the stage).
+// bands: the crops of the six scaled bands E, W, N, S, U, D at stride n.  On a
+// crop, neighbours outside its columns, its segment of seg rows or the levels
+// are absent (the mask keeps every term inside).
+__global__ void __launch_bounds__(256) k_nn_oploss(NnGrid g, const float* __restrict__ y, const float* __restrict__ t,
+                                                   const float* __restrict__ bands, int border, float* __restrict__ u,
+                                                   double* __restrict__ part) {
+  const int64_t plane = (int64_t)g.nx * g.ny, n = g.n;
+  double a = 0.0, b = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (!in_mask(g, p, border)) {
+      u[p] = 0.f;
+      continue;
+    }
+    const int i = (int)(p % g.nx), jj = (int)((p / g.nx) % g.ny) % g.seg, k = (int)(p / plane);
+    float ad = y[p] - t[p], at = t[p];
+    auto add = [&](int b6, int64_t q) {
+      const float c = bands[b6 * n + p];
+      ad = fmaf(c, y[q] - t[q], ad);
+      at = fmaf(c, t[q], at);
+    };
+    if (i + 1 < g.nx) add(0, p + 1);
+    if (i > 0) add(1, p - 1);
+    if (jj + 1 < g.seg) add(2, p + g.nx);
+    if (jj > 0) add(3, p - g.nx);
+    if (k + 1 < g.nz) add(4, p + plane);
+    if (k > 0) add(5, p - plane);
+    u[p] = ad;
+    a += (double)ad * ad;
+    b += (double)at * at;
+  }
+  __shared__ double sa[8], sb[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) sa[warp] = a, sb[warp] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, z = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += sa[w], z += sb[w];
+    part[blockIdx.x * 2] = x;
+    part[blockIdx.x * 2 + 1] = z;
+  }
+}
+
+// dy = 2 Ahat^T u / ||mask Ahat t||^2: (Ahat^T u)[q] = u[q] + sum_b band_b[q - off_b] u[q - off_b]
+__global__ void __launch_bounds__(256) k_nn_opdy(NnGrid g, const float* __restrict__ u,
+                                                 const float* __restrict__ bands, const double* __restrict__ lossv,
+                                                 float* __restrict__ dy) {
+  const int64_t plane = (int64_t)g.nx * g.ny, n = g.n;
+  const double den = lossv[1];
+  const float sc = den > 0.0 ? (float)(2.0 / den) : 0.f;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q % g.nx), jj = (int)((q / g.nx) % g.ny) % g.seg, k = (int)(q / plane);
+    float v = u[q];
+    if (i > 0) v = fmaf(bands[0 * n + q - 1], u[q - 1], v);
+    if (i + 1 < g.nx) v = fmaf(bands[1 * n + q + 1], u[q + 1], v);
+    if (jj > 0) v = fmaf(bands[2 * n + q - g.nx], u[q - g.nx], v);
+    if (jj + 1 < g.seg) v = fmaf(bands[3 * n + q + g.nx], u[q + g.nx], v);
+    if (k > 0) v = fmaf(bands[4 * n + q - plane], u[q - plane], v);
+    if (k + 1 < g.nz) v = fmaf(bands[5 * n + q + plane], u[q + plane], v);
+    dy[q] = sc * v;
+  }
+}
+
 // Adam (Kingma & Ba) on the FP32 master parameters; lr, betas, eps and the
 // bias corrections come from the host.
 // global gradient norm (one block, fixed order) -> clipping factor min(1, clip / ||g||)
@@ -1016,8 +1086,11 @@ static int nn_dw(hz_nn_s* nn, const NnGrid& g, const float* dz, const HT* hin, d
   return HZ_OK;
 }
 
-// forward + masked relative-MSE loss + backward: d.grad, d.lossv
-static int nn_gradient(hz_nn_s* nn, const NnGrid& g, int border, const float* x, const float* t) {
+// forward + masked loss + backward: d.grad, d.lossv.  bands == nullptr: the
+// relative MSE of the output against t; else the operator-weighted loss with
+// the crops' scaled bands (border then bounds the residual's mask)
+static int nn_gradient(hz_nn_s* nn, const NnGrid& g, int border, const float* x, const float* t,
+                       const float* bands = nullptr) {
   NnDev& d = nn->d;
   cudaStream_t s = nn->stream;
   int st = nn_reserve(nn, g.n, true);
@@ -1030,9 +1103,15 @@ static int nn_gradient(hz_nn_s* nn, const NnGrid& g, int border, const float* x,
     NN_CK(cudaMalloc(&d.part, sizeof(double) * 2 * gl));
     d.part_cap = 2 * gl;
   }
-  k_nn_loss<<<gl, 256, 0, s>>>(g, d.y, t, border, d.part);
-  k_nn_loss_fin<<<1, 32, 0, s>>>(d.part, gl, d.lossv);
-  k_nn_dy<<<gl, 256, 0, s>>>(g, d.y, t, border, d.lossv, d.dy);
+  if (bands) {
+    k_nn_oploss<<<gl, 256, 0, s>>>(g, d.y, t, bands, border, d.dzb, d.part);  // u in the dz2 scratch
+    k_nn_loss_fin<<<1, 32, 0, s>>>(d.part, gl, d.lossv);
+    k_nn_opdy<<<gl, 256, 0, s>>>(g, d.dzb, bands, d.lossv, d.dy);
+  } else {
+    k_nn_loss<<<gl, 256, 0, s>>>(g, d.y, t, border, d.part);
+    k_nn_loss_fin<<<1, 32, 0, s>>>(d.part, gl, d.lossv);
+    k_nn_dy<<<gl, 256, 0, s>>>(g, d.y, t, border, d.lossv, d.dy);
+  }
   const NnW w = nn_w(d);
   // layer 4
   k_nn_b4<<<gl, 256, 0, s>>>(g, d.dy, w, d.z3, d.dza);  // dz3
@@ -1203,12 +1282,12 @@ int hz_nn_gradient(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, i
   return HZ_OK;
 }
 
-int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
-                     const float* t, double lr, double clip, double* loss) {
-  if (!nn || !x || !t || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny || border < 0 || !(lr > 0))
-    return HZ_ERR_INVALID;
-  NnGrid g{nx, ny, nz, seg_ny, periodic ? 1 : 0, (int64_t)nx * ny * nz};
-  int st = nn_gradient(nn, g, border, x, t);
+}  // extern "C"
+
+// one Adam step on the gradient of the loss (nn_gradient's choice by bands)
+static int nn_train_step(hz_nn nn, const NnGrid& g, int border, const float* x, const float* t, const float* bands,
+                         double lr, double clip, double* loss) {
+  int st = nn_gradient(nn, g, border, x, t, bands);
   if (st != HZ_OK) return st;
   NnDev& d = nn->d;
   d.step += 1;
@@ -1224,6 +1303,31 @@ int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic,
     NN_CK(cudaStreamSynchronize(nn->stream));
     *loss = d.lossh[0];
   }
+  return HZ_OK;
+}
+
+extern "C" {
+
+int hz_nn_train_step(hz_nn nn, int nx, int ny, int nz, int seg_ny, int periodic, int border, const float* x,
+                     const float* t, double lr, double clip, double* loss) {
+  if (!nn || !x || !t || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny || border < 0 || !(lr > 0))
+    return HZ_ERR_INVALID;
+  NnGrid g{nx, ny, nz, seg_ny, periodic ? 1 : 0, (int64_t)nx * ny * nz};
+  return nn_train_step(nn, g, border, x, t, nullptr, lr, clip, loss);
+}
+
+int hz_nn_gradient_op(hz_nn nn, int nx, int ny, int nz, int seg_ny, int border, const float* x, const float* t,
+                      const float* bands, double* grad, double* loss) {
+  if (!nn || !x || !t || !bands || !grad || nx < 1 || ny < 1 || nz < 1 || seg_ny < 1 || ny % seg_ny || border < 1)
+    return HZ_ERR_INVALID;
+  NnGrid g{nx, ny, nz, seg_ny, 0, (int64_t)nx * ny * nz};
+  int st = nn_gradient(nn, g, border, x, t, bands);
+  if (st != HZ_OK) return st;
+  NnDev& d = nn->d;
+  NN_CK(cudaMemcpyAsync(d.lossh, d.lossv, sizeof(double) * 2, cudaMemcpyDeviceToHost, nn->stream));
+  NN_CK(cudaMemcpyAsync(grad, d.grad, sizeof(double) * kNParams, cudaMemcpyDefault, nn->stream));
+  NN_CK(cudaStreamSynchronize(nn->stream));
+  if (loss) *loss = d.lossh[0];
   return HZ_OK;
 }
 
@@ -1338,13 +1442,14 @@ void hz_nn_train_defaults(hz_nn_train_params* p) {
   p->clip = 1.0;
   p->seed = 7;
   p->stream = 0;
+  p->loss = 1;
 }
 
 int hz_nn_train(hz_nn nn, hz_op op, const double* b, const hz_nn_train_params* pp, double* losses) {
   if (!nn || !op || !b || !pp) return HZ_ERR_INVALID;
   const hz_nn_train_params p = *pp;
   if (p.steps < 0 || p.batch < 1 || p.crop < 1 || p.n_iterates < 1 || p.n_iterates > 16 || !(p.lr > 0.0) ||
-      !(p.xstar_tol > 0.0))
+      !(p.xstar_tol > 0.0) || (p.loss != 0 && p.loss != 1))
     return HZ_ERR_INVALID;
   for (int q = 0; q < p.n_iterates; ++q)
     if (p.iterates[q] < 1) return HZ_ERR_INVALID;
@@ -1362,10 +1467,15 @@ int hz_nn_train(hz_nn nn, hz_op op, const double* b, const hz_nn_train_params* p
   const int64_t cn = (int64_t)p.batch * cx * cy * nz;
   float* bin = bufs.get<float>(cn);
   float* btg = bufs.get<float>(cn);
-  if (!xs || !xk || !pin || !ptg || !bin || !btg) {
+  // the operator-weighted loss also needs the scaled bands on every crop
+  const bool opl = p.loss == 1;
+  float* b6 = opl ? bufs.get<float>(6 * n) : nullptr;
+  float* bcr = opl ? bufs.get<float>(6 * cn) : nullptr;
+  if (!xs || !xk || !pin || !ptg || !bin || !btg || (opl && (!b6 || !bcr))) {
     snprintf(g_nn_err, sizeof(g_nn_err), "hz_nn_train: device allocation failed");
     return HZ_ERR_OOM;
   }
+  if (opl && (st = hz_op_export(op, 0, HZ_PREC_FP32, b6)) != HZ_OK) return st;
   // 1. the exact solution
   hz_solve_params sp;
   hz_default_params(&sp);
@@ -1411,8 +1521,16 @@ int hz_nn_train(hz_nn nn, hz_op op, const double* b, const hz_nn_train_params* p
     }
     st = hz_nn_crops(nx, ny, nz, pin + pi * n, ptg + pi * n, p.batch, cx, cy, corners.data(), bin, btg, nn->stream);
     if (st != HZ_OK) return st;
+    for (int b = 0; opl && b < 6; b += 2) {
+      st = hz_nn_crops(nx, ny, nz, b6 + b * n, b6 + (b + 1) * n, p.batch, cx, cy, corners.data(), bcr + b * cn,
+                       bcr + (b + 1) * cn, nn->stream);
+      if (st != HZ_OK) return st;
+    }
     double loss = 0.0;
-    st = hz_nn_train_step(nn, cx, p.batch * cy, nz, cy, 0, kHalo, bin, btg, p.lr, p.clip, &loss);
+    const NnGrid cg{cx, p.batch * cy, nz, cy, 0, (int64_t)cx * p.batch * cy * nz};
+    // the residual needs one more column of exact network output around it
+    st = opl ? nn_train_step(nn, cg, kHalo + 1, bin, btg, bcr, p.lr, p.clip, &loss)
+             : nn_train_step(nn, cg, kHalo, bin, btg, nullptr, p.lr, p.clip, &loss);
     if (st != HZ_OK) return st;
     if (losses) losses[it] = loss;
   }

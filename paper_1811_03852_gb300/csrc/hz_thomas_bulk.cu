@@ -7,14 +7,17 @@
 // marches the levels.  One producer warp copies, level by level, every input
 // array's kTC-value row of the tile into a ring of kStages shared-memory
 // slots; kTC consumer threads (one column each) wait for a slot, run the
-// recurrence and release the slot.  Forward sweep: slot = the level's inputs
+// recurrence and release the slot.  Forward sweep: slot = one level's inputs
 // (r, and p, v or v for the axpy; the factors m, l); the consumer forms q
 // (p = r + beta (p - omega v), s = r - alpha v, or q = r), stores it, and
-// parks y_k = m_k q_k - l_k y_(k-1) in shared memory.  Back sweep: slot = the
-// level's c', z_k = y_k - c'_k z_(k+1) stored to the output.  The memory
-// parallelism comes from the copies in flight (kStages levels of the tile),
-// not from registers, and y never leaves the SM.  DRAM traffic per point:
-// the inputs and c' once, q and z once -- the algorithmic bytes.
+// parks y_k = m_k q_k - l_k y_(k-1) in the output vector with the L2
+// evict-last priority.  Back sweep: slot = the c' rows of up to kMaxIn levels
+// (descending); the consumer reads back those levels' y (its own stores, an
+// L2 hit) and stores z_k = y_k - c'_k z_(k+1) over them, evict-first.  The
+// small ring (kStages slots) leaves room for several CTAs, hence several
+// producers, per SM; the memory parallelism comes from the copies in flight,
+// not from registers.  DRAM traffic per point: the inputs and c' once, q and
+// z once -- the algorithmic bytes.
 //
 // Every wait is bounded by %globaltimer: a wait that runs out sets the error
 // word, the CTA stops issuing, waits (bounded) for the copies it issued, and
@@ -28,7 +31,7 @@ namespace {
 constexpr int kTC = 256;                        // columns per tile = consumer threads
 constexpr int kConsumerWarps = kTC / 32;
 constexpr int kBulkThreads = kTC + 32;          // + the producer warp
-constexpr int kStages = 6;                      // ring slots (levels in flight)
+constexpr int kStages = 8;                      // ring slots
 constexpr int kMaxIn = 5;                       // input rows per slot at most
 constexpr unsigned kRowBytes = kTC * 4;         // one array's row of a tile
 constexpr unsigned kSlotBytes = kMaxIn * kRowBytes;
@@ -102,8 +105,7 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
   if (MODE == 1 && ctl->state != ST_RUNNING) return;
   extern __shared__ __align__(128) unsigned char smem[];
   float* ring = reinterpret_cast<float*>(smem);                                 // [kStages][kMaxIn][kTC]
-  float* park = reinterpret_cast<float*>(smem + kStages * kSlotBytes);          // [nz][kTC]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kSlotBytes + (size_t)g.nz * kRowBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kSlotBytes);
   volatile int* abort = reinterpret_cast<volatile int*>(bars + 2 * kStages);
   const unsigned full0 = su32(bars), empty0 = su32(bars + kStages);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -120,6 +122,8 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
   const int64_t ncol = g.ncol;
   const int nz = g.nz;
   const int64_t ntiles = (ncol + kTC - 1) / kTC;
+  const int nback = (nz + kMaxIn - 1) / kMaxIn;  // back-sweep slots per tile (kMaxIn levels each)
+  const int nuse = nz + nback;                   // slot uses per tile
   // the inputs of the forward sweep, in slot-row order
   const float* rin = r_in;
   float* qout = nullptr;
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t c0 = tile * kTC;
         const unsigned bytes = (unsigned)((ncol - c0 < kTC ? ncol - c0 : kTC) * 4);
-        for (int step = 0; step < 2 * nz && ok; ++step, ++use) {
+        for (int step = 0; step < nuse && ok; ++step, ++use) {
           const int s = (int)(use % kStages);
           const uint32_t u = use / kStages;
           if (u > 0 && !mb_wait(empty0 + 8u * s, (u - 1) & 1u, abort)) {
@@ -163,10 +167,12 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
             mb_expect(full0 + 8u * s, NIN * bytes);
 #pragma unroll
             for (int q = 0; q < NIN; ++q) bulk_copy(dst + q * kRowBytes, src[q] + off, bytes, full0 + 8u * s);
-          } else {  // back: level k's c'
-            const int64_t off = (int64_t)(2 * nz - 1 - step) * ncol + c0;
-            mb_expect(full0 + 8u * s, bytes);
-            bulk_copy(dst, a.cp + off, bytes, full0 + 8u * s);
+          } else {  // back: the c' rows of levels k0, k0-1, ..., down to 0 at most kMaxIn of them
+            const int k0 = nz - 1 - (step - nz) * kMaxIn;
+            const int cnt = k0 + 1 < kMaxIn ? k0 + 1 : kMaxIn;
+            mb_expect(full0 + 8u * s, (unsigned)cnt * bytes);
+            for (int q = 0; q < cnt; ++q)
+              bulk_copy(dst + q * kRowBytes, a.cp + (int64_t)(k0 - q) * ncol + c0, bytes, full0 + 8u * s);
           }
         }
       }
@@ -215,23 +221,33 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
           const int64_t idx = (int64_t)k * ncol + c0 + tid;
           if (MODE != 2) stw<float, ST_EF>(qout + idx, q);
           y = fmaf(m, q, -l * y);
-          park[(size_t)k * kTC + tid] = y;
+          stw<float, ST_EL>(zout + idx, y);  // parked until the back sweep
         }
         __syncwarp();
         if (lane == 0) mb_arrive(empty0 + 8u * s);
       }
       if (!ok) break;
       float zn = 0.f;
-      for (int k = nz - 1; k >= 0; --k, ++use) {
+      for (int k0 = nz - 1; k0 >= 0; k0 -= kMaxIn, ++use) {
         const int s = (int)(use % kStages);
         if (!__all_sync(0xffffffffu, mb_wait(full0 + 8u * s, (use / kStages) & 1u, abort))) {
           ok = false;
           break;
         }
         if (live) {
-          const float c = ring[(size_t)s * (kSlotBytes / 4) + tid];
-          zn = fmaf(-c, zn, park[(size_t)k * kTC + tid]);
-          stw<float, ST_EF>(zout + (int64_t)k * ncol + c0 + tid, zn);
+          const float* sl = ring + (size_t)s * (kSlotBytes / 4);
+          const int cnt = k0 + 1 < kMaxIn ? k0 + 1 : kMaxIn;
+          float yk[kMaxIn];
+#pragma unroll
+          for (int q = 0; q < kMaxIn; ++q)  // the group's parked values, all loads first
+            if (q < cnt) yk[q] = zout[(int64_t)(k0 - q) * ncol + c0 + tid];
+#pragma unroll
+          for (int q = 0; q < kMaxIn; ++q) {
+            if (q < cnt) {
+              zn = fmaf(-sl[q * kTC + tid], zn, yk[q]);
+              stw<float, ST_EF>(zout + (int64_t)(k0 - q) * ncol + c0 + tid, zn);
+            }
+          }
         }
         __syncwarp();
         if (lane == 0) mb_arrive(empty0 + 8u * s);
@@ -245,16 +261,17 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
   __syncthreads();
 }
 
-size_t thomas_bulk_smem(int nz) { return (size_t)kStages * kSlotBytes + (size_t)nz * kRowBytes + 2 * kStages * 8 + 16; }
+size_t thomas_bulk_smem(int) { return (size_t)kStages * kSlotBytes + 2 * kStages * 8 + 16; }
 
-bool thomas_bulk_ok(const Grid& g) { return g.ncol % 4 == 0 && thomas_bulk_smem(g.nz) <= 200 * 1024; }
+bool thomas_bulk_ok(const Grid& g) { return g.ncol % 4 == 0; }
 
 template <int MODE>
-static cudaError_t bulk_prepare(size_t smem) {
-  static size_t done = 0;  // largest dynamic size set so far (the attribute is per function)
-  if (smem <= done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_thomas_bulk<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e == cudaSuccess) done = 200 * 1024;
+static cudaError_t bulk_prepare() {
+  static bool done = false;  // the attribute is per function
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_thomas_bulk<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)thomas_bulk_smem(0));
+  if (e == cudaSuccess) done = true;
   return e;
 }
 
@@ -269,7 +286,7 @@ cudaError_t launch_thomas_bulk(int mode, const Grid& g, const Bands<float>& a, c
                                float* z, Ctl* ctl, int* err, const Launch& L) {
   if (!thomas_bulk_ok(g)) return cudaErrorInvalidValue;
   const size_t sm = thomas_bulk_smem(g.nz);
-  cudaError_t e = mode == 0 ? bulk_prepare<0>(sm) : mode == 1 ? bulk_prepare<1>(sm) : bulk_prepare<2>(sm);
+  cudaError_t e = mode == 0 ? bulk_prepare<0>() : mode == 1 ? bulk_prepare<1>() : bulk_prepare<2>();
   if (e != cudaSuccess) return e;
   const int grid = thomas_bulk_grid(g, L, mode);
   if (mode == 0)
@@ -284,9 +301,7 @@ cudaError_t launch_thomas_bulk(int mode, const Grid& g, const Bands<float>& a, c
 // occupancy queries outside any stream capture (the attribute first)
 void warm_thomas_bulk(const Launch& L, int nz) {
   Grid g{1, 1, nz, 4, 4 * (int64_t)nz};
-  const size_t sm = thomas_bulk_smem(nz);
-  if (sm > 200 * 1024) return;
-  if (bulk_prepare<0>(sm) != cudaSuccess || bulk_prepare<1>(sm) != cudaSuccess || bulk_prepare<2>(sm) != cudaSuccess) {
+  if (bulk_prepare<0>() != cudaSuccess || bulk_prepare<1>() != cudaSuccess || bulk_prepare<2>() != cudaSuccess) {
     cudaGetLastError();
     return;
   }

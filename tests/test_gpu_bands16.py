@@ -117,8 +117,9 @@ def test_format_switch_and_paper_solver():
     x1 = torch.empty_like(x0)
     ref_op.solve(dev(b), x0)
     op.set_band_format(hz.HZ_BANDS_BF16)
-    i16 = op.solve(dev(b), x1)
-    assert i16["status"] == 0
+    # 8 significant bits slow the refinement on this hard system: more than the default 10 steps
+    i16 = op.solve(dev(b), x1, max_outer=30)
+    assert i16["status"] == 0, i16
     op.set_band_format(hz.HZ_BANDS_FP32)
     i32 = op.solve(dev(b), x1)
     assert torch.equal(x0, x1) and i32["status"] == 0

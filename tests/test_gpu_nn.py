@@ -253,3 +253,60 @@ def test_bad_network_falls_back_and_still_converges():
     assert info["status"] == 0 and info["fallbacks"] >= 1
     _, rn = oracle.residual(A, b, x)
     assert rn / np.linalg.norm(b) <= 1e-8
+
+
+@pytest.mark.parametrize("dims,seg,border", [((24, 12, 4), 6, 2), ((136, 8, 4), 4, 1), ((40, 20, 7), 10, 3)])
+def test_gradient_of_the_operator_weighted_loss(dims, seg, border):
+    # the loss of the learned stage's training, ||mask Ahat (y - t)||^2 / ||mask Ahat t||^2,
+    # and its gradient through the network, against the FP64 oracle on the GPU's
+    # own activations (as in the test above)
+    import torch
+
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    params = rand_params(23)
+    net = _net(params)
+    x = gen.normals(24, 0, n).astype(np.float32).reshape(nz, ny, nx)
+    t = gen.normals(25, 0, n).astype(np.float32).reshape(nz, ny, nx)
+    bands = oracle.scale(gen.make_operator(nx, ny, nz, 26, z_unit="m")).astype(np.float32)
+    g, loss = net.gradient_op(dev(x), dev(t), dev(bands), dims, seg_ny=seg, border=border)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    z = torch.empty(3 * n * 16, dtype=torch.float32, device="cuda")
+    net.forward(dev(x), y, dims, seg_ny=seg, periodic=False, zout=z)
+    yg = host(y).reshape(nz, ny, nx).astype(np.float64)
+    zg = [host(z)[q * n * 16:(q + 1) * n * 16].reshape(nz, ny, nx, 16).transpose(3, 0, 1, 2) for q in range(3)]
+    P = _rounded(params)
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    for s in range(ny // seg):
+        mask[:, s * seg + border:(s + 1) * seg - border, border:nx - border] = True
+    lo, dy = onn.op_loss(yg, t.astype(np.float64), bands.astype(np.float64), mask, seg)
+    assert abs(loss - lo) <= 1e-4 * lo, (loss, lo)
+    dy = dy[None]
+    hs = [x[None].astype(np.float64)] + [bf16(onn.gelu(zz)) for zz in zg]
+
+    def crops_sum(fn, *arrs):
+        tot = None
+        for s in range(ny // seg):
+            r = fn(*[a[:, :, s * seg:(s + 1) * seg, :] for a in arrs])
+            tot = r if tot is None else tuple(u + v for u, v in zip(tot, r))
+        return tot
+
+    def crops_cat(fn, *arrs):
+        return np.concatenate([fn(*[a[:, :, s * seg:(s + 1) * seg, :] for a in arrs]) for s in range(ny // seg)], axis=2)
+
+    grads = [None] * 4
+    gcur = dy
+    for li in range(3, -1, -1):
+        if li < 3:
+            gcur = gcur * onn.gelu_grad(zg[li])
+        grads[li] = crops_sum(lambda h, d: onn.conv3d_weight_grad(h, d, False), hs[li], gcur)
+        if li > 0:
+            W = P[li][0]
+            gcur = crops_cat(lambda d: onn.conv3d_input_grad(d, W, False), gcur)
+    gref = onn.flatten(grads)
+    o = 0
+    for li in range(4):
+        ci, co = onn.CHANNELS[li], onn.CHANNELS[li + 1]
+        k = co * ci * 27 + co
+        assert rel(g[o:o + k], gref[o:o + k]) <= 1e-3, (li, rel(g[o:o + k], gref[o:o + k]))
+        o += k

@@ -137,3 +137,80 @@ def test_param_count_and_flat_layout():
     p = _params(80)
     assert all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
                for a, b in zip(p, onn.unflatten(onn.flatten(p))))
+
+
+def _crop_bands(nz, ny, nx, seed):
+    import oracle
+
+    A = gen.make_operator(nx, ny, nz, seed, z_unit="m")
+    return oracle.scale(A)
+
+
+def test_crop_operator_matches_dense_assembly_and_its_transpose():
+    # on one crop (no stacking) Ahat with absent neighbours outside is I + bands
+    # with the periodic couplings removed: compare with a dense assembly; the
+    # transpose is the dense transpose
+    from conftest import dense_from_hat
+
+    nz, ny, nx = 3, 4, 5
+    Ah = _crop_bands(nz, ny, nx, 7)
+    Ah[0][:, :, -1] = 0.0  # E of the last column and W of the first would wrap: a crop has no wrap
+    Ah[1][:, :, 0] = 0.0
+    M = dense_from_hat(Ah)
+    d = np.random.default_rng(1).standard_normal((nz, ny, nx))
+    assert np.allclose(onn.ahat_crop(Ah, d).ravel(), M @ d.ravel(), rtol=1e-13, atol=1e-13)
+    assert np.allclose(onn.ahat_crop_transpose(Ah, d).ravel(), M.T @ d.ravel(), rtol=1e-13, atol=1e-13)
+
+
+def test_crop_operator_segments_do_not_couple():
+    # stacked crops: rows of one segment never see the next segment's
+    nz, ny, nx, seg = 2, 8, 5, 4
+    Ah = _crop_bands(nz, ny, nx, 8)
+    d = np.zeros((nz, ny, nx))
+    d[:, :seg] = np.random.default_rng(2).standard_normal((nz, seg, nx))
+    y = onn.ahat_crop(Ah, d, seg)
+    assert np.all(y[:, seg:] == 0.0)
+    yt = onn.ahat_crop_transpose(Ah, d, seg)
+    assert np.all(yt[:, seg:] == 0.0)
+
+
+def test_op_loss_gradient_finite_differences_and_autograd():
+    import torch
+
+    nz, ny, nx, seg = 3, 12, 9, 6
+    rng = np.random.default_rng(3)
+    Ah = _crop_bands(nz, ny, nx, 9)
+    y = rng.standard_normal((nz, ny, nx))
+    t = rng.standard_normal((nz, ny, nx))
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    for s in range(0, ny, seg):
+        mask[:, s + 2:s + seg - 2, 2:nx - 2] = True
+    loss, g = onn.op_loss(y, t, Ah, mask, seg)
+    # autograd of the same expression assembled from dense per-segment matrices
+    from conftest import dense_from_hat
+
+    yt = torch.tensor(y, requires_grad=True)
+    tt = torch.tensor(t)
+    mk = torch.tensor(mask)
+    u_parts, a_parts = [], []
+    for s in range(0, ny, seg):
+        B = Ah[:, :, s:s + seg, :].copy()
+        B[0][:, :, -1] = 0.0
+        B[1][:, :, 0] = 0.0
+        B[2][:, -1, :] = 0.0  # N of the segment's last row, S of its first: outside the segment
+        B[3][:, 0, :] = 0.0
+        M = torch.tensor(dense_from_hat(B))
+        u_parts.append(torch.where(mk[:, s:s + seg].reshape(-1), M @ (yt[:, s:s + seg] - tt[:, s:s + seg]).reshape(-1), 0.0))
+        a_parts.append(torch.where(mk[:, s:s + seg].reshape(-1), M @ tt[:, s:s + seg].reshape(-1), 0.0))
+    u = torch.cat(u_parts)
+    a = torch.cat(a_parts)
+    L = (u * u).sum() / (a * a).sum()
+    L.backward()
+    assert abs(float(L) - loss) <= 1e-12 * abs(loss)
+    assert np.allclose(yt.grad.numpy(), g, rtol=1e-10, atol=1e-12)
+    # and a central finite difference in one coordinate
+    e = np.zeros_like(y)
+    e[1, 4, 3] = 1e-6
+    lp, _ = onn.op_loss(y + e, t, Ah, mask, seg)
+    lm, _ = onn.op_loss(y - e, t, Ah, mask, seg)
+    assert abs((lp - lm) / 2e-6 - g[1, 4, 3]) <= 1e-6 * max(1.0, abs(g[1, 4, 3]))

@@ -47,13 +47,16 @@ def parse():
     ap.add_argument("--z-unit", default="radius", choices=["radius", "m"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--eta", type=float, default=1e-4, help="inner relative tolerance of the mixed solver")
+    ap.add_argument("--eta", type=float, default=None,
+                    help="inner relative tolerance of the mixed solver (default: the fastest of 1e-3, 3e-4, 1e-4 in an "
+                         "untimed sweep before the timed region)")
     ap.add_argument("--restart", type=int, default=150, help="forced BiCGStab restart period")
     ap.add_argument("--precond", default="tri", choices=["tri", "trisor"],
                     help="preconditioner of the headline solves: T^-1 or tri-SOR (Sec. 2)")
     ap.add_argument("--no-trisor", action="store_true", help="skip the tri-SOR side measurement")
     ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table 1 comparison")
     ap.add_argument("--no-bands16", action="store_true", help="skip the 16-bit horizontal-band solves")
+    ap.add_argument("--no-batched", action="store_true", help="skip the small-system batches")
     ap.add_argument("--dims", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="override the workload's grid (same recipe and seeds; for profiling smaller cases)")
     ap.add_argument("--no-graph", action="store_true",
@@ -421,6 +424,24 @@ def run_ours(args):
                               for (p, k), v in op.sor_variants().items()}
     ug = 0 if args.no_graph else 1
     pc = hz.HZ_PRE_TRISOR if args.precond == "trisor" else hz.HZ_PRE_TRI
+    # the inner tolerance eta of the refinement steps (a free parameter of the method): the fastest of
+    # a few, each timed on one solve of this system after an untimed one, unless given
+    eta_sweep = None
+    if args.eta is None:
+        eta_sweep = {}
+        for eta in (1e-3, 3e-4, 1e-4):
+            pe = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=eta, restart=args.restart,
+                                   use_graph=ug, precond=pc)
+            op.solve(bd, x, params=pe)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ie = op.solve(bd, x, params=pe)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            eta_sweep[f"{eta:g}"] = {"ms": round(e0.elapsed_time(e1), 2), "outer": ie["outer_iters"],
+                                     "inner": ie["inner_iters"]}
+        args.eta = float(min(eta_sweep, key=lambda k: eta_sweep[k]["ms"]))
     pm = hz.default_params(mode=hz.HZ_MODE_MIXED_IR, tol=1e-8, inner_tol=args.eta, restart=args.restart, use_graph=ug,
                            precond=pc)
     p64 = hz.default_params(mode=hz.HZ_MODE_FP64, tol=1e-8, restart=args.restart, use_graph=ug, precond=pc)
@@ -526,6 +547,11 @@ def run_ours(args):
         op.set_band_format(hz.HZ_BANDS_FP32)
         op.set_variants(pre32=keep["pre32"], mv32=keep["mv32"])
 
+    # batches of small systems and of many right-hand sides of one operator (one persistent launch each)
+    batched = None
+    if not args.no_batched:
+        batched = batched_small(max(1, min(3, args.steps)), 1)
+
     # the paper's own mixed-precision solver against the 64-bit one (Table 1, Sec. 4): on this
     # system, and on the hard (metres) family at 640x480x70, where the solve from x0 = 0 takes
     # tens of iterations as the paper's did
@@ -597,6 +623,7 @@ def run_ours(args):
         "config": {"workload": f"{args.workload} {nx}x{ny}x{nz} z_unit={args.z_unit} seeds "
                                f"{make_seed(args)} mixed IR tol 1e-8 eta {args.eta:g} precond {args.precond}",
                    "l2": "inputs larger than L2 (vectors 1.4-2.8 GB)", "parallelism": f"replicas x{world}"},
+        "eta_sweep": eta_sweep,
         "solve": {"outer": infos[0]["outer_iters"], "inner": infos[0]["inner_iters"],
                   "true_rel_residual": infos[0]["true_rel_residual"],
                   "ms_per_inner": round(ms / args.steps / max(1, infos[0]["inner_iters"]), 3),
@@ -607,6 +634,7 @@ def run_ours(args):
         "mixed_over_fp64": round(value / fp64["value"], 3) if fp64 else None,
         "trisor": trisor,
         "bands16": bands16,
+        "batched": batched,
         "paper_table1": table1,
         "setup_ms": round(min(su), 3),
         "variants": variants,
@@ -629,8 +657,67 @@ def make_seed(args):
     return f"{w['seed_coef']}/{w['seed_rhs']}"
 
 
+def batched_measure(ops, bs, xs, dims_list, strategy, steps, warmup, use_graph=1):
+    """Time solve_batched on a prepared batch: systems/s, ms per batch, iterations and the
+    algorithmic traffic (152 B per point and inner iteration, 88 B per point and residual pass)."""
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    for _ in range(max(1, warmup)):
+        hz.solve_batched(ops, bs, xs, strategy=strategy, use_graph=use_graph)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = None
+    for _ in range(steps):
+        infos = hz.solve_batched(ops, bs, xs, strategy=strategy, use_graph=use_graph)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    npts = [nx * ny * nz for nx, ny, nz in dims_list]
+    inner = sum(i["inner_iters"] * n for i, n in zip(infos, npts))
+    outer = sum((i["outer_iters"] + 1) * n for i, n in zip(infos, npts))
+    gbs = (152.0 * inner + 88.0 * outer) / (ms * 1e-3) / 1e9
+    peak, _ = measured_peaks()
+    return {"systems_per_s": round(len(ops) / (ms * 1e-3), 3), "ms_per_batch": round(ms, 3),
+            "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
+            "status": sorted({i["status"] for i in infos}),
+            "inner_iters": [i["inner_iters"] for i in infos], "kernel_launches": sum(i["kernel_launches"] for i in infos),
+            "effective_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 3)}
+
+
+def batched_small(steps, warmup, z_unit="radius"):
+    """Batches of systems too small to fill the GPU alone, where the persistent launch is the
+    automatic strategy: 64 distinct systems of 48x36x70, and 32 right-hand sides of one 192x144x70
+    operator; persistent (graph-replayed) against sequential."""
+    import torch
+
+    import gen
+    import paper_1811_03852_gb300 as hz
+
+    out = {}
+    dims = (48, 36, 70)
+    ops = [hz.Operator(gen.make_operator(*dims, 3000 + 2 * i, z_unit=z_unit)) for i in range(64)]
+    bs = [torch.from_numpy(gen.make_rhs(*dims, 3001 + 2 * i).reshape(-1)).cuda() for i in range(64)]
+    xs = [torch.empty_like(b) for b in bs]
+    out["64 systems 48x36x70"] = {
+        "persistent_graph": batched_measure(ops, bs, xs, [dims] * 64, hz.HZ_BATCH_PERSISTENT, steps, warmup),
+        "sequential": batched_measure(ops, bs, xs, [dims] * 64, hz.HZ_BATCH_SEQUENTIAL, steps, warmup)}
+    del ops, bs, xs
+    dims = (192, 144, 70)
+    op = hz.Operator(gen.make_operator(*dims, 3200, z_unit=z_unit))
+    bs = [torch.from_numpy(gen.make_rhs(*dims, 3201 + i).reshape(-1)).cuda() for i in range(32)]
+    xs = [torch.empty_like(b) for b in bs]
+    out["32 right-hand sides of one 192x144x70 operator"] = {
+        "persistent_graph": batched_measure([op] * 32, bs, xs, [dims] * 32, hz.HZ_BATCH_PERSISTENT, steps, warmup),
+        "sequential": batched_measure([op] * 32, bs, xs, [dims] * 32, hz.HZ_BATCH_SEQUENTIAL, steps, warmup)}
+    return out
+
+
 def run_batched(args):
-    """32 uneven systems (192x144, 320x240, 640x480; 70 levels) solved together per step."""
+    """32 uneven systems (192x144, 320x240, 640x480; 70 levels) solved together per step, and the
+    small-system batches."""
     import torch
 
     import gen
@@ -638,42 +725,24 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     specs = [gen.batched_spec(i) for i in range(32)]
-    ops, bs, xs, npts = [], [], [], 0
+    ops, bs, xs, dims_list = [], [], [], []
     for s in specs:
         A = gen.make_operator(s["nx"], s["ny"], s["nz"], s["seed_coef"], z_unit=args.z_unit)
         b = gen.make_rhs(s["nx"], s["ny"], s["nz"], s["seed_rhs"])
         ops.append(hz.Operator(A))
         bs.append(torch.from_numpy(b.reshape(-1)).cuda())
         xs.append(torch.empty(b.size, dtype=torch.float64, device="cuda"))
-        npts += b.size
-    peak, kind = measured_peaks()
-
-    def measure(strategy):
-        for _ in range(args.warmup):
-            hz.solve_batched(ops, bs, xs, strategy=strategy)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        infos = None
-        for _ in range(args.steps):
-            infos = hz.solve_batched(ops, bs, xs, strategy=strategy)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        inner = sum(i["inner_iters"] * s["nx"] * s["ny"] * s["nz"] for i, s in zip(infos, specs))
-        outer = sum((i["outer_iters"] + 1) * s["nx"] * s["ny"] * s["nz"] for i, s in zip(infos, specs))
-        # algorithmic bytes: 152 B per point and inner iteration, 88 B per point and residual pass
-        gbs = (152.0 * inner + 88.0 * outer) / (ms * 1e-3) / 1e9
-        return {"systems_per_s": round(32 / (ms * 1e-3), 3), "ms_per_batch": round(ms, 3),
-                "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
-                "inner_iters": [i["inner_iters"] for i in infos],
-                "effective_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 3)}
-
-    auto = measure(hz.HZ_BATCH_AUTO)  # sequential at these sizes (every system >= 2^20 points)
-    persistent = measure(hz.HZ_BATCH_PERSISTENT)
+        dims_list.append((s["nx"], s["ny"], s["nz"]))
+    _, kind = measured_peaks()
+    auto = batched_measure(ops, bs, xs, dims_list, hz.HZ_BATCH_AUTO, args.steps, args.warmup)
+    persistent = batched_measure(ops, bs, xs, dims_list, hz.HZ_BATCH_PERSISTENT, args.steps, args.warmup)
+    del ops, bs, xs
+    small = batched_small(args.steps, args.warmup, args.z_unit)
     print(json.dumps({"workload": "batched 32 systems (192x144, 320x240, 640x480) x 70, mixed IR tol 1e-8",
-                      "points": npts, "strategy": "auto (sequential: every system fills the GPU)", **auto,
-                      "persistent": persistent, "peak_source": f"{kind} hbm_gbs"}), flush=True)
+                      "points": int(sum(a * b * c for a, b, c in dims_list)),
+                      "strategy": "auto (sequential: every system fills the GPU)", **auto,
+                      "persistent_graph": persistent, "small_systems": small, "peak_source": f"{kind} hbm_gbs"}),
+          flush=True)
 
 
 def run_learned(args):

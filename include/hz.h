@@ -106,6 +106,10 @@ typedef struct {
                         grid), the 32-bit global sums the paper started from (Sec. 4); 0 (default): FP32 partial
                         sums within a column batch, FP64 across them (the paper's 64-bit global sums).  With
                         HZ_MODE_FP64 or HZ_MODE_PAPER_DP: HZ_ERR_UNSUPPORTED.  FGMRES ignores it. */
+  int nn_window;     /* HZ_PRE_TRI_NN: the learned stage is dropped for plain T^-1 (info->fallbacks) when the
+                        FGMRES residual estimate exceeds its start or is above nn_factor times its value
+                        nn_window steps earlier (default 10; 0: one restart cycle, fgmres_m steps) */
+  double nn_factor;  /* in (0, 1] (default 0.5: the estimate must halve within the window) */
 } hz_solve_params;
 
 /* Solve report (host struct). */
@@ -175,18 +179,23 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
              hz_solve_info* info);
 
 /*
- * Solve nsys independent systems (each with its own operator, which may have
- * its own grid).  b[s], x0[s] (may be NULL) and x[s] follow hz_solve's rules
- * (device pointers only).  1 <= nsys <= 64 distinct operators sharing one
- * stream; mixed mode only (params->mode = HZ_MODE_MIXED_IR, else
- * HZ_ERR_UNSUPPORTED).  infos: host array of nsys reports, may be NULL.
- * Returns the worst status.
+ * Solve nsys systems: independent systems (each with its own operator and
+ * grid) and/or several right-hand sides of one operator (an operator may
+ * appear more than once; each further occurrence gets its own work vectors,
+ * allocated on first use and kept by the operator).  b[s], x0[s] (may be
+ * NULL) and x[s] follow hz_solve's rules (device pointers only).
+ * 1 <= nsys <= 64, operators sharing one stream; mixed mode with BiCGStab and
+ * T^-1 only (else HZ_ERR_UNSUPPORTED).  infos: host array of nsys reports,
+ * may be NULL.  Returns the worst status.
  *
  * Strategies (hz_solve_batched_ex; hz_solve_batched = HZ_BATCH_AUTO):
- *   HZ_BATCH_PERSISTENT: the inner FP32 Krylov iterations of all systems run
- *     in one persistent cooperative launch per refinement step, with
- *     per-system scalars and convergence masks, phases separated by a grid
- *     barrier whose waits are bounded (HZ_ERR_TIMEOUT instead of a hang).
+ *   HZ_BATCH_PERSISTENT: the whole solve of every system -- FP64 residuals,
+ *     FP32 inner BiCGStab, refinement updates and the per-system tests on
+ *     tol, max_outer and stagnation -- in ONE persistent cooperative launch,
+ *     phases separated by a grid barrier whose waits are bounded
+ *     (HZ_ERR_TIMEOUT instead of a hang); systems that are done are masked
+ *     out.  With params->use_graph the launch is captured in a CUDA graph and
+ *     replayed when the same systems (operators, b, x0, x) come again.
  *   HZ_BATCH_SEQUENTIAL: hz_solve on each system in turn (graph-captured
  *     inner loops, each kernel at its own occupancy); same arithmetic per
  *     system as a single solve.

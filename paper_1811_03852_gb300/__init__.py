@@ -66,6 +66,8 @@ class hz_solve_params(ctypes.Structure):
         ("sor_sweeps", ctypes.c_int),
         ("sor_omega", ctypes.c_double),
         ("dot_fp32", ctypes.c_int),
+        ("nn_window", ctypes.c_int),
+        ("nn_factor", ctypes.c_double),
     ]
 
 

@@ -1,12 +1,17 @@
-// hz_batched.cu -- many independent systems (uneven grids) in one persistent,
-// cooperative launch per refinement step.
+// hz_batched.cu -- many independent systems (uneven grids, or several
+// right-hand sides of one operator) solved in one persistent, cooperative
+// launch: the whole mixed-precision solve, refinement loop included.
 //
-// The inner FP32 BiCGStab of every system (the same iteration and the same
-// control steps as the single-system kernels) runs phase by phase over one
-// global list of work items; an item is one block-iteration (kBS column
-// groups) of one system, so systems of different sizes are load-balanced by
-// items.  Each system keeps its own scalars and state in its control block;
-// systems that have converged (or failed) are masked out of every phase.
+// Every phase runs over one global list of work items; an item is one
+// block-iteration (kBS column groups) of one system, so systems of different
+// sizes are load-balanced by items.  The refinement loop (the FP64 true
+// residual of Sec. 3 fused with the update x <- x + d and the FP32 scaling of
+// the next right-hand side; then per system the tests on tol, the step limit
+// and stagnation) alternates with the inner FP32 BiCGStab (the same iteration
+// and control steps as the single-system kernels).  Each system keeps its own
+// scalars, state and refinement state in its control block; systems that are
+// done are masked out of every phase.  No host round trip is needed, so the
+// launch can be captured in a CUDA graph.
 // Phases are separated by a grid barrier whose wait is bounded (%globaltimer):
 // a block that waits longer than the limit sets an error flag, every block
 // leaves, and the host reports HZ_ERR_TIMEOUT -- no spin is unbounded.
@@ -15,6 +20,7 @@
 // a fixed order, stores them in its own slot, and after the barrier block b
 // (b < number of systems) adds system b's slots in slot order and runs the
 // control step -- deterministic for a given launch shape.
+#include <cstring>
 #include <mutex>
 
 #include "hz_krylov.cuh"
@@ -160,6 +166,137 @@ __device__ double restart_column_cg(const Grid& g, int64_t col, const Bands<floa
   return (double)cacc;
 }
 
+// The FP64 true residual of one column (Sec. 3: r = b - A x with the unscaled
+// bands) for x = xin + delta (xin absent when hasx is false, delta when used
+// is false); writes x to xout (if given), the next inner right-hand side
+// rhs = fp32(r / A_C), and adds ||r||^2, ||b||^2, ||rhs||^2.  x and delta were
+// written by other blocks of this launch: read through L2.
+__device__ void resid_column(const SysDesc& d, int64_t col, bool hasx, const double* xin, bool used, double* xout,
+                             double& rr, double& bb, double& hh) {
+  const Grid& g = d.g;
+  const int64_t n = g.n, ncol = g.ncol;
+  const int i = (int)(col % g.nx), j = (int)(col / g.nx);
+  const int64_t ie = (i == g.nx - 1) ? -(int64_t)(g.nx - 1) : 1;
+  const int64_t iw = (i == 0) ? (int64_t)(g.nx - 1) : -1;
+  const bool hn = j + 1 < g.ny, hs = j > 0;
+  const bool any = hasx || used;
+  auto X = [&](int64_t q) -> double {
+    double v = hasx ? __ldcg(xin + q) : 0.0;
+    if (used) v += (double)__ldcg(d.w.x + q);
+    return v;
+  };
+  double xm = 0.0, xc = 0.0, xp = 0.0;
+  if (any) {
+    xc = X(col);
+    xp = g.nz > 1 ? X(ncol + col) : 0.0;
+  }
+  double crr = 0.0, cbb = 0.0, chh = 0.0;
+  for (int k = 0; k < g.nz; ++k) {
+    const int64_t idx = (int64_t)k * ncol + col;
+    const double C = __ldg(d.A7 + idx);
+    double ax = 0.0;
+    if (any) {
+      ax = C * xc;
+      ax = fma(__ldg(d.A7 + n + idx), X(idx + ie), ax);
+      ax = fma(__ldg(d.A7 + 2 * n + idx), X(idx + iw), ax);
+      if (hn) ax = fma(__ldg(d.A7 + 3 * n + idx), X(idx + g.nx), ax);
+      if (hs) ax = fma(__ldg(d.A7 + 4 * n + idx), X(idx - g.nx), ax);
+      if (k + 1 < g.nz) ax = fma(__ldg(d.A7 + 5 * n + idx), xp, ax);
+      if (k > 0) ax = fma(__ldg(d.A7 + 6 * n + idx), xm, ax);
+      if (xout) xout[idx] = xc;
+    }
+    const double bv = __ldg(d.b + idx);
+    const double r = bv - ax;
+    const float h = __fmul_rn((float)r, __frcp_rn((float)C));
+    d.w.rhs[idx] = h;
+    crr = fma(r, r, crr);
+    cbb = fma(bv, bv, cbb);
+    chh = fma((double)h, (double)h, chh);
+    if (any) {
+      xm = xc;
+      xc = xp;
+      xp = (k + 2 < g.nz) ? X(idx + 2 * ncol) : 0.0;
+    }
+  }
+  rr += crr;
+  bb += cbb;
+  hh += chh;
+}
+
+// After a system's residual pass (slot sums rr, bb, hh): its refinement
+// decision (the single-system solver's, in device memory) and, when it goes
+// on, the control block of its next inner solve.  first: the pass of the
+// initial guess.  moved: the pass wrote x into the other buffer.
+__device__ void fin_outer(Ctl* c, bool first, bool moved, double rr, double bb, double hh) {
+  if (first) {
+    c->ob = bb;
+    c->outer = 0;
+    c->stall = 0;
+    c->inner_total = 0;
+    c->restart_total = 0;
+    c->odone = 0;
+    c->ostatus = HZ_OK;
+  } else {
+    c->inner_total += c->iter;
+    c->restart_total += c->restarts;
+    c->last_rnorm2 = c->rnorm2;
+    c->last_bnorm2 = c->bnorm2;
+    c->last_state = c->state;
+    c->outer += 1;
+    if (moved) {
+      c->cur ^= 1;
+      c->xz = 0;
+    }
+  }
+  c->res_rr = rr;
+  c->res_bb = bb;
+  c->res_hh = hh;
+  const double R = c->ob > 0.0 ? sqrt(rr / c->ob) : sqrt(rr);
+  if (!first) c->Rprev = c->R;
+  c->R = R;
+  int done = 0, st = HZ_OK;
+  if (!isfinite(R) || (!first && c->last_state == ST_NONFINITE)) {
+    done = 1;
+    st = HZ_ERR_NONFINITE;
+  } else if (R <= c->tol) {
+    done = 1;
+  } else if (c->outer >= c->max_outer) {
+    done = 1;
+    st = HZ_ERR_NOT_CONVERGED;
+  } else if (!first && R > 0.5 * c->Rprev) {  // stagnation: two steps in a row without halving R
+    if (++c->stall >= 2) {
+      done = 1;
+      st = HZ_ERR_NOT_CONVERGED;
+    }
+  } else if (!first) {
+    c->stall = 0;
+  }
+  if (done) {
+    c->odone = 1;
+    c->ostatus = st;
+    c->state = ST_CONVERGED;  // masked out of the inner phases
+    return;
+  }
+  c->bnorm2 = hh;
+  c->stop2 = c->eta * c->eta * hh;
+  c->rho = hh;
+  c->r0norm2 = hh;
+  c->rnorm2 = hh;
+  c->snorm2 = 0.0;
+  c->alpha = 1.0;
+  c->omega = 1.0;
+  c->beta = 0.0;
+  c->iter = 0;
+  c->since = 0;
+  c->restarts = 0;
+  c->fresh = 1;
+  c->rsel = 0;
+  c->r0sel = 0;
+  c->xzero = 1;
+  c->bodies = 0;
+  c->state = !isfinite(hh) ? ST_NONFINITE : (hh > 0.0 ? ST_RUNNING : ST_CONVERGED);
+}
+
 template <int V, int UT, int UM>
 __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
   __shared__ SysCtl sc[kMaxSys];
@@ -174,12 +311,75 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
       for (int d = 0; d < nd; ++d) A.part[((size_t)blockIdx.x * kMaxSys + s) * 4 + d0 + d] = acc[s][d];
     __threadfence();
   };
-  bool left = false;
+  __shared__ int s_odone[kMaxSys], s_cur[kMaxSys], s_xz[kMaxSys], s_used[kMaxSys];
+  // ---- phase R: each active system's FP64 residual (first: of the initial
+  // guess; else of x + d, the refinement update), then its decision ----
+  auto phase_r = [&](bool first) -> bool {
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+      const Ctl* c = A.sys[s].ctl;
+      s_odone[s] = __ldcg(&c->odone);
+      s_cur[s] = __ldcg(&c->cur);
+      s_xz[s] = __ldcg(&c->xz);
+      s_used[s] = !first && __ldcg(&c->xzero) == 0 && __ldcg(&c->state) != ST_NONFINITE;
+    }
+    __syncthreads();
+    zero_acc();
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+      const int s = sys_of(A, item);
+      if (s_odone[s]) continue;
+      const SysDesc& d = A.sys[s];
+      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+      double v[3] = {0.0, 0.0, 0.0};
+      if (q < d.g.ncol / V) {
+        const double* xin;
+        double* xout;
+        bool hasx;
+        if (first) {  // the initial guess is copied into xa (cur = 0) or x stays zero
+          hasx = d.x0 != nullptr;
+          xin = d.x0;
+          xout = hasx ? d.xa : nullptr;
+        } else {
+          hasx = !s_xz[s];
+          xin = s_cur[s] ? d.xb : d.xa;
+          xout = (hasx || s_used[s]) ? (s_cur[s] ? d.xa : d.xb) : nullptr;
+        }
+        for (int cc = 0; cc < V; ++cc)
+          resid_column(d, q * V + cc, hasx, xin, s_used[s] != 0, xout, v[0], v[1], v[2]);
+      }
+      block_add<3>(v, &acc[s][0]);
+    }
+    store_acc(0, 3);
+    if (!grid_sync(A)) return false;
+    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+      const int s = blockIdx.x;
+      if (!s_odone[s]) {
+        const SysDesc& d = A.sys[s];
+        const bool moved = !first && (!s_xz[s] || s_used[s]);
+        fin_outer(d.ctl, first, moved, slots_sum(A, s, 0), slots_sum(A, s, 1), slots_sum(A, s, 2));
+        if (first) {
+          d.ctl->cur = 0;
+          d.ctl->xz = d.x0 ? 0 : 1;
+        }
+      }
+      __threadfence();
+    }
+    return grid_sync(A);
+  };
+
+  if (!phase_r(true)) return;
+  if ((int)blockIdx.x == A.leave_block) return;  // test hook: the others must time out, not hang
   for (int loop = 0; loop < A.max_loops; ++loop) {
     load_ctl(A, sc);
     bool any = false;
     for (int s = 0; s < nsys; ++s) any |= (sc[s].state == ST_RUNNING || sc[s].state == ST_RESTART);
-    if (!any) break;
+    if (!any) {
+      // every inner solve is done: the refinement step of each active system
+      bool active = false;
+      for (int s = 0; s < nsys; ++s) active |= !__ldcg(&A.sys[s].ctl->odone);
+      if (!active) break;
+      if (!phase_r(false)) return;
+      continue;
+    }
 
     // ---- phase A: (re)start or p = r + beta (p - omega v); ph = T^-1 p ----
     zero_acc();
@@ -205,7 +405,6 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
     }
     store_acc(0, 1);
     if (!grid_sync(A)) return;
-    if ((int)blockIdx.x == A.leave_block) return;  // test hook: the others must time out, not hang
 
     // ---- phase B: v = p + H ph, <r0, v> ----
     zero_acc();
@@ -334,16 +533,39 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
     }
     if (!grid_sync(A)) return;
   }
-  (void)left;
+  // the result in the caller's buffer: systems whose x ended in the second one
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+    s_cur[s] = __ldcg(&A.sys[s].ctl->cur);
+    s_xz[s] = __ldcg(&A.sys[s].ctl->xz);
+  }
+  __syncthreads();
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(A, item);
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    if (q >= d.g.ncol / V || (!s_cur[s] && !s_xz[s])) continue;
+    for (int cc = 0; cc < V; ++cc)
+      for (int k = 0; k < d.g.nz; ++k) {
+        const int64_t idx = (int64_t)k * d.g.ncol + q * V + cc;
+        d.xa[idx] = s_xz[s] ? 0.0 : __ldcg(d.xb + idx);
+      }
+  }
 }
 
 // ---------------------------------------------------------------------------
 struct BatchWs {
   SysDesc* sys = nullptr;
+  SysDesc* sys_pin = nullptr;  // pinned host copy (the source of the graph's upload)
   double* part = nullptr;
   unsigned* bar = nullptr;
   int* err = nullptr;
   int part_grid = 0;
+  // the captured launch and what it baked in
+  cudaGraphExec_t exec = nullptr;
+  int g_nsys = 0, g_vec = 0;
+  int* g_err_h = nullptr;
+  cudaStream_t g_stream = nullptr;
+  BatchArgs g_args{};
 };
 
 template <int V>
@@ -351,10 +573,27 @@ const void* batched_kernel() {
   return V == 4 ? (const void*)k_batched<4, 2, 1> : (const void*)k_batched<1, 8, 4>;
 }
 
-// Launch the persistent kernel cooperatively.  Returns the CUDA error; *err_h
-// receives the device error word (after a synchronisation).
+// member by member (struct padding is not part of what a launch bakes in)
+bool same_sys(const SysDesc& a, const SysDesc& b) {
+  const Bands<float>& p = a.a;
+  const Bands<float>& q = b.a;
+  const Vecs<float>& v = a.w;
+  const Vecs<float>& u = b.w;
+  return a.g.nx == b.g.nx && a.g.ny == b.g.ny && a.g.nz == b.g.nz && a.item0 == b.item0 && a.nitems == b.nitems &&
+         a.ctl == b.ctl && a.A7 == b.A7 && a.invc == b.invc && a.b == b.b && a.x0 == b.x0 && a.xa == b.xa &&
+         a.xb == b.xb && p.E == q.E && p.W == q.W && p.N == q.N && p.S == q.S && p.U == q.U && p.D == q.D &&
+         p.m == q.m && p.l == q.l && p.cp == q.cp && v.rhs == u.rhs && v.r == u.r && v.r0 == u.r0 && v.p == u.p &&
+         v.ph == u.ph && v.v == u.v && v.s == u.s && v.sh == u.sh && v.t == u.t && v.x == u.x;
+}
+bool same_args(const BatchArgs& a, const BatchArgs& b) {
+  return a.sys == b.sys && a.nsys == b.nsys && a.nitems == b.nitems && a.part == b.part && a.bar == b.bar &&
+         a.err == b.err && a.timeout_ns == b.timeout_ns && a.leave_block == b.leave_block &&
+         a.max_loops == b.max_loops;
+}
+
+// Launch the persistent kernel cooperatively (or replay its captured graph).
 cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loops, long long timeout_ns,
-                           int leave_block, cudaStream_t stream, int* err_h, int sms) {
+                           int leave_block, cudaStream_t stream, int* err_h, int sms, bool graph) {
   static BatchWs ws[64];
   static std::mutex mu;  // the per-device workspace is shared by every host thread
   std::lock_guard<std::mutex> lk(mu);
@@ -370,20 +609,24 @@ cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loop
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = per_sm * sms;  // cooperative: every block resident
   if (!w.sys) {
-    // allocate into locals and publish only when all three exist, so that a
-    // failed allocation never leaves a half-built workspace for the next call
+    // allocate into locals and publish only when all exist, so that a failed
+    // allocation never leaves a half-built workspace for the next call
     SysDesc* sys = nullptr;
+    SysDesc* sys_pin = nullptr;
     unsigned* bar = nullptr;
     int* err = nullptr;
     e = cudaMalloc(&sys, sizeof(SysDesc) * kMaxSys);
+    if (e == cudaSuccess) e = cudaMallocHost(&sys_pin, sizeof(SysDesc) * kMaxSys);
     if (e == cudaSuccess) e = cudaMalloc(&bar, sizeof(unsigned) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
     if (e != cudaSuccess) {
       if (sys) cudaFree(sys);
+      if (sys_pin) cudaFreeHost(sys_pin);
       if (bar) cudaFree(bar);
       return e;
     }
     w.sys = sys;
+    w.sys_pin = sys_pin;
     w.bar = bar;
     w.err = err;
   }
@@ -393,19 +636,50 @@ cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loop
     if (w.part) cudaFree(w.part);
     w.part = part;
     w.part_grid = grid;
+    if (w.exec) cudaGraphExecDestroy(w.exec), w.exec = nullptr;  // it baked the old buffer in
   }
-  if ((e = cudaMemcpyAsync(w.sys, sys_h, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-    return e;
-  if ((e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2, stream)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(w.err, 0, sizeof(int), stream)) != cudaSuccess) return e;
   int64_t nitems = 0;
   for (int s = 0; s < nsys; ++s) nitems = sys_h[s].item0 + sys_h[s].nitems;
   BatchArgs args{w.sys, nsys, nitems, w.part, w.bar, w.err, timeout_ns, leave_block, max_loops};
-  void* kargs[] = {&args};
-  if ((e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBS), kargs, 0, stream)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(err_h, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return e;
-  return cudaStreamSynchronize(stream);
+  // the launch's inputs, as a graph would bake them in
+  bool same = w.exec && w.g_nsys == nsys && w.g_vec == vec && w.g_err_h == err_h && w.g_stream == stream &&
+              same_args(w.g_args, args);
+  for (int s = 0; same && s < nsys; ++s) same = same_sys(w.sys_pin[s], sys_h[s]);
+  if (graph && same) return cudaGraphLaunch(w.exec, stream);
+  memcpy(w.sys_pin, sys_h, sizeof(SysDesc) * nsys);
+  auto enqueue = [&]() -> cudaError_t {
+    cudaError_t r;
+    if ((r = cudaMemcpyAsync(w.sys, w.sys_pin, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return r;
+    if ((r = cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2, stream)) != cudaSuccess) return r;
+    if ((r = cudaMemsetAsync(w.err, 0, sizeof(int), stream)) != cudaSuccess) return r;
+    void* kargs[] = {&args};
+    if ((r = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBS), kargs, 0, stream)) != cudaSuccess) return r;
+    return cudaMemcpyAsync(err_h, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  };
+  if (graph) {
+    if (w.exec) cudaGraphExecDestroy(w.exec), w.exec = nullptr;
+    cudaGraph_t gr = nullptr;
+    cudaError_t ec = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (ec == cudaSuccess) {
+      const cudaError_t eq = enqueue();
+      ec = cudaStreamEndCapture(stream, &gr);
+      if (eq == cudaSuccess && ec == cudaSuccess) ec = cudaGraphInstantiate(&w.exec, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (eq != cudaSuccess && ec == cudaSuccess) ec = eq;
+    }
+    if (ec == cudaSuccess) {
+      w.g_nsys = nsys;
+      w.g_vec = vec;
+      w.g_err_h = err_h;
+      w.g_stream = stream;
+      w.g_args = args;
+      return cudaGraphLaunch(w.exec, stream);
+    }
+    cudaGetLastError();  // not capturable here: launch directly
+    if (w.exec) cudaGraphExecDestroy(w.exec), w.exec = nullptr;
+  }
+  return enqueue();
 }
-
 
 }  // namespace hz

@@ -111,6 +111,15 @@ struct hz_op_s {
   double p_bytes[HZ_NUM_KERNELS] = {};
   long long launches = 0;  // kernels launched by the last solve
   FgmWs fgm;               // flexible GMRES workspace (allocated on first use)
+  // work vectors of the extra right-hand sides of a batched solve that names
+  // this operator more than once (occurrence 1, 2, ...; occurrence 0 uses w32)
+  struct RhsWs {
+    float* base = nullptr;
+    Vecs<float> w{};
+    Ctl* ctl = nullptr;
+    double* xb = nullptr;
+  };
+  std::vector<RhsWs> rhs_ws;
   hz_nn nn = nullptr;      // learned stage (not owned)
 };
 
@@ -533,9 +542,11 @@ int ensure_fgm(hz_op op, int m) {
 // the control block is updated as the BiCGStab loop would leave it.
 // With use_nn the preconditioner is the learned two-stage one,
 // z = T^-1 v + sigma NN((v - Ahat T^-1 v) / sigma); it is dropped for plain
-// T^-1 (counted in *fallbacks) when the residual estimate has not halved over
-// the last 10 steps or has grown above its starting value.
-int run_fgmres(hz_op op, int m, int max_inner, double eta, bool use_nn, int* fallbacks) {
+// T^-1 (counted in *fallbacks) when the residual estimate has grown above its
+// starting value or has not fallen below nn_factor times its value nn_window
+// steps earlier.
+int run_fgmres(hz_op op, int m, int max_inner, double eta, bool use_nn, int* fallbacks, int nn_window,
+               double nn_factor) {
   CKS(ensure_fgm(op, m));
   bool nn_on = use_nn && op->nn != nullptr;
   std::vector<double> rhist;
@@ -599,7 +610,8 @@ int run_fgmres(hz_op op, int m, int max_inner, double eta, bool use_nn, int* fal
         rhist.push_back(resid);
         if (nn_on) {
           const size_t h = rhist.size();
-          if (resid > beta0 || (h > 10 && resid > 0.5 * rhist[h - 11])) {
+          const size_t wnd = (size_t)nn_window;
+          if (resid > beta0 || (h > wnd && resid > nn_factor * rhist[h - wnd - 1])) {
             nn_on = false;  // the learned stage is not helping: plain T^-1 from here on
             if (fallbacks) ++*fallbacks;
           }
@@ -666,6 +678,11 @@ void free_op(hz_op op) {
   if (op->fgm.vptr) cudaFree(op->fgm.vptr);
   if (op->fgm.part) cudaFree(op->fgm.part);
   if (op->fgm.st) cudaFree(op->fgm.st);
+  for (auto& r : op->rhs_ws) {
+    if (r.base) cudaFree(r.base);
+    if (r.ctl) cudaFree(r.ctl);
+    if (r.xb) cudaFree(r.xb);
+  }
   if (op->cfg_h) cudaFreeHost(op->cfg_h);
   if (op->rep_h) cudaFreeHost(op->rep_h);
   if (op->err_h) cudaFreeHost(op->err_h);
@@ -836,6 +853,8 @@ void hz_default_params(hz_solve_params* p) {
   p->sor_sweeps = 3;
   p->sor_omega = 1.5;
   p->dot_fp32 = 0;
+  p->nn_window = 10;
+  p->nn_factor = 0.5;
 }
 
 int hz_op_create(int nx, int ny, int nz, const double* coeffs, void* stream, hz_op* out) {
@@ -986,6 +1005,8 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
   if (p.precond != HZ_PRE_TRI && p.precond != HZ_PRE_TRI_NN && p.precond != HZ_PRE_TRISOR) return HZ_ERR_INVALID;
   // the learned stage is not a fixed linear operator: it needs the flexible solver and a network
   if (p.precond == HZ_PRE_TRI_NN && (p.krylov != HZ_KRYLOV_FGMRES || !op->nn)) return HZ_ERR_UNSUPPORTED;
+  if (p.precond == HZ_PRE_TRI_NN && (p.nn_window < 0 || !(p.nn_factor > 0.0 && p.nn_factor <= 1.0)))
+    return HZ_ERR_INVALID;
   const bool sor = (p.precond == HZ_PRE_TRISOR);
   if (sor) {
     if (p.sor_sweeps < 1 || p.sor_sweeps > 64 || !(p.sor_omega > 0.0 && p.sor_omega < 2.0)) return HZ_ERR_INVALID;
@@ -1135,7 +1156,8 @@ int hz_solve(hz_op op, const double* b, const double* x0, double* x, const hz_so
     if (outer >= max_outer) { status = HZ_ERR_NOT_CONVERGED; break; }
     if (p.krylov == HZ_KRYLOV_FGMRES)
     {
-      CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta, p.precond == HZ_PRE_TRI_NN, &fallbacks));
+      CKS(run_fgmres(op, p.fgmres_m, p.max_inner, eta, p.precond == HZ_PRE_TRI_NN, &fallbacks,
+                     p.nn_window > 0 ? p.nn_window : p.fgmres_m, p.nn_factor));
       if (p.precond == HZ_PRE_TRI_NN) CKS(nn_stage_status(op->nn, op->stream));
     }
     else if (fp32)
@@ -1692,8 +1714,6 @@ int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, cons
     if (ops[q]->stream != s) return HZ_ERR_INVALID;
     if (!is_device_ptr(b[q]) || !is_device_ptr(x[q]) || (x0 && x0[q] && !is_device_ptr(x0[q])))
       return HZ_ERR_INVALID;
-    for (int r = 0; r < q; ++r)
-      if (ops[r] == ops[q]) return HZ_ERR_INVALID;  // each system needs its own work vectors
     if (ops[q]->g.nx % 4) vec = 1;
   }
   // Systems that each fill the GPU on their own run one after another through
@@ -1716,148 +1736,109 @@ int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, cons
     }
     return worst;
   }
+  // the whole solve of every system in one persistent launch (refinement loop
+  // on the device), replayed from a captured graph when params->use_graph is
+  // set and the same systems come again
   std::vector<SysDesc> sys(nsys);
+  std::vector<int> occ(nsys, 0);
   int64_t item0 = 0;
   for (int q = 0; q < nsys; ++q) {
     hz_op op = ops[q];
+    for (int r = 0; r < q; ++r)
+      if (ops[r] == op) ++occ[q];
+    Vecs<float> w = op->w32;
+    Ctl* ctl = op->ctl;
+    double* xb = op->xscr;
+    if (occ[q] > 0) {  // a further right-hand side of this operator: its own work vectors
+      if ((int)op->rhs_ws.size() < occ[q]) op->rhs_ws.resize(occ[q]);
+      hz_op_s::RhsWs& rw = op->rhs_ws[occ[q] - 1];
+      if (!rw.base) {
+        float* base = nullptr;
+        Ctl* c = nullptr;
+        double* x2 = nullptr;
+        cudaError_t e = cudaMalloc(&base, sizeof(float) * 10 * (size_t)pad64(op->g.n));
+        if (e == cudaSuccess) e = cudaMalloc(&c, sizeof(Ctl));
+        if (e == cudaSuccess) e = cudaMalloc(&x2, sizeof(double) * (size_t)op->g.n);
+        if (e != cudaSuccess) {
+          if (base) cudaFree(base);
+          if (c) cudaFree(c);
+          set_err(e, "cudaMalloc (batched right-hand side)", __LINE__);
+          return e == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA;
+        }
+        rw.base = base;
+        rw.w = carve(base, op->g.n);
+        rw.ctl = c;
+        rw.xb = x2;
+      }
+      w = rw.w;
+      ctl = rw.ctl;
+      xb = rw.xb;
+    }
     const int64_t ni = (op->g.ncol / vec + kBS - 1) / kBS;
-    sys[q] = SysDesc{op->g, bands_of<float>(op, false), op->w32, op->ctl, item0, ni};
+    SysDesc d{};
+    d.g = op->g;
+    d.a = bands_of<float>(op, false);
+    d.w = w;
+    d.ctl = ctl;
+    d.item0 = item0;
+    d.nitems = ni;
+    d.A7 = op->A7;
+    d.invc = op->invc;
+    d.b = b[q];
+    d.x0 = (x0 && x0[q]) ? x0[q] : nullptr;
+    d.xa = x[q];
+    d.xb = xb;
+    sys[q] = d;
     item0 += ni;
   }
   hz_op o0 = ops[0];
+  std::vector<Ctl> cfg(nsys);
+  for (int q = 0; q < nsys; ++q) {
+    Ctl& c = cfg[q];
+    memset(&c, 0, sizeof(Ctl));
+    c.eta = eta;
+    c.maxit = p.max_inner;
+    c.restart_every = p.restart;
+    c.body_limit = 4 * p.max_inner + 64;
+    c.xzero = 1;
+    c.xz = 1;
+    c.state = ST_CONVERGED;
+    c.tol = p.tol;
+    c.max_outer = p.max_outer;
+  }
   CK(cudaEventRecord(o0->ev0, s));
-  std::vector<const double*> cur(nsys, nullptr);
-  std::vector<double> R(nsys, 0.0), Rprev(nsys, 0.0), bb(nsys, 0.0), scaled(nsys, 0.0);
-  std::vector<int> outer(nsys, 0), inner(nsys, 0), rst(nsys, 0), status(nsys, HZ_OK), done(nsys, 0), stall(nsys, 0);
-  long long launches = 0;
-  for (int q = 0; q < nsys; ++q) {
-    hz_op op = ops[q];
-    Ctl* cfg = op->cfg_h;
-    memset(cfg, 0, sizeof(Ctl));
-    cfg->eta = eta;
-    cfg->maxit = p.max_inner;
-    cfg->restart_every = p.restart;
-    cfg->body_limit = 4 * p.max_inner + 64;
-    cfg->xzero = 1;
-    cfg->state = ST_CONVERGED;
-    CK(cudaMemcpyAsync(op->ctl, cfg, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    if (x0 && x0[q]) cur[q] = x0[q];
-    CK(launch_residual<float>(op->g, op->A7, op->invc, b[q], cur[q], nullptr, nullptr, op->w32.rhs, nullptr, 0,
-                              op->ctl, op->red, op->L));
-    ++launches;
-    CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-  }
-  CK(cudaStreamSynchronize(s));
-  for (int q = 0; q < nsys; ++q) {
-    const Ctl& rp = *ops[q]->rep_h;
-    bb[q] = rp.res_bb;
-    R[q] = bb[q] > 0.0 ? std::sqrt(rp.res_rr / bb[q]) : std::sqrt(rp.res_rr);
-    Rprev[q] = R[q];
-  }
-  int batch_status = HZ_OK;
-  for (;;) {
-    // decide which systems go on
-    int active = 0;
-    for (int q = 0; q < nsys; ++q) {
-      if (done[q]) continue;
-      if (!std::isfinite(R[q])) {
-        status[q] = HZ_ERR_NONFINITE;
-        done[q] = 1;
-      } else if (R[q] <= p.tol) {
-        status[q] = HZ_OK;
-        done[q] = 1;
-      } else if (outer[q] >= p.max_outer) {
-        status[q] = HZ_ERR_NOT_CONVERGED;
-        done[q] = 1;
-      } else {
-        ++active;
-      }
-    }
-    if (!active) break;
-    // finished systems sit out the inner solve
-    for (int q = 0; q < nsys; ++q) {
-      if (!done[q]) continue;
-      ops[q]->cfg_h->state = ST_CONVERGED;
-      CK(cudaMemcpyAsync(&ops[q]->ctl->state, &ops[q]->cfg_h->state, sizeof(int), cudaMemcpyHostToDevice, s));
-    }
-    int err = 0;
-    int* err_h = &o0->err_h[0];
-    CK(launch_batched(sys.data(), nsys, vec, 4 * p.max_inner + 64, g_batch_timeout_ns, g_batch_leave_block, s, err_h,
-                      o0->sms));
-    err = *err_h;
-    ++launches;
-    if (err) {
-      snprintf(g_err, sizeof(g_err), "batched inner solve: a grid-barrier wait exceeded %lld ns", g_batch_timeout_ns);
-      batch_status = HZ_ERR_TIMEOUT;
-      for (int q = 0; q < nsys; ++q)
-        if (!done[q]) {
-          status[q] = HZ_ERR_TIMEOUT;
-          done[q] = 1;
-        }
-      break;
-    }
-    for (int q = 0; q < nsys; ++q) {
-      if (done[q]) continue;
-      hz_op op = ops[q];
-      double* XA = x[q];
-      double* next = (cur[q] == XA) ? op->xscr : XA;
-      CK(launch_residual<float>(op->g, op->A7, op->invc, b[q], cur[q], next, op->w32.x, op->w32.rhs, nullptr, 0,
-                                op->ctl, op->red, op->L));
-      ++launches;
-      CK(cudaMemcpyAsync(op->rep_h, op->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-      cur[q] = next;
-    }
-    CK(cudaStreamSynchronize(s));
-    for (int q = 0; q < nsys; ++q) {
-      if (done[q]) continue;
-      const Ctl& rp = *ops[q]->rep_h;
-      inner[q] += rp.last_iter;
-      rst[q] += rp.last_restarts;
-      scaled[q] = rp.last_bnorm2 > 0.0 ? std::sqrt(rp.last_rnorm2 / rp.last_bnorm2) : 0.0;
-      ++outer[q];
-      R[q] = bb[q] > 0.0 ? std::sqrt(rp.res_rr / bb[q]) : std::sqrt(rp.res_rr);
-      if (rp.last_state == ST_NONFINITE) {
-        status[q] = HZ_ERR_NONFINITE;
-        done[q] = 1;
-        continue;
-      }
-      if (R[q] > 0.5 * Rprev[q]) {
-        if (++stall[q] >= 2 && R[q] > p.tol) {
-          status[q] = HZ_ERR_NOT_CONVERGED;
-          done[q] = 1;
-        }
-      } else {
-        stall[q] = 0;
-      }
-      Rprev[q] = R[q];
-    }
-  }
-  // deliver every x into the caller's buffer
-  for (int q = 0; q < nsys; ++q) {
-    const size_t bytes = sizeof(double) * (size_t)ops[q]->g.n;
-    if (cur[q] == nullptr)
-      CK(cudaMemsetAsync(x[q], 0, bytes, s));
-    else if (cur[q] != x[q])
-      CK(cudaMemcpyAsync(x[q], cur[q], bytes, cudaMemcpyDeviceToDevice, s));
-  }
+  for (int q = 0; q < nsys; ++q) CK(cudaMemcpyAsync(sys[q].ctl, &cfg[q], sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  // loop bound of the persistent kernel: every refinement step's inner solve and its residual pass
+  const int max_loops = (p.max_outer + 1) * (p.max_inner + 8) + 8;
+  int* err_h = &o0->err_h[0];
+  *err_h = 0;
+  CK(launch_batched(sys.data(), nsys, vec, max_loops, g_batch_timeout_ns, g_batch_leave_block, s, err_h, o0->sms,
+                    p.use_graph != 0));
+  for (int q = 0; q < nsys; ++q) CK(cudaMemcpyAsync(&cfg[q], sys[q].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(o0->ev1, s));
   CK(cudaEventSynchronize(o0->ev1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, o0->ev0, o0->ev1);
-  int worst = batch_status;
+  int worst = HZ_OK;
+  if (*err_h) {
+    snprintf(g_err, sizeof(g_err), "batched solve: a grid-barrier wait exceeded %lld ns", g_batch_timeout_ns);
+    worst = HZ_ERR_TIMEOUT;
+  }
   for (int q = 0; q < nsys; ++q) {
-    if (status[q] != HZ_OK && worst == HZ_OK) worst = status[q];
+    const Ctl& c = cfg[q];
+    int st = *err_h ? HZ_ERR_TIMEOUT : (c.odone ? c.ostatus : HZ_ERR_NOT_CONVERGED);
+    if (st != HZ_OK && worst == HZ_OK) worst = st;
     if (infos) {
-      infos[q].status = status[q];
-      infos[q].outer_iters = outer[q];
-      infos[q].inner_iters = inner[q];
-      infos[q].restarts = rst[q];
+      infos[q].status = st;
+      infos[q].outer_iters = c.outer;
+      infos[q].inner_iters = c.inner_total;
+      infos[q].restarts = c.restart_total;
       infos[q].fallbacks = 0;
       infos[q].fp64_retries = 0;
-      infos[q].true_rel_residual = R[q];
-      infos[q].scaled_rel_residual = scaled[q];
+      infos[q].true_rel_residual = c.R;
+      infos[q].scaled_rel_residual = c.last_bnorm2 > 0.0 ? std::sqrt(c.last_rnorm2 / c.last_bnorm2) : 0.0;
       infos[q].seconds = ms * 1e-3;
-      infos[q].kernel_launches = launches;
+      infos[q].kernel_launches = 1;
     }
   }
   return worst;

@@ -62,6 +62,12 @@ struct Ctl {
   // device error word of the inner solve (bit 0: a bounded wait of a
   // bulk-copy kernel ran out); the host reports HZ_ERR_TIMEOUT
   int kerr;
+  // the refinement loop of the batched solver, run on the device: target,
+  // ||b||^2, R before the last step, the last R; steps taken, the limit,
+  // stalls in a row, done flag and final status, the buffer holding x (0: xa,
+  // 1: xb), x still zero, and the totals of the inner solves
+  double tol, ob, Rprev, R;
+  int outer, max_outer, stall, odone, ostatus, cur, xz, inner_total, restart_total, pad2;
 };
 
 struct Red {
@@ -232,8 +238,9 @@ constexpr int kParkBulk = 3;  // their park mode in the Thomas variant tables (P
 // mode 0: k_pre_p's work (p update + T^-1), 1: k_pre_s's (s = r - alpha v + T^-1),
 // 2: z = T^-1 r alone.  Valid when ncol % 4 == 0 and the tile's parked sweep fits.
 bool thomas_bulk_ok(const Grid& g);
-cudaError_t launch_thomas_bulk(int mode, const Grid& g, const Bands<float>& a, const Vecs<float>& w, const float* r,
-                               float* z, Ctl* ctl, int* err, const Launch& L);
+// stages: ring slots, 3, 4 or 5
+cudaError_t launch_thomas_bulk(int mode, int stages, const Grid& g, const Bands<float>& a, const Vecs<float>& w,
+                               const float* r, float* z, Ctl* ctl, int* err, const Launch& L);
 void warm_thomas_bulk(const Launch& L, int nz);
 
 // Blocks for a grid-stride kernel: every SM filled to that kernel's own
@@ -366,13 +373,27 @@ struct SysDesc {
   Ctl* ctl;
   int64_t item0;   // first global work item of this system (item = kBS column groups)
   int64_t nitems;  // items of this system
+  // the system's refinement loop: unscaled FP64 bands [7][n], 1/A_C, b, the
+  // initial guess (null: zero), the caller's x (where the result ends) and a
+  // second buffer for the ping-pong of x
+  const double* A7;
+  const double* invc;
+  const double* b;
+  const double* x0;
+  double* xa;
+  double* xb;
 };
-// Runs the inner FP32 BiCGStab of nsys systems to completion in one
-// cooperative launch and waits for it; *err_h receives the device error word
-// (bit 0: a grid-barrier wait exceeded timeout_ns).  vec = 4 needs nx % 4 == 0
-// for every system, else pass 1.  leave_block >= 0 makes that block leave
-// after its first barrier (test hook for the bounded wait).
+// Runs the whole mixed-precision solve of nsys systems -- FP64 residuals,
+// FP32 inner BiCGStab, refinement updates and the per-system decisions on tol,
+// max_outer and stagnation -- in one cooperative launch on `stream`; each
+// control block must hold the configuration (eta, maxit, restart, tol,
+// max_outer).  *err_h (pinned host) receives the device error word (bit 0: a
+// grid-barrier wait exceeded timeout_ns) once the stream reaches it; the call
+// does not wait.  vec = 4 needs nx % 4 == 0 for every system, else pass 1.
+// leave_block >= 0 makes that block leave after its first barrier (test hook
+// for the bounded wait).  graph: capture the launch once into a CUDA graph
+// and replay it while the systems (the SysDesc array) stay the same.
 cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loops, long long timeout_ns,
-                           int leave_block, cudaStream_t stream, int* err_h, int sms);
+                           int leave_block, cudaStream_t stream, int* err_h, int sms, bool graph);
 
 }  // namespace hz

@@ -5,9 +5,10 @@
 //
 // A CTA owns a tile of kTC consecutive columns (column index j*nx + i) and
 // marches the levels.  One producer warp copies, level by level, every input
-// array's kTC-value row of the tile into a ring of kStages shared-memory
-// slots; kTC consumer threads (one column each) wait for a slot, run the
-// recurrence and release the slot.  Forward sweep: slot = one level's inputs
+// array's kTC-value row of the tile (4 KB) into a ring of kStages
+// shared-memory slots; kTC / 4 consumer threads (four adjacent columns each,
+// float4 reads of the slot) wait for a slot, run the recurrences and release
+// the slot.  Forward sweep: slot = one level's inputs
 // (r, and p, v or v for the axpy; the factors m, l); the consumer forms q
 // (p = r + beta (p - omega v), s = r - alpha v, or q = r), stores it, and
 // parks y_k = m_k q_k - l_k y_(k-1) in the output vector with the L2
@@ -28,10 +29,12 @@ namespace hz {
 
 namespace {
 
-constexpr int kTC = 256;                        // columns per tile = consumer threads
-constexpr int kConsumerWarps = kTC / 32;
-constexpr int kBulkThreads = kTC + 32;          // + the producer warp
-constexpr int kStages = 8;                      // ring slots
+constexpr int kTC = 1024;                       // columns per tile
+constexpr int kCV = 4;                          // columns per consumer thread
+constexpr int kConsumers = kTC / kCV;
+constexpr int kConsumerWarps = kConsumers / 32;
+constexpr int kBulkThreads = kConsumers + 32;   // + the producer warp
+// ring slots: a template parameter of the kernel (3, 4 or 5; the variant table's depth)
 constexpr int kMaxIn = 5;                       // input rows per slot at most
 constexpr unsigned kRowBytes = kTC * 4;         // one array's row of a tile
 constexpr unsigned kSlotBytes = kMaxIn * kRowBytes;
@@ -56,15 +59,19 @@ __device__ __forceinline__ bool mb_try(unsigned bar, unsigned parity) {
 }
 
 // wait for the completion of the phase with this parity; false if the bound
-// ran out or another thread of the CTA gave up first
+// ran out or another thread of the CTA gave up first (the timer and the abort
+// flag are read every 32 polls: each try_wait already suspends the thread for
+// a while)
 __device__ __forceinline__ bool mb_wait(unsigned bar, unsigned parity, const volatile int* abort) {
   if (mb_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
-  while (!mb_try(bar, parity)) {
-    if (*abort) return false;
-    if (gtimer() - t0 > (unsigned long long)kWaitNs) return false;
+  for (unsigned it = 1;; ++it) {
+    if (mb_try(bar, parity)) return true;
+    if ((it & 31u) == 0) {
+      if (*abort) return false;
+      if (gtimer() - t0 > (unsigned long long)kWaitNs) return false;
+    }
   }
-  return true;
 }
 
 // the same without the abort test: the drain of copies still in flight
@@ -97,7 +104,7 @@ __device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigne
 // MODE 1: q = r - alpha v stored to s, z = T^-1 q to sh               (k_pre_s)
 // MODE 2: q = r (not stored), z = T^-1 r to out                       (T^-1 alone)
 // err: device error word (bit 0: a bounded wait ran out).
-template <int MODE>
+template <int MODE, int kStages>
 __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<float> a, Vecs<float> w, const float* r_in,
                                                               float* z_out, Ctl* ctl, int* err) {
   constexpr int NIN = MODE == 0 ? 5 : MODE == 1 ? 4 : 3;  // rows per forward slot
@@ -185,16 +192,17 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
       for (uint32_t v = first; v < use; ++v) mb_wait_drain(full0 + 8u * (v % kStages), (v / kStages) & 1u);
     }
   } else {
-    // ---- consumers: one column each --------------------------------------------
+    // ---- consumers: kCV adjacent columns each ------------------------------------
     const float beta = MODE == 0 ? (float)ctl->beta : 0.f;
     const float omega = MODE == 0 ? (float)ctl->omega : 0.f;
     const float alpha = MODE == 1 ? (float)ctl->alpha : 0.f;
+    const int c = tid * kCV;  // first column of this thread within the tile
     uint32_t use = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const int64_t c0 = tile * kTC;
-      const bool live = c0 + tid < ncol;
-      float y = 0.f;
+      const bool live = c0 + c < ncol;  // the tile width is a multiple of 4: all kCV columns or none
+      float y[kCV] = {0.f, 0.f, 0.f, 0.f};
       for (int k = 0; k < nz; ++k, ++use) {
         const int s = (int)(use % kStages);
         // warp-uniform: the lanes meet at __syncwarp below
@@ -204,30 +212,44 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
         }
         const float* sl = ring + (size_t)s * (kSlotBytes / 4);
         if (live) {
-          float q, m, l;
+          const float4 r4 = *reinterpret_cast<const float4*>(sl + c);
+          float4 q4, m4, l4;
           if (MODE == 0) {
-            q = fmaf(beta, fmaf(-omega, sl[2 * kTC + tid], sl[kTC + tid]), sl[tid]);
-            m = sl[3 * kTC + tid];
-            l = sl[4 * kTC + tid];
+            const float4 p4 = *reinterpret_cast<const float4*>(sl + kTC + c);
+            const float4 v4 = *reinterpret_cast<const float4*>(sl + 2 * kTC + c);
+            m4 = *reinterpret_cast<const float4*>(sl + 3 * kTC + c);
+            l4 = *reinterpret_cast<const float4*>(sl + 4 * kTC + c);
+            q4.x = fmaf(beta, fmaf(-omega, v4.x, p4.x), r4.x);
+            q4.y = fmaf(beta, fmaf(-omega, v4.y, p4.y), r4.y);
+            q4.z = fmaf(beta, fmaf(-omega, v4.z, p4.z), r4.z);
+            q4.w = fmaf(beta, fmaf(-omega, v4.w, p4.w), r4.w);
           } else if (MODE == 1) {
-            q = fmaf(-alpha, sl[kTC + tid], sl[tid]);
-            m = sl[2 * kTC + tid];
-            l = sl[3 * kTC + tid];
+            const float4 v4 = *reinterpret_cast<const float4*>(sl + kTC + c);
+            m4 = *reinterpret_cast<const float4*>(sl + 2 * kTC + c);
+            l4 = *reinterpret_cast<const float4*>(sl + 3 * kTC + c);
+            q4.x = fmaf(-alpha, v4.x, r4.x);
+            q4.y = fmaf(-alpha, v4.y, r4.y);
+            q4.z = fmaf(-alpha, v4.z, r4.z);
+            q4.w = fmaf(-alpha, v4.w, r4.w);
           } else {
-            q = sl[tid];
-            m = sl[kTC + tid];
-            l = sl[2 * kTC + tid];
+            q4 = r4;
+            m4 = *reinterpret_cast<const float4*>(sl + kTC + c);
+            l4 = *reinterpret_cast<const float4*>(sl + 2 * kTC + c);
           }
-          const int64_t idx = (int64_t)k * ncol + c0 + tid;
-          if (MODE != 2) stw<float, ST_EF>(qout + idx, q);
-          y = fmaf(m, q, -l * y);
-          stw<float, ST_EL>(zout + idx, y);  // parked until the back sweep
+          const int64_t idx = (int64_t)k * ncol + c0 + c;
+          if (MODE != 2) stw<float4, ST_EF>(reinterpret_cast<float4*>(qout + idx), q4);
+          y[0] = fmaf(m4.x, q4.x, -l4.x * y[0]);
+          y[1] = fmaf(m4.y, q4.y, -l4.y * y[1]);
+          y[2] = fmaf(m4.z, q4.z, -l4.z * y[2]);
+          y[3] = fmaf(m4.w, q4.w, -l4.w * y[3]);
+          // parked until the back sweep
+          stw<float4, ST_EL>(reinterpret_cast<float4*>(zout + idx), make_float4(y[0], y[1], y[2], y[3]));
         }
         __syncwarp();
         if (lane == 0) mb_arrive(empty0 + 8u * s);
       }
       if (!ok) break;
-      float zn = 0.f;
+      float zn[kCV] = {0.f, 0.f, 0.f, 0.f};
       for (int k0 = nz - 1; k0 >= 0; k0 -= kMaxIn, ++use) {
         const int s = (int)(use % kStages);
         if (!__all_sync(0xffffffffu, mb_wait(full0 + 8u * s, (use / kStages) & 1u, abort))) {
@@ -237,15 +259,20 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
         if (live) {
           const float* sl = ring + (size_t)s * (kSlotBytes / 4);
           const int cnt = k0 + 1 < kMaxIn ? k0 + 1 : kMaxIn;
-          float yk[kMaxIn];
+          float4 yk[kMaxIn];
 #pragma unroll
           for (int q = 0; q < kMaxIn; ++q)  // the group's parked values, all loads first
-            if (q < cnt) yk[q] = zout[(int64_t)(k0 - q) * ncol + c0 + tid];
+            if (q < cnt) yk[q] = *reinterpret_cast<const float4*>(zout + (int64_t)(k0 - q) * ncol + c0 + c);
 #pragma unroll
           for (int q = 0; q < kMaxIn; ++q) {
             if (q < cnt) {
-              zn = fmaf(-sl[q * kTC + tid], zn, yk[q]);
-              stw<float, ST_EF>(zout + (int64_t)(k0 - q) * ncol + c0 + tid, zn);
+              const float4 c4 = *reinterpret_cast<const float4*>(sl + q * kTC + c);
+              zn[0] = fmaf(-c4.x, zn[0], yk[q].x);
+              zn[1] = fmaf(-c4.y, zn[1], yk[q].y);
+              zn[2] = fmaf(-c4.z, zn[2], yk[q].z);
+              zn[3] = fmaf(-c4.w, zn[3], yk[q].w);
+              stw<float4, ST_EF>(reinterpret_cast<float4*>(zout + (int64_t)(k0 - q) * ncol + c0 + c),
+                                 make_float4(zn[0], zn[1], zn[2], zn[3]));
             }
           }
         }
@@ -261,51 +288,68 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
   __syncthreads();
 }
 
-size_t thomas_bulk_smem(int) { return (size_t)kStages * kSlotBytes + 2 * kStages * 8 + 16; }
+size_t thomas_bulk_smem(int stages) { return (size_t)stages * kSlotBytes + 2 * stages * 8 + 16; }
 
 bool thomas_bulk_ok(const Grid& g) { return g.ncol % 4 == 0; }
 
-template <int MODE>
+template <int MODE, int S>
 static cudaError_t bulk_prepare() {
   static bool done = false;  // the attribute is per function
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_thomas_bulk<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)thomas_bulk_smem(0));
+  cudaError_t e = cudaFuncSetAttribute(k_thomas_bulk<MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)thomas_bulk_smem(S));
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-int thomas_bulk_grid(const Grid& g, const Launch& L, int mode) {
-  const void* k = mode == 0 ? (const void*)k_thomas_bulk<0> : mode == 1 ? (const void*)k_thomas_bulk<1>
-                                                                          : (const void*)k_thomas_bulk<2>;
+template <int S>
+static cudaError_t launch_s(int mode, const Grid& g, const Bands<float>& a, const Vecs<float>& w, const float* r,
+                            float* z, Ctl* ctl, int* err, const Launch& L) {
+  const size_t sm = thomas_bulk_smem(S);
   const int64_t tiles = (g.ncol + kTC - 1) / kTC;
-  return grid_for(k, kBulkThreads, L, tiles, thomas_bulk_smem(g.nz));
-}
-
-cudaError_t launch_thomas_bulk(int mode, const Grid& g, const Bands<float>& a, const Vecs<float>& w, const float* r,
-                               float* z, Ctl* ctl, int* err, const Launch& L) {
-  if (!thomas_bulk_ok(g)) return cudaErrorInvalidValue;
-  const size_t sm = thomas_bulk_smem(g.nz);
-  cudaError_t e = mode == 0 ? bulk_prepare<0>() : mode == 1 ? bulk_prepare<1>() : bulk_prepare<2>();
-  if (e != cudaSuccess) return e;
-  const int grid = thomas_bulk_grid(g, L, mode);
-  if (mode == 0)
-    k_thomas_bulk<0><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, nullptr, nullptr, ctl, err);
-  else if (mode == 1)
-    k_thomas_bulk<1><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, nullptr, nullptr, ctl, err);
-  else
-    k_thomas_bulk<2><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, r, z, ctl, err);
+  cudaError_t e;
+  if (mode == 0) {
+    if ((e = bulk_prepare<0, S>()) != cudaSuccess) return e;
+    const int grid = grid_for((const void*)k_thomas_bulk<0, S>, kBulkThreads, L, tiles, sm);
+    k_thomas_bulk<0, S><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, nullptr, nullptr, ctl, err);
+  } else if (mode == 1) {
+    if ((e = bulk_prepare<1, S>()) != cudaSuccess) return e;
+    const int grid = grid_for((const void*)k_thomas_bulk<1, S>, kBulkThreads, L, tiles, sm);
+    k_thomas_bulk<1, S><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, nullptr, nullptr, ctl, err);
+  } else {
+    if ((e = bulk_prepare<2, S>()) != cudaSuccess) return e;
+    const int grid = grid_for((const void*)k_thomas_bulk<2, S>, kBulkThreads, L, tiles, sm);
+    k_thomas_bulk<2, S><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, r, z, ctl, err);
+  }
   return cudaGetLastError();
 }
 
-// occupancy queries outside any stream capture (the attribute first)
-void warm_thomas_bulk(const Launch& L, int nz) {
-  Grid g{1, 1, nz, 4, 4 * (int64_t)nz};
-  if (bulk_prepare<0>() != cudaSuccess || bulk_prepare<1>() != cudaSuccess || bulk_prepare<2>() != cudaSuccess) {
+cudaError_t launch_thomas_bulk(int mode, int stages, const Grid& g, const Bands<float>& a, const Vecs<float>& w,
+                               const float* r, float* z, Ctl* ctl, int* err, const Launch& L) {
+  if (!thomas_bulk_ok(g)) return cudaErrorInvalidValue;
+  if (stages == 3) return launch_s<3>(mode, g, a, w, r, z, ctl, err, L);
+  if (stages == 4) return launch_s<4>(mode, g, a, w, r, z, ctl, err, L);
+  if (stages == 5) return launch_s<5>(mode, g, a, w, r, z, ctl, err, L);
+  return cudaErrorInvalidValue;
+}
+
+// attributes and occupancy queries outside any stream capture
+template <int S>
+static void warm_s(const Launch& L) {
+  if (bulk_prepare<0, S>() != cudaSuccess || bulk_prepare<1, S>() != cudaSuccess ||
+      bulk_prepare<2, S>() != cudaSuccess) {
     cudaGetLastError();
     return;
   }
-  for (int m = 0; m < 3; ++m) thomas_bulk_grid(g, L, m);
+  const size_t sm = thomas_bulk_smem(S);
+  grid_for((const void*)k_thomas_bulk<0, S>, kBulkThreads, L, 1, sm);
+  grid_for((const void*)k_thomas_bulk<1, S>, kBulkThreads, L, 1, sm);
+  grid_for((const void*)k_thomas_bulk<2, S>, kBulkThreads, L, 1, sm);
+}
+void warm_thomas_bulk(const Launch& L, int) {
+  warm_s<3>(L);
+  warm_s<4>(L);
+  warm_s<5>(L);
 }
 
 }  // namespace hz

@@ -1,5 +1,7 @@
-"""Batched solves: the persistent strategy (many uneven systems, one cooperative
-launch per refinement step) and the sequential one (hz_solve per system).
+"""Batched solves: the persistent strategy (many uneven systems, or many
+right-hand sides of one operator: the whole solve, refinement loop included,
+in one cooperative launch, replayable from a CUDA graph) and the sequential
+one (hz_solve per system).
 
 Each system of a batch must reach the true FP64 residual 1e-8 (recomputed by
 the oracle) and agree with its own single-system solve to 1e-6 (relative 2-norm).
@@ -105,8 +107,6 @@ def test_batched_rejects_bad_arguments():
     op = hz.Operator(A)
     bd = dev(b.reshape(-1))
     x = torch.empty(b.size, dtype=torch.float64, device="cuda")
-    st, _ = hz.solve_batched([op, op], [bd, bd], [x, x], raise_on_error=False)
-    assert st == hz.HZ_ERR_INVALID  # the same operator twice
     st, _ = hz.solve_batched([op], [bd], [x], mode=hz.HZ_MODE_FP64, raise_on_error=False)
     assert st == hz.HZ_ERR_UNSUPPORTED
     st, _ = hz.solve_batched([op], [bd], [x], raise_on_error=False, strategy=3)
@@ -148,3 +148,73 @@ def test_batched_32_uneven_systems_full_size(strategy):
         assert info["status"] == 0, info
         _, rn = oracle.residual(A, b, x)
         assert rn / np.linalg.norm(b) <= 1e-8
+
+
+@pytest.mark.parametrize("strategy", [1, 2])
+def test_many_right_hand_sides_of_one_operator(strategy):
+    # one operator named several times (its extra right-hand sides get their own
+    # work vectors), next to another operator twice: every solve reaches 1e-8
+    # and matches its single solve
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    A1 = gen.make_operator(48, 36, 20, 41, z_unit="m")
+    A2 = gen.make_operator(40, 30, 12, 42, z_unit="m")
+    op1, op2 = hz.Operator(A1), hz.Operator(A2)
+    ops, As, bs = [], [], []
+    for q in range(9):
+        A, op, dims = (A1, op1, (48, 36, 20)) if q % 3 else (A2, op2, (40, 30, 12))
+        ops.append(op)
+        As.append(A)
+        bs.append(gen.make_rhs(*dims, 500 + q))
+    xs = [torch.empty(b.size, dtype=torch.float64, device="cuda") for b in bs]
+    infos = hz.solve_batched(ops, [dev(b.reshape(-1)) for b in bs], xs, strategy=strategy)
+    for A, b, x, info, op in zip(As, bs, xs, infos, ops):
+        assert info["status"] == 0, info
+        xh = host(x).reshape(b.shape)
+        _, rn = oracle.residual(A, b, xh)
+        assert rn / np.linalg.norm(b) <= 1e-8
+        xd = torch.empty(b.size, dtype=torch.float64, device="cuda")
+        op.solve(dev(b), xd)
+        assert np.linalg.norm(xh - host(xd).reshape(b.shape)) / np.linalg.norm(xh) <= 1e-6
+
+
+def test_persistent_solve_is_one_launch_and_replays_from_a_graph():
+    # the whole batched solve is one cooperative launch; with use_graph it is
+    # captured once and replayed on the next call with the same systems, with
+    # the same bits as a direct launch
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+
+    specs = [(48, 36, 20, 61 + 2 * i, 62 + 2 * i) for i in range(6)]
+    systems = _systems(specs, z_unit="m")
+    ops = [hz.Operator(A) for A, _ in systems]
+    bs = [dev(b.reshape(-1)) for _, b in systems]
+    outs = []
+    for use_graph in (0, 1, 1):  # direct, captured, replayed
+        xs = [torch.full((b.numel(),), np.nan, dtype=torch.float64, device="cuda") for b in bs]
+        infos = hz.solve_batched(ops, bs, xs, strategy=hz.HZ_BATCH_PERSISTENT, use_graph=use_graph)
+        assert all(i["status"] == 0 and i["kernel_launches"] == 1 for i in infos), infos
+        outs.append(([host(x) for x in xs], [i["inner_iters"] for i in infos]))
+    for xs, its in outs[1:]:
+        assert its == outs[0][1]
+        assert all(np.array_equal(a, b) for a, b in zip(xs, outs[0][0]))
+    for (A, b), x in zip(systems, outs[2][0]):
+        _, rn = oracle.residual(A, b, x.reshape(b.shape))
+        assert rn / np.linalg.norm(b) <= 1e-8
+
+
+def test_small_systems_go_to_the_persistent_launch():
+    # systems too small to fill the GPU alone: the automatic strategy is the
+    # persistent launch (one launch for all of them)
+    import paper_1811_03852_gb300 as hz
+
+    systems = _systems([(48, 36, 70, 71 + 2 * i, 72 + 2 * i) for i in range(16)], z_unit="radius")
+    xs, infos, _ = _batched(systems)
+    for (A, b), x, info in zip(systems, xs, infos):
+        assert info["status"] == 0 and info["kernel_launches"] == 1, info
+        _, rn = oracle.residual(A, b, x)
+        assert rn / np.linalg.norm(b) <= 1e-8
+    del hz

@@ -1,9 +1,11 @@
 """Learned preconditioner end to end (GPU): train on a few systems, evaluate on held-out ones.
 
-Shows what the trained stage gains over plain T^-1 inside the same FGMRES
-solver (printed), and checks that every learned solve still reaches the true
-FP64 residual 1e-8 (recomputed by the oracle) and is never much worse than the
-plain one (the stall fallback bounds the loss).
+What the trained stage gains, on held-out systems: it shrinks the residual it
+is given (the part of a residual the tridiagonal stage leaves) -- asserted.
+Inside FGMRES that gain does not turn into fewer iterations (printed; the
+measurements at 640x480x70 are in the design notes): every learned solve
+still reaches the true FP64 residual 1e-8 (recomputed by the oracle) and is
+never much worse than the plain one (the stall fallback bounds the loss).
 """
 import numpy as np
 import pytest
@@ -29,7 +31,7 @@ def test_train_then_solve_held_out(z_unit):
                          iters=(1, 2, 4, 8, 16))
     assert np.isfinite(losses).all()
     if z_unit == "m":  # on the easy family T^-1 leaves almost nothing to learn
-        assert np.mean(losses[-10:]) < np.mean(losses[:10])
+        assert np.median(losses[-20:]) < np.median(losses[:20])
     rows = learn.evaluate(net, test_sys, dims, z_unit=z_unit)
     gains = []
     for (sc, sr), row in zip(test_sys, rows):
@@ -49,3 +51,44 @@ def test_train_then_solve_held_out(z_unit):
     print(f"\n[{z_unit}] loss {losses[0]:.3f} -> {np.mean(losses[-10:]):.3f}; plain/learned FGMRES iterations per "
           f"held-out system: {[round(g, 2) for g in gains]} (>1 = the learned stage saves iterations); "
           f"details: {[(r['plain']['inner_iters'], r['learned']['inner_iters'], r['learned']['fallbacks']) for r in rows]}")
+
+
+def test_trained_stage_shrinks_the_residual_on_held_out_systems():
+    # the stage's own gain: for a held-out system's pair (stage input e1 / sigma),
+    # the residual left after the stage, e1 - Ahat sigma NN(e1 / sigma), against
+    # e1 itself -- the operator-weighted loss the training minimises, measured
+    # on full fields of systems the network never saw
+    import torch
+
+    import paper_1811_03852_gb300 as hz
+    from paper_1811_03852_gb300 import learn
+
+    dims = (64, 48, 20)
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    net = hz.Net(learn.init_params(5))
+    train_sys = [(300 + 2 * i, 301 + 2 * i) for i in range(8)]
+    learn.train(net, train_sys, dims, steps=240, batch=8, crop=24, lr=1e-3, seed=3, z_unit="m",
+                iters=(1, 2, 4, 8, 16))
+    untrained = hz.Net(learn.init_params(5))
+    ratios, ratios0 = [], []
+    for sc, sr in [(400 + 2 * i, 401 + 2 * i) for i in range(3)]:
+        A = gen.make_operator(*dims, sc, z_unit="m")
+        b = torch.from_numpy(gen.make_rhs(*dims, sr).reshape(-1)).cuda()
+        op = hz.Operator(A)
+        xs = torch.empty(n, dtype=torch.float64, device="cuda")
+        op.solve(b, xs, mode=hz.HZ_MODE_FP64, tol=1e-11)
+        xk = torch.empty_like(xs)
+        op.solve(b, xk, max_outer=1, max_inner=4, inner_tol=1e-12, raise_on_error=False)
+        inp = torch.empty(n, dtype=torch.float32, device="cuda")
+        tg = torch.empty_like(inp)
+        op.make_pair(b, xk, xs, inp, tg)
+        for nn_, out in ((net, ratios), (untrained, ratios0)):
+            y = torch.empty_like(inp)
+            nn_.forward(inp, y, dims, periodic=True)
+            ay = torch.empty_like(inp)
+            op.matvec(y, ay, hz.HZ_PREC_FP32)
+            out.append(float(torch.linalg.norm(inp - ay) / torch.linalg.norm(inp)))
+    print(f"\nresidual left after the stage / its input, held-out systems: trained {[round(r, 3) for r in ratios]}, "
+          f"untrained {[round(r, 3) for r in ratios0]}")
+    assert max(ratios) < 0.8 and max(ratios) < min(ratios0)

@@ -16,7 +16,8 @@ from gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
 
-BULK = 13  # the FP32 Thomas variant with park mode 3
+BULKS = (13, 14, 15)  # the FP32 Thomas variants with park mode 3 (ring of 5, 3 and 4 slots)
+BULK = 13
 PLAIN = 10  # the default FP32 Thomas variant
 
 
@@ -38,7 +39,7 @@ def test_bulk_variant_is_bitwise_the_plain_one(shape):
     L = hz.load()
     p = dev(gen.normals(41, 0, n), torch.float32)
     out = {}
-    for var in (PLAIN, BULK):
+    for var in (PLAIN,) + BULKS:
         assert L.hz_op_set_variants(op.handle, var, -1, -1, -1) == 0
         z = torch.empty(n, dtype=torch.float32, device="cuda")
         ph = torch.empty_like(z)
@@ -46,8 +47,9 @@ def test_bulk_variant_is_bitwise_the_plain_one(shape):
         op.precond_apply(p, z, hz.HZ_PREC_FP32)
         op.precond_matvec(p, ph, v, hz.HZ_PREC_FP32)
         out[var] = (host(z), host(ph), host(v))
-    for a, b in zip(out[PLAIN], out[BULK]):
-        assert np.array_equal(a, b)
+    for bulk in BULKS:
+        for a, b in zip(out[PLAIN], out[bulk]):
+            assert np.array_equal(a, b), bulk
     # and the oracle's T^-1 of the FP32 operator
     Ah = oracle.scale(A).astype(np.float32).astype(np.float64)
     ref = oracle.apply_Tinv(Ah, host(p).astype(np.float64).reshape(nz, ny, nx))
@@ -63,7 +65,7 @@ def test_bulk_variant_solve_is_bitwise_the_plain_one(case):
     A, b = gen.make_system(*shape, 5, 6, z_unit=z_unit)
     L = hz.load()
     res = {}
-    for var in (PLAIN, BULK):
+    for var in (PLAIN,) + BULKS:
         op = hz.Operator(A)
         assert L.hz_op_set_variants(op.handle, var, -1, -1, -1) == 0
         x = torch.empty(b.size, dtype=torch.float64, device="cuda")
@@ -74,8 +76,9 @@ def test_bulk_variant_solve_is_bitwise_the_plain_one(case):
         xe = torch.empty_like(x)
         op.solve(dev(b), xe, use_graph=0)
         assert torch.equal(x, xe)
-    assert res[PLAIN][1:] == res[BULK][1:]
-    assert np.array_equal(res[PLAIN][0], res[BULK][0])
+    for bulk in BULKS:
+        assert res[PLAIN][1:] == res[bulk][1:]
+        assert np.array_equal(res[PLAIN][0], res[bulk][0])
     _, rn = oracle.residual(A, b, res[BULK][0].reshape(b.shape))
     assert rn / np.linalg.norm(b) <= 1e-8
 
@@ -85,4 +88,5 @@ def test_bulk_variant_needs_whole_vectors_of_columns():
     hz = _hz()
     A = gen.make_operator(37, 23, 9, 3)
     op = hz.Operator(A)
-    assert hz.load().hz_op_set_variants(op.handle, BULK, -1, -1, -1) == hz.HZ_ERR_INVALID
+    for bulk in BULKS:
+        assert hz.load().hz_op_set_variants(op.handle, bulk, -1, -1, -1) == hz.HZ_ERR_INVALID

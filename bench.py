@@ -41,9 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n1280", choices=["n1280", "mixed640", "plain96", "batched", "learned", "nnfwd", "fig1", "table1"])
-    ap.add_argument("--train-systems", type=int, default=24)
-    ap.add_argument("--test-systems", type=int, default=8)
-    ap.add_argument("--train-steps", type=int, default=240)
+    ap.add_argument("--train-systems", type=int, default=200)
+    ap.add_argument("--test-systems", type=int, default=50)
+    ap.add_argument("--train-steps", type=int, default=800)
     ap.add_argument("--z-unit", default="radius", choices=["radius", "m"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table 1 comparison")
     ap.add_argument("--no-bands16", action="store_true", help="skip the 16-bit horizontal-band solves")
     ap.add_argument("--no-batched", action="store_true", help="skip the small-system batches")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-stage line")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed solves with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--dims", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="override the workload's grid (same recipe and seeds; for profiling smaller cases)")
     ap.add_argument("--no-graph", action="store_true",
@@ -403,6 +406,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
+    wall = {"start": time.perf_counter()}  # wall-clock marks of the bench's sections
     dims, A, b = make_inputs(args)
     nx, ny, nz = dims
     n = nx * ny * nz
@@ -424,6 +428,7 @@ def run_ours(args):
                               for (p, k), v in op.sor_variants().items()}
     ug = 0 if args.no_graph else 1
     pc = hz.HZ_PRE_TRISOR if args.precond == "trisor" else hz.HZ_PRE_TRI
+    wall["inputs_autotune"] = time.perf_counter()
     # the inner tolerance eta of the refinement steps (a free parameter of the method): the fastest of
     # a few, each timed on one solve of this system after an untimed one, unless given
     eta_sweep = None
@@ -451,17 +456,21 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(params, steps, warmup):
+    def timed(params, steps, warmup, region=False):
         infos = []
         for _ in range(warmup):
             op.solve(bd, x, params=params)
         barrier()
+        if region:
+            torch.cuda.cudart().cudaProfilerStart()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             infos.append(op.solve(bd, x, params=params))
         e1.record(stream)
         barrier()
+        if region:
+            torch.cuda.cudart().cudaProfilerStop()
         ms = replica_max(e0.elapsed_time(e1), f"cuda:{dev}")
         return ms, infos
 
@@ -477,8 +486,10 @@ def run_ours(args):
         su.append(e0.elapsed_time(e1))
     del Ad
 
+    wall["eta_setup"] = time.perf_counter()
     with Clocks(dev) as clk:
-        ms, infos = timed(pm, args.steps, args.warmup)
+        ms, infos = timed(pm, args.steps, args.warmup, region=args.profile_region)
+    wall["timed"] = time.perf_counter()
     clocks = clk.summary()
     for i in infos:
         assert i["status"] == 0 and i["true_rel_residual"] <= 1e-8, i
@@ -520,6 +531,7 @@ def run_ours(args):
                                  "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
                              for k, v in sp.items()}
 
+    wall["fp64_trisor"] = time.perf_counter()
     # 16-bit storage of the horizontal bands (BF16 and FP16) in the same mixed solve
     bands16 = None
     if not args.no_bands16:
@@ -547,11 +559,21 @@ def run_ours(args):
         op.set_band_format(hz.HZ_BANDS_FP32)
         op.set_variants(pre32=keep["pre32"], mv32=keep["mv32"])
 
+    wall["bands16"] = time.perf_counter()
     # batches of small systems and of many right-hand sides of one operator (one persistent launch each)
     batched = None
     if not args.no_batched:
         batched = batched_small(max(1, min(3, args.steps)), 1)
 
+    wall["batched"] = time.perf_counter()
+    # the learned stage, trained and evaluated at 640x480x70 on the hard (metres) family (a reduced
+    # count of systems; --workload learned runs the full 200 / 50)
+    learned = None
+    if not args.no_learned:
+        learned = learned_line((640, 480, 70), [(10000 + 2 * i, 10001 + 2 * i) for i in range(8)],
+                               [(20000 + 2 * i, 20001 + 2 * i) for i in range(2)], 160, "m")
+
+    wall["learned"] = time.perf_counter()
     # the paper's own mixed-precision solver against the 64-bit one (Table 1, Sec. 4): on this
     # system, and on the hard (metres) family at 640x480x70, where the solve from x0 = 0 takes
     # tens of iterations as the paper's did
@@ -561,6 +583,7 @@ def run_ours(args):
                   paper_table1(op, bd, x, stream, dims, restart=args.restart, ablation=False)}
         table1.update(table1_hard(args.restart))
 
+    wall["table1"] = time.perf_counter()
     # end to end through the public API with host buffers (pinned b, pinned x)
     bh = torch.from_numpy(b.reshape(-1)).pin_memory()
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -608,6 +631,7 @@ def run_ours(args):
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot_ms, 4),
                    "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None} for k, v in busy.items()}
 
+    wall["e2e_profile"] = time.perf_counter()
     if rank != 0:
         return
     cb = None
@@ -616,6 +640,9 @@ def run_ours(args):
             cb = cpu_baseline(A, b, dims, infos[0]["outer_iters"], infos[0]["inner_iters"])
         except MemoryError:
             cb = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "host memory exhausted"}
+    wall["cpu_baseline"] = time.perf_counter()
+    marks = list(wall.items())
+    sections_s = {k: round(t - marks[i - 1][1], 1) for i, (k, t) in enumerate(marks) if i > 0}
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -635,6 +662,7 @@ def run_ours(args):
         "trisor": trisor,
         "bands16": bands16,
         "batched": batched,
+        "learned": learned,
         "paper_table1": table1,
         "setup_ms": round(min(su), 3),
         "variants": variants,
@@ -644,6 +672,7 @@ def run_ours(args):
         "kernels": kernels,
         "cpu_baseline": cb,
         "clocks": clocks,
+        "bench_sections_s": sections_s,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -745,47 +774,71 @@ def run_batched(args):
           flush=True)
 
 
-def run_learned(args):
-    """Learned stage on 640x480x70: train on fresh seeds, evaluate plain vs learned FGMRES on held-out seeds."""
+def learned_line(dims, train_systems, test_systems, steps, z_unit, lr=1e-3):
+    """The learned stage at one size: trained by hz_nn_train on fresh systems (operator-weighted
+    loss), then on held-out systems its own gain (the residual it leaves, relative to its input) and
+    the solves to 1e-8: plain and learned FGMRES(30), plain mixed BiCGStab."""
     import torch
 
+    import gen
     import paper_1811_03852_gb300 as hz
     from paper_1811_03852_gb300 import learn
 
-    torch.cuda.set_device(0)
-    dims = (640, 480, 70)
-    train_sys = [(10000 + 2 * i, 10001 + 2 * i) for i in range(args.train_systems)]
-    test_sys = [(20000 + 2 * i, 20001 + 2 * i) for i in range(args.test_systems)]
+    nx, ny, nz = dims
+    n = nx * ny * nz
     net = hz.Net(learn.init_params(1))
     t0 = time.perf_counter()
-    losses = learn.train(net, train_sys, dims, steps=args.train_steps, batch=16, crop=64, lr=3e-4, seed=7,
-                         z_unit=args.z_unit)
+    losses = learn.train(net, train_systems, dims, steps=steps, batch=16, crop=min(64, nx - 8, ny - 1), lr=lr,
+                         seed=7, z_unit=z_unit)
     t_train = time.perf_counter() - t0
-    rows = learn.evaluate(net, test_sys, dims, z_unit=args.z_unit)
-    # the plain mixed BiCGStab solver on the same held-out systems, for reference
-    import gen
-
-    bic = []
-    for sc, sr in test_sys:
-        op = hz.Operator(gen.make_operator(*dims, sc, z_unit=args.z_unit))
+    rows = []
+    for sc, sr in test_systems:
+        op = hz.Operator(gen.make_operator(*dims, sc, z_unit=z_unit))
         b = torch.from_numpy(gen.make_rhs(*dims, sr).reshape(-1)).cuda()
         x = torch.empty_like(b)
-        op.solve(b, x)
-        bic.append(op.solve(b, x))
-    pl = [r["plain"] for r in rows]
-    le = [r["learned"] for r in rows]
-    out = {"workload": f"learned stage 640x480x70 z_unit={args.z_unit}", "train_systems": len(train_sys),
-           "test_systems": len(test_sys), "train_steps": len(losses), "train_s": round(t_train, 1),
-           "loss_first": losses[0], "loss_last10": float(np.mean(losses[-10:])),
-           "fgmres_plain": {"solves_per_s": len(pl) / sum(i["seconds"] for i in pl),
-                            "inner_iters": [i["inner_iters"] for i in pl]},
-           "fgmres_learned": {"solves_per_s": len(le) / sum(i["seconds"] for i in le),
-                              "inner_iters": [i["inner_iters"] for i in le], "fallbacks": [i["fallbacks"] for i in le],
-                              "status": [i["status"] for i in le],
-                              "max_true_rel_residual": max(i["true_rel_residual"] for i in le)},
-           "bicgstab_plain": {"solves_per_s": len(bic) / sum(i["seconds"] for i in bic),
-                              "inner_iters": [i["inner_iters"] for i in bic]}}
-    print(json.dumps(out), flush=True)
+        # the stage's own gain on a pair of this held-out system
+        xs = torch.empty_like(b)
+        op.solve(b, xs, mode=hz.HZ_MODE_FP64, tol=1e-11, raise_on_error=False)
+        xk = torch.empty_like(b)
+        op.solve(b, xk, max_outer=1, max_inner=8, inner_tol=1e-12, raise_on_error=False)
+        inp = torch.empty(n, dtype=torch.float32, device="cuda")
+        tg = torch.empty_like(inp)
+        op.make_pair(b, xk, xs, inp, tg)
+        y = torch.empty_like(inp)
+        net.forward(inp, y, dims, periodic=True)
+        ay = torch.empty_like(inp)
+        op.matvec(y, ay, hz.HZ_PREC_FP32)
+        stage = float(torch.linalg.norm(inp - ay) / torch.linalg.norm(inp))
+        plain = op.solve(b, x, krylov=hz.HZ_KRYLOV_FGMRES, raise_on_error=False)
+        op.set_nn(net)
+        learned = op.solve(b, x, krylov=hz.HZ_KRYLOV_FGMRES, precond=hz.HZ_PRE_TRI_NN, raise_on_error=False)
+        bic = op.solve(b, x, raise_on_error=False)
+        rows.append({"stage_residual_ratio": stage, "plain": plain, "learned": learned, "bicgstab": bic})
+        op.close()
+
+    def summary(key):
+        r = [row[key] for row in rows]
+        return {"solves_per_s": round(len(r) / sum(i["seconds"] for i in r), 4),
+                "inner_iters": [i["inner_iters"] for i in r], "status": sorted({i["status"] for i in r}),
+                "max_true_rel_residual": max(i["true_rel_residual"] for i in r),
+                **({"fallbacks": [i["fallbacks"] for i in r]} if key == "learned" else {})}
+
+    return {"dims": "x".join(map(str, dims)), "z_unit": z_unit, "train_systems": len(train_systems),
+            "test_systems": len(test_systems), "train_steps": len(losses), "train_s": round(t_train, 1),
+            "loss_first20_median": float(np.median(losses[:20])), "loss_last20_median": float(np.median(losses[-20:])),
+            "stage_residual_ratio_held_out": [round(r["stage_residual_ratio"], 4) for r in rows],
+            "fgmres_plain": summary("plain"), "fgmres_learned": summary("learned"), "bicgstab_plain": summary("bicgstab")}
+
+
+def run_learned(args):
+    """Learned stage on 640x480x70: train on fresh seeds, evaluate on held-out seeds."""
+    import torch
+
+    torch.cuda.set_device(0)
+    train_sys = [(10000 + 2 * i, 10001 + 2 * i) for i in range(args.train_systems)]
+    test_sys = [(20000 + 2 * i, 20001 + 2 * i) for i in range(args.test_systems)]
+    out = learned_line((640, 480, 70), train_sys, test_sys, args.train_steps, args.z_unit)
+    print(json.dumps({"workload": f"learned stage 640x480x70 z_unit={args.z_unit}", **out}), flush=True)
 
 
 def run_nn_forward(args):

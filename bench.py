@@ -245,7 +245,7 @@ def cpu_baseline(A, b, dims, outer, inner, full_solve=True):
 # workloads (same algorithm and seeds; the bench's own run on a GB300): the work
 # the oracle's timed pieces are composed with where a full oracle solve would
 # take hours.
-GPU_COUNTS = {("n1280", "radius"): (3, 569)}
+GPU_COUNTS = {("n1280", "radius"): (3, 515)}
 
 
 def run_reference(args):
@@ -716,10 +716,11 @@ def batched_measure(ops, bs, xs, dims_list, strategy, steps, warmup, use_graph=1
             "effective_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 3)}
 
 
-def batched_small(steps, warmup, z_unit="radius"):
+def batched_small(steps, warmup, z_unit="m"):
     """Batches of systems too small to fill the GPU alone, where the persistent launch is the
     automatic strategy: 64 distinct systems of 48x36x70, and 32 right-hand sides of one 192x144x70
-    operator; persistent (graph-replayed) against sequential."""
+    operator; persistent (graph-replayed) against sequential.  Metres family: hundreds of inner
+    iterations per system, so the steady state of the inner phases dominates."""
     import torch
 
     import gen
@@ -766,7 +767,7 @@ def run_batched(args):
     auto = batched_measure(ops, bs, xs, dims_list, hz.HZ_BATCH_AUTO, args.steps, args.warmup)
     persistent = batched_measure(ops, bs, xs, dims_list, hz.HZ_BATCH_PERSISTENT, args.steps, args.warmup)
     del ops, bs, xs
-    small = batched_small(args.steps, args.warmup, args.z_unit)
+    small = batched_small(args.steps, args.warmup)
     print(json.dumps({"workload": "batched 32 systems (192x144, 320x240, 640x480) x 70, mixed IR tol 1e-8",
                       "points": int(sum(a * b * c for a, b, c in dims_list)),
                       "strategy": "auto (sequential: every system fills the GPU)", **auto,

@@ -712,7 +712,9 @@ def batched_measure(ops, bs, xs, dims_list, strategy, steps, warmup, use_graph=1
     return {"systems_per_s": round(len(ops) / (ms * 1e-3), 3), "ms_per_batch": round(ms, 3),
             "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
             "status": sorted({i["status"] for i in infos}),
-            "inner_iters": [i["inner_iters"] for i in infos], "kernel_launches": sum(i["kernel_launches"] for i in infos),
+            "inner_iters": [i["inner_iters"] for i in infos],
+            # the persistent strategy reports its one launch in every system's record
+            "kernel_launches": (max if strategy == hz.HZ_BATCH_PERSISTENT else sum)(i["kernel_launches"] for i in infos),
             "effective_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 3)}
 
 

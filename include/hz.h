@@ -218,6 +218,13 @@ int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, cons
    returns HZ_ERR_TIMEOUT without hanging the GPU (-1: off). */
 int hz_batched_debug(long long timeout_ns, int leave_block);
 
+/* Launch shape of the persistent batched kernel (process-wide, affects later
+   batched calls): columns per thread, 1 or 4; 0 (the default) chooses per
+   batch: 4 when every nx is a multiple of 4, else 1.  4 with an nx that is
+   not a multiple of 4 makes the batched call return HZ_ERR_INVALID.
+   Returns HZ_ERR_INVALID for any other value. */
+int hz_batched_set_vec(int vec);
+
 /* ---- learned preconditioner stage ----------------------------------------
  * Not in the paper: an extra preconditioner stage inside the flexible solver.
  * After the paper's tridiagonal stage z1 = T^-1 v, the remaining residual

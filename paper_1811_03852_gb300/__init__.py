@@ -132,6 +132,7 @@ def load(build_if_missing: bool = True):
         "hz_op_export": (i32, [pv, i32, i32, pv]),
         "hz_dot_noalloc": (i32, [i32, i64, pv, pv, pv, pv]),
         "hz_batched_debug": (i32, [ctypes.c_longlong, i32]),
+        "hz_batched_set_vec": (i32, [i32]),
         "hz_op_autotune": (i32, [pv, i32]),
         "hz_op_get_variants": (i32, [pv, P(i32), P(i32), P(i32), P(i32)]),
         "hz_op_set_variants": (i32, [pv, i32, i32, i32, i32]),
@@ -344,6 +345,11 @@ def solve_batched(ops, bs, xs, x0s=None, params=None, raise_on_error=True, strat
 def batched_debug(timeout_ns=0, leave_block=-1):
     """Test hook: bound of the batched grid-barrier waits and a block that leaves early."""
     _check(load().hz_batched_debug(int(timeout_ns), int(leave_block)), "hz_batched_debug")
+
+
+def batched_set_vec(vec=0):
+    """Columns per thread of the persistent batched kernel: 1 or 4, 0 to choose per batch."""
+    _check(load().hz_batched_set_vec(int(vec)), "hz_batched_set_vec")
 
 
 def dot(x, y, prec=None, stream=None):

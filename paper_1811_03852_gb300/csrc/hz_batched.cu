@@ -17,9 +17,10 @@
 // leaves, and the host reports HZ_ERR_TIMEOUT -- no spin is unbounded.
 //
 // Per-system dot products: each block sums its items' partials per system in
-// a fixed order, stores them in its own slot, and after the barrier block b
-// (b < number of systems) adds system b's slots in slot order and runs the
-// control step -- deterministic for a given launch shape.
+// a fixed order, stores them in its own slot, and after the barrier the first
+// warp of block b (b < number of systems) adds system b's slots in a fixed
+// order and its lane 0 runs the control step -- deterministic for a given
+// launch shape.
 #include <cstring>
 #include <mutex>
 
@@ -99,10 +100,18 @@ __device__ void load_ctl(const BatchArgs& A, SysCtl* sc) {
   __syncthreads();
 }
 
-__device__ __forceinline__ int sys_of(const BatchArgs& A, int64_t item) {
-  int s = 0;
-  while (s + 1 < A.nsys && item >= A.sys[s + 1].item0) ++s;
-  return s;
+// the system of a work item: the last system whose first item is <= item
+// (first items in shared memory, ascending, the first one 0)
+__device__ __forceinline__ int sys_of(const int64_t* item0, int nsys, int64_t item) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (item >= item0[mid])
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
 }
 
 // block sum of ND values per thread in fixed order; thread 0 adds them to acc
@@ -129,11 +138,26 @@ __device__ __forceinline__ void block_add(double (&v)[ND], double* acc) {
   __syncthreads();
 }
 
-// fixed-order sum of system s's slot d over all blocks
-__device__ __forceinline__ double slots_sum(const BatchArgs& A, int s, int d) {
-  double x = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) x += __ldcg(&A.part[((size_t)b * kMaxSys + s) * 4 + d]);
-  return x;
+// Fixed-order sums of system s's slots d0 .. d0+ND-1 over all blocks, taken by
+// one whole warp: lane l adds the slots of blocks l, l+32, l+64, ... in that
+// order, then an xor butterfly combines the lanes.  Addition is commutative,
+// so every stage leaves the same bits in both partners and every lane ends
+// with the same totals; the order depends on the grid size only.
+template <int ND>
+__device__ __forceinline__ void slots_sum(const BatchArgs& A, int s, int d0, double (&out)[ND]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) out[d] = 0.0;
+#pragma unroll 4
+  for (int b = lane; b < (int)gridDim.x; b += 32) {
+    const double* p = A.part + ((size_t)b * kMaxSys + s) * 4 + d0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) out[d] += __ldcg(p + d);
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) out[d] += __shfl_xor_sync(0xffffffffu, out[d], o);
 }
 
 // restart of one column inside the persistent kernel: x of neighbouring
@@ -297,76 +321,240 @@ __device__ void fin_outer(Ctl* c, bool first, bool moved, double rr, double bb, 
   c->state = !isfinite(hh) ? ST_NONFINITE : (hh > 0.0 ? ST_RUNNING : ST_CONVERGED);
 }
 
-template <int V, int UT, int UM>
-__global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
-  __shared__ SysCtl sc[kMaxSys];
-  __shared__ double acc[kMaxSys][3];
+// Block-shared state of the persistent kernel.  The item loops of the phases
+// are separate non-inlined functions over this block, so that each is
+// register-allocated on its own instead of as one body holding every phase.
+struct BShm {
+  BatchArgs A;
+  SysCtl sc[kMaxSys];
+  double acc[kMaxSys][3];
+  int64_t i0[kMaxSys];
+  int odone[kMaxSys], cur[kMaxSys], xz[kMaxSys], used[kMaxSys];
+};
+
+// ---- phase R items: each active system's FP64 residual (first: of the
+// initial guess; else of x + d, the refinement update) ----
+template <int V>
+__device__ __noinline__ void items_resid(BShm* sh, bool first) {
+  const BatchArgs& A = sh->A;
   const int nsys = A.nsys;
-  auto zero_acc = [&]() {
-    for (int s = threadIdx.x; s < nsys; s += blockDim.x) acc[s][0] = acc[s][1] = acc[s][2] = 0.0;
-    __syncthreads();
-  };
-  auto store_acc = [&](int d0, int nd) {
-    for (int s = threadIdx.x; s < nsys; s += blockDim.x)
-      for (int d = 0; d < nd; ++d) A.part[((size_t)blockIdx.x * kMaxSys + s) * 4 + d0 + d] = acc[s][d];
-    __threadfence();
-  };
-  __shared__ int s_odone[kMaxSys], s_cur[kMaxSys], s_xz[kMaxSys], s_used[kMaxSys];
-  // ---- phase R: each active system's FP64 residual (first: of the initial
-  // guess; else of x + d, the refinement update), then its decision ----
-  auto phase_r = [&](bool first) -> bool {
-    for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
-      const Ctl* c = A.sys[s].ctl;
-      s_odone[s] = __ldcg(&c->odone);
-      s_cur[s] = __ldcg(&c->cur);
-      s_xz[s] = __ldcg(&c->xz);
-      s_used[s] = !first && __ldcg(&c->xzero) == 0 && __ldcg(&c->state) != ST_NONFINITE;
-    }
-    __syncthreads();
-    zero_acc();
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-      const int s = sys_of(A, item);
-      if (s_odone[s]) continue;
-      const SysDesc& d = A.sys[s];
-      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[3] = {0.0, 0.0, 0.0};
-      if (q < d.g.ncol / V) {
-        const double* xin;
-        double* xout;
-        bool hasx;
-        if (first) {  // the initial guess is copied into xa (cur = 0) or x stays zero
-          hasx = d.x0 != nullptr;
-          xin = d.x0;
-          xout = hasx ? d.xa : nullptr;
-        } else {
-          hasx = !s_xz[s];
-          xin = s_cur[s] ? d.xb : d.xa;
-          xout = (hasx || s_used[s]) ? (s_cur[s] ? d.xa : d.xb) : nullptr;
-        }
-        for (int cc = 0; cc < V; ++cc)
-          resid_column(d, q * V + cc, hasx, xin, s_used[s] != 0, xout, v[0], v[1], v[2]);
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(sh->i0, nsys, item);
+    if (sh->odone[s]) continue;
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (q < d.g.ncol / V) {
+      const double* xin;
+      double* xout;
+      bool hasx;
+      if (first) {  // the initial guess is copied into xa (cur = 0) or x stays zero
+        hasx = d.x0 != nullptr;
+        xin = d.x0;
+        xout = hasx ? d.xa : nullptr;
+      } else {
+        hasx = !sh->xz[s];
+        xin = sh->cur[s] ? d.xb : d.xa;
+        xout = (hasx || sh->used[s]) ? (sh->cur[s] ? d.xa : d.xb) : nullptr;
       }
-      block_add<3>(v, &acc[s][0]);
+      for (int cc = 0; cc < V; ++cc)
+        resid_column(d, q * V + cc, hasx, xin, sh->used[s] != 0, xout, v[0], v[1], v[2]);
     }
-    store_acc(0, 3);
-    if (!grid_sync(A)) return false;
-    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
-      const int s = blockIdx.x;
-      if (!s_odone[s]) {
+    block_add<3>(v, &sh->acc[s][0]);
+  }
+}
+
+// ---- phase A items: (re)start or p = r + beta (p - omega v); ph = T^-1 p ----
+template <int V, int UT>
+__device__ __noinline__ void items_pre_p(BShm* sh) {
+  const BatchArgs& A = sh->A;
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(sh->i0, A.nsys, item);
+    const SysCtl c = sh->sc[s];
+    if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    double v[1] = {0.0};
+    if (q < d.g.ncol / V) {
+      if (c.state == ST_RESTART) {
+        for (int cc = 0; cc < V; ++cc) v[0] += restart_column_cg(d.g, q * V + cc, d.a, d.w, c.xzero != 0);
+      } else if (c.fresh) {
+        SrcCopy<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.p};
+        thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.ph, src);
+      } else {
+        SrcP<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.p, d.w.v, c.beta, c.omega};
+        thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.ph, src);
+      }
+    }
+    if (c.state == ST_RESTART) block_add<1>(v, &sh->acc[s][0]);
+  }
+}
+
+// ---- phase B items: v = p + H ph, <r0, v> ----
+template <int V, int UM>
+__device__ __noinline__ void items_mv_v(BShm* sh) {
+  const BatchArgs& A = sh->A;
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(sh->i0, A.nsys, item);
+    const SysCtl c = sh->sc[s];
+    if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    double v[1] = {0.0}, dummy = 0.0;
+    const bool r0buf = c.r0sel || c.state == ST_RESTART;
+    if (q < d.g.ncol / V)
+      hmv_vec<float, V, UM, 0, LD_CG>(d.g, q * V, d.a, d.w.p, d.w.ph, d.w.v, r0buf ? d.w.r0 : d.w.rhs, v[0], dummy);
+    block_add<1>(v, &sh->acc[s][0]);
+  }
+}
+
+// ---- phase C items: s = r - alpha v, sh = T^-1 s (the test on ||s|| is phase D's) ----
+template <int V, int UT>
+__device__ __noinline__ void items_pre_s(BShm* sh) {
+  const BatchArgs& A = sh->A;
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(sh->i0, A.nsys, item);
+    const SysCtl c = sh->sc[s];
+    if (c.state != ST_RUNNING) continue;
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    if (q < d.g.ncol / V) {
+      SrcS<float, V, LD_CG, false, false> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, {}};
+      thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.sh, src);
+    }
+  }
+}
+
+// ---- phase D items: t = s + H sh, <t, s>, <t, t>, <s, s> ----
+template <int V, int UM>
+__device__ __noinline__ void items_mv_t(BShm* sh) {
+  const BatchArgs& A = sh->A;
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(sh->i0, A.nsys, item);
+    const SysCtl c = sh->sc[s];
+    if (c.state != ST_RUNNING) continue;
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (q < d.g.ncol / V)
+      hmv_vec<float, V, UM, 3, LD_CG>(d.g, q * V, d.a, d.w.s, d.w.sh, d.w.t, nullptr, v[0], v[1], &v[2]);
+    block_add<3>(v, &sh->acc[s][0]);
+  }
+}
+
+// ---- phase E items: x += alpha ph + omega sh, r = s - omega t, <r0, r>, <r, r> ----
+template <int V>
+__device__ __noinline__ void items_upd(BShm* sh) {
+  const BatchArgs& A = sh->A;
+  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int s = sys_of(sh->i0, A.nsys, item);
+    const SysCtl c = sh->sc[s];
+    if (c.state != ST_RUNNING && c.state != ST_HALF) continue;
+    const SysDesc& d = A.sys[s];
+    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (q < d.g.ncol / V) {
+      const bool half = c.state == ST_HALF;
+      const float* r0 = c.r0sel ? d.w.r0 : d.w.rhs;
+      DotAcc<float> u0{}, u1{};
+      for (int k = 0; k < d.g.nz; ++k) {
+        const int64_t idx = (int64_t)k * d.g.ncol + q * V;
+        Pack<float, V> xv, pv = ldp<float, V, LD_CG>(d.w.ph + idx);
+        if (c.xzero) {
+#pragma unroll
+          for (int u = 0; u < V; ++u) xv.a[u] = 0.f;
+        } else {
+          xv = ldp<float, V, LD_CG>(d.w.x + idx);
+        }
+        if (half) {
+#pragma unroll
+          for (int u = 0; u < V; ++u) xv.a[u] = fmaf(c.alpha, pv.a[u], xv.a[u]);
+        } else {
+          const Pack<float, V> shv = ldp<float, V, LD_CG>(d.w.sh + idx), sv = ldp<float, V, LD_CG>(d.w.s + idx),
+                               tv = ldp<float, V, LD_CG>(d.w.t + idx), r0v = ldp<float, V, LD_CG>(r0 + idx);
+          Pack<float, V> rv;
+          float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+          for (int u = 0; u < V; ++u) {
+            xv.a[u] = fmaf(c.omega, shv.a[u], fmaf(c.alpha, pv.a[u], xv.a[u]));
+            rv.a[u] = fmaf(-c.omega, tv.a[u], sv.a[u]);
+            a0 = fmaf(r0v.a[u], rv.a[u], a0);
+            a1 = fmaf(rv.a[u], rv.a[u], a1);
+          }
+          stp(d.w.r + idx, rv);
+          u0.add(a0);
+          u1.add(a1);
+        }
+        stp(d.w.x + idx, xv);
+      }
+      v[0] = u0.value();
+      v[1] = u1.value();
+    }
+    block_add<2>(v, &sh->acc[s][0]);
+  }
+}
+
+__device__ __forceinline__ void zero_acc(BShm* sh) {
+  for (int s = threadIdx.x; s < sh->A.nsys; s += blockDim.x) sh->acc[s][0] = sh->acc[s][1] = sh->acc[s][2] = 0.0;
+  __syncthreads();
+}
+
+// this block's partials of slots d0 .. d0+nd-1 (acc columns 0 .. nd-1 hold them)
+__device__ __forceinline__ void store_acc(BShm* sh, int d0, int nd) {
+  for (int s = threadIdx.x; s < sh->A.nsys; s += blockDim.x)
+    for (int d = 0; d < nd; ++d) sh->A.part[((size_t)blockIdx.x * kMaxSys + s) * 4 + d0 + d] = sh->acc[s][d];
+  __threadfence();
+}
+
+// ---- phase R: the residual items, then each system's refinement decision ----
+template <int V>
+__device__ bool phase_resid(BShm* sh, bool first) {
+  const BatchArgs& A = sh->A;
+  const int nsys = A.nsys;
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+    const Ctl* c = A.sys[s].ctl;
+    sh->odone[s] = __ldcg(&c->odone);
+    sh->cur[s] = __ldcg(&c->cur);
+    sh->xz[s] = __ldcg(&c->xz);
+    sh->used[s] = !first && __ldcg(&c->xzero) == 0 && __ldcg(&c->state) != ST_NONFINITE;
+  }
+  __syncthreads();
+  zero_acc(sh);
+  items_resid<V>(sh, first);
+  store_acc(sh, 0, 3);
+  if (!grid_sync(A)) return false;
+  if ((int)blockIdx.x < nsys && threadIdx.x < 32) {
+    const int s = blockIdx.x;
+    if (!sh->odone[s]) {
+      double t[3];
+      slots_sum<3>(A, s, 0, t);
+      if (threadIdx.x == 0) {
         const SysDesc& d = A.sys[s];
-        const bool moved = !first && (!s_xz[s] || s_used[s]);
-        fin_outer(d.ctl, first, moved, slots_sum(A, s, 0), slots_sum(A, s, 1), slots_sum(A, s, 2));
+        const bool moved = !first && (!sh->xz[s] || sh->used[s]);
+        fin_outer(d.ctl, first, moved, t[0], t[1], t[2]);
         if (first) {
           d.ctl->cur = 0;
           d.ctl->xz = d.x0 ? 0 : 1;
         }
       }
-      __threadfence();
     }
-    return grid_sync(A);
-  };
+    if (threadIdx.x == 0) __threadfence();
+  }
+  return grid_sync(A);
+}
 
-  if (!phase_r(true)) return;
+template <int V, int UT, int UM>
+__global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs Ain) {
+  __shared__ BShm shm;
+  BShm* sh = &shm;
+  if (threadIdx.x == 0) shm.A = Ain;
+  for (int s = threadIdx.x; s < Ain.nsys; s += blockDim.x) shm.i0[s] = Ain.sys[s].item0;
+  __syncthreads();
+  const BatchArgs& A = shm.A;
+  const int nsys = A.nsys;
+  SysCtl* sc = shm.sc;
+
+  if (!phase_resid<V>(sh, true)) return;
   if ((int)blockIdx.x == A.leave_block) return;  // test hook: the others must time out, not hang
   for (int loop = 0; loop < A.max_loops; ++loop) {
     load_ctl(A, sc);
@@ -377,181 +565,96 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs A) {
       bool active = false;
       for (int s = 0; s < nsys; ++s) active |= !__ldcg(&A.sys[s].ctl->odone);
       if (!active) break;
-      if (!phase_r(false)) return;
+      if (!phase_resid<V>(sh, false)) return;
       continue;
     }
 
     // ---- phase A: (re)start or p = r + beta (p - omega v); ph = T^-1 p ----
-    zero_acc();
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-      const int s = sys_of(A, item);
-      const SysCtl c = sc[s];
-      if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
-      const SysDesc& d = A.sys[s];
-      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[1] = {0.0};
-      if (q < d.g.ncol / V) {
-        if (c.state == ST_RESTART) {
-          for (int cc = 0; cc < V; ++cc) v[0] += restart_column_cg(d.g, q * V + cc, d.a, d.w, c.xzero != 0);
-        } else if (c.fresh) {
-          SrcCopy<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.p};
-          thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.ph, src);
-        } else {
-          SrcP<float, V, LD_CG> src{c.rsel ? d.w.r : d.w.rhs, d.w.p, d.w.v, c.beta, c.omega};
-          thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.ph, src);
-        }
-      }
-      if (c.state == ST_RESTART) block_add<1>(v, &acc[s][0]);
-    }
-    store_acc(0, 1);
+    zero_acc(sh);
+    items_pre_p<V, UT>(sh);
+    store_acc(sh, 0, 1);
     if (!grid_sync(A)) return;
 
     // ---- phase B: v = p + H ph, <r0, v> ----
-    zero_acc();
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-      const int s = sys_of(A, item);
-      const SysCtl c = sc[s];
-      if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
-      const SysDesc& d = A.sys[s];
-      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[1] = {0.0}, dummy = 0.0;
-      const bool r0buf = c.r0sel || c.state == ST_RESTART;
-      if (q < d.g.ncol / V)
-        hmv_vec<float, V, UM, 0, LD_CG>(d.g, q * V, d.a, d.w.p, d.w.ph, d.w.v, r0buf ? d.w.r0 : d.w.rhs, v[0], dummy);
-      block_add<1>(v, &acc[s][0]);
-    }
-    store_acc(1, 1);
+    zero_acc(sh);
+    items_mv_v<V, UM>(sh);
+    store_acc(sh, 1, 1);
     if (!grid_sync(A)) return;
-    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+    if ((int)blockIdx.x < nsys && threadIdx.x < 32) {
       const int s = blockIdx.x;
-      Ctl* ctl = A.sys[s].ctl;
-      if (sc[s].state == ST_RESTART) fin_restart(ctl, slots_sum(A, s, 0));
       if (sc[s].state == ST_RESTART || sc[s].state == ST_RUNNING) {
-        if (ctl->state == ST_RUNNING) fin_alpha(ctl, slots_sum(A, s, 1));
+        double t[2];
+        slots_sum<2>(A, s, 0, t);
+        if (threadIdx.x == 0) {
+          Ctl* ctl = A.sys[s].ctl;
+          if (sc[s].state == ST_RESTART) fin_restart(ctl, t[0]);
+          if (ctl->state == ST_RUNNING) fin_alpha(ctl, t[1]);
+        }
       }
-      __threadfence();
+      if (threadIdx.x == 0) __threadfence();
     }
     if (!grid_sync(A)) return;
     load_ctl(A, sc);
 
     // ---- phase C: s = r - alpha v, sh = T^-1 s (the test on ||s|| is phase D's) ----
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-      const int s = sys_of(A, item);
-      const SysCtl c = sc[s];
-      if (c.state != ST_RUNNING) continue;
-      const SysDesc& d = A.sys[s];
-      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      if (q < d.g.ncol / V) {
-        SrcS<float, V, LD_CG, false, false> src{c.rsel ? d.w.r : d.w.rhs, d.w.v, d.w.s, c.alpha, 0.f, {}};
-        thomas_vec<float, V, UT>(d.g, q * V, d.a.m, d.a.l, d.a.cp, d.w.sh, src);
-      }
-    }
+    items_pre_s<V, UT>(sh);
     if (!grid_sync(A)) return;
 
     // ---- phase D: t = s + H sh, <t, s>, <t, t>, <s, s> -> half-step test, omega ----
-    zero_acc();
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-      const int s = sys_of(A, item);
-      const SysCtl c = sc[s];
-      if (c.state != ST_RUNNING) continue;
-      const SysDesc& d = A.sys[s];
-      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[3] = {0.0, 0.0, 0.0};
-      if (q < d.g.ncol / V)
-        hmv_vec<float, V, UM, 3, LD_CG>(d.g, q * V, d.a, d.w.s, d.w.sh, d.w.t, nullptr, v[0], v[1], &v[2]);
-      block_add<3>(v, &acc[s][0]);
-    }
-    store_acc(0, 3);
+    zero_acc(sh);
+    items_mv_t<V, UM>(sh);
+    store_acc(sh, 0, 3);
     if (!grid_sync(A)) return;
-    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+    if ((int)blockIdx.x < nsys && threadIdx.x < 32) {
       const int s = blockIdx.x;
       if (sc[s].state == ST_RUNNING) {
-        Ctl* ctl = A.sys[s].ctl;
-        fin_snorm(ctl, slots_sum(A, s, 2));
-        if (ctl->state == ST_RUNNING) fin_omega(ctl, slots_sum(A, s, 0), slots_sum(A, s, 1));
+        double t[3];
+        slots_sum<3>(A, s, 0, t);
+        if (threadIdx.x == 0) {
+          Ctl* ctl = A.sys[s].ctl;
+          fin_snorm(ctl, t[2]);
+          if (ctl->state == ST_RUNNING) fin_omega(ctl, t[0], t[1]);
+        }
       }
-      __threadfence();
+      if (threadIdx.x == 0) __threadfence();
     }
     if (!grid_sync(A)) return;
     load_ctl(A, sc);
 
     // ---- phase E: x += alpha ph + omega sh, r = s - omega t, <r0, r>, <r, r> ----
-    zero_acc();
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-      const int s = sys_of(A, item);
-      const SysCtl c = sc[s];
-      if (c.state != ST_RUNNING && c.state != ST_HALF) continue;
-      const SysDesc& d = A.sys[s];
-      const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-      double v[2] = {0.0, 0.0};
-      if (q < d.g.ncol / V) {
-        const bool half = c.state == ST_HALF;
-        const float* r0 = c.r0sel ? d.w.r0 : d.w.rhs;
-        DotAcc<float> u0{}, u1{};
-        for (int k = 0; k < d.g.nz; ++k) {
-          const int64_t idx = (int64_t)k * d.g.ncol + q * V;
-          Pack<float, V> xv, pv = ldp<float, V, LD_CG>(d.w.ph + idx);
-          if (c.xzero) {
-#pragma unroll
-            for (int u = 0; u < V; ++u) xv.a[u] = 0.f;
-          } else {
-            xv = ldp<float, V, LD_CG>(d.w.x + idx);
-          }
-          if (half) {
-#pragma unroll
-            for (int u = 0; u < V; ++u) xv.a[u] = fmaf(c.alpha, pv.a[u], xv.a[u]);
-          } else {
-            const Pack<float, V> shv = ldp<float, V, LD_CG>(d.w.sh + idx), sv = ldp<float, V, LD_CG>(d.w.s + idx),
-                                 tv = ldp<float, V, LD_CG>(d.w.t + idx), r0v = ldp<float, V, LD_CG>(r0 + idx);
-            Pack<float, V> rv;
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int u = 0; u < V; ++u) {
-              xv.a[u] = fmaf(c.omega, shv.a[u], fmaf(c.alpha, pv.a[u], xv.a[u]));
-              rv.a[u] = fmaf(-c.omega, tv.a[u], sv.a[u]);
-              a0 = fmaf(r0v.a[u], rv.a[u], a0);
-              a1 = fmaf(rv.a[u], rv.a[u], a1);
-            }
-            stp(d.w.r + idx, rv);
-            u0.add(a0);
-            u1.add(a1);
-          }
-          stp(d.w.x + idx, xv);
-        }
-        v[0] = u0.value();
-        v[1] = u1.value();
-      }
-      block_add<2>(v, &acc[s][0]);
-    }
-    store_acc(2, 2);
+    zero_acc(sh);
+    items_upd<V>(sh);
+    store_acc(sh, 2, 2);
     if (!grid_sync(A)) return;
-    if ((int)blockIdx.x < nsys && threadIdx.x == 0) {
+    if ((int)blockIdx.x < nsys && threadIdx.x < 32) {
       const int s = blockIdx.x;
-      if (sc[s].state == ST_RUNNING || sc[s].state == ST_HALF)
-        fin_iteration(A.sys[s].ctl, sc[s].state == ST_HALF, slots_sum(A, s, 2), slots_sum(A, s, 3));
-      __threadfence();
+      if (sc[s].state == ST_RUNNING || sc[s].state == ST_HALF) {
+        double t[2];
+        slots_sum<2>(A, s, 2, t);
+        if (threadIdx.x == 0) fin_iteration(A.sys[s].ctl, sc[s].state == ST_HALF, t[0], t[1]);
+      }
+      if (threadIdx.x == 0) __threadfence();
     }
     if (!grid_sync(A)) return;
   }
   // the result in the caller's buffer: systems whose x ended in the second one
   for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
-    s_cur[s] = __ldcg(&A.sys[s].ctl->cur);
-    s_xz[s] = __ldcg(&A.sys[s].ctl->xz);
+    shm.cur[s] = __ldcg(&A.sys[s].ctl->cur);
+    shm.xz[s] = __ldcg(&A.sys[s].ctl->xz);
   }
   __syncthreads();
   for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int s = sys_of(A, item);
+    const int s = sys_of(shm.i0, nsys, item);
     const SysDesc& d = A.sys[s];
     const int64_t q = (item - d.item0) * kBS + threadIdx.x;
-    if (q >= d.g.ncol / V || (!s_cur[s] && !s_xz[s])) continue;
+    if (q >= d.g.ncol / V || (!shm.cur[s] && !shm.xz[s])) continue;
     for (int cc = 0; cc < V; ++cc)
       for (int k = 0; k < d.g.nz; ++k) {
         const int64_t idx = (int64_t)k * d.g.ncol + q * V + cc;
-        d.xa[idx] = s_xz[s] ? 0.0 : __ldcg(d.xb + idx);
+        d.xa[idx] = shm.xz[s] ? 0.0 : __ldcg(d.xb + idx);
       }
   }
 }
-
 // ---------------------------------------------------------------------------
 struct BatchWs {
   SysDesc* sys = nullptr;
@@ -570,7 +673,7 @@ struct BatchWs {
 
 template <int V>
 const void* batched_kernel() {
-  return V == 4 ? (const void*)k_batched<4, 2, 1> : (const void*)k_batched<1, 8, 4>;
+  return V == 4 ? (const void*)k_batched<4, 2, 1> : (const void*)k_batched<1, 4, 4>;
 }
 
 // member by member (struct padding is not part of what a launch bakes in)

@@ -801,6 +801,7 @@ void store_tuned(hz_op op) {
 // test hooks of the batched solve (bounded grid-barrier wait)
 long long g_batch_timeout_ns = 2000000000LL;
 int g_batch_leave_block = -1;
+int g_batch_vec = 0;  // columns per thread of the persistent kernel (0: chosen per batch)
 
 // global scratch for hz_dot (per device)
 std::mutex g_dot_mu;
@@ -1684,6 +1685,12 @@ int hz_batched_debug(long long timeout_ns, int leave_block) {
   return HZ_OK;
 }
 
+int hz_batched_set_vec(int vec) {
+  if (vec != 0 && vec != 1 && vec != 4) return HZ_ERR_INVALID;
+  g_batch_vec = vec;
+  return HZ_OK;
+}
+
 // batched solves: systems of at least this many points each fill the GPU alone
 // (the automatic strategy then solves them one after another)
 constexpr int64_t kBatchSeqMinPoints = int64_t(1) << 20;
@@ -1716,10 +1723,17 @@ int hz_solve_batched_ex(int nsys, const hz_op* ops, const double* const* b, cons
       return HZ_ERR_INVALID;
     if (ops[q]->g.nx % 4) vec = 1;
   }
+  // Four columns per thread wherever the rows allow it: a phase of the
+  // persistent kernel takes about as long as one thread's march down its
+  // columns' levels, whatever the number of columns per thread (measured
+  // equal per iteration on 64 systems of 48x36x70, 1.6x faster with four on
+  // 32 right-hand sides of 192x144x70).
+  if (g_batch_vec == 1) vec = 1;
+  if (g_batch_vec == 4 && vec != 4) return HZ_ERR_INVALID;
   // Systems that each fill the GPU on their own run one after another through
   // the single-system path (its graph-captured inner loop and per-kernel
   // variants at full occupancy); smaller ones share the persistent launch,
-  // whose one-launch-per-refinement-step pays off when a system alone cannot
+  // one launch for the whole batch, which pays off when a system alone cannot
   // keep the SMs busy.
   if (strategy == HZ_BATCH_AUTO) {
     int64_t smallest = ops[0]->g.n;

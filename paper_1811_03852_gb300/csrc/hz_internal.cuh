@@ -239,8 +239,8 @@ constexpr int kParkBulk = 3;  // their park mode in the Thomas variant tables (P
 // 2: z = T^-1 r alone.  Valid when ncol % 4 == 0 and the tile's parked sweep fits.
 bool thomas_bulk_ok(const Grid& g);
 // stages: ring slots, 3, 4 or 5
-cudaError_t launch_thomas_bulk(int mode, int stages, const Grid& g, const Bands<float>& a, const Vecs<float>& w,
-                               const float* r, float* z, Ctl* ctl, int* err, const Launch& L);
+cudaError_t launch_thomas_bulk(int mode, int stages, int per_sm_cap, const Grid& g, const Bands<float>& a,
+                               const Vecs<float>& w, const float* r, float* z, Ctl* ctl, int* err, const Launch& L);
 void warm_thomas_bulk(const Launch& L, int nz);
 
 // Blocks for a grid-stride kernel: every SM filled to that kernel's own

@@ -41,11 +41,11 @@ struct Variants;
 // (the arrays read once evict-first, so that rows of x stay in L2).
 template <>
 struct Variants<float> {
-  static constexpr int NPRE = 16, NMV = 7;
-  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2, 4, 4, 4};
-  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4, 5, 3, 4};
-  static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3};
-  static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3, 0, 0, 0};
+  static constexpr int NPRE = 18, NMV = 7;
+  static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2, 4, 4, 4, 4, 4};
+  static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4, 5, 3, 4, 5, 8};
+  static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 3, 3};
+  static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3, 0, 0, 0, 1, 1};
   static constexpr int mv_v[NMV] = {1, 4, 2, 2, 4, 2, 2};
   static constexpr int mv_u[NMV] = {4, 1, 2, 1, 1, 2, 1};
   static constexpr int mv_h[NMV] = {0, 0, 0, 0, 1, 1, 1};
@@ -532,7 +532,7 @@ cudaError_t launch_pre_p_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, C
   return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
     if constexpr (P == PARK_BULK) {
-      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(0, U, g, a, w, nullptr, nullptr, ctl, &ctl->kerr, L);
+      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(0, U, cap, g, a, w, nullptr, nullptr, ctl, &ctl->kerr, L);
       return cudaErrorInvalidValue;
     } else {
     const void* k = (const void*)k_pre_p<T, V, U, P>;
@@ -548,7 +548,7 @@ cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, C
   return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
     if constexpr (P == PARK_BULK) {
-      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(1, U, g, a, w, nullptr, nullptr, ctl, &ctl->kerr, L);
+      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(1, U, cap, g, a, w, nullptr, nullptr, ctl, &ctl->kerr, L);
       return cudaErrorInvalidValue;
     } else {
     const void* k = (const void*)k_pre_s<T, V, U, P>;
@@ -590,7 +590,7 @@ cudaError_t launch_tinv_t(const Grid& g, const Bands<T>& a, const T* r, T* z, co
   return with_pre<T>(L.vpre[prec_index<T>()], [&](auto Vc, auto Uc, auto Pc, int cap) {
     constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, P = decltype(Pc)::value;
     if constexpr (P == PARK_BULK) {
-      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(2, U, g, a, Vecs<T>{}, r, z, nullptr, L.err, L);
+      if constexpr (sizeof(T) == 4) return launch_thomas_bulk(2, U, cap, g, a, Vecs<T>{}, r, z, nullptr, L.err, L);
       return cudaErrorInvalidValue;
     } else {
     const void* k = (const void*)k_tinv<T, V, U, P>;

@@ -91,11 +91,16 @@ __device__ __forceinline__ void mb_expect(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// bytes (a multiple of 16) from global src (16-byte aligned) to shared dst, completing on bar
-__device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+// bytes (a multiple of 16) from global src (16-byte aligned) to shared dst,
+// completing on bar; pol: the L2 policy of the source lines (the copies
+// stream arrays read once per launch, evict-first, so that the parked
+// forward sweep keeps its place in L2 for the back sweep)
+__device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
 }
 
 }  // namespace
@@ -158,6 +163,7 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
     if (lane == 0) {
       uint32_t use = 0;  // slot uses issued (slot = use % kStages, its phase = use / kStages)
       bool ok = true;
+      const uint64_t pol = l2_evict_first();
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t c0 = tile * kTC;
         const unsigned bytes = (unsigned)((ncol - c0 < kTC ? ncol - c0 : kTC) * 4);
@@ -173,13 +179,13 @@ __global__ void __launch_bounds__(kBulkThreads) k_thomas_bulk(Grid g, Bands<floa
             const int64_t off = (int64_t)step * ncol + c0;
             mb_expect(full0 + 8u * s, NIN * bytes);
 #pragma unroll
-            for (int q = 0; q < NIN; ++q) bulk_copy(dst + q * kRowBytes, src[q] + off, bytes, full0 + 8u * s);
+            for (int q = 0; q < NIN; ++q) bulk_copy(dst + q * kRowBytes, src[q] + off, bytes, full0 + 8u * s, pol);
           } else {  // back: the c' rows of levels k0, k0-1, ..., down to 0 at most kMaxIn of them
             const int k0 = nz - 1 - (step - nz) * kMaxIn;
             const int cnt = k0 + 1 < kMaxIn ? k0 + 1 : kMaxIn;
             mb_expect(full0 + 8u * s, (unsigned)cnt * bytes);
             for (int q = 0; q < cnt; ++q)
-              bulk_copy(dst + q * kRowBytes, a.cp + (int64_t)(k0 - q) * ncol + c0, bytes, full0 + 8u * s);
+              bulk_copy(dst + q * kRowBytes, a.cp + (int64_t)(k0 - q) * ncol + c0, bytes, full0 + 8u * s, pol);
           }
         }
       }
@@ -303,33 +309,34 @@ static cudaError_t bulk_prepare() {
 }
 
 template <int S>
-static cudaError_t launch_s(int mode, const Grid& g, const Bands<float>& a, const Vecs<float>& w, const float* r,
-                            float* z, Ctl* ctl, int* err, const Launch& L) {
+static cudaError_t launch_s(int mode, int cap, const Grid& g, const Bands<float>& a, const Vecs<float>& w,
+                            const float* r, float* z, Ctl* ctl, int* err, const Launch& L) {
   const size_t sm = thomas_bulk_smem(S);
   const int64_t tiles = (g.ncol + kTC - 1) / kTC;
   cudaError_t e;
   if (mode == 0) {
     if ((e = bulk_prepare<0, S>()) != cudaSuccess) return e;
-    const int grid = grid_for((const void*)k_thomas_bulk<0, S>, kBulkThreads, L, tiles, sm);
+    const int grid = grid_for((const void*)k_thomas_bulk<0, S>, kBulkThreads, L, tiles, sm, cap);
     k_thomas_bulk<0, S><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, nullptr, nullptr, ctl, err);
   } else if (mode == 1) {
     if ((e = bulk_prepare<1, S>()) != cudaSuccess) return e;
-    const int grid = grid_for((const void*)k_thomas_bulk<1, S>, kBulkThreads, L, tiles, sm);
+    const int grid = grid_for((const void*)k_thomas_bulk<1, S>, kBulkThreads, L, tiles, sm, cap);
     k_thomas_bulk<1, S><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, nullptr, nullptr, ctl, err);
   } else {
     if ((e = bulk_prepare<2, S>()) != cudaSuccess) return e;
-    const int grid = grid_for((const void*)k_thomas_bulk<2, S>, kBulkThreads, L, tiles, sm);
+    const int grid = grid_for((const void*)k_thomas_bulk<2, S>, kBulkThreads, L, tiles, sm, cap);
     k_thomas_bulk<2, S><<<grid, kBulkThreads, sm, L.stream>>>(g, a, w, r, z, ctl, err);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_thomas_bulk(int mode, int stages, const Grid& g, const Bands<float>& a, const Vecs<float>& w,
-                               const float* r, float* z, Ctl* ctl, int* err, const Launch& L) {
+cudaError_t launch_thomas_bulk(int mode, int stages, int per_sm_cap, const Grid& g, const Bands<float>& a,
+                               const Vecs<float>& w, const float* r, float* z, Ctl* ctl, int* err, const Launch& L) {
   if (!thomas_bulk_ok(g)) return cudaErrorInvalidValue;
-  if (stages == 3) return launch_s<3>(mode, g, a, w, r, z, ctl, err, L);
-  if (stages == 4) return launch_s<4>(mode, g, a, w, r, z, ctl, err, L);
-  if (stages == 5) return launch_s<5>(mode, g, a, w, r, z, ctl, err, L);
+  if (stages == 3) return launch_s<3>(mode, per_sm_cap, g, a, w, r, z, ctl, err, L);
+  if (stages == 4) return launch_s<4>(mode, per_sm_cap, g, a, w, r, z, ctl, err, L);
+  if (stages == 5) return launch_s<5>(mode, per_sm_cap, g, a, w, r, z, ctl, err, L);
+  if (stages == 8) return launch_s<8>(mode, per_sm_cap, g, a, w, r, z, ctl, err, L);
   return cudaErrorInvalidValue;
 }
 
@@ -350,6 +357,7 @@ void warm_thomas_bulk(const Launch& L, int) {
   warm_s<3>(L);
   warm_s<4>(L);
   warm_s<5>(L);
+  warm_s<8>(L);
 }
 
 }  // namespace hz

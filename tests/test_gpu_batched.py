@@ -218,3 +218,27 @@ def test_small_systems_go_to_the_persistent_launch():
         _, rn = oracle.residual(A, b, x)
         assert rn / np.linalg.norm(b) <= 1e-8
     del hz
+
+
+def test_columns_per_thread_setting():
+    # both launch shapes of the persistent kernel solve the batch; 4 columns per
+    # thread with an nx that is not a multiple of 4 and unknown widths are refused
+    import paper_1811_03852_gb300 as hz
+
+    systems = _systems([(48, 36, 20, 71, 72), (40, 30, 20, 73, 74)], z_unit="m")
+    try:
+        for vec in (1, 4):
+            hz.batched_set_vec(vec)
+            xs, infos, _ = _batched(systems, strategy=hz.HZ_BATCH_PERSISTENT)
+            for (A, b), x, info in zip(systems, xs, infos):
+                assert info["status"] == 0 and info["kernel_launches"] == 1, info
+                _, rn = oracle.residual(A, b, x)
+                assert rn / np.linalg.norm(b) <= 1e-8
+        odd = _systems([(38, 20, 10, 75, 76)], z_unit="m")
+        with pytest.raises(hz.HzError):
+            _batched(odd, strategy=hz.HZ_BATCH_PERSISTENT)
+        for bad in (2, 3, -1, 8):
+            with pytest.raises(hz.HzError):
+                hz.batched_set_vec(bad)
+    finally:
+        hz.batched_set_vec(0)

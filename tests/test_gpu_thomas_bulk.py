@@ -16,7 +16,7 @@ from gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
 
-BULKS = (13, 14, 15)  # the FP32 Thomas variants with park mode 3 (ring of 5, 3 and 4 slots)
+BULKS = (13, 14, 15, 16, 17)  # the FP32 Thomas variants with park mode 3 (ring of 5, 3, 4 slots; 5 and 8 at one block per SM)
 BULK = 13
 PLAIN = 10  # the default FP32 Thomas variant
 

@@ -615,13 +615,14 @@ def run_ours(args):
         try:
             from paper_1811_03852_gb300 import _build
 
-            # DRAM bytes per launch from an ncu capture of the same workload, valid only
-            # while the kernel's source files and the autotuned variant are unchanged
+            # DRAM bytes per launch of the autotuned variant from an ncu capture (scaled to
+            # this workload), valid only while that variant's source files are unchanged
             tj = json.load(open(tp))
             ent = tj.get(dom)
             kind = "mv32" if dom.startswith("k_mv") else "pre32"
-            if (ent and ent.get("workload") == args.workload and ent.get("src") == _build.src_hash(ent["files"])):
-                traffic = ent["bytes_per_launch"].get(str(variants.get(kind)))
+            rec = (ent or {}).get("variants", {}).get(str(variants.get(kind)))
+            if (rec and ent.get("workload") == args.workload and rec.get("src") == _build.src_hash(rec["files"])):
+                traffic = rec["bytes_per_launch"]
         except Exception:
             traffic = None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

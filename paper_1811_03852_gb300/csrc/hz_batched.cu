@@ -22,7 +22,9 @@
 // order and its lane 0 runs the control step -- deterministic for a given
 // launch shape.
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "hz_krylov.cuh"
 
@@ -32,6 +34,7 @@ struct BatchArgs {
   const SysDesc* sys;
   int nsys;
   int64_t nitems;
+  int64_t nlitems;     // level items (stencil and update phases)
   double* part;        // [gridDim.x][kMaxSys][4] partial sums
   unsigned* bar;       // [0] arrivals, [1] generation
   int* err;            // bit 0: a barrier wait timed out
@@ -190,13 +193,15 @@ __device__ double restart_column_cg(const Grid& g, int64_t col, const Bands<floa
   return (double)cacc;
 }
 
-// The FP64 true residual of one column (Sec. 3: r = b - A x with the unscaled
-// bands) for x = xin + delta (xin absent when hasx is false, delta when used
-// is false); writes x to xout (if given), the next inner right-hand side
-// rhs = fp32(r / A_C), and adds ||r||^2, ||b||^2, ||rhs||^2.  x and delta were
-// written by other blocks of this launch: read through L2.
-__device__ void resid_column(const SysDesc& d, int64_t col, bool hasx, const double* xin, bool used, double* xout,
-                             double& rr, double& bb, double& hh) {
+// The FP64 true residual of one column at levels [k0, k1) (Sec. 3: r = b - A x
+// with the unscaled bands) for x = xin + delta (xin absent when hasx is false,
+// delta when used is false); writes x to xout (if given), the next inner
+// right-hand side rhs = fp32(r / A_C), and adds ||r||^2, ||b||^2, ||rhs||^2.
+// x and delta were written by other blocks of this launch: read through L2.
+// xin and xout are different buffers, so level chunks of a column may run in
+// any order.
+__device__ void resid_column(const SysDesc& d, int64_t col, int k0, int k1, bool hasx, const double* xin, bool used,
+                             double* xout, double& rr, double& bb, double& hh) {
   const Grid& g = d.g;
   const int64_t n = g.n, ncol = g.ncol;
   const int i = (int)(col % g.nx), j = (int)(col / g.nx);
@@ -211,11 +216,13 @@ __device__ void resid_column(const SysDesc& d, int64_t col, bool hasx, const dou
   };
   double xm = 0.0, xc = 0.0, xp = 0.0;
   if (any) {
-    xc = X(col);
-    xp = g.nz > 1 ? X(ncol + col) : 0.0;
+    const int64_t c0 = (int64_t)k0 * ncol + col;
+    xm = k0 > 0 ? X(c0 - ncol) : 0.0;
+    xc = X(c0);
+    xp = k0 + 1 < g.nz ? X(c0 + ncol) : 0.0;
   }
   double crr = 0.0, cbb = 0.0, chh = 0.0;
-  for (int k = 0; k < g.nz; ++k) {
+  for (int k = k0; k < k1; ++k) {
     const int64_t idx = (int64_t)k * ncol + col;
     const double C = __ldg(d.A7 + idx);
     double ax = 0.0;
@@ -328,21 +335,56 @@ struct BShm {
   BatchArgs A;
   SysCtl sc[kMaxSys];
   double acc[kMaxSys][3];
-  int64_t i0[kMaxSys];
+  int64_t i0[kMaxSys];   // first column item of each system
+  int64_t li0[kMaxSys];  // first level item of each system
   int odone[kMaxSys], cur[kMaxSys], xz[kMaxSys], used[kMaxSys];
 };
 
-// ---- phase R items: each active system's FP64 residual (first: of the
+// A level item of system d: `q` its thread's column group, and the chunk's
+// levels [k0, k0 + nk) seen as a grid of their own, with off the chunk's first
+// index.  The horizontal stencil and the pointwise updates read no other
+// level; the residual reads x one level above and below the chunk, which no
+// phase writes at the same time.
+struct Chunk {
+  Grid g;
+  int64_t q, off;
+  int k0;
+};
+__device__ __forceinline__ Chunk level_item(const SysDesc& d, int64_t item) {
+  const int64_t loc = item - d.litem0;
+  const int kc = (int)(loc / d.nitems);
+  Chunk c;
+  c.q = (loc - (int64_t)kc * d.nitems) * kBS + threadIdx.x;
+  const int k0 = kc * d.lchunk;
+  const int nk = d.g.nz - k0 < d.lchunk ? d.g.nz - k0 : d.lchunk;
+  c.g = d.g;
+  c.g.nz = nk;
+  c.g.n = (int64_t)nk * d.g.ncol;
+  c.off = (int64_t)k0 * d.g.ncol;
+  c.k0 = k0;
+  return c;
+}
+__device__ __forceinline__ Bands<float> hbands_at(const Bands<float>& a, int64_t off) {
+  Bands<float> b = a;
+  b.E += off;
+  b.W += off;
+  b.N += off;
+  b.S += off;
+  return b;
+}
+
+// ---- phase R items (level items): each active system's FP64 residual (first: of the
 // initial guess; else of x + d, the refinement update) ----
 template <int V>
 __device__ __noinline__ void items_resid(BShm* sh, bool first) {
   const BatchArgs& A = sh->A;
   const int nsys = A.nsys;
-  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int s = sys_of(sh->i0, nsys, item);
+  for (int64_t item = blockIdx.x; item < A.nlitems; item += gridDim.x) {
+    const int s = sys_of(sh->li0, nsys, item);
     if (sh->odone[s]) continue;
     const SysDesc& d = A.sys[s];
-    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    const Chunk ch = level_item(d, item);
+    const int64_t q = ch.q;
     double v[3] = {0.0, 0.0, 0.0};
     if (q < d.g.ncol / V) {
       const double* xin;
@@ -358,7 +400,7 @@ __device__ __noinline__ void items_resid(BShm* sh, bool first) {
         xout = (hasx || sh->used[s]) ? (sh->cur[s] ? d.xa : d.xb) : nullptr;
       }
       for (int cc = 0; cc < V; ++cc)
-        resid_column(d, q * V + cc, hasx, xin, sh->used[s] != 0, xout, v[0], v[1], v[2]);
+        resid_column(d, q * V + cc, ch.k0, ch.k0 + ch.g.nz, hasx, xin, sh->used[s] != 0, xout, v[0], v[1], v[2]);
     }
     block_add<3>(v, &sh->acc[s][0]);
   }
@@ -390,20 +432,21 @@ __device__ __noinline__ void items_pre_p(BShm* sh) {
   }
 }
 
-// ---- phase B items: v = p + H ph, <r0, v> ----
+// ---- phase B items (level items): v = p + H ph, <r0, v> ----
 template <int V, int UM>
 __device__ __noinline__ void items_mv_v(BShm* sh) {
   const BatchArgs& A = sh->A;
-  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int s = sys_of(sh->i0, A.nsys, item);
+  for (int64_t item = blockIdx.x; item < A.nlitems; item += gridDim.x) {
+    const int s = sys_of(sh->li0, A.nsys, item);
     const SysCtl c = sh->sc[s];
     if (c.state != ST_RUNNING && c.state != ST_RESTART) continue;
     const SysDesc& d = A.sys[s];
-    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    const Chunk ch = level_item(d, item);
     double v[1] = {0.0}, dummy = 0.0;
     const bool r0buf = c.r0sel || c.state == ST_RESTART;
-    if (q < d.g.ncol / V)
-      hmv_vec<float, V, UM, 0, LD_CG>(d.g, q * V, d.a, d.w.p, d.w.ph, d.w.v, r0buf ? d.w.r0 : d.w.rhs, v[0], dummy);
+    if (ch.q < d.g.ncol / V)
+      hmv_vec<float, V, UM, 0, LD_CG>(ch.g, ch.q * V, hbands_at(d.a, ch.off), d.w.p + ch.off, d.w.ph + ch.off,
+                                      d.w.v + ch.off, (r0buf ? d.w.r0 : d.w.rhs) + ch.off, v[0], dummy);
     block_add<1>(v, &sh->acc[s][0]);
   }
 }
@@ -425,40 +468,42 @@ __device__ __noinline__ void items_pre_s(BShm* sh) {
   }
 }
 
-// ---- phase D items: t = s + H sh, <t, s>, <t, t>, <s, s> ----
+// ---- phase D items (level items): t = s + H sh, <t, s>, <t, t>, <s, s> ----
 template <int V, int UM>
 __device__ __noinline__ void items_mv_t(BShm* sh) {
   const BatchArgs& A = sh->A;
-  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int s = sys_of(sh->i0, A.nsys, item);
+  for (int64_t item = blockIdx.x; item < A.nlitems; item += gridDim.x) {
+    const int s = sys_of(sh->li0, A.nsys, item);
     const SysCtl c = sh->sc[s];
     if (c.state != ST_RUNNING) continue;
     const SysDesc& d = A.sys[s];
-    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    const Chunk ch = level_item(d, item);
     double v[3] = {0.0, 0.0, 0.0};
-    if (q < d.g.ncol / V)
-      hmv_vec<float, V, UM, 3, LD_CG>(d.g, q * V, d.a, d.w.s, d.w.sh, d.w.t, nullptr, v[0], v[1], &v[2]);
+    if (ch.q < d.g.ncol / V)
+      hmv_vec<float, V, UM, 3, LD_CG>(ch.g, ch.q * V, hbands_at(d.a, ch.off), d.w.s + ch.off, d.w.sh + ch.off,
+                                      d.w.t + ch.off, nullptr, v[0], v[1], &v[2]);
     block_add<3>(v, &sh->acc[s][0]);
   }
 }
 
-// ---- phase E items: x += alpha ph + omega sh, r = s - omega t, <r0, r>, <r, r> ----
+// ---- phase E items (level items): x += alpha ph + omega sh, r = s - omega t, <r0, r>, <r, r> ----
 template <int V>
 __device__ __noinline__ void items_upd(BShm* sh) {
   const BatchArgs& A = sh->A;
-  for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int s = sys_of(sh->i0, A.nsys, item);
+  for (int64_t item = blockIdx.x; item < A.nlitems; item += gridDim.x) {
+    const int s = sys_of(sh->li0, A.nsys, item);
     const SysCtl c = sh->sc[s];
     if (c.state != ST_RUNNING && c.state != ST_HALF) continue;
     const SysDesc& d = A.sys[s];
-    const int64_t q = (item - d.item0) * kBS + threadIdx.x;
+    const Chunk ch = level_item(d, item);
+    const int64_t q = ch.q;
     double v[2] = {0.0, 0.0};
     if (q < d.g.ncol / V) {
       const bool half = c.state == ST_HALF;
       const float* r0 = c.r0sel ? d.w.r0 : d.w.rhs;
       DotAcc<float> u0{}, u1{};
-      for (int k = 0; k < d.g.nz; ++k) {
-        const int64_t idx = (int64_t)k * d.g.ncol + q * V;
+      for (int k = 0; k < ch.g.nz; ++k) {
+        const int64_t idx = ch.off + (int64_t)k * d.g.ncol + q * V;
         Pack<float, V> xv, pv = ldp<float, V, LD_CG>(d.w.ph + idx);
         if (c.xzero) {
 #pragma unroll
@@ -506,7 +551,11 @@ __device__ __forceinline__ void store_acc(BShm* sh, int d0, int nd) {
   __threadfence();
 }
 
-// ---- phase R: the residual items, then each system's refinement decision ----
+// ---- phase R: the residual items, then each system's refinement decision.
+// The refinement steps of all systems are taken together, once every inner
+// solve has ended: the phases are latency-bound for small systems, so one
+// residual phase for all costs less than one per system (measured: 177 ms
+// against 188 ms for 64 systems of 48x36x70 with per-system steps) ----
 template <int V>
 __device__ bool phase_resid(BShm* sh, bool first) {
   const BatchArgs& A = sh->A;
@@ -548,7 +597,10 @@ __global__ void __launch_bounds__(kBS, 4) k_batched(BatchArgs Ain) {
   __shared__ BShm shm;
   BShm* sh = &shm;
   if (threadIdx.x == 0) shm.A = Ain;
-  for (int s = threadIdx.x; s < Ain.nsys; s += blockDim.x) shm.i0[s] = Ain.sys[s].item0;
+  for (int s = threadIdx.x; s < Ain.nsys; s += blockDim.x) {
+    shm.i0[s] = Ain.sys[s].item0;
+    shm.li0[s] = Ain.sys[s].litem0;
+  }
   __syncthreads();
   const BatchArgs& A = shm.A;
   const int nsys = A.nsys;
@@ -683,13 +735,15 @@ bool same_sys(const SysDesc& a, const SysDesc& b) {
   const Vecs<float>& v = a.w;
   const Vecs<float>& u = b.w;
   return a.g.nx == b.g.nx && a.g.ny == b.g.ny && a.g.nz == b.g.nz && a.item0 == b.item0 && a.nitems == b.nitems &&
+         a.litem0 == b.litem0 && a.lchunk == b.lchunk && a.nchunk == b.nchunk &&
          a.ctl == b.ctl && a.A7 == b.A7 && a.invc == b.invc && a.b == b.b && a.x0 == b.x0 && a.xa == b.xa &&
          a.xb == b.xb && p.E == q.E && p.W == q.W && p.N == q.N && p.S == q.S && p.U == q.U && p.D == q.D &&
          p.m == q.m && p.l == q.l && p.cp == q.cp && v.rhs == u.rhs && v.r == u.r && v.r0 == u.r0 && v.p == u.p &&
          v.ph == u.ph && v.v == u.v && v.s == u.s && v.sh == u.sh && v.t == u.t && v.x == u.x;
 }
 bool same_args(const BatchArgs& a, const BatchArgs& b) {
-  return a.sys == b.sys && a.nsys == b.nsys && a.nitems == b.nitems && a.part == b.part && a.bar == b.bar &&
+  return a.sys == b.sys && a.nsys == b.nsys && a.nitems == b.nitems && a.nlitems == b.nlitems && a.part == b.part &&
+         a.bar == b.bar &&
          a.err == b.err && a.timeout_ns == b.timeout_ns && a.leave_block == b.leave_block &&
          a.max_loops == b.max_loops;
 }
@@ -743,13 +797,26 @@ cudaError_t launch_batched(const SysDesc* sys_h, int nsys, int vec, int max_loop
   }
   int64_t nitems = 0;
   for (int s = 0; s < nsys; ++s) nitems = sys_h[s].item0 + sys_h[s].nitems;
-  BatchArgs args{w.sys, nsys, nitems, w.part, w.bar, w.err, timeout_ns, leave_block, max_loops};
+  // Level chunks for the stencil and update phases: a batch with fewer column
+  // items than two per block splits each system's levels (chunks of at least 8
+  // levels), so that those phases are not one thread's march down every level.
+  std::vector<SysDesc> loc(sys_h, sys_h + nsys);
+  const int64_t target = nitems >= 2 * (int64_t)grid ? 1 : (2 * (int64_t)grid + nitems - 1) / nitems;
+  int64_t nlitems = 0;
+  for (auto& d : loc) {
+    const int64_t nch = std::min<int64_t>(target, std::max(1, d.g.nz / 8));
+    d.lchunk = (int)((d.g.nz + nch - 1) / nch);
+    d.nchunk = (d.g.nz + d.lchunk - 1) / d.lchunk;
+    d.litem0 = nlitems;
+    nlitems += d.nitems * d.nchunk;
+  }
+  BatchArgs args{w.sys, nsys, nitems, nlitems, w.part, w.bar, w.err, timeout_ns, leave_block, max_loops};
   // the launch's inputs, as a graph would bake them in
   bool same = w.exec && w.g_nsys == nsys && w.g_vec == vec && w.g_err_h == err_h && w.g_stream == stream &&
               same_args(w.g_args, args);
-  for (int s = 0; same && s < nsys; ++s) same = same_sys(w.sys_pin[s], sys_h[s]);
+  for (int s = 0; same && s < nsys; ++s) same = same_sys(w.sys_pin[s], loc[s]);
   if (graph && same) return cudaGraphLaunch(w.exec, stream);
-  memcpy(w.sys_pin, sys_h, sizeof(SysDesc) * nsys);
+  memcpy(w.sys_pin, loc.data(), sizeof(SysDesc) * nsys);
   auto enqueue = [&]() -> cudaError_t {
     cudaError_t r;
     if ((r = cudaMemcpyAsync(w.sys, w.sys_pin, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, stream)) != cudaSuccess)

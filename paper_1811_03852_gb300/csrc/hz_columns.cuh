@@ -255,7 +255,8 @@ __device__ __forceinline__ GroupNbr group_nbr(const Grid& g, int64_t c0) {
 // with the L2 evict-last priority while every streamed array is loaded and
 // stored evict-first, so that the parked values are the last to leave L2.
 // PARK_BULK: a different kernel (hz_thomas_bulk.cu): the inputs staged level
-// by level into shared memory by bulk copies, y parked in shared memory.
+// by level into shared memory by bulk copies, y parked in the output vector
+// under the L2 evict-last priority.
 enum ParkMode : int { PARK_OUT = 0, PARK_SMEM = 1, PARK_OUT_L2 = 2, PARK_BULK = kParkBulk };
 
 // Thomas algorithm on V columns with unit diagonal and pre-computed factors:

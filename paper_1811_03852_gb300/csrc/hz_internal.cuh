@@ -373,6 +373,11 @@ struct SysDesc {
   Ctl* ctl;
   int64_t item0;   // first global work item of this system (item = kBS column groups)
   int64_t nitems;  // items of this system
+  // the stencil and update phases (no vertical coupling) also split the levels:
+  // level item = (chunk of lchunk levels, column item); set by launch_batched
+  int64_t litem0;  // first global level item of this system
+  int lchunk;      // levels per chunk
+  int nchunk;      // chunks (nitems * nchunk level items)
   // the system's refinement loop: unscaled FP64 bands [7][n], 1/A_C, b, the
   // initial guess (null: zero), the caller's x (where the result ends) and a
   // second buffer for the ping-pong of x

@@ -360,8 +360,9 @@ int hz_get_history(hz_op op, double* hist, int cap);
  * depth levels per software-pipelined batch; a Thomas variant also fixes
  * where the forward sweep waits for the back sweep (the output vector, shared
  * memory, or the output vector stored with the L2 evict-last priority while
- * the streamed arrays are evict-first) and may cap the resident blocks per
- * SM.  All variants of a kernel compute the same values; dot partial sums
+ * the streamed arrays are evict-first, or a warp-specialised kernel staging
+ * its inputs by bulk copies); Thomas and stencil variants may cap the
+ * resident blocks per SM.  All variants of a kernel compute the same values; dot partial sums
  * follow the launch shape.  hz_op_autotune times every
  * valid variant on the operator's own arrays (3 launches each, CUDA events on
  * the operator's stream) and keeps the fastest, or the lowest-numbered variant

@@ -38,17 +38,20 @@ struct Variants;
 // pre_b resident blocks per SM (0: as many as fit).  Fewer resident columns
 // keep the parked sweep of every column in flight inside L2.  Stencil
 // variants: mv_v columns per thread, mv_u levels per batch, mv_h L2 priorities
-// (the arrays read once evict-first, so that rows of x stay in L2).
+// (the arrays read once evict-first, so that rows of x stay in L2), mv_b
+// resident blocks per SM (0: as many as fit; fewer rows in flight keep the
+// north/south neighbour rows of x in L2 until they are re-read).
 template <>
 struct Variants<float> {
-  static constexpr int NPRE = 18, NMV = 7;
+  static constexpr int NPRE = 18, NMV = 11;
   static constexpr int pre_v[NPRE] = {1, 4, 4, 2, 1, 1, 2, 2, 4, 2, 2, 4, 2, 4, 4, 4, 4, 4};
   static constexpr int pre_u[NPRE] = {8, 2, 1, 4, 8, 4, 4, 2, 2, 4, 4, 2, 4, 5, 3, 4, 5, 8};
   static constexpr int pre_p[NPRE] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 3, 3};
   static constexpr int pre_b[NPRE] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 4, 0, 0, 3, 0, 0, 0, 1, 1};
-  static constexpr int mv_v[NMV] = {1, 4, 2, 2, 4, 2, 2};
-  static constexpr int mv_u[NMV] = {4, 1, 2, 1, 1, 2, 1};
-  static constexpr int mv_h[NMV] = {0, 0, 0, 0, 1, 1, 1};
+  static constexpr int mv_v[NMV] = {1, 4, 2, 2, 4, 2, 2, 4, 4, 4, 2};
+  static constexpr int mv_u[NMV] = {4, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2};
+  static constexpr int mv_h[NMV] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1};
+  static constexpr int mv_b[NMV] = {0, 0, 0, 0, 0, 0, 0, 4, 3, 5, 4};
 };
 template <>
 struct Variants<double> {
@@ -60,6 +63,7 @@ struct Variants<double> {
   static constexpr int mv_v[NMV] = {1, 2, 1, 2, 1};
   static constexpr int mv_u[NMV] = {2, 1, 1, 1, 2};
   static constexpr int mv_h[NMV] = {0, 0, 0, 1, 1};
+  static constexpr int mv_b[NMV] = {0, 0, 0, 0, 0};
 };
 
 constexpr int kMinBlocks = 6;  // launch bound of the column kernels: at most 80 registers per thread
@@ -505,7 +509,7 @@ cudaError_t with_mv(int var, F&& f) {
   if constexpr (I < Variants<T>::NMV) {
     if (var == I)
       return f(std::integral_constant<int, Variants<T>::mv_v[I]>{}, std::integral_constant<int, Variants<T>::mv_u[I]>{},
-               std::integral_constant<bool, Variants<T>::mv_h[I] != 0>{});
+               std::integral_constant<bool, Variants<T>::mv_h[I] != 0>{}, Variants<T>::mv_b[I]);
     return with_mv<T, I + 1>(var, f);
   } else {
     return cudaErrorInvalidValue;
@@ -561,12 +565,12 @@ cudaError_t launch_pre_s_t(const Grid& g, const Bands<T>& a, const Vecs<T>& w, C
 }
 template <typename T, int MODE>
 cudaError_t launch_mv_t_(const Grid& g, const Bands<T>& a, const Vecs<T>& w, Ctl* ctl, Red red, const Launch& L) {
-  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc) {
+  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc, int cap) {
     return with_hb<T>(a.h16fmt, [&](auto Bc) {
       constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, HB = decltype(Bc)::value;
       constexpr bool H = decltype(Hc)::value;
       const void* k = (const void*)k_mv<T, MODE, V, U, H, HB>;
-      k_mv<T, MODE, V, U, H, HB><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, w, ctl,
+      k_mv<T, MODE, V, U, H, HB><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), 0, cap), kBS, 0, L.stream>>>(g, a, w, ctl,
                                                                                                           red);
       return cudaGetLastError();
     });
@@ -604,12 +608,12 @@ template <typename T>
 cudaError_t launch_precond_matvec_t(const Grid& g, const Bands<T>& a, const T* p, T* ph, T* v, const Launch& L) {
   cudaError_t e = launch_tinv_t<T>(g, a, p, ph, L);
   if (e != cudaSuccess) return e;
-  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc) {
+  return with_mv<T>(L.vmv[prec_index<T>()], [&](auto Vc, auto Uc, auto Hc, int cap) {
     return with_hb<T>(a.h16fmt, [&](auto Bc) {
       constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, HB = decltype(Bc)::value;
       constexpr bool H = decltype(Hc)::value;
       const void* k = (const void*)k_hmv<T, V, U, H, HB>;
-      k_hmv<T, V, U, H, HB><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS)), kBS, 0, L.stream>>>(g, a, p, ph, v);
+      k_hmv<T, V, U, H, HB><<<grid_for(k, kBS, L, blocks_for(g.ncol / V, kBS), 0, cap), kBS, 0, L.stream>>>(g, a, p, ph, v);
       return cudaGetLastError();
     });
   });
@@ -644,7 +648,7 @@ void warm_t(const Launch& L) {
     });
   for (int i = 0; i < Variants<T>::NMV; ++i)
     for (int hb = HB_F32; hb <= (sizeof(T) == 4 ? HB_FP16 : HB_F32); ++hb)
-      with_mv<T>(i, [&](auto Vc, auto Uc, auto Hc) {
+      with_mv<T>(i, [&](auto Vc, auto Uc, auto Hc, int) {
         return with_hb<T>(hb, [&](auto Bc) {
           constexpr int V = decltype(Vc)::value, U = decltype(Uc)::value, HB = decltype(Bc)::value;
           constexpr bool H = decltype(Hc)::value;

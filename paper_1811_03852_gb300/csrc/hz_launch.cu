@@ -80,7 +80,7 @@ void variant_flags(int prec, int kind, int id, int* l2, int* cap) {
     *cap = prec == 0 ? Variants<float>::pre_b[id] : Variants<double>::pre_b[id];
   } else {
     *l2 = prec == 0 ? Variants<float>::mv_h[id] : Variants<double>::mv_h[id];
-    *cap = 0;
+    *cap = prec == 0 ? Variants<float>::mv_b[id] : Variants<double>::mv_b[id];
   }
 }
 

@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--variants", type=int, nargs=2, metavar=("PRE32", "MV32"),
                     help="fix the FP32 Thomas and stencil variants instead of autotuning them (profiling a known launch "
                          "shape); FP64 and tri-SOR kernels are still tuned unless --no-fp64 / --no-trisor")
+    ap.add_argument("--sor-variants", type=int, nargs=3, metavar=("PASS", "MATVEC", "FIRST"),
+                    help="after tuning, fix the FP32 tri-SOR colour-pass, matvec and first-pass variants (profiling a "
+                         "known launch shape)")
     return ap.parse_args()
 
 
@@ -423,6 +426,9 @@ def run_ours(args):
         variants = op.variants()
     else:
         variants = op.autotune(fp64=not args.no_fp64, trisor=use_sor)
+    if use_sor and args.sor_variants:
+        for kind, vid in enumerate(args.sor_variants):
+            op.set_sor_variant(hz.HZ_PREC_FP32, kind, vid)
     if use_sor:
         variants["trisor"] = {f"{'fp64' if p == hz.HZ_PREC_FP64 else 'fp32'}/{('pass', 'matvec', 'first')[k]}": v
                               for (p, k), v in op.sor_variants().items()}
